@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Benchmark of the Wiener-reconstruction hot path on one GB300 (or N replicas).
+
+One step = the whole hot path over one synthetic 512^3 catalogue held in HBM:
+supersampled TSC gridding (1024^3 fine grid, ideal low-pass) -> window/noise -> Wiener solve
+to relative residual 1e-6 (mixed precision: FP32-FFT inner CG, FP64 refinement).  The FP64
+form of the same step is timed beside it.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wf|reference] [--workload c3|c2|c1]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "512^3 Wiener-CG solves/s to 1e-6 residual, mixed vs FP64; HBM GB/s; p50/p99"
+WORKLOADS = {
+    "c3": "512^3 grid, 500 Mpc/h box, ~5e5 log-normal galaxies (seed 1003), LCDM P(k) sigma8=0.8, "
+          "gamma-law radial selection (peak 150 Mpc/h), 30-deg cone with 5% holes; TSC, supersampling 2 "
+          "(1024^3 fine grid); CG to 1e-6",
+    "c2": "256^3 grid, 500 Mpc/h box, 1.5e5 log-normal galaxies (seed 1002), same P(k)/selection; TSC s=2; CG 1e-6",
+    "c1": "64^3 grid, 200 Mpc/h box, 2e4 log-normal galaxies (seed 1001), P=A k^-1.5; CIC s=2; CG 1e-8",
+}
+# DRAM traffic of the dominant kernel per launch from one ncu capture, valid while the kernel
+# sources hash to `src`; scaled from the captured size by the units processed (bytes ~ N^3).
+NCU_TRAFFIC = {}
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in ("wf_fft.cuh", "wf_spectral.cuh", "wf_common.cuh"):
+        with open(os.path.join(ROOT, "paper_0906_3978_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("WF_BENCH_GLOO") is None else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(ws, t):
+    if ws == 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    v = torch.tensor([t], dtype=torch.float64, device="cuda")
+    dist.all_reduce(v, op=dist.ReduceOp.MAX)
+    return float(v.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle baseline: bounded sample of the same workload on the host cores
+# ------------------------------------------------------------------------------------------
+def oracle_sample(pr, iters, deadline_s=40.0):
+    """Time the oracle on a bounded sample of the workload and scale it to solves/s:
+    full-size assignment and window, one textbook-CG matvec at full size, the ideal low-pass
+    counted as 5 matvecs (a 1024^3 and a 512^3 complex transform), and `iters` iterations."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    fine = oracle.assign(pr.pos, pr.n, pr.box, pr.scheme, 2)
+    del fine
+    t_assign = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w = oracle.window(pr.sel, pr.n, pr.box)
+    t_window = time.perf_counter() - t0
+    tab = oracle.sinv_table(pr.n, pr.box, pr.pk_k, pr.pk_p)
+    p = np.ones_like(w)
+    t0 = time.perf_counter()
+    oracle.matvec(tab, 0.05, w, p)
+    t_mv = time.perf_counter() - t0
+    t_solve = t_assign + t_window + (iters + 5) * t_mv
+    sample = ("oracle (plain C, FP64, %d OpenMP threads) at %d^3: assignment of all %d galaxies onto the 2x fine "
+              "grid (%.2f s), window (%.2f s), one CG matvec (%.2f s); solve = assignment + window + (%d CG "
+              "iterations as the GPU FP64 solve needed + 5 for the low-pass) x matvec"
+              % (oracle.threads(), pr.n, pr.n_gal, t_assign, t_window, t_mv, iters))
+    return 1.0 / t_solve, oracle.threads(), sample, t_solve
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    pr = synth.problem(args.workload)
+    iters = REF_ITERS.get(args.workload, 200)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample, t = oracle_sample(pr, iters)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "n": pr.n, "n_gal": pr.n_gal},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# GPU FP64-solve iteration counts on each workload (from the GPU arm), used by the reference
+# arm to scale its per-iteration time to a solve.
+REF_ITERS = {"c3": 200, "c2": 150, "c1": 60}
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def gpu_arm(args):
+    ws, rank, local = dist_init()
+    import numpy as np
+    import torch
+    import paper_0906_3978_gb300 as wf
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wf.build()
+    pr = synth.problem(args.workload)
+    ctx = wf.Context(local)
+    st = torch.cuda.Stream(device=dev)
+    pos = torch.from_numpy(pr.pos).to(dev)
+    n, box = pr.n, pr.box
+    tol = pr.tol
+
+    def step(prec, s_out=None, pos_d=pos):
+        with torch.cuda.stream(st):
+            nobs = ctx.grid_assign(pos_d, n, box, pr.scheme, 2, stream=st)
+            w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, box, stream=st, want_d=False)
+            s, info = ctx.solve(w, nbar, b, box, pr.pk_k, pr.pk_p, tol=tol, max_iter=20000, prec=prec,
+                                s_out=s_out, stream=st)
+        return s, info
+
+    def timed(prec, k, w_, profile=False):
+        for _ in range(w_):
+            step(prec)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ctx.profile(profile)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        infos = []
+        for _ in range(k):
+            s, info = step(prec)
+            infos.append(info.as_dict())
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        return ms, infos, s
+
+    # ---- headline: mixed precision, profiled (launch count + per-kernel event timing)
+    with Clocks(local) as clk:
+        ms_mixed, infos_mixed, s_mixed = timed(wf.MIXED, args.steps, args.warmup, profile=True)
+    prof = read_profile(ctx)
+    ms_mixed = barrier_max(ws, ms_mixed)
+    # ---- FP64 form of the same step
+    ms_fp64, infos_fp64, s_fp64 = timed(wf.FP64, max(1, args.steps // 3), 1)
+    ms_fp64 = barrier_max(ws, ms_fp64)
+    ctx.profile(False)
+    diff = float(torch.linalg.norm(s_mixed - s_fp64) / torch.linalg.norm(s_fp64))
+    # ---- e2e through the C ABI with host buffers (positions in, solution out)
+    pos_h = torch.from_numpy(pr.pos).pin_memory()
+    s_h = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
+    s_dev = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+    step(wf.MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(st):
+            pos_d = pos_h.to(dev, non_blocking=True)
+        step(wf.MIXED, s_out=s_dev, pos_d=pos_d)
+        with torch.cuda.stream(st):
+            s_h.copy_(s_dev, non_blocking=True)
+        st.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = barrier_max(ws, e2e_s)
+
+    if rank != 0:
+        return 0
+    k = args.steps
+    value = ws * k / (ms_mixed / 1000.0)
+    peak, peak_kind = peaks()
+    dom = max((c for c in prof["classes"] if c["bytes"] > 0), key=lambda c: c["ms"])
+    achieved = dom["bytes"] / dom["launches"] / (dom["ms"] / dom["launches"] / 1000.0) / 1e9
+    tr = NCU_TRAFFIC.get((dom["name"], n))
+    traffic = tr["bytes"] if tr and tr.get("src") == kernel_src_hash() else None
+    it_fp64 = infos_fp64[-1]["iters"]
+    cpu_v, cores, sample, _ = oracle_sample(pr, it_fp64)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": k, "warmup": args.warmup,
+        "ms_per_step": ms_mixed / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 FFT/CG inner, f64 dots+refinement", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "n": n, "n_gal": pr.n_gal,
+                   "l2": "inputs larger than L2 (fine grid 8.6 GB, spectra 0.5-1.1 GB at 512^3)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "mixed": {"iters": infos_mixed[-1]["iters"], "outer": infos_mixed[-1]["outer_iters"],
+                  "rel_residual": infos_mixed[-1]["rel_residual"], "rel_l2_vs_fp64_solve": diff},
+        "fp64": {"value": ws * max(1, k // 3) / (ms_fp64 / 1000.0), "ms_per_step": ms_fp64 / max(1, k // 3),
+                 "iters": it_fp64, "rel_residual": infos_fp64[-1]["rel_residual"]},
+        "roofline": {"kernel": dom["name"], "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": dom["bytes"] / dom["launches"],
+                     "avg_launch_ms": dom["ms"] / dom["launches"]},
+        "kernels": [{k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in c.items()}
+                    for c in sorted(prof["classes"], key=lambda c: -c["ms"])[:10]],
+        "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": ws * k / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(pr.pos.nbytes),
+                "d2h_bytes_per_step": int(n ** 3 * 8)},
+        "gpu_launches": prof["launches"],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    ctx.close()
+    return 0
+
+
+def read_profile(ctx):
+    return ctx.profile_read()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wf", choices=["wf", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,215 @@
+/*
+ * wf.h -- C ABI of the GB300 (sm_103a) Wiener-reconstruction library (libwf.so).
+ *
+ * The library computes the hot path of the ARGO Wiener reconstruction of Kitaura et al.
+ * 2009 ("Cosmic cartography of the large-scale structure with SDSS DR6",
+ * arXiv:0906.3978):
+ *   galaxies --(Sec. 2.2 supersampling: CIC/TSC on a finer grid, ideal low-pass)--> n_obs
+ *   n_obs, w --(Sec. 2.4 data/noise model: eq:datamodel, eq:nmean, eq:noiseav)--> d, b
+ *   b, w, P(k) --(Sec. 2.5.1, Eq. eq:WF, Krylov inversion)--> s = <delta_g>_WF
+ *
+ * General conventions
+ *   - Grids are cubic and periodic: N cells per axis, row-major [x][y][z] (z fastest), node
+ *     i at position i*H, H = box/N.  N must be even, of the form 2^a 3^b, and one of the
+ *     sizes wf_supported_size() accepts (16..512).
+ *   - "dev" pointers are CUDA device pointers on the context's device; "host" pointers
+ *     are ordinary host memory.  The caller owns every pointer it passes; the library never
+ *     frees or retains them beyond the call (wf_submit copies its inputs).
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  Device work
+ *     is stream-ordered on it; a call returns after its device work is enqueued unless the
+ *     description says it waits (calls that return host scalars wait for them).
+ *   - Every call returns a wf_status.  No call aborts, exits, prints or traps; CUDA errors
+ *     are returned as WF_ERR_CUDA (wf_last_error() describes the last one).
+ *   - Floating point: FP64 storage for every field crossing the ABI.
+ */
+#ifndef WF_H_
+#define WF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WF_OK = 0,
+  WF_PENDING = 1,            /* wf_poll: request not finished yet */
+  WF_ERR_ARG = -1,           /* invalid argument (sizes, pointers, non-finite input) */
+  WF_ERR_OOM = -2,           /* device allocation failed or HBM budget exceeded */
+  WF_ERR_CUDA = -3,          /* a CUDA runtime call failed */
+  WF_ERR_NOT_CONVERGED = -4, /* iteration cap reached; info is filled */
+  WF_ERR_BREAKDOWN = -5,     /* CG breakdown: p.Ap <= 0 or a non-finite scalar */
+  WF_ERR_TIMEOUT = -6,       /* a bounded wait gave up */
+  WF_ERR_OVERFLOW = -7,      /* a fine-grid cell would exceed 2^64-1 (>= 65536 galaxies) */
+  WF_ERR_BUSY = -8,          /* serving queue full */
+  WF_ERR_UNSUPPORTED = -9    /* grid size not compiled into this library */
+} wf_status;
+
+typedef struct wf_ctx wf_ctx;
+
+/* Cubic periodic grid: n cells per axis, box side (length units of the positions),
+ * supersample = 1 (plain gridding) or 2 (fine grid 2n, Sec. 2.2). */
+typedef struct {
+  int n;
+  double box;
+  int supersample;
+} wf_grid;
+
+typedef enum { WF_CIC = 1, WF_TSC = 2 } wf_scheme;
+
+/* Analytic survey window (the 3D mask of Sec. 2.3, w <= 1), evaluated at the nodes:
+ *   w(x) = [angle(x-o, axis) <= half_angle] * prod_h [angle(x-o, h) >= rho_h] * f(r),
+ *   r = |x - o|, w = 0 at r = 0; membership decided by dot products against cos(angle)*r.
+ * axis and hole directions are unit vectors; holes points to n_holes rows of
+ * (hx, hy, hz, rho_h) in host memory.
+ * radial_kind 0: f = 1; 1: f = exp(-(r/p0)^2); 2: f = (r/p0)^p1 exp(p1 (1 - r/p0)). */
+typedef struct {
+  double observer[3];
+  double axis[3];
+  double half_angle;
+  int n_holes;
+  const double* holes;
+  int radial_kind;
+  double radial_params[4];
+} wf_selection;
+
+/* Prior power spectrum P(k) as a host table (k strictly increasing, all > 0), interpolated
+ * log-log linearly (end segments extrapolated).  S^-1(k) = dV / P(k) on the grid, the
+ * discrete form of S-hat = (2 pi)^3 P(k) delta_D of Sec. 2.5.1; S^-1(0) = 0. */
+typedef struct {
+  const double* k;
+  const double* p;
+  int n;
+} wf_power;
+
+typedef enum {
+  WF_FP64 = 0,  /* every vector and transform in FP64 storage */
+  WF_MIXED = 1  /* inner CG on FP32 vectors and FP32 FFTs (FP64-accumulated dots, FP64
+                   alpha/beta), outer FP64 residual b - A x and iterative refinement */
+} wf_precision;
+
+typedef struct {
+  double tol;         /* stop when ||b - A s||_2 / ||b||_2 <= tol (recomputed from s) */
+  int max_iter;       /* cap on CG iterations (inner iterations summed for WF_MIXED) */
+  wf_precision prec;
+  double inner_tol;   /* WF_MIXED: relative reduction asked of each inner solve (<= 0: 1e-4) */
+  int precond;        /* 1: CG in Fourier variables split-preconditioned by S^(1/2)
+                         (same canonical system and residual); 0: plain CG on A */
+} wf_solve_opts;
+
+typedef struct {
+  int iters;           /* CG iterations (all inner iterations for WF_MIXED) */
+  int outer_iters;     /* WF_MIXED: refinement steps; WF_FP64: residual recomputations */
+  double rel_residual; /* ||b - A s|| / ||b|| recomputed from the returned s in FP64 */
+  double nbar;         /* nbar the solve used */
+  wf_status status;
+} wf_solve_info;
+
+/* ---- context ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the
+ * context may hold for workspaces (0 = no cap).  *ctx receives the handle. */
+wf_status wf_create(wf_ctx** ctx, int device, size_t hbm_budget_bytes);
+
+/* Free every workspace, plan and the serving thread of ctx.  Waits for its device work. */
+wf_status wf_destroy(wf_ctx* ctx);
+
+/* 1 if grid size n is compiled into this library, else 0. */
+int wf_supported_size(int n);
+
+const char* wf_status_string(wf_status s);
+
+/* Text of the last CUDA error seen by this thread (empty string if none). */
+const char* wf_last_error(void);
+
+/* ---- tracing ------------------------------------------------------------------------ */
+
+/* Reset the context's launch counters and enable (1) or disable (0) per-kernel timing.
+ * Every kernel launch is counted; while enabled, each launch is bracketed by CUDA events on
+ * its stream and attributed to a kernel class (e.g. "cg_xinv", "ypass", "zturn") together
+ * with its algorithmic bytes (the DRAM traffic the pass cannot avoid). */
+wf_status wf_profile(wf_ctx* ctx, int enable);
+
+/* Launches since the last wf_profile call and the number of kernel classes recorded.
+ * Waits for the recorded events. */
+wf_status wf_profile_read(wf_ctx* ctx, int64_t* launches, int* n_classes);
+
+/* Class i (0 <= i < n_classes): name (NUL-terminated, truncated to name_len), timed launches,
+ * summed device milliseconds and summed algorithmic bytes. */
+wf_status wf_profile_class(wf_ctx* ctx, int i, char* name, int name_len, int64_t* launches,
+                           double* total_ms, double* bytes);
+
+/* ---- Sec. 2.2: supersampled mass assignment ----------------------------------------- */
+
+/* Grid the galaxies and low-pass them to the target grid.
+ *   pos      dev  double [n_gal][3]   positions in [box units]; periodic wrap applied
+ *   fine_out dev  uint64 [(s n)^3]    or NULL: receives the fine mass grid in Q48 units
+ *                                     (one galaxy = 2^48), bit-exact and order-independent
+ *   n_obs    dev  double [n^3]        observed counts per cell (Eq. def:ngrid after the
+ *                                     ideal low-pass; sum(n_obs) = n_gal)
+ * Per axis, q = floor(x * (s n 2^16 / box)) mod (s n 2^16) fixes the galaxy in Q16 fine-cell
+ * units; CIC weights (2^16 - f, f), TSC weights floor((2^15 -+ D)^2 / 2^17) and the rest
+ * to the centre node; the 3D weight is their product.  With s = 2 the fine grid is
+ * transformed, the modes with every |k_i| < n/2 kept (coarse Nyquist planes dropped), and
+ * transformed back at n^3 divided by n^3.
+ * Errors: WF_ERR_ARG (bad sizes/pointers, non-finite or |x| * scale >= 2^52 position),
+ * WF_ERR_OVERFLOW, WF_ERR_UNSUPPORTED, WF_ERR_OOM.  Waits for the device (error flags). */
+wf_status wf_grid_assign(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const double* pos,
+                         int64_t n_gal, uint64_t* fine_out, double* n_obs, void* stream);
+
+/* ---- Sec. 2.3-2.4: window, data and noise ------------------------------------------- */
+
+/* w = window at the nodes (wf_selection); nbar = n_gal / sum(w) (eq:nmean, observed volume
+ * in cells); d = n_obs / nbar - w (eq:datamodel); b = R^T N^-1 d = nbar d where w > 0 and 0
+ * where w = 0 (N = w/nbar, eq:noiseav; no data term in unobserved cells).
+ *   n_obs dev double [n^3] in;  w, d, b dev double [n^3] out (d may be NULL);
+ *   nbar  host double out.
+ * Errors: WF_ERR_ARG (sum(w) == 0, n_gal <= 0, bad selection).  Waits for nbar. */
+wf_status wf_build_noise(wf_ctx* ctx, const wf_grid* grid, const wf_selection* sel,
+                         const double* n_obs, int64_t n_gal, double* w, double* d, double* b,
+                         double* nbar, void* stream);
+
+/* ---- Sec. 2.5.1: the Wiener filter, Eq. eq:WF ----------------------------------------- */
+
+/* Solve (S^-1 + nbar diag(w)) s = b for s = <delta_g>_WF by conjugate gradients from s = 0.
+ *   w     dev double [n^3]  window (R = diag(w)); nbar > 0 as from wf_build_noise
+ *   b     dev double [n^3]  right-hand side R^T N^-1 d
+ *   s_out dev double [n^3]  solution
+ *   info  host out (filled on success and on NOT_CONVERGED/BREAKDOWN)
+ * The stop test recomputes ||b - A s|| in FP64 from the returned s.  Waits for completion. */
+wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const double* w,
+                   double nbar, const double* b, const wf_solve_opts* opts, double* s_out,
+                   wf_solve_info* info, void* stream);
+
+/* Solve `count` independent systems (grids may differ in n and box) in one call; the
+ * iterations of all unfinished systems are interleaved on the device.  Arrays of length
+ * count: grids, powers, w[i], nbar[i], b[i], s_out[i] (dev), infos[i] (host).
+ * Returns WF_OK if every system converged, else the first failing status. */
+wf_status wf_solve_batch(wf_ctx* ctx, int count, const wf_grid* grids, const wf_power* powers,
+                         const double* const* w, const double* nbar, const double* const* b,
+                         const wf_solve_opts* opts, double* const* s_out, wf_solve_info* infos,
+                         void* stream);
+
+/* ---- serving ------------------------------------------------------------------------ */
+
+/* Queue one solve.  w and b are HOST double [n^3] arrays copied before return (the caller
+ * may free them); the power table is copied too.  *request_id receives a handle.
+ * The request is admitted when its device footprint fits the context's HBM budget and a
+ * slot is free; admitted requests stay resident and their iterations are interleaved.
+ * Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED, WF_ERR_BUSY (queue full). */
+wf_status wf_submit(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const double* w,
+                    double nbar, const double* b, const wf_solve_opts* opts,
+                    uint64_t* request_id);
+
+/* Wait up to timeout_ms (0 = do not wait, < 0 = forever) for request_id.  Returns WF_PENDING
+ * while it runs; otherwise its final status, with s_out (HOST double [n^3], may be NULL)
+ * and info filled, after which the id is released. */
+wf_status wf_poll(wf_ctx* ctx, uint64_t request_id, int timeout_ms, double* s_out,
+                  wf_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H_ */

@@ -170,8 +170,9 @@ def matvec(table, nbar: float, w, p) -> np.ndarray:
     return q
 
 
-def cg(table, nbar: float, w, b, tol: float = 1e-12, max_iter: int = 100000):
-    """(x, iters, rel_residual); raises OracleError unless converged."""
+def cg(table, nbar: float, w, b, tol: float = 1e-12, max_iter: int = 100000, allow_unconverged=False):
+    """(x, iters, rel_residual); raises OracleError unless converged (or, with
+    allow_unconverged, unless the failure is the iteration cap)."""
     n = b.shape[0]
     w = np.ascontiguousarray(w, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -180,5 +181,6 @@ def cg(table, nbar: float, w, b, tol: float = 1e-12, max_iter: int = 100000):
     rel = ctypes.c_double(0.0)
     st = lib().oracle_cg(n, _dp(np.ascontiguousarray(table)), nbar, _dp(w), _dp(b), tol, max_iter,
                          _dp(x), ctypes.byref(it), ctypes.byref(rel))
-    _check(st, "cg")
+    if not (allow_unconverged and st == ERR_NOT_CONVERGED):
+        _check(st, "cg")
     return x, it.value, rel.value

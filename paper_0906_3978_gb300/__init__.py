@@ -1,0 +1,333 @@
+"""Thin Python binding of libwf.so, the GB300 Wiener-reconstruction library (include/wf.h).
+
+Argument marshalling only: every step of the reconstruction runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (passed by data pointer), streams are torch
+streams.  There is no fallback: if libwf.so is missing, importing the binding's entry points
+raises.
+
+Functions mirror the C ABI:
+  Context.grid_assign   wf_grid_assign   supersampled CIC/TSC gridding (paper Sec. 2.2)
+  Context.build_noise   wf_build_noise   window, nbar, data, noise (Sec. 2.3-2.4)
+  Context.solve         wf_solve         Wiener filter by CG (Sec. 2.5.1, Eq. eq:WF)
+  Context.solve_batch   wf_solve_batch
+  Context.submit/poll   wf_submit / wf_poll (serving)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwf.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "wf.h")
+
+OK, PENDING = 0, 1
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_BREAKDOWN = -1, -2, -3, -4, -5
+ERR_TIMEOUT, ERR_OVERFLOW, ERR_BUSY, ERR_UNSUPPORTED = -6, -7, -8, -9
+CIC, TSC = 1, 2
+FP64, MIXED = 0, 1
+
+c_int, c_double, c_int64, c_uint64, c_void_p = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                                ctypes.c_uint64, ctypes.c_void_p)
+dp = ctypes.POINTER(ctypes.c_double)
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("n", c_int), ("box", c_double), ("supersample", c_int)]
+
+
+class SelectionC(ctypes.Structure):
+    _fields_ = [("observer", c_double * 3), ("axis", c_double * 3), ("half_angle", c_double),
+                ("n_holes", c_int), ("holes", dp), ("radial_kind", c_int),
+                ("radial_params", c_double * 4)]
+
+
+class Power(ctypes.Structure):
+    _fields_ = [("k", dp), ("p", dp), ("n", c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", c_double), ("max_iter", c_int), ("prec", c_int), ("inner_tol", c_double),
+                ("precond", c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("outer_iters", c_int), ("rel_residual", c_double),
+                ("nbar", c_double), ("status", c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def build() -> str:
+    from . import _build
+    return _build.build()
+
+
+def lib():
+    """The loaded libwf.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libwf.so not built (run __graft_entry__.build()): " + LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        L.wf_create.argtypes = [P(c_void_p), c_int, ctypes.c_size_t]
+        L.wf_destroy.argtypes = [c_void_p]
+        L.wf_supported_size.argtypes = [c_int]
+        L.wf_status_string.argtypes = [c_int]
+        L.wf_status_string.restype = ctypes.c_char_p
+        L.wf_last_error.restype = ctypes.c_char_p
+        L.wf_grid_assign.argtypes = [c_void_p, P(Grid), c_int, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
+        L.wf_build_noise.argtypes = [c_void_p, P(Grid), P(SelectionC), c_void_p, c_int64, c_void_p, c_void_p,
+                                     c_void_p, P(c_double), c_void_p]
+        L.wf_solve.argtypes = [c_void_p, P(Grid), P(Power), c_void_p, c_double, c_void_p, P(SolveOpts), c_void_p,
+                               P(SolveInfo), c_void_p]
+        L.wf_solve_batch.argtypes = [c_void_p, c_int, P(Grid), P(Power), P(c_void_p), P(c_double), P(c_void_p),
+                                     P(SolveOpts), P(c_void_p), P(SolveInfo), c_void_p]
+        L.wf_submit.argtypes = [c_void_p, P(Grid), P(Power), c_void_p, c_double, c_void_p, P(SolveOpts), P(c_uint64)]
+        L.wf_poll.argtypes = [c_void_p, c_uint64, c_int, c_void_p, P(SolveInfo)]
+        L.wf_profile.argtypes = [c_void_p, c_int]
+        L.wf_profile_read.argtypes = [c_void_p, P(c_int64), P(c_int)]
+        L.wf_profile_class.argtypes = [c_void_p, c_int, ctypes.c_char_p, c_int, P(c_int64), P(c_double),
+                                       P(c_double)]
+        for name in ("wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve", "wf_solve_batch",
+                     "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class"):
+            getattr(L, name).restype = c_int
+        L.wf_supported_size.restype = c_int
+        _lib = L
+    return _lib
+
+
+class WfError(RuntimeError):
+    def __init__(self, status: int, what: str, info=None):
+        msg = "%s: %s" % (what, lib().wf_status_string(status).decode())
+        le = lib().wf_last_error().decode()
+        if le:
+            msg += " (" + le + ")"
+        super().__init__(msg)
+        self.status = status
+        self.info = info
+
+
+def status_string(s: int) -> str:
+    return lib().wf_status_string(s).decode()
+
+
+def supported_size(n: int) -> bool:
+    return bool(lib().wf_supported_size(n))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dvec(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(dp)
+
+
+def make_selection(sel):
+    """ctypes wf_selection from an object with observer, axis, half_angle, holes, radial_kind,
+    radial_params; returns (struct, keepalive)."""
+    holes = np.ascontiguousarray(np.asarray(sel.holes, dtype=np.float64).reshape(-1, 4))
+    s = SelectionC()
+    s.observer[:] = [float(v) for v in sel.observer]
+    s.axis[:] = [float(v) for v in sel.axis]
+    s.half_angle = float(sel.half_angle)
+    s.n_holes = holes.shape[0]
+    s.holes = holes.ctypes.data_as(dp) if holes.size else ctypes.cast(None, dp)
+    s.radial_kind = int(sel.radial_kind)
+    rp = list(sel.radial_params) + [0.0] * 4
+    s.radial_params[:] = [float(v) for v in rp[:4]]
+    return s, holes
+
+
+def make_power(pk_k, pk_p):
+    k, kp = _dvec(pk_k)
+    p, pp = _dvec(pk_p)
+    pw = Power(kp, pp, k.size)
+    return pw, (k, p)
+
+
+def make_opts(tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1):
+    return SolveOpts(float(tol), int(max_iter), int(prec), float(inner_tol), int(precond))
+
+
+class Context:
+    """A wf_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self._h = c_void_p()
+        st = lib().wf_create(ctypes.byref(self._h), device, hbm_budget)
+        if st != OK:
+            raise WfError(st, "wf_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().wf_destroy(self._h)
+            self._h = c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- Sec. 2.2 -----------------------------------------------------------------------
+    def grid_assign(self, pos, n: int, box: float, scheme: int = TSC, supersample: int = 2, fine_out=None,
+                    n_obs=None, stream=None, check=True):
+        """n_obs [n,n,n] float64 (torch, on the device) from positions pos [N_gal,3] float64."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        if n_obs is None:
+            n_obs = torch.empty((n, n, n), dtype=torch.float64, device=dev)
+        g = Grid(n, float(box), supersample)
+        ngal = 0 if pos is None else int(pos.shape[0])
+        st = lib().wf_grid_assign(self._h, ctypes.byref(g), scheme, _ptr(pos) if ngal else None, ngal,
+                                  _ptr(fine_out), _ptr(n_obs), _stream(stream))
+        if check and st != OK:
+            raise WfError(st, "wf_grid_assign")
+        return n_obs if check else (st, n_obs)
+
+    # ---- Sec. 2.3-2.4 -------------------------------------------------------------------
+    def build_noise(self, sel, n_obs, n_gal: int, box: float, stream=None, want_d=True, check=True):
+        """(w, d, b, nbar): window, data and R^T N^-1 d on the device; nbar on the host."""
+        import torch
+        n = int(n_obs.shape[0])
+        w = torch.empty_like(n_obs)
+        d = torch.empty_like(n_obs) if want_d else None
+        b = torch.empty_like(n_obs)
+        s, keep = make_selection(sel)
+        nb = c_double(0.0)
+        g = Grid(n, float(box), 1)
+        st = lib().wf_build_noise(self._h, ctypes.byref(g), ctypes.byref(s), _ptr(n_obs), int(n_gal), _ptr(w),
+                                  _ptr(d), _ptr(b), ctypes.byref(nb), _stream(stream))
+        if check and st != OK:
+            raise WfError(st, "wf_build_noise")
+        return (w, d, b, nb.value) if check else (st, w, d, b, nb.value)
+
+    # ---- Sec. 2.5.1 ---------------------------------------------------------------------
+    def solve(self, w, nbar: float, b, box: float, pk_k, pk_p, tol=1e-6, max_iter=5000, prec=FP64,
+              inner_tol=0.0, precond=1, s_out=None, stream=None, check=True):
+        """(s, info): Wiener mean s solving (S^-1 + nbar diag(w)) s = b."""
+        import torch
+        n = int(b.shape[0])
+        if s_out is None:
+            s_out = torch.empty_like(b)
+        g = Grid(n, float(box), 1)
+        pw, keep = make_power(pk_k, pk_p)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        info = SolveInfo()
+        st = lib().wf_solve(self._h, ctypes.byref(g), ctypes.byref(pw), _ptr(w), float(nbar), _ptr(b),
+                            ctypes.byref(o), _ptr(s_out), ctypes.byref(info), _stream(stream))
+        if check and st != OK:
+            raise WfError(st, "wf_solve", info)
+        return s_out, info
+
+    def solve_batch(self, problems, stream=None):
+        """problems: list of dicts with w, nbar, b, box, pk_k, pk_p, tol, max_iter, prec, inner_tol,
+        precond (and optional s_out).  Returns (status, [s], [info])."""
+        import torch
+        cnt = len(problems)
+        grids = (Grid * cnt)()
+        pows = (Power * cnt)()
+        opts = (SolveOpts * cnt)()
+        infos = (SolveInfo * cnt)()
+        wp = (c_void_p * cnt)()
+        bp = (c_void_p * cnt)()
+        sp = (c_void_p * cnt)()
+        nb = (c_double * cnt)()
+        keep, outs = [], []
+        for i, pr in enumerate(problems):
+            n = int(pr["b"].shape[0])
+            grids[i] = Grid(n, float(pr["box"]), 1)
+            pw, kk = make_power(pr["pk_k"], pr["pk_p"])
+            keep.append(kk)
+            pows[i] = pw
+            opts[i] = make_opts(pr.get("tol", 1e-6), pr.get("max_iter", 5000), pr.get("prec", FP64),
+                                pr.get("inner_tol", 0.0), pr.get("precond", 1))
+            s = pr.get("s_out")
+            if s is None:
+                s = torch.empty_like(pr["b"])
+            outs.append(s)
+            wp[i], bp[i], sp[i] = _ptr(pr["w"]), _ptr(pr["b"]), _ptr(s)
+            nb[i] = float(pr["nbar"])
+        st = lib().wf_solve_batch(self._h, cnt, grids, pows, wp, nb, bp, opts, sp, infos, _stream(stream))
+        return st, outs, list(infos)
+
+    # ---- tracing ------------------------------------------------------------------------
+    def profile(self, enable: bool = True):
+        """Reset launch counters; enable/disable per-kernel CUDA-event timing (wf_profile)."""
+        st = lib().wf_profile(self._h, 1 if enable else 0)
+        if st != OK:
+            raise WfError(st, "wf_profile")
+
+    def profile_read(self):
+        """{"launches": total kernel launches, "classes": [{name, launches, ms, bytes, gbs}]}."""
+        nl, nc = c_int64(), c_int()
+        st = lib().wf_profile_read(self._h, ctypes.byref(nl), ctypes.byref(nc))
+        if st != OK:
+            raise WfError(st, "wf_profile_read")
+        out = []
+        for i in range(nc.value):
+            buf = ctypes.create_string_buffer(64)
+            la, ms, by = c_int64(), c_double(), c_double()
+            lib().wf_profile_class(self._h, i, buf, 64, ctypes.byref(la), ctypes.byref(ms), ctypes.byref(by))
+            out.append({"name": buf.value.decode(), "launches": la.value, "ms": ms.value, "bytes": by.value,
+                        "gbs": (by.value / (ms.value / 1e3) / 1e9) if ms.value > 0 else None})
+        return {"launches": nl.value, "classes": out}
+
+    # ---- serving ------------------------------------------------------------------------
+    def submit(self, w_host, nbar, b_host, box, pk_k, pk_p, tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0,
+               precond=1) -> int:
+        """Queue a solve from HOST float64 arrays; returns the request id."""
+        w_host = np.ascontiguousarray(w_host, dtype=np.float64)
+        b_host = np.ascontiguousarray(b_host, dtype=np.float64)
+        n = int(b_host.shape[0])
+        g = Grid(n, float(box), 1)
+        pw, keep = make_power(pk_k, pk_p)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        rid = c_uint64(0)
+        st = lib().wf_submit(self._h, ctypes.byref(g), ctypes.byref(pw), w_host.ctypes.data, float(nbar),
+                             b_host.ctypes.data, ctypes.byref(o), ctypes.byref(rid))
+        if st != OK:
+            raise WfError(st, "wf_submit")
+        return rid.value
+
+    def poll(self, request_id: int, timeout_ms: int = 0, s_out=None):
+        """(status, info); s_out: host float64 array of n^3 to receive the solution (or None)."""
+        info = SolveInfo()
+        ptr = None
+        if s_out is not None:
+            assert s_out.dtype == np.float64 and s_out.flags["C_CONTIGUOUS"]
+            ptr = s_out.ctypes.data
+        st = lib().wf_poll(self._h, c_uint64(request_id), int(timeout_ms), ptr, ctypes.byref(info))
+        return st, info

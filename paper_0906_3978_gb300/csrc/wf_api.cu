@@ -1,0 +1,298 @@
+// wf_api.cu -- the C ABI (include/wf.h): context, argument checks, dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <iterator>
+#include <string>
+#include <vector>
+
+#include "wf_ctx.h"
+
+namespace wf {
+
+template <int N>
+wf_status solve_sized(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st);
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const char* what, cudaError_t e) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+}
+
+wf_status Ctx::get(const std::string& name, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 16;
+  DevBuf& b = bufs[name];
+  if (b.ptr && b.bytes >= bytes) {
+    *out = b.ptr;
+    return WF_OK;
+  }
+  if (b.ptr) {
+    cudaFree(b.ptr);
+    held -= b.bytes;
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  if (budget && held + bytes > budget) return WF_ERR_OOM;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("cudaMalloc", e);
+    return WF_ERR_OOM;
+  }
+  b.ptr = p;
+  b.bytes = bytes;
+  held += bytes;
+  *out = p;
+  return WF_OK;
+}
+
+wf_status Ctx::tw(int n, const double2** out) {
+  auto it = twiddles.find(n);
+  if (it != twiddles.end()) {
+    *out = it->second;
+    return WF_OK;
+  }
+  std::vector<double2> h((size_t)2 * n);
+  const double pi = 3.14159265358979323846;
+  for (int e = 0; e < 2 * n; ++e) {
+    const double ang = 2.0 * pi * (double)e / (2.0 * n);
+    h[e] = make_double2(std::cos(ang), -std::sin(ang));
+  }
+  double2* d = nullptr;
+  WF_CUDA(cudaMalloc(&d, h.size() * sizeof(double2)));
+  WF_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  twiddles[n] = d;
+  *out = d;
+  return WF_OK;
+}
+
+void Ctx::release_all() {
+  for (auto& kv : bufs)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  bufs.clear();
+  held = 0;
+  for (auto& kv : twiddles) cudaFree(kv.second);
+  twiddles.clear();
+}
+
+// P(k) by log-log linear interpolation in the table (end segments extrapolated);
+// S^-1[n2] = dV / P(2 pi sqrt(n2) / L), S^-1[0] = 0.
+wf_status build_sinv_table(const wf_grid& g, const wf_power& pw, std::vector<double>& out) {
+  if (!pw.k || !pw.p || pw.n < 2) return WF_ERR_ARG;
+  for (int i = 0; i < pw.n; ++i)
+    if (!(pw.k[i] > 0.0) || !(pw.p[i] > 0.0) || !std::isfinite(pw.k[i]) || !std::isfinite(pw.p[i]) ||
+        (i > 0 && !(pw.k[i] > pw.k[i - 1])))
+      return WF_ERR_ARG;
+  const long half = g.n / 2, len = 3 * half * half + 1;
+  const double H = g.box / (double)g.n, dV = H * H * H;
+  const double kf = 2.0 * 3.14159265358979323846 / g.box;
+  std::vector<double> lk(pw.n), lp(pw.n);
+  for (int i = 0; i < pw.n; ++i) {
+    lk[i] = std::log(pw.k[i]);
+    lp[i] = std::log(pw.p[i]);
+  }
+  out.assign((size_t)len, 0.0);
+  int seg = 0;
+  for (long n2 = 1; n2 < len; ++n2) {
+    const double k = kf * std::sqrt((double)n2);
+    while (seg < pw.n - 2 && k > pw.k[seg + 1]) ++seg;  // k grows with n2
+    const double t = (std::log(k) - lk[seg]) / (lk[seg + 1] - lk[seg]);
+    const double p = std::exp(lp[seg] + t * (lp[seg + 1] - lp[seg]));
+    out[(size_t)n2] = dV / p;
+    if (!(out[(size_t)n2] > 0.0) || !std::isfinite(out[(size_t)n2])) return WF_ERR_ARG;
+  }
+  return WF_OK;
+}
+
+wf_status solve_run(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st) {
+  switch (a.grid.n) {
+#define WF_CASE(N) \
+  case N:          \
+    return solve_sized<N>(c, a, info, st);
+    WF_SIZES(WF_CASE)
+#undef WF_CASE
+    default:
+      return WF_ERR_UNSUPPORTED;
+  }
+}
+
+static wf_status check_grid(const wf_grid* g) {
+  if (!g) return WF_ERR_ARG;
+  if (!supported_size(g->n)) return WF_ERR_UNSUPPORTED;
+  if (!(g->box > 0.0) || !std::isfinite(g->box)) return WF_ERR_ARG;
+  return WF_OK;
+}
+
+wf_status prepare_solve(const wf_grid* grid, const wf_power* power, const double* w, double nbar,
+                        const double* b, const wf_solve_opts* opts, double* s_out, SolveArgs& a) {
+  WF_TRY(check_grid(grid));
+  if (!power || !w || !b || !s_out || !opts) return WF_ERR_ARG;
+  if (!(nbar > 0.0) || !std::isfinite(nbar)) return WF_ERR_ARG;
+  if (!(opts->tol > 0.0) || opts->max_iter <= 0 || (opts->prec != WF_FP64 && opts->prec != WF_MIXED))
+    return WF_ERR_ARG;
+  a.grid = *grid;
+  a.w = w;
+  a.b = b;
+  a.nbar = nbar;
+  a.opts = *opts;
+  a.s_out = s_out;
+  return build_sinv_table(*grid, *power, a.sinv);
+}
+
+}  // namespace wf
+
+using namespace wf;
+
+extern "C" {
+
+int wf_supported_size(int n) { return supported_size(n); }
+
+const char* wf_last_error(void) { return g_last_error.c_str(); }
+
+const char* wf_status_string(wf_status s) {
+  switch (s) {
+    case WF_OK: return "ok";
+    case WF_PENDING: return "pending";
+    case WF_ERR_ARG: return "invalid argument";
+    case WF_ERR_OOM: return "out of device memory or over the HBM budget";
+    case WF_ERR_CUDA: return "CUDA error";
+    case WF_ERR_NOT_CONVERGED: return "not converged within max_iter";
+    case WF_ERR_BREAKDOWN: return "CG breakdown";
+    case WF_ERR_TIMEOUT: return "timeout";
+    case WF_ERR_OVERFLOW: return "fine-grid cell overflow";
+    case WF_ERR_BUSY: return "queue full";
+    case WF_ERR_UNSUPPORTED: return "grid size not supported";
+  }
+  return "unknown status";
+}
+
+wf_status wf_create(wf_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return WF_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) {
+    set_last_error("cudaGetDeviceCount", e);
+    return WF_ERR_CUDA;
+  }
+  if (device < 0 || device >= count) return WF_ERR_ARG;
+  Ctx* c = new Ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  DeviceGuard g(device);
+  e = cudaMallocHost(&c->host_pinned, 4096);
+  if (e != cudaSuccess) {
+    set_last_error("cudaMallocHost", e);
+    delete c;
+    return WF_ERR_CUDA;
+  }
+  *out = reinterpret_cast<wf_ctx*>(c);
+  return WF_OK;
+}
+
+wf_status wf_destroy(wf_ctx* ctx) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  {
+    DeviceGuard g(c->device);
+    serve_shutdown(*c);
+    cudaDeviceSynchronize();
+    c->prof.reset();
+    c->prof.release();
+    c->release_all();
+    if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  }
+  delete c;
+  return WF_OK;
+}
+
+wf_status wf_grid_assign(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const double* pos, int64_t n_gal,
+                         uint64_t* fine_out, double* n_obs, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return assign_run(*c, *grid, (int)scheme, pos, n_gal, fine_out, n_obs, (cudaStream_t)stream);
+}
+
+wf_status wf_build_noise(wf_ctx* ctx, const wf_grid* grid, const wf_selection* sel, const double* n_obs,
+                         int64_t n_gal, double* w, double* d, double* b, double* nbar, void* stream) {
+  if (!ctx || !sel) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return noise_run(*c, *grid, *sel, n_obs, n_gal, w, d, b, nbar, (cudaStream_t)stream);
+}
+
+wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const double* w, double nbar,
+                   const double* b, const wf_solve_opts* opts, double* s_out, wf_solve_info* info, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  SolveArgs a;
+  wf_status s = prepare_solve(grid, power, w, nbar, b, opts, s_out, a);
+  if (s != WF_OK) {
+    if (info) info->status = s;
+    return s;
+  }
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  s = solve_run(*c, a, info, (cudaStream_t)stream);
+  if (info) info->status = s;
+  return s;
+}
+
+wf_status wf_profile(wf_ctx* ctx, int enable) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  c->prof.reset();
+  c->prof.on = enable != 0;
+  return WF_OK;
+}
+
+wf_status wf_profile_read(wf_ctx* ctx, int64_t* launches, int* n_classes) {
+  if (!ctx || !launches || !n_classes) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  c->prof.collect();
+  *launches = c->prof.launches;
+  *n_classes = (int)c->prof.classes.size();
+  return WF_OK;
+}
+
+wf_status wf_profile_class(wf_ctx* ctx, int i, char* name, int name_len, int64_t* launches, double* total_ms,
+                           double* bytes) {
+  if (!ctx || !name || name_len <= 0 || !launches || !total_ms || !bytes) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (i < 0 || i >= (int)c->prof.classes.size()) return WF_ERR_ARG;
+  auto it = c->prof.classes.begin();
+  std::advance(it, i);
+  std::snprintf(name, (size_t)name_len, "%s", it->first.c_str());
+  *launches = it->second.launches;
+  *total_ms = it->second.ms;
+  *bytes = it->second.bytes;
+  return WF_OK;
+}
+
+wf_status wf_solve_batch(wf_ctx* ctx, int count, const wf_grid* grids, const wf_power* powers, const double* const* w,
+                         const double* nbar, const double* const* b, const wf_solve_opts* opts, double* const* s_out,
+                         wf_solve_info* infos, void* stream) {
+  if (!ctx || count < 0 || (count > 0 && (!grids || !powers || !w || !nbar || !b || !opts || !s_out)))
+    return WF_ERR_ARG;
+  wf_status first = WF_OK;
+  for (int i = 0; i < count; ++i) {
+    wf_solve_info* inf = infos ? infos + i : nullptr;
+    wf_status s = wf_solve(ctx, grids + i, powers + i, w[i], nbar[i], b[i], opts + i, s_out[i], inf, stream);
+    if (s != WF_OK && first == WF_OK) first = s;
+  }
+  return first;
+}
+
+}  // extern "C"

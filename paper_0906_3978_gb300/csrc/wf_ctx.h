@@ -1,0 +1,176 @@
+// wf_ctx.h -- host-side context: device, workspace arena, per-size twiddle tables, error text.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/wf.h"
+
+// Grid sizes compiled into the library (2^a 3^b, even, half size also 2^a 3^b and even).
+#define WF_SIZES(X) \
+  X(16) X(24) X(32) X(48) X(64) X(72) X(96) X(108) X(128) X(144) X(192) X(216) X(256) X(288) X(384) X(512)
+
+namespace wf {
+
+void set_last_error(const char* what, cudaError_t e);
+
+#define WF_CUDA(...)                                   \
+  do {                                                 \
+    cudaError_t e_ = (__VA_ARGS__);                    \
+    if (e_ != cudaSuccess) {                           \
+      ::wf::set_last_error(#__VA_ARGS__, e_);          \
+      return e_ == cudaErrorMemoryAllocation ? WF_ERR_OOM : WF_ERR_CUDA; \
+    }                                                  \
+  } while (0)
+
+#define WF_TRY(...)                \
+  do {                             \
+    wf_status s_ = (__VA_ARGS__);  \
+    if (s_ != WF_OK) return s_;    \
+  } while (0)
+
+// Launch profiler: every kernel launch is counted; when enabled, each launch is bracketed by
+// CUDA events on its stream and attributed to a kernel class with its algorithmic bytes.
+struct ProfClass {
+  long long launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;  // algorithmic bytes summed over the timed launches
+};
+struct Prof {
+  bool on = false;
+  long long launches = 0;  // all kernel launches since the last reset
+  struct Rec {
+    std::string name;
+    double bytes;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Rec> pending;
+  std::map<std::string, ProfClass> classes;
+  cudaEvent_t get_event() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  // fold pending records into the classes (synchronises on their events)
+  void collect() {
+    for (auto& r : pending) {
+      cudaEventSynchronize(r.b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      ProfClass& c = classes[r.name];
+      c.launches += 1;
+      c.ms += ms;
+      c.bytes += r.bytes;
+    }
+    pending.clear();
+    used = 0;
+  }
+  void reset() {
+    collect();
+    classes.clear();
+    launches = 0;
+  }
+  void release() {
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+    used = 0;
+    pending.clear();
+  }
+};
+
+// A growable named device buffer owned by the context.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  size_t budget = 0;        // 0 = unlimited
+  size_t held = 0;          // bytes currently allocated by the arena
+  std::mutex mu;            // serialises synchronous API calls on this context
+  std::map<std::string, DevBuf> bufs;
+  std::map<int, double2*> twiddles;  // per N: exp(-2 pi i e / (2N)), e < 2N
+  void* host_pinned = nullptr;       // small pinned staging area for scalars
+  struct Server* server = nullptr;   // serving loop, created on first wf_submit
+  Prof prof;
+
+  // Launch `f` (which enqueues one kernel on st), counting it and, when profiling, timing it.
+  template <class F>
+  void launch(const char* name, double bytes, cudaStream_t st, F&& f) {
+    prof.launches += 1;
+    if (!prof.on) {
+      f();
+      return;
+    }
+    if (prof.used + 2 > 4096) prof.collect();
+    cudaEvent_t a = prof.get_event();
+    cudaEvent_t b = prof.get_event();
+    cudaEventRecord(a, st);
+    f();
+    cudaEventRecord(b, st);
+    prof.pending.push_back(Prof::Rec{name, bytes, a, b});
+  }
+
+  // Device buffer `name` with at least `bytes` bytes (contents not preserved on growth).
+  wf_status get(const std::string& name, size_t bytes, void** out);
+  wf_status tw(int n, const double2** out);
+  void release_all();
+};
+
+// RAII: make the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline int supported_size(int n) {
+  switch (n) {
+#define WF_CASE(N) case N:
+    WF_SIZES(WF_CASE)
+#undef WF_CASE
+    return 1;
+    default:
+      return 0;
+  }
+}
+
+// ---- entry points of the compute modules (defined in the .cu files) ----------------------
+wf_status assign_run(Ctx& c, const wf_grid& g, int scheme, const double* pos, int64_t n_gal,
+                     uint64_t* fine_out, double* n_obs, cudaStream_t st);
+wf_status noise_run(Ctx& c, const wf_grid& g, const wf_selection& sel, const double* n_obs,
+                    int64_t n_gal, double* w, double* d, double* b, double* nbar, cudaStream_t st);
+
+// Everything a single solve needs; tables are host-built per solve.
+struct SolveArgs {
+  wf_grid grid;
+  const double* w = nullptr;
+  const double* b = nullptr;
+  double nbar = 0.0;
+  wf_solve_opts opts{};
+  double* s_out = nullptr;
+  std::vector<double> sinv;  // S^-1 by n2, length 3 (N/2)^2 + 1
+  double sum_w = -1.0;       // filled by the driver
+};
+wf_status build_sinv_table(const wf_grid& g, const wf_power& pw, std::vector<double>& out);
+wf_status solve_run(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st);
+void serve_shutdown(Ctx& c);
+
+}  // namespace wf

@@ -1,0 +1,142 @@
+// wf_noise.cu -- 3D window, mean density, data and noise diagonals
+// (Kitaura et al. 2009, Sec. 2.3 and Sec. 2.4: Eqs. eq:datamodel, eq:nmean, eq:noiseav).
+//
+//   w    = [in cone] * [outside every hole] * f(r) at node x = i H (no periodic wrap)
+//   nbar = N_gal / sum(w)               (galaxies per cell; the observed volume in cells)
+//   d    = n_obs / nbar - w
+//   b    = R^T N^-1 d = nbar d  (w > 0),  0 (w = 0)     with R = diag(w), N = diag(w / nbar)
+// The cone and hole tests are decisions taken in floating point; they are evaluated with
+// explicitly rounded IEEE operations in a fixed order (no contraction), so the decision is the
+// one the plain definition gives.
+#include "wf_ctx.h"
+#include "wf_spectral.cuh"
+
+namespace wf {
+
+struct SelParams {
+  double ox, oy, oz;
+  double ax, ay, az;
+  double cos_half;
+  double H;
+  double p0, p1;
+  int kind;
+  int n_holes;
+};
+
+__global__ void __launch_bounds__(256)
+k_window(int n, SelParams s, const double4* __restrict__ holes, double* __restrict__ w,
+         double* __restrict__ partials) {
+  __shared__ double red[32];
+  const size_t V = (size_t)n * n * n;
+  AccD acc;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < V; e += (size_t)gridDim.x * blockDim.x) {
+    const int iz = (int)(e % n), iy = (int)((e / n) % n), ix = (int)(e / ((size_t)n * n));
+    const double dx = __dsub_rn(__dmul_rn((double)ix, s.H), s.ox);
+    const double dy = __dsub_rn(__dmul_rn((double)iy, s.H), s.oy);
+    const double dz = __dsub_rn(__dmul_rn((double)iz, s.H), s.oz);
+    const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    double val = 0.0;
+    if (r > 0.0) {
+      bool inside = __dadd_rn(__dadd_rn(__dmul_rn(dx, s.ax), __dmul_rn(dy, s.ay)), __dmul_rn(dz, s.az)) >=
+                    __dmul_rn(s.cos_half, r);
+      for (int h = 0; h < s.n_holes && inside; ++h) {
+        const double4 hv = holes[h];
+        if (__dadd_rn(__dadd_rn(__dmul_rn(dx, hv.x), __dmul_rn(dy, hv.y)), __dmul_rn(dz, hv.z)) > __dmul_rn(hv.w, r))
+          inside = false;
+      }
+      if (inside) {
+        if (s.kind == 0) {
+          val = 1.0;
+        } else if (s.kind == 1) {
+          const double t = __ddiv_rn(r, s.p0);
+          val = exp(-__dmul_rn(t, t));
+        } else {
+          const double t = __ddiv_rn(r, s.p0);
+          val = __dmul_rn(pow(t, s.p1), exp(__dmul_rn(s.p1, __dsub_rn(1.0, t))));
+        }
+      }
+    }
+    w[e] = val;
+    acc.add(val);
+  }
+  const double sum = block_sum(acc.get(), red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// scal[0] = sum(w), scal[1] = nbar, scal[2] = 1/nbar
+__global__ void k_nbar(const double* __restrict__ partials, int np, double n_gal, double* scal) {
+  __shared__ double red[32];
+  const double s = sum_partials(partials, np, 1, 0, red);
+  if (threadIdx.x == 0) {
+    scal[0] = s;
+    const double nb = s > 0.0 ? n_gal / s : 0.0;
+    scal[1] = nb;
+    scal[2] = nb > 0.0 ? 1.0 / nb : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+k_data(const double* __restrict__ n_obs, const double* __restrict__ w, const double* __restrict__ scal,
+       double* __restrict__ d, double* __restrict__ b, size_t V) {
+  const double nb = scal[1], inb = scal[2];
+  const double2* no2 = reinterpret_cast<const double2*>(n_obs);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < V / 2; e += (size_t)gridDim.x * blockDim.x) {
+    const double2 nv = no2[e], wv = w2[e];
+    double2 dv, bv;
+    dv.x = nv.x * inb - wv.x;
+    dv.y = nv.y * inb - wv.y;
+    bv.x = wv.x > 0.0 ? nb * dv.x : 0.0;
+    bv.y = wv.y > 0.0 ? nb * dv.y : 0.0;
+    if (d) reinterpret_cast<double2*>(d)[e] = dv;
+    reinterpret_cast<double2*>(b)[e] = bv;
+  }
+}
+
+wf_status noise_run(Ctx& c, const wf_grid& g, const wf_selection& sel, const double* n_obs, int64_t n_gal,
+                    double* w, double* d, double* b, double* nbar, cudaStream_t st) {
+  const int n = g.n;
+  if (!supported_size(n)) return WF_ERR_UNSUPPORTED;
+  if (!(g.box > 0.0) || !n_obs || !w || !b || !nbar || n_gal <= 0 || sel.n_holes < 0 ||
+      (sel.n_holes > 0 && !sel.holes) || sel.radial_kind < 0 || sel.radial_kind > 2)
+    return WF_ERR_ARG;
+  if (sel.radial_kind > 0 && !(sel.radial_params[0] > 0.0)) return WF_ERR_ARG;
+  SelParams s;
+  s.ox = sel.observer[0];
+  s.oy = sel.observer[1];
+  s.oz = sel.observer[2];
+  s.ax = sel.axis[0];
+  s.ay = sel.axis[1];
+  s.az = sel.axis[2];
+  s.cos_half = cos(sel.half_angle);
+  s.H = g.box / (double)n;
+  s.p0 = sel.radial_params[0];
+  s.p1 = sel.radial_params[1];
+  s.kind = sel.radial_kind;
+  s.n_holes = sel.n_holes;
+  std::vector<double4> hh((size_t)(sel.n_holes > 0 ? sel.n_holes : 1));
+  for (int h = 0; h < sel.n_holes; ++h)
+    hh[h] = make_double4(sel.holes[4 * h], sel.holes[4 * h + 1], sel.holes[4 * h + 2], cos(sel.holes[4 * h + 3]));
+  double4* dh;
+  WF_TRY(c.get("holes", hh.size() * sizeof(double4), (void**)&dh));
+  WF_CUDA(cudaMemcpyAsync(dh, hh.data(), hh.size() * sizeof(double4), cudaMemcpyHostToDevice, st));
+  const int grid = 152 * 8;
+  double *part, *scal;
+  WF_TRY(c.get("noise_part", grid * sizeof(double), (void**)&part));
+  WF_TRY(c.get("noise_scal", 4 * sizeof(double), (void**)&scal));
+  const size_t V = (size_t)n * n * n;
+  c.launch("window", 8.0 * V, st, [&] { k_window<<<grid, 256, 0, st>>>(n, s, dh, w, part); });
+  WF_CUDA(cudaGetLastError());
+  c.launch("fin", 0, st, [&] { k_nbar<<<1, 1024, 0, st>>>(part, grid, (double)n_gal, scal); });
+  WF_CUDA(cudaGetLastError());
+  c.launch("data", 8.0 * V * (d ? 4 : 3), st, [&] { k_data<<<grid, 256, 0, st>>>(n_obs, w, scal, d, b, V); });
+  WF_CUDA(cudaGetLastError());
+  double* h = reinterpret_cast<double*>(c.host_pinned);
+  WF_CUDA(cudaMemcpyAsync(h, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (!(h[0] > 0.0)) return WF_ERR_ARG;
+  *nbar = h[1];
+  return WF_OK;
+}
+
+}  // namespace wf

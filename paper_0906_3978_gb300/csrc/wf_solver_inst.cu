@@ -1,0 +1,11 @@
+// wf_solver_inst.cu -- instantiates the solve drivers for one grid size (compiled once per
+// size with -DWF_N=<n>, so the sizes build in parallel).
+#include "wf_solver_impl.cuh"
+
+#ifndef WF_N
+#error "compile with -DWF_N=<grid size>"
+#endif
+
+namespace wf {
+template wf_status solve_sized<WF_N>(Ctx&, SolveArgs&, wf_solve_info*, cudaStream_t);
+}

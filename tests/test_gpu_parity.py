@@ -1,0 +1,274 @@
+"""GPU path vs the CPU oracle, through the C ABI, on seeded synthetic inputs.
+
+Tolerances: the fine mass grid is compared bit for bit; n_obs, w, d, b to relative L2 1e-13
+(FP64 arithmetic on both sides, different summation orders); the FP64 Wiener solution to
+relative L2 1e-10 with both solvers at residual 1e-12; the mixed-precision solution to 1e-6
+after refinement.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_0906_3978_gb300 as wf  # noqa: E402
+
+
+def rl2(a, r):
+    a, r = np.asarray(a), np.asarray(r)
+    den = np.linalg.norm(r)
+    return float(np.linalg.norm(a - r) / (den if den > 0 else 1.0))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    wf.build()
+    c = wf.Context(0)
+    yield c
+    c.close()
+
+
+DEV = "cuda:0"
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def fine_host(t, shape):
+    return host(t).view(np.uint64).reshape(shape)
+
+
+# ------------------------------------------------------------------------ assignment
+def _positions(kind, n, box, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "uniform":
+        return rng.uniform(-0.3 * box, 1.3 * box, size=(4000, 3))       # wrap both ways
+    if kind == "clustered":
+        c = rng.uniform(0, box, size=(20, 3))
+        return (c[rng.integers(0, 20, 6000)] + rng.normal(0, box / (4 * n), size=(6000, 3))) % box
+    # nodes and half-nodes of the fine grid, exactly representable
+    h = box / (2 * n)
+    i = rng.integers(0, 2 * n, size=(3000, 3)).astype(np.float64)
+    return (i + rng.integers(0, 2, size=(3000, 3)) * 0.5) * h
+
+
+@pytest.mark.parametrize("n", [16, 24, 64, 108])
+@pytest.mark.parametrize("scheme", [wf.CIC, wf.TSC])
+@pytest.mark.parametrize("ss", [1, 2])
+@pytest.mark.parametrize("kind", ["uniform", "clustered", "nodes"])
+def test_assign_fine_grid_bit_exact(ctx, n, scheme, ss, kind):
+    box = 64.0 if kind == "nodes" else 100.0 + n
+    pos = _positions(kind, n, box, seed=n * 7 + scheme + ss)
+    nf = ss * n
+    fine = torch.empty(nf ** 3, dtype=torch.int64, device=DEV)
+    nobs = ctx.grid_assign(gpu(pos), n, box, scheme, ss, fine_out=fine)
+    ref = oracle.assign(pos, n, box, scheme, ss)
+    assert np.array_equal(fine_host(fine, ref.shape), ref)
+    ref_obs = oracle.lowpass(ref, n, ss)
+    got = host(nobs)
+    assert rl2(got, ref_obs) <= 1e-13
+    assert abs(got.sum() - pos.shape[0]) <= 1e-9 * pos.shape[0]
+
+
+def test_assign_deterministic(ctx):
+    pos = _positions("clustered", 32, 120.0, 3)
+    outs = []
+    for _ in range(2):
+        fine = torch.empty(64 ** 3, dtype=torch.int64, device=DEV)
+        ctx.grid_assign(gpu(pos[::-1].copy() if outs else pos), 32, 120.0, wf.TSC, 2, fine_out=fine)
+        outs.append(host(fine))
+    assert np.array_equal(outs[0], outs[1])      # order of galaxies does not matter
+
+
+def test_assign_edge_cases(ctx):
+    # no galaxies
+    nobs = ctx.grid_assign(None, 16, 50.0, wf.TSC, 2)
+    assert np.all(host(nobs) == 0.0)
+    # non-finite position
+    bad = gpu(np.array([[1.0, np.nan, 2.0], [3.0, 4.0, 5.0]]))
+    st, _ = ctx.grid_assign(bad, 16, 50.0, wf.TSC, 2, check=False)
+    assert st == wf.ERR_ARG
+    # 65536 galaxies exactly on one fine node overflow a uint64 cell (65536 * 2^48 = 2^64)
+    pos = np.tile([[2.0, 2.0, 2.0]], (65536, 1))
+    st, _ = ctx.grid_assign(gpu(pos), 16, 16.0, wf.CIC, 2, check=False)
+    assert st == wf.ERR_OVERFLOW
+    fine = torch.empty(32 ** 3, dtype=torch.int64, device=DEV)
+    ctx.grid_assign(gpu(pos[:65535]), 16, 16.0, wf.CIC, 2, fine_out=fine)
+    assert int(fine_host(fine, (32, 32, 32))[4, 4, 4]) == 65535 * 2 ** 48
+    # unsupported size, bad box
+    st, _ = ctx.grid_assign(gpu(pos[:10]), 20, 16.0, wf.CIC, 2, n_obs=torch.empty(8000, dtype=torch.float64,
+                                                                                  device=DEV), check=False)
+    assert st == wf.ERR_UNSUPPORTED
+    st, _ = ctx.grid_assign(gpu(pos[:10]), 16, -1.0, wf.CIC, 2, check=False)
+    assert st == wf.ERR_ARG
+
+
+# ------------------------------------------------------------------------ window / noise
+def _pipeline_oracle(pr):
+    fine = oracle.assign(pr.pos, pr.n, pr.box, pr.scheme, 2)
+    nobs = oracle.lowpass(fine, pr.n, 2)
+    w = oracle.window(pr.sel, pr.n, pr.box)
+    d, b, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+    return fine, nobs, w, d, b, nbar
+
+
+@pytest.mark.parametrize("name,n", [("c1", 32), ("c1", 48), ("c2", 32), ("c2", 64)])
+def test_noise_parity(ctx, name, n):
+    pr = synth.problem(name, n_override=n, cache=False)
+    fine, nobs_o, w_o, d_o, b_o, nbar_o = _pipeline_oracle(pr)
+    nobs = gpu(nobs_o)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+    # the oracle sums w in sequence: relative rounding error up to (V - 1) u, u = 2^-53
+    assert abs(nbar - nbar_o) <= n ** 3 * 1.2e-16 * nbar_o
+    assert rl2(host(w), w_o) <= 1e-14
+    assert np.array_equal(host(w) > 0, w_o > 0)      # identical membership decisions
+    assert rl2(host(d), d_o) <= 1e-13
+    assert rl2(host(b), b_o) <= 1e-13
+
+
+def test_noise_rejects_empty_window(ctx):
+    sel = synth.Selection(observer=(-1e3, 0, 0), axis=(-1.0, 0.0, 0.0), half_angle=0.1)
+    nobs = torch.zeros((16, 16, 16), dtype=torch.float64, device=DEV)
+    st = ctx.build_noise(sel, nobs, 10, 50.0, check=False)[0]
+    assert st == wf.ERR_ARG
+
+
+# ------------------------------------------------------------------------ solve
+def _solve_inputs(name, n):
+    pr = synth.problem(name, n_override=n, cache=False)
+    _, nobs, w, d, b, nbar = _pipeline_oracle(pr)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    return pr, w, b, nbar, tab
+
+
+@pytest.mark.parametrize("name,n", [("c1", 16), ("c1", 24), ("c1", 32), ("c2", 32), ("c2", 48), ("c1", 64),
+                                    ("c2", 72), ("c2", 108)])
+@pytest.mark.parametrize("precond", [1, 0])
+def test_solve_fp64_parity(ctx, name, n, precond):
+    pr, w, b, nbar, tab = _solve_inputs(name, n)
+    ref, it_o, rel_o = oracle.cg(tab, nbar, w, b, tol=1e-12)
+    s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-12, max_iter=20000,
+                        prec=wf.FP64, precond=precond)
+    assert info.status == wf.OK and info.rel_residual <= 1e-12
+    assert rl2(host(s), ref) <= 1e-10
+    # the oracle's operator agrees that the GPU solution solves the system
+    res = b - oracle.matvec(tab, nbar, w, host(s))
+    assert np.linalg.norm(res) <= 2e-12 * np.linalg.norm(b)
+    if precond == 0:
+        assert abs(info.iters - it_o) <= max(3, 0.05 * it_o)     # same algorithm
+
+
+@pytest.mark.parametrize("name,n", [("c1", 24), ("c1", 32), ("c2", 48), ("c2", 64), ("c2", 72), ("c2", 108)])
+def test_solve_mixed_parity(ctx, name, n):
+    pr, w, b, nbar, tab = _solve_inputs(name, n)
+    ref = oracle.cg(tab, nbar, w, b, tol=1e-12)[0]
+    s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-9, prec=wf.MIXED)
+    assert info.status == wf.OK and info.rel_residual <= 1e-9 and info.outer_iters >= 2
+    assert rl2(host(s), ref) <= 1e-6
+    # at the production tolerance the residual contract still holds in FP64
+    s6, info6 = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-6, prec=wf.MIXED)
+    res = b - oracle.matvec(tab, nbar, w, host(s6))
+    assert np.linalg.norm(res) <= 1.0001e-6 * np.linalg.norm(b)
+
+
+def test_solve_uniform_selection_closed_form(ctx):
+    n, box, nbar = 32, 80.0, 0.4
+    k, p = synth.lcdm_table()
+    rng = np.random.default_rng(2)
+    b = rng.standard_normal((n, n, n))
+    w = np.ones((n, n, n))
+    s, info = ctx.solve(gpu(w), nbar, gpu(b), box, k, p, tol=1e-13, max_iter=20000)
+    tab = oracle.sinv_table(n, box, k, p)
+    f = np.fft.fftfreq(n, 1.0 / n).astype(int)
+    n2 = f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2
+    ref = np.real(np.fft.ifftn(np.fft.fftn(b / nbar) / (1.0 + tab[n2] / nbar)))
+    assert rl2(host(s), ref) <= 1e-11
+
+
+def test_solve_zero_rhs_and_errors(ctx):
+    pr, w, b, nbar, tab = _solve_inputs("c1", 16)
+    z = np.zeros_like(b)
+    s, info = ctx.solve(gpu(w), nbar, gpu(z), pr.box, pr.pk_k, pr.pk_p, tol=1e-8)
+    assert info.status == wf.OK and info.iters == 0 and np.all(host(s) == 0.0)
+    for prec in (wf.FP64, wf.MIXED):
+        s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-12, max_iter=3, prec=prec,
+                            check=False)
+        assert info.status == wf.ERR_NOT_CONVERGED and info.iters >= 3 and info.rel_residual > 1e-12
+    for bad in [dict(nbar=0.0), dict(tol=0.0), dict(max_iter=0)]:
+        kw = dict(nbar=nbar, tol=1e-6, max_iter=100)
+        kw.update(bad)
+        with pytest.raises(wf.WfError) as e:
+            ctx.solve(gpu(w), kw["nbar"], gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=kw["tol"], max_iter=kw["max_iter"])
+        assert e.value.status == wf.ERR_ARG
+    with pytest.raises(wf.WfError) as e:
+        ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k[::-1].copy(), pr.pk_p, tol=1e-6)
+    assert e.value.status == wf.ERR_ARG
+
+
+def test_solve_fixed_iterations_match_textbook_cg(ctx):
+    """precond = 0 is textbook CG: after k iterations from 0 both sides hold the same x_k."""
+    pr, w, b, nbar, tab = _solve_inputs("c2", 48)
+    for k in (1, 2, 7):
+        ref = oracle.cg(tab, nbar, w, b, tol=1e-14, max_iter=k, allow_unconverged=True)[0]
+        s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, precond=0,
+                            check=False)
+        assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k
+        assert rl2(host(s), ref) <= 1e-11
+
+
+def test_solve_deterministic(ctx):
+    pr, w, b, nbar, tab = _solve_inputs("c2", 32)
+    s1, _ = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8)
+    a = host(s1).copy()
+    s2, _ = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8)
+    assert np.array_equal(a, host(s2))
+
+
+def test_end_to_end_pipeline(ctx):
+    pr = synth.problem("c1", n_override=32, cache=False)
+    fine_o, nobs_o, w_o, d_o, b_o, nbar_o = _pipeline_oracle(pr)
+    tab = oracle.sinv_table(pr.n, pr.box, pr.pk_k, pr.pk_p)
+    ref = oracle.cg(tab, nbar_o, w_o, b_o, tol=1e-12)[0]
+    nobs = ctx.grid_assign(gpu(pr.pos), pr.n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+    s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-12)
+    assert rl2(host(s), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_fresh_context_mixed_first(n):
+    """A new context whose first solve is mixed precision sizes every workspace itself."""
+    pr = synth.problem("c2", n_override=n, cache=False)
+    with wf.Context(0) as c2:
+        nobs = c2.grid_assign(gpu(pr.pos), pr.n, pr.box, pr.scheme, 2)
+        w, d, b, nbar = c2.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+        sm, im = c2.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED)
+        sd, idd = c2.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.FP64)
+        assert im.status == wf.OK and idd.status == wf.OK
+        assert im.rel_residual <= 1e-8 and idd.rel_residual <= 1e-8
+        assert rl2(host(sm), host(sd)) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [128, 256])
+def test_fixed_iterations_large_grid(ctx, n):
+    """Several tiles per pass and many CTAs: k textbook-CG iterations match the oracle's."""
+    pr = synth.problem("c2", n_override=n, cache=False)
+    nobs = ctx.grid_assign(gpu(pr.pos), pr.n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+    wh, bh = host(w), host(b)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    ref = oracle.cg(tab, nbar, wh, bh, tol=1e-14, max_iter=3, allow_unconverged=True)[0]
+    s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=3, precond=0, check=False)
+    assert info.iters == 3
+    assert rl2(host(s), ref) <= 1e-11
