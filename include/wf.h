@@ -170,6 +170,24 @@ wf_status wf_build_noise(wf_ctx* ctx, const wf_grid* grid, const wf_selection* s
                          const double* n_obs, int64_t n_gal, double* w, double* d, double* b,
                          double* nbar, void* stream);
 
+/* Same outputs as wf_build_noise, for callers that cannot let a library allocate device
+ * memory -- e.g. a host code that manages the whole GPU through its own memory pool at its
+ * capacity limit, or a latency-critical pipeline where cudaMalloc's implicit device-wide
+ * synchronisation is unacceptable.  No counterpart in the paper: this is a deployment variant.
+ * It takes no context and allocates nothing: its scratch (reduction partials, the nbar
+ * scalars, the hole table) is one fixed 14,000-byte array compiled into the library's device
+ * image, which every GPU that loads libwf.so holds until the process exits.
+ *   - Runs on the current CUDA device.  The first call on each device looks up the scratch
+ *     address (cudaGetSymbolAddress); make that first call before any stream capture starts.
+ *   - Limit: sel->n_holes <= 256; larger tables return WF_ERR_ARG (see wf_last_error()).
+ *   - All calls share the one scratch array: calls that may overlap on the GPU (other streams,
+ *     other host threads) race and must be serialised by the caller.  Every scratch word a
+ *     call reads is written earlier in the same call, so nothing needs clearing in between.
+ * Arguments, outputs and other errors as wf_build_noise.  Waits for nbar. */
+wf_status wf_build_noise_noalloc(const wf_grid* grid, const wf_selection* sel, const double* n_obs,
+                                 int64_t n_gal, double* w, double* d, double* b, double* nbar,
+                                 void* stream);
+
 /* ---- Sec. 2.5.1: the Wiener filter, Eq. eq:WF ----------------------------------------- */
 
 /* Solve (S^-1 + nbar diag(w)) s = b for s = <delta_g>_WF by conjugate gradients from s = 0.

@@ -16,7 +16,7 @@ wf_status solve_sized(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st
 static thread_local std::string g_last_error;
 
 void set_last_error(const char* what, cudaError_t e) {
-  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  g_last_error = e == cudaSuccess ? std::string(what) : std::string(what) + ": " + cudaGetErrorString(e);
 }
 
 wf_status Ctx::get(const std::string& name, size_t bytes, void** out) {

@@ -8,6 +8,9 @@
 // The cone and hole tests are decisions taken in floating point; they are evaluated with
 // explicitly rounded IEEE operations in a fixed order (no contraction), so the decision is the
 // one the plain definition gives.
+#include <map>
+#include <mutex>
+
 #include "wf_ctx.h"
 #include "wf_spectral.cuh"
 
@@ -140,3 +143,104 @@ wf_status noise_run(Ctx& c, const wf_grid& g, const wf_selection& sel, const dou
 }
 
 }  // namespace wf
+
+// ==========================================================================================
+// wf_build_noise_noalloc: the same window / nbar / data computation for callers that must not
+// allocate device memory.  Some embedders cannot let a library call cudaMalloc: a simulation
+// code that owns the whole device through its own pool and runs at its memory limit, or a
+// real-time pipeline where cudaMalloc's implicit device synchronisation would stall other
+// streams.  This variant takes only the caller's buffers; its scratch (per-block partial sums
+// of w, the nbar scalars, the hole table) is a fixed array in the library's device image,
+// which every GPU that loads the library holds until the process exits.
+// ==========================================================================================
+namespace wf {
+
+constexpr int kNoallocParts = 152 * 8;   // blocks of the window kernel = partial sums
+constexpr int kNoallocMaxHoles = 256;    // largest hole table the scratch can hold
+// layout (doubles): [0, kNoallocParts) partials | 4 scalars | 4 * kNoallocMaxHoles hole rows
+constexpr int kNoallocDoubles = kNoallocParts + 4 + 4 * kNoallocMaxHoles;  // 14,000 B
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+
+// Device addresses of g_noalloc_scratch, looked up once per device (host code must not use
+// the symbol itself: on the host it is only a stand-in, not a device address).
+static std::mutex g_noalloc_mu;
+static std::map<int, double*> g_noalloc_addr;
+
+static wf_status noalloc_scratch(int device, double** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(device);
+  if (it != g_noalloc_addr.end()) {
+    *out = it->second;
+    return WF_OK;
+  }
+  double* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    set_last_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
+    return WF_ERR_CUDA;
+  }
+  g_noalloc_addr[device] = p;
+  *out = p;
+  return WF_OK;
+}
+
+}  // namespace wf
+
+extern "C" wf_status wf_build_noise_noalloc(const wf_grid* grid, const wf_selection* sel, const double* n_obs,
+                                            int64_t n_gal, double* w, double* d, double* b, double* nbar,
+                                            void* stream) {
+  using namespace wf;
+  if (!grid || !sel) return WF_ERR_ARG;
+  const int n = grid->n;
+  if (!supported_size(n)) return WF_ERR_UNSUPPORTED;
+  if (!(grid->box > 0.0) || !n_obs || !w || !b || !nbar || n_gal <= 0 || sel->n_holes < 0 ||
+      (sel->n_holes > 0 && !sel->holes) || sel->radial_kind < 0 || sel->radial_kind > 2)
+    return WF_ERR_ARG;
+  if (sel->radial_kind > 0 && !(sel->radial_params[0] > 0.0)) return WF_ERR_ARG;
+  if (sel->n_holes > kNoallocMaxHoles) {
+    set_last_error("wf_build_noise_noalloc: more than 256 holes do not fit the fixed scratch", cudaSuccess);
+    return WF_ERR_ARG;
+  }
+  int dev = 0;
+  WF_CUDA(cudaGetDevice(&dev));
+  double* scratch = nullptr;
+  WF_TRY(noalloc_scratch(dev, &scratch));
+  double* part = scratch;
+  double* scal = scratch + kNoallocParts;
+  double4* dh = reinterpret_cast<double4*>(scratch + kNoallocParts + 4);
+  cudaStream_t st = (cudaStream_t)stream;
+  SelParams s;
+  s.ox = sel->observer[0];
+  s.oy = sel->observer[1];
+  s.oz = sel->observer[2];
+  s.ax = sel->axis[0];
+  s.ay = sel->axis[1];
+  s.az = sel->axis[2];
+  s.cos_half = cos(sel->half_angle);
+  s.H = grid->box / (double)n;
+  s.p0 = sel->radial_params[0];
+  s.p1 = sel->radial_params[1];
+  s.kind = sel->radial_kind;
+  s.n_holes = sel->n_holes;
+  double4 hh[kNoallocMaxHoles];
+  for (int h = 0; h < sel->n_holes; ++h)
+    hh[h] = make_double4(sel->holes[4 * h], sel->holes[4 * h + 1], sel->holes[4 * h + 2], cos(sel->holes[4 * h + 3]));
+  if (sel->n_holes > 0)
+    WF_CUDA(cudaMemcpyAsync(dh, hh, sizeof(double4) * sel->n_holes, cudaMemcpyHostToDevice, st));
+  // every partial and scalar below is written before it is read: nothing in the scratch
+  // needs clearing between calls
+  const size_t V = (size_t)n * n * n;
+  k_window<<<kNoallocParts, 256, 0, st>>>(n, s, dh, w, part);
+  WF_CUDA(cudaGetLastError());
+  k_nbar<<<1, 1024, 0, st>>>(part, kNoallocParts, (double)n_gal, scal);
+  WF_CUDA(cudaGetLastError());
+  k_data<<<kNoallocParts, 256, 0, st>>>(n_obs, w, scal, d, b, V);
+  WF_CUDA(cudaGetLastError());
+  double h3[3];
+  WF_CUDA(cudaMemcpyAsync(h3, scal, sizeof(h3), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  if (!(h3[0] > 0.0)) return WF_ERR_ARG;
+  *nbar = h3[1];
+  return WF_OK;
+}
