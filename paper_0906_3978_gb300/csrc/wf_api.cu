@@ -6,12 +6,16 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <memory>
+
 #include "wf_ctx.h"
 
 namespace wf {
 
+struct Group;
 template <int N>
-wf_status solve_sized(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st);
+Group* make_group(int prec);
 
 static thread_local std::string g_last_error;
 
@@ -67,6 +71,34 @@ wf_status Ctx::tw(int n, const double2** out) {
   return WF_OK;
 }
 
+wf_status Ctx::get_pinned(const std::string& name, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 16;
+  DevBuf& b = pinned[name];
+  if (b.ptr && b.bytes >= bytes) {
+    *out = b.ptr;
+    return WF_OK;
+  }
+  if (b.ptr) {
+    cudaFreeHost(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+  }
+  WF_CUDA(cudaMallocHost(&b.ptr, bytes));
+  b.bytes = bytes;
+  *out = b.ptr;
+  return WF_OK;
+}
+
+wf_status Ctx::stream(int i, cudaStream_t* out) {
+  while ((int)streams.size() <= i) {
+    cudaStream_t s;
+    WF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    streams.push_back(s);
+  }
+  *out = streams[i];
+  return WF_OK;
+}
+
 void Ctx::release_all() {
   for (auto& kv : bufs)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
@@ -74,6 +106,11 @@ void Ctx::release_all() {
   held = 0;
   for (auto& kv : twiddles) cudaFree(kv.second);
   twiddles.clear();
+  for (auto& kv : pinned)
+    if (kv.second.ptr) cudaFreeHost(kv.second.ptr);
+  pinned.clear();
+  for (auto s : streams) cudaStreamDestroy(s);
+  streams.clear();
 }
 
 // P(k) by log-log linear interpolation in the table (end segments extrapolated);
@@ -105,16 +142,79 @@ wf_status build_sinv_table(const wf_grid& g, const wf_power& pw, std::vector<dou
   return WF_OK;
 }
 
-wf_status solve_run(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st) {
-  switch (a.grid.n) {
+static Group* make_group_n(int n, int prec) {
+  switch (n) {
 #define WF_CASE(N) \
   case N:          \
-    return solve_sized<N>(c, a, info, st);
+    return make_group<N>(prec);
     WF_SIZES(WF_CASE)
 #undef WF_CASE
     default:
-      return WF_ERR_UNSUPPORTED;
+      return nullptr;
   }
+}
+
+}  // namespace wf
+#include "wf_solver_group.h"
+namespace wf {
+
+wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_info*>& infos, cudaStream_t st) {
+  std::map<std::pair<int, int>, std::unique_ptr<Group>> groups;
+  for (size_t i = 0; i < sys.size(); ++i) {
+    const auto key = std::make_pair(sys[i]->grid.n, (int)sys[i]->opts.prec);
+    auto& g = groups[key];
+    if (!g) {
+      g.reset(make_group_n(key.first, key.second));
+      if (!g) return WF_ERR_UNSUPPORTED;
+    }
+    g->sys.push_back(sys[i]);
+    g->info.push_back(infos[i]);
+  }
+  // one stream per group (the caller's stream when there is a single group)
+  std::vector<Group*> gl;
+  std::vector<cudaStream_t> gs;
+  cudaEvent_t ev;
+  WF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  WF_CUDA(cudaEventRecord(ev, st));
+  int k = 0;
+  for (auto& kv : groups) {
+    cudaStream_t s = st;
+    if (groups.size() > 1) {
+      WF_TRY(c.stream(k, &s));
+      WF_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    }
+    gl.push_back(kv.second.get());
+    gs.push_back(s);
+    ++k;
+  }
+  wf_status status = WF_OK;
+  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) status = gl[i]->prepare(c, gs[i]);
+  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) WF_CUDA(cudaStreamSynchronize(gs[i]));
+  bool busy = status == WF_OK;
+  while (busy && status == WF_OK) {
+    busy = false;
+    for (size_t i = 0; i < gl.size() && status == WF_OK; ++i)
+      if (!gl[i]->done()) status = gl[i]->enqueue(c, gs[i]);
+    for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) {
+      if (gl[i]->done()) continue;
+      WF_CUDA(cudaStreamSynchronize(gs[i]));
+      status = gl[i]->advance(c);
+      busy = busy || !gl[i]->done();
+    }
+  }
+  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) {
+    status = gl[i]->finish(c, gs[i]);
+    if (status == WF_OK && gs[i] != st) {
+      WF_CUDA(cudaEventRecord(ev, gs[i]));
+      WF_CUDA(cudaStreamWaitEvent(st, ev, 0));
+    }
+  }
+  WF_CUDA(cudaStreamSynchronize(st));
+  cudaEventDestroy(ev);
+  if (status != WF_OK) return status;
+  for (auto* inf : infos)
+    if (inf && inf->status != WF_OK) return inf->status;
+  return WF_OK;
 }
 
 static wf_status check_grid(const wf_grid* g) {
@@ -240,7 +340,10 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   std::lock_guard<std::mutex> lk(c->mu);
   DeviceGuard g(c->device);
-  s = solve_run(*c, a, info, (cudaStream_t)stream);
+  wf_solve_info tmp{};
+  std::vector<SolveArgs*> sys{&a};
+  std::vector<wf_solve_info*> infos{info ? info : &tmp};
+  s = solve_many(*c, sys, infos, (cudaStream_t)stream);
   if (info) info->status = s;
   return s;
 }
@@ -286,13 +389,26 @@ wf_status wf_solve_batch(wf_ctx* ctx, int count, const wf_grid* grids, const wf_
                          wf_solve_info* infos, void* stream) {
   if (!ctx || count < 0 || (count > 0 && (!grids || !powers || !w || !nbar || !b || !opts || !s_out)))
     return WF_ERR_ARG;
-  wf_status first = WF_OK;
+  if (count == 0) return WF_OK;
+  std::vector<SolveArgs> args((size_t)count);
+  std::vector<wf_solve_info> tmp((size_t)count);
+  std::vector<SolveArgs*> sys;
+  std::vector<wf_solve_info*> inf;
   for (int i = 0; i < count; ++i) {
-    wf_solve_info* inf = infos ? infos + i : nullptr;
-    wf_status s = wf_solve(ctx, grids + i, powers + i, w[i], nbar[i], b[i], opts + i, s_out[i], inf, stream);
-    if (s != WF_OK && first == WF_OK) first = s;
+    wf_solve_info* pi = infos ? infos + i : &tmp[i];
+    std::memset(pi, 0, sizeof(*pi));
+    wf_status s = prepare_solve(grids + i, powers + i, w[i], nbar[i], b[i], opts + i, s_out[i], args[i]);
+    if (s != WF_OK) {
+      pi->status = s;
+      return s;
+    }
+    sys.push_back(&args[i]);
+    inf.push_back(pi);
   }
-  return first;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return solve_many(*c, sys, inf, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -100,6 +100,8 @@ struct Ctx {
   std::mutex mu;            // serialises synchronous API calls on this context
   std::map<std::string, DevBuf> bufs;
   std::map<int, double2*> twiddles;  // per N: exp(-2 pi i e / (2N)), e < 2N
+  std::map<std::string, DevBuf> pinned;  // page-locked host buffers (scalar staging)
+  std::vector<cudaStream_t> streams;     // non-blocking streams for interleaved groups
   void* host_pinned = nullptr;       // small pinned staging area for scalars
   struct Server* server = nullptr;   // serving loop, created on first wf_submit
   Prof prof;
@@ -124,6 +126,10 @@ struct Ctx {
   // Device buffer `name` with at least `bytes` bytes (contents not preserved on growth).
   wf_status get(const std::string& name, size_t bytes, void** out);
   wf_status tw(int n, const double2** out);
+  // Page-locked host buffer `name` with at least `bytes` bytes.
+  wf_status get_pinned(const std::string& name, size_t bytes, void** out);
+  // i-th library-owned non-blocking stream.
+  wf_status stream(int i, cudaStream_t* out);
   void release_all();
 };
 
@@ -170,7 +176,9 @@ struct SolveArgs {
   double sum_w = -1.0;       // filled by the driver
 };
 wf_status build_sinv_table(const wf_grid& g, const wf_power& pw, std::vector<double>& out);
-wf_status solve_run(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st);
+// Solve every system (grouped by size and precision, groups interleaved on the device).
+// Returns WF_OK if all converged, else the first failing status; infos[i] filled for each.
+wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_info*>& infos, cudaStream_t st);
 void serve_shutdown(Ctx& c);
 
 }  // namespace wf

@@ -79,14 +79,14 @@ template <int RAD, int DIR, class R> WF_D void dft(cx<R>* v) {
 
 // ---- one Stockham pass -------------------------------------------------------------------
 template <class R, int M, int RAD, int NS, int TPL, int LD, int DIR, int TWS>
-WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw) {
+WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw, bool act) {
   constexpr int NB = M / RAD;
   constexpr int PER = (NB + TPL - 1) / TPL;
   cx<R> v[PER][RAD];
 #pragma unroll
   for (int m = 0; m < PER; ++m) {
     const int j = t + m * TPL;
-    if ((NB % TPL) == 0 || j < NB) {
+    if (act && ((NB % TPL) == 0 || j < NB)) {
 #pragma unroll
       for (int r = 0; r < RAD; ++r) v[m][r] = col[(j + r * NB) * LD];
     }
@@ -95,7 +95,7 @@ WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw) {
 #pragma unroll
   for (int m = 0; m < PER; ++m) {
     const int j = t + m * TPL;
-    if ((NB % TPL) == 0 || j < NB) {
+    if (act && ((NB % TPL) == 0 || j < NB)) {
       const int k = j % NS;
       if constexpr (NS > 1) {
 #pragma unroll
@@ -115,20 +115,21 @@ WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw) {
 }
 
 template <class R, int M, int S, int NS, int TPL, int LD, int DIR, int TWS>
-WF_D void fft_passes(cx<R>* col, int t, const cx<R>* tw) {
+WF_D void fft_passes(cx<R>* col, int t, const cx<R>* tw, bool act) {
   if constexpr (NS < M) {
     constexpr int RAD = radix_at(M, S);
-    fft_pass<R, M, RAD, NS, TPL, LD, DIR, TWS>(col, t, tw);
-    fft_passes<R, M, S + 1, NS * RAD, TPL, LD, DIR, TWS>(col, t, tw);
+    fft_pass<R, M, RAD, NS, TPL, LD, DIR, TWS>(col, t, tw, act);
+    fft_passes<R, M, S + 1, NS * RAD, TPL, LD, DIR, TWS>(col, t, tw, act);
   }
 }
 
 // Transform column `col` (stride LD) of length M with TPL threads (thread index t in
-// [0, TPL)).  Every thread of the CTA must call this (it synchronises the CTA).  The
-// twiddle table holds exp(-2 pi i e / (M TWS)), so W_M^e = tw[TWS e].
+// [0, TPL)).  Every thread of the CTA must call this (it synchronises the CTA); threads with
+// act = false only take part in the barriers.  The twiddle table holds
+// exp(-2 pi i e / (M TWS)), so W_M^e = tw[TWS e].
 template <class R, int M, int TPL, int LD, int DIR, int TWS = 1>
-WF_D void fft_line(cx<R>* col, int t, const cx<R>* tw) {
-  fft_passes<R, M, 0, 1, TPL, LD, DIR, TWS>(col, t, tw);
+WF_D void fft_line(cx<R>* col, int t, const cx<R>* tw, bool act = true) {
+  fft_passes<R, M, 0, 1, TPL, LD, DIR, TWS>(col, t, tw, act);
 }
 
 // Threads per line for a line of length M: one radix-8-or-smaller butterfly group per thread

@@ -1,0 +1,22 @@
+// wf_solver_group.h -- the host-side interface of a group of systems solved together
+// (implemented per grid size in wf_solver_impl.cuh).
+#pragma once
+#include <vector>
+
+#include "wf_ctx.h"
+
+namespace wf {
+
+struct Group {
+  virtual ~Group() {}
+  virtual wf_status prepare(Ctx& c, cudaStream_t st) = 0;  // allocate, copy inputs, start CG
+  virtual wf_status enqueue(Ctx& c, cudaStream_t st) = 0;  // next block of device work
+  virtual wf_status advance(Ctx& c) = 0;                   // after a sync: consume scalars
+  virtual bool done() const = 0;
+  virtual wf_status finish(Ctx& c, cudaStream_t st) = 0;   // copy the solutions out
+  std::vector<SolveArgs*> sys;
+  std::vector<wf_solve_info*> info;
+  int nb = 0;
+};
+
+}  // namespace wf

@@ -25,36 +25,50 @@
 #include <vector>
 
 #include "wf_ctx.h"
+#include "wf_solver_group.h"
 #include "wf_spectral.cuh"
 
 namespace wf {
+
+// Arithmetic of the FP64-storage transforms.  The engine also runs in double-float (df32, FP32
+// units, ~2^-48 relative accuracy), which measured slower than native FP64 for the y pass at
+// the tile shapes used here, so native FP64 is used.
+using FP64Arith = double;
 
 template <class K>
 static inline cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Launch geometry and launchers of the spectral passes for one arithmetic type and size.
+// Launch geometry and launchers of the spectral passes for one arithmetic type and size; every
+// launcher covers `nb` systems laid out with the strides `bt` (blockIdx.z = system).
 template <class R, int N>
 struct Spec {
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
   static constexpr int NH = N / 2;
-  static constexpr int NLxy = xy_lines<R, N>();
+  static constexpr int NLxy = XYG<R, N>::NL;
   static_assert(NH % NLxy == 0 && (N * N) % tile_lines<R>() == 0, "tile widths must divide the grid");
-  static constexpr int TPLn = tpl<R, N>();
-  static constexpr int NTy = NLxy * TPLn;
-  static constexpr int NTx = (NLxy + 1) * TPLn;
-  static constexpr size_t SMxy = (size_t)(N * (NLxy + 1) + N) * sizeof(cx<R>);
-  static constexpr int NLz = tile_lines<R>();
-  static constexpr int TPLh = tpl<R, NH>();
-  static constexpr int NTz = NLz * TPLh;
-  static constexpr size_t SMz = (size_t)(NH * (NLz + 1) + 2 * N) * sizeof(cx<R>);
-  static constexpr int GXY = (NH / NLxy) * N;   // blocks of an x or y pass
-  static constexpr int GZ = N * N / NLz;        // blocks of a z pass
-  static constexpr int GU = 152 * 4;            // blocks of the update sweep
+  static constexpr int NTy = XYG<R, N>::NT;
+  static constexpr int NTx = XYG<R, N>::NT;
+  static constexpr size_t SMxy = XYG<R, N>::SMEM;
+  static constexpr int NLz = ZG<R, N>::NL;
+  static constexpr int NTz = ZG<R, N>::NT;
+  static constexpr size_t SMz = ZG<R, N>::SMEM;
+  static constexpr int GXY = (NH / NLxy) * N;   // blocks of an x or y pass (per system)
+  static constexpr int GZ = N * N / NLz;        // blocks of a z pass (per system)
+  static constexpr int GU = 152 * 4;            // blocks of the update sweep (per system)
   static constexpr size_t SPEC = (size_t)N * N * NH;  // complex elements of a spectrum
-  static dim3 gxy() { return dim3(NH / NLxy, N); }
+  static constexpr size_t V = (size_t)N * N * N;
+  static constexpr int TAB = 3 * (N / 2) * (N / 2) + 1;
+  static constexpr int NPART = GXY > GZ ? (GXY > 2 * GU ? GXY : 2 * GU) : (GZ > 2 * GU ? GZ : 2 * GU);
+  static dim3 gxy(int nb) { return dim3(NH / NLxy, N, nb); }
+  static dim3 gz(int nb) { return dim3(GZ, 1, nb); }
+  static Bat bat() { return Bat{SPEC, V, TAB, NPART}; }
+
+  // algorithmic bytes of one launch per system (DRAM traffic the pass cannot avoid)
+  static constexpr double BS = (double)SPEC * sizeof(ST);
+  static constexpr double BV = (double)V;
 
   static cudaError_t attrs() {
     static bool done = false;
@@ -64,9 +78,9 @@ struct Spec {
     WF_A((k_ypass<R, N, -1>), SMxy);
     WF_A((k_ypass<R, N, +1>), SMxy);
     WF_A((k_cg_xinv<R, N>), SMxy);
-    WF_A((k_cg_xfwd<R, N>), SMxy);
+    WF_A((k_cg_xfwd<R, N, true>), SMxy);
+    WF_A((k_cg_xfwd<R, N, false>), SMxy);
     WF_A((k_xmul<R, N, true, false, true>), SMxy);
-    WF_A((k_xmul<R, N, true, false, false>), SMxy);
     WF_A((k_xmul<R, N, false, true, false>), SMxy);
     WF_A((k_xmul<R, N, true, true, false>), SMxy);
     WF_A((k_zturn<R, N>), SMz);
@@ -80,81 +94,86 @@ struct Spec {
     return e;
   }
 
-  // algorithmic bytes of one launch (DRAM traffic the pass cannot avoid)
-  static constexpr double BS = (double)SPEC * sizeof(ST);   // one spectrum
-  static constexpr double BV = (double)N * N * N;           // cells
-
-  static void ypass(Ctx& c, ST* t, const double2* tw, const CgScal* sc, int dir, cudaStream_t st) {
-    c.launch("ypass", 2 * BS, st, [&] {
-      if (dir < 0) k_ypass<R, N, -1><<<gxy(), NTy, SMxy, st>>>(t, tw, sc);
-      else k_ypass<R, N, +1><<<gxy(), NTy, SMxy, st>>>(t, tw, sc);
+  static void ypass(Ctx& c, int nb, ST* t, const double2* tw, const CgScal* sc, int dir, cudaStream_t st) {
+    c.launch("ypass", 2 * BS * nb, st, [&] {
+      if (dir < 0) k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(t, tw, sc, bat());
+      else k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(t, tw, sc, bat());
     });
   }
   // out = [IFFT_x] tab (.) [FFT_x] in
   template <bool FWD, bool INV, bool DOT>
-  static void xmul(Ctx& c, const ST* in, ST* out, const SS* tab, const double2* tw, double* part,
+  static void xmul(Ctx& c, int nb, const ST* in, ST* out, const SS* tab, const double2* tw, double* part,
                    const CgScal* sc, cudaStream_t st) {
-    c.launch("xmul", 2 * BS, st, [&] { k_xmul<R, N, FWD, INV, DOT><<<gxy(), NTx, SMxy, st>>>(in, out, tab, tw, part, sc); });
+    c.launch("xmul", 2 * BS * nb, st,
+             [&] { k_xmul<R, N, FWD, INV, DOT><<<gxy(nb), NTx, SMxy, st>>>(in, out, tab, tw, part, sc, bat()); });
   }
-  static void zfwd(Ctx& c, const double* in, ST* out, const double2* tw, double* part, bool sq, const CgScal* sc,
-                   cudaStream_t st) {
-    c.launch("zfwd", BS + 8 * BV, st, [&] {
-      if (sq) k_zfwd<R, N, true><<<GZ, NTz, SMz, st>>>(in, out, tw, part, sc);
-      else k_zfwd<R, N, false><<<GZ, NTz, SMz, st>>>(in, out, tw, part, sc);
+  static void zfwd(Ctx& c, int nb, const double* in, ST* out, const double2* tw, double* part, bool sq,
+                   const CgScal* sc, cudaStream_t st) {
+    c.launch("zfwd", (BS + 8 * BV) * nb, st, [&] {
+      if (sq) k_zfwd<R, N, true><<<gz(nb), NTz, SMz, st>>>(in, out, tw, part, sc, bat());
+      else k_zfwd<R, N, false><<<gz(nb), NTz, SMz, st>>>(in, out, tw, part, sc, bat());
     });
   }
   template <int MODE>
-  static void zinv(Ctx& c, const ST* in, double* out, const double* s, const double* w, const double* b, double nbar,
+  static void zinv(Ctx& c, int nb, const ST* in, double* out, const double* s, const double* w, const double* b,
                    double scl, const double2* tw, double* part, const CgScal* sc, cudaStream_t st) {
     const double vb = MODE == ZI_RESID ? 4 : (MODE == ZI_ACCUM ? 2 : 1);
-    c.launch("zinv", BS + 8 * vb * BV, st,
-             [&] { k_zinv<R, N, MODE><<<GZ, NTz, SMz, st>>>(in, out, s, w, b, nbar, scl, tw, part, sc); });
+    c.launch("zinv", (BS + 8 * vb * BV) * nb, st,
+             [&] { k_zinv<R, N, MODE><<<gz(nb), NTz, SMz, st>>>(in, out, s, w, b, scl, tw, part, sc, bat()); });
   }
 
-  // One CG iteration on the device (no host synchronisation).
-  static void iteration(Ctx& c, ST* r, ST* pold, ST* pnew, ST* x, ST* T, ST* q, const SS* D, const SS* ctab,
-                        const SS* mtab, const double2* tw, double* part, CgScal* sc, double inv_vc,
+  // One CG iteration of every unfinished system (no host synchronisation).
+  static void iteration(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, ST* q, const SS* D, const SS* ctab,
+                        const SS* mtab, bool unit_m, const double2* tw, double* part, CgScal* sc, double inv_vc,
                         cudaStream_t st) {
-    c.launch("cg_xinv", 6 * BS, st, [&] { k_cg_xinv<R, N><<<gxy(), NTx, SMxy, st>>>(r, pold, pnew, x, T, ctab, tw, sc); });
-    c.launch("ypass", 2 * BS, st, [&] { k_ypass<R, N, +1><<<gxy(), NTy, SMxy, st>>>(T, tw, sc); });
-    c.launch("zturn", 2 * BS + sizeof(SS) * BV, st, [&] { k_zturn<R, N><<<GZ, NTz, SMz, st>>>(T, D, tw, sc); });
-    c.launch("ypass", 2 * BS, st, [&] { k_ypass<R, N, -1><<<gxy(), NTy, SMxy, st>>>(T, tw, sc); });
-    c.launch("cg_xfwd", 3 * BS, st, [&] { k_cg_xfwd<R, N><<<gxy(), NTx, SMxy, st>>>(T, pnew, q, ctab, mtab, tw, part, sc); });
-    c.launch("fin", 0, st, [&] { k_fin_alpha<<<1, 1024, 0, st>>>(part, GXY, sc); });
-    c.launch("cg_update", 3 * BS, st, [&] { k_update<R, N><<<GU, 256, 0, st>>>(r, q, ctab, part, sc); });
-    c.launch("fin", 0, st, [&] { k_fin_beta<<<1, 1024, 0, st>>>(part, GU, inv_vc, sc); });
+    const Bat b = bat();
+    c.launch("cg_xinv", 6 * BS * nb, st,
+             [&] { k_cg_xinv<R, N><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, tw, sc, b); });
+    c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
+    c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st,
+             [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, sc, b); });
+    c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
+    c.launch("cg_xfwd", 3 * BS * nb, st, [&] {
+      if (unit_m) k_cg_xfwd<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(T, P0, P1, q, ctab, mtab, tw, part, sc, b);
+      else k_cg_xfwd<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(T, P0, P1, q, ctab, mtab, tw, part, sc, b);
+    });
+    c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, GXY, sc, b); });
+    c.launch("cg_update", 3 * BS * nb, st,
+             [&] { k_update<R, N><<<dim3(GU, nb), 256, 0, st>>>(r, q, ctab, part, sc, b); });
+    c.launch("fin", 0, st, [&] { k_fin_beta<<<nb, 1024, 0, st>>>(part, GU, inv_vc, sc, b); });
   }
 };
 
-// ---- small elementwise helpers -----------------------------------------------------------
+// ---- small batched elementwise helpers (blockIdx.y = system) -----------------------------
+// D = w * nbar / V_c (nbar from the system's scalars), in the type of the spectral arithmetic
 template <class SSo>
-__global__ void k_scale_copy(const double* __restrict__ in, SSo* __restrict__ out, double f, size_t n) {
+__global__ void k_make_D(const double* __restrict__ w, SSo* __restrict__ D, const CgScal* __restrict__ sc,
+                         double inv_vc, size_t n) {
+  const int z = blockIdx.y;
+  const double f = sc[z].nbar * inv_vc;
+  w += z * n;
+  D += z * n;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = (SSo)(in[i] * f);
+    D[i] = (SSo)(w[i] * f);
 }
-static __global__ void k_sum(const double* __restrict__ in, size_t n, double* __restrict__ partials) {
+// partials[z * pstride + block] of sum(in) (SQ = false) or sum(in^2) (SQ = true)
+template <bool SQ>
+__global__ void k_sum(const double* __restrict__ in, size_t n, double* __restrict__ partials, int pstride) {
   __shared__ double red[32];
+  const int z = blockIdx.y;
+  in += z * n;
   AccD acc;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc.add(in[i]);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    if (SQ) acc.add_prod(in[i], in[i]);
+    else acc.add(in[i]);
+  }
   const double s = block_sum(acc.get(), red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-static __global__ void k_sumsq(const double* __restrict__ in, size_t n, double* __restrict__ partials) {
-  __shared__ double red[32];
-  AccD acc;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    acc.add_prod(in[i], in[i]);
-  const double s = block_sum(acc.get(), red);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (threadIdx.x == 0) partials[z * pstride + blockIdx.x] = s;
 }
 
-// Tables: sinv[n2]; ctab[n2] = c(k), mtab[n2] = c^2 S^-1 (k).
-static void make_tables(const std::vector<double>& sinv, bool precond, double c0, std::vector<double>& ct,
-                        std::vector<double>& mt) {
+// Tables: ctab[n2] = c(k), mtab[n2] = c^2 S^-1 (k) for one system.
+static void make_tables(const std::vector<double>& sinv, bool precond, double c0, double* ct, double* mt) {
   const size_t L = sinv.size();
-  ct.resize(L);
-  mt.resize(L);
   for (size_t i = 0; i < L; ++i) {
     if (!precond) {
       ct[i] = 1.0;
@@ -169,23 +188,9 @@ static void make_tables(const std::vector<double>& sinv, bool precond, double c0
   }
 }
 
-static inline wf_status read_scal(Ctx& c, const CgScal* dsc, CgScal* out, cudaStream_t st) {
-  CgScal* h = reinterpret_cast<CgScal*>(c.host_pinned);
-  WF_CUDA(cudaMemcpyAsync(h, dsc, sizeof(CgScal), cudaMemcpyDeviceToHost, st));
-  WF_CUDA(cudaStreamSynchronize(st));
-  *out = *h;
-  return WF_OK;
-}
-static inline wf_status write_scal(Ctx& c, CgScal* dsc, const CgScal& v, cudaStream_t st) {
-  CgScal* h = reinterpret_cast<CgScal*>(c.host_pinned) + 1;
-  *h = v;
-  WF_CUDA(cudaMemcpyAsync(dsc, h, sizeof(CgScal), cudaMemcpyHostToDevice, st));
-  WF_CUDA(cudaStreamSynchronize(st));
-  return WF_OK;
-}
-
 template <class T>
-static inline wf_status upload(Ctx& c, const char* name, const std::vector<double>& v, const T** out, cudaStream_t st) {
+static inline wf_status upload_tables(Ctx& c, const std::string& name, const std::vector<double>& v, T** out,
+                                      cudaStream_t st) {
   std::vector<T> tmp(v.begin(), v.end());
   T* d;
   WF_TRY(c.get(name, tmp.size() * sizeof(T), (void**)&d));
@@ -195,289 +200,401 @@ static inline wf_status upload(Ctx& c, const char* name, const std::vector<doubl
   return WF_OK;
 }
 
-// Explicit canonical residual: res = b - A s (FP64 storage), returns ||res||^2 via *rr.
-// Uses spectra T, T2 and the FP64 S^-1 table.
-template <class RD, int N>
-static wf_status residual(Ctx& c, const double* s, const double* w, const double* b, double nbar,
-                          const double* sinv_d, double* res, typename Store<RD>::T* T, typename Store<RD>::T* T2,
-                          double* part, CgScal* sc, double* rr, cudaStream_t st) {
-  using SP = Spec<RD, N>;
-  const double2* tw;
-  WF_TRY(c.tw(N, &tw));
-  const double inv_vc = 1.0 / ((double)N * N * N);
-  SP::zfwd(c, s, T, tw, part, false, nullptr, st);
-  SP::ypass(c, T, tw, nullptr, -1, st);
-  SP::template xmul<true, true, false>(c, T, T2, sinv_d, tw, part, nullptr, st);
-  SP::ypass(c, T2, tw, nullptr, +1, st);
-  SP::template zinv<ZI_RESID>(c, T2, res, s, w, b, nbar, inv_vc, tw, part, nullptr, st);
-  c.launch("fin", 0, st, [&] { k_fin_sum<<<1, 1024, 0, st>>>(part, SP::GZ, 0, sc); });
-  WF_CUDA(cudaGetLastError());
-  CgScal h;
-  WF_TRY(read_scal(c, sc, &h, st));
-  *rr = h.aux[0];
-  return WF_OK;
-}
-
-// Run CG iterations until the device reports done; returns the final CgScal.
-// P[0], P[1]: ping-pong search directions; `j0` = iterations run since they were reset.
-template <class R, int N>
-static wf_status cg_loop(Ctx& c, typename Store<R>::T* r, typename Store<R>::T** P, typename Store<R>::T* x,
-                         typename Store<R>::T* T, typename Store<R>::T* q, const typename Store<R>::S* D,
-                         const typename Store<R>::S* ctab, const typename Store<R>::S* mtab, double* part, CgScal* sc,
-                         CgScal* out, cudaStream_t st) {
-  using SP = Spec<R, N>;
-  const double2* tw;
-  WF_TRY(c.tw(N, &tw));
-  const double inv_vc = 1.0 / ((double)N * N * N);
-  CgScal h;
-  WF_TRY(read_scal(c, sc, &h, st));
-  const int it_start = h.iter;
-  int launched = 0;
-  // check the device flag every `blk` iterations; small grids check less often
-  const int blk = N >= 256 ? 4 : (N >= 128 ? 16 : 32);
-  while (!h.done) {
-    for (int i = 0; i < blk; ++i) {
-      const int j = launched + i;
-      SP::iteration(c, r, P[j & 1], P[(j + 1) & 1], x, T, q, D, ctab, mtab, tw, part, sc, inv_vc, st);
-    }
-    WF_CUDA(cudaGetLastError());
-    launched += blk;
-    WF_TRY(read_scal(c, sc, &h, st));
-  }
-  // apply the last alpha: the direction of the last completed iteration
-  const int jl = h.iter - it_start - 1;
-  if (jl >= 0) {
-    c.launch("axpy", 3 * SP::BS, st, [&] { k_axpy_final<<<152 * 4, 256, 0, st>>>(x, P[(jl + 1) & 1], SP::SPEC, sc); });
-    WF_CUDA(cudaGetLastError());
-  }
-  *out = h;
-  return WF_OK;
-}
-
 // ==========================================================================================
-// FP64 solve: FP64 storage; spectral arithmetic in R (double or df32).
+// A group: `nb` systems of one grid size and precision, solved together.  The host drives it
+// as a state machine: enqueue() launches the next block of device work (ending with a copy of
+// the scalars to pinned host memory), advance() consumes those scalars after the stream is
+// synchronised and picks the next phase.
 // ==========================================================================================
-template <class R, int N>
-static wf_status solve_fp64(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st) {
-  using SP = Spec<R, N>;
-  using ST = double2;
-  static_assert(sizeof(typename Store<R>::T) == sizeof(double2), "FP64 storage");
-  WF_CUDA(SP::attrs());
-  WF_CUDA(Spec<double, N>::attrs());
-  const size_t V = (size_t)N * N * N, SPEC = SP::SPEC;
-  const double inv_vc = 1.0 / (double)V;
-  const double2* tw;
-  WF_TRY(c.tw(N, &tw));
-  ST *xh, *rh, *P[2], *qh, *T, *T2;
-  double *D, *res, *part;
-  CgScal* sc;
-  WF_TRY(c.get("s_x", SPEC * sizeof(ST), (void**)&xh));
-  WF_TRY(c.get("s_r", SPEC * sizeof(ST), (void**)&rh));
-  WF_TRY(c.get("s_p0", SPEC * sizeof(ST), (void**)&P[0]));
-  WF_TRY(c.get("s_p1", SPEC * sizeof(ST), (void**)&P[1]));
-  WF_TRY(c.get("s_q", SPEC * sizeof(ST), (void**)&qh));
-  WF_TRY(c.get("s_T", SPEC * sizeof(ST), (void**)&T));
-  WF_TRY(c.get("s_T2", SPEC * sizeof(ST), (void**)&T2));
-  WF_TRY(c.get("s_D", V * sizeof(double), (void**)&D));
-  WF_TRY(c.get("s_res", V * sizeof(double), (void**)&res));
-  const size_t np = (size_t)std::max({SP::GXY, SP::GZ, 2 * SP::GU});
-  WF_TRY(c.get("s_part", np * sizeof(double), (void**)&part));
-  WF_TRY(c.get("s_sc", sizeof(CgScal), (void**)&sc));
 
-  // sum(w) for c_0 and ||b||^2
-  CgScal init{};
-  init.max_iter = a.opts.max_iter;
-  init.tol2 = a.opts.tol * a.opts.tol;
-  WF_TRY(write_scal(c, sc, init, st));
-  c.launch("reduce", 8.0 * V, st, [&] { k_sum<<<SP::GU, 256, 0, st>>>(a.w, V, part); });
-  c.launch("fin", 0, st, [&] { k_fin_sum<<<1, 1024, 0, st>>>(part, SP::GU, 1, sc); });
-  WF_CUDA(cudaGetLastError());
-  CgScal h;
-  WF_TRY(read_scal(c, sc, &h, st));
-  const double sum_w = h.aux[1];
-  if (!(sum_w > 0.0)) return WF_ERR_ARG;
-  const double c0 = 1.0 / std::sqrt(a.nbar * sum_w * inv_vc);
-  std::vector<double> ct, mt;
-  make_tables(a.sinv, a.opts.precond != 0, c0, ct, mt);
-  const double *ctab, *mtab, *stab;
-  WF_TRY(upload<double>(c, "t_c", ct, &ctab, st));
-  WF_TRY(upload<double>(c, "t_m", mt, &mtab, st));
-  WF_TRY(upload<double>(c, "t_s", a.sinv, &stab, st));
-  c.launch("scale_copy", 16.0 * V, st, [&] { k_scale_copy<double><<<SP::GU, 256, 0, st>>>(a.w, D, a.nbar * inv_vc, V); });
-
-  int iters = 0, restarts = 0;
-  double rel = 1.0;
-  wf_status status = WF_OK;
-  // r = C b (with ||b||^2), x = 0
-  const double* rhs = a.b;
-  for (;;) {
-    SP::zfwd(c, rhs, T, tw, part, true, nullptr, st);
-    if (rhs == a.b) c.launch("fin", 0, st, [&] { k_fin_sum<<<1, 1024, 0, st>>>(part, SP::GZ, -1, sc); });
-    SP::ypass(c, T, tw, nullptr, -1, st);
-    SP::template xmul<true, false, true>(c, T, rh, ctab, tw, part, nullptr, st);
-    c.launch("fin", 0, st, [&] { k_fin_init<<<1, 1024, 0, st>>>(part, SP::GXY, sc); });
-    WF_CUDA(cudaMemsetAsync(P[0], 0, SPEC * sizeof(ST), st));
-    WF_CUDA(cudaMemsetAsync(P[1], 0, SPEC * sizeof(ST), st));
-    if (rhs == a.b) WF_CUDA(cudaMemsetAsync(xh, 0, SPEC * sizeof(ST), st));
-    WF_CUDA(cudaGetLastError());
-    CgScal fin;
-    WF_TRY(cg_loop<R, N>(c, rh, P, xh, T, qh, D, ctab, mtab, part, sc, &fin, st));
-    iters = fin.iter;
-    if (fin.bb == 0.0) {  // b = 0: s = 0
-      WF_CUDA(cudaMemsetAsync(a.s_out, 0, V * sizeof(double), st));
-      rel = 0.0;
-      break;
-    }
-    // s = C x (real space)
-    SP::template xmul<false, true, false>(c, xh, T, ctab, tw, part, nullptr, st);
-    SP::ypass(c, T, tw, nullptr, +1, st);
-    SP::template zinv<ZI_STORE>(c, T, a.s_out, nullptr, nullptr, nullptr, 0.0, inv_vc, tw, part, nullptr, st);
-    WF_CUDA(cudaGetLastError());
-    double rr;
-    WF_TRY((residual<R, N>(c, a.s_out, a.w, a.b, a.nbar, stab, res, T, T2, part, sc, &rr, st)));
-    rel = std::sqrt(rr / fin.bb);
-    if (rel <= a.opts.tol) break;
-    if (fin.done == 3) {
-      status = WF_ERR_BREAKDOWN;
-      break;
-    }
-    if (fin.iter >= a.opts.max_iter || restarts >= 8) {
-      status = WF_ERR_NOT_CONVERGED;
-      break;
-    }
-    // restart from the recomputed residual; the done flag is cleared by k_fin_init
-    ++restarts;
-    rhs = res;
-  }
-  if (info) {
-    info->iters = iters;
-    info->outer_iters = restarts;
-    info->rel_residual = rel;
-    info->nbar = a.nbar;
-    info->status = status;
-  }
-  return status;
-}
-
-// ==========================================================================================
-// Mixed precision: outer FP64 refinement x += e, inner CG on A e = res in FP32 spectra.
-// ==========================================================================================
+// Shared pieces: contiguous copies of w and b, sum(w), ||b||^2, tables, scalars.
 template <int N>
-static wf_status solve_mixed(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st) {
+struct GroupCommon : Group {
+  static constexpr size_t V = (size_t)N * N * N;
+  static constexpr int TAB = 3 * (N / 2) * (N / 2) + 1;
+  std::string key;
+  double *W = nullptr, *B = nullptr, *S = nullptr, *RES = nullptr, *part = nullptr;
+  CgScal *sc = nullptr, *hsc = nullptr;
+  const double2* tw = nullptr;
+  std::vector<CgScal> h;       // host copy of the scalars
+  std::vector<double> bb0, sumw, rel;
+  std::vector<int> state;      // 0 running, 1 finished
+  int phase = 0;
+  double inv_vc = 1.0 / (double)V;
+
+  wf_status push_scalars(cudaStream_t st) {
+    for (int m = 0; m < nb; ++m) hsc[m] = h[m];
+    WF_CUDA(cudaMemcpyAsync(sc, hsc, nb * sizeof(CgScal), cudaMemcpyHostToDevice, st));
+    return WF_OK;
+  }
+  wf_status pull_scalars(cudaStream_t st) {
+    WF_CUDA(cudaMemcpyAsync(hsc, sc, nb * sizeof(CgScal), cudaMemcpyDeviceToHost, st));
+    return WF_OK;
+  }
+  void read_scalars() { h.assign(hsc, hsc + nb); }
+  bool all_done() const {
+    for (int m = 0; m < nb; ++m)
+      if (h[m].done == 0) return false;
+    return true;
+  }
+};
+
+// Per-system sums of w and b^2: two reductions into the partial slots [0,152) and [152,304).
+template <int N>
+static wf_status group_sums(Ctx& c, GroupCommon<N>& g, int npart, cudaStream_t st) {
+  const size_t V = GroupCommon<N>::V;
+  g.h.assign(g.nb, CgScal{});
+  WF_TRY(g.push_scalars(st));
+  const Bat b{0, 0, 0, npart};
+  c.launch("reduce", 8.0 * V * g.nb, st, [&] { k_sum<false><<<dim3(152, g.nb), 256, 0, st>>>(g.W, V, g.part, npart); });
+  c.launch("fin", 0, st, [&] { k_fin_sum<<<g.nb, 1024, 0, st>>>(g.part, 152, 0, g.sc, b); });
+  c.launch("reduce", 8.0 * V * g.nb, st, [&] { k_sum<true><<<dim3(152, g.nb), 256, 0, st>>>(g.B, V, g.part, npart); });
+  c.launch("fin", 0, st, [&] { k_fin_sum<<<g.nb, 1024, 0, st>>>(g.part, 152, 1, g.sc, b); });
+  WF_CUDA(cudaGetLastError());
+  WF_TRY(g.pull_scalars(st));
+  WF_CUDA(cudaStreamSynchronize(st));
+  g.read_scalars();
+  g.sumw.resize(g.nb);
+  g.bb0.resize(g.nb);
+  for (int m = 0; m < g.nb; ++m) {
+    g.sumw[m] = g.h[m].aux[0];
+    g.bb0[m] = g.h[m].aux[1];
+    if (!(g.sumw[m] > 0.0)) return WF_ERR_ARG;
+  }
+  return WF_OK;
+}
+
+// Check interval: grids of 256^3 and up check the device flags every 4 iterations.
+template <int N> constexpr int check_every() { return N >= 256 ? 4 : (N >= 128 ? 8 : 16); }
+
+// ------------------------------------------------------------------------------------------
+// FP64 group: FP64 storage, spectral arithmetic R.
+// Phases: 1 CG loop, 2 post (s = C x, explicit residual), 3 restart, 9 done.
+// ------------------------------------------------------------------------------------------
+template <class R, int N>
+struct GroupFP64 : GroupCommon<N> {
+  using SP = Spec<R, N>;
+  using ST = typename Store<R>::T;
+  using Base = GroupCommon<N>;
+  using Base::nb; using Base::sys; using Base::info; using Base::key; using Base::W; using Base::B;
+  using Base::S; using Base::RES; using Base::part; using Base::sc; using Base::tw; using Base::h;
+  using Base::phase; using Base::inv_vc; using Base::bb0; using Base::rel; using Base::state;
+  ST *xh, *rh, *P0, *P1, *qh, *T, *T2;
+  double *D, *ct, *mt, *stab;
+  std::vector<int> restarts;
+  bool unit_m = true;
+
+  wf_status prepare(Ctx& c, cudaStream_t st) override {
+    nb = (int)sys.size();
+    key = "f64_" + std::to_string(N) + "_";
+    WF_CUDA(SP::attrs());
+    const size_t SPEC = SP::SPEC, V = SP::V;
+    WF_TRY(c.tw(N, &tw));
+    const char* nm[7] = {"x", "r", "p0", "p1", "q", "T", "T2"};
+    ST** ptr[7] = {&xh, &rh, &P0, &P1, &qh, &T, &T2};
+    for (int i = 0; i < 7; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(ST), (void**)ptr[i]));
+    WF_TRY(c.get(key + "D", nb * V * sizeof(double), (void**)&D));
+    WF_TRY(c.get(key + "W", nb * V * sizeof(double), (void**)&W));
+    WF_TRY(c.get(key + "B", nb * V * sizeof(double), (void**)&B));
+    WF_TRY(c.get(key + "S", nb * V * sizeof(double), (void**)&S));
+    WF_TRY(c.get(key + "RES", nb * V * sizeof(double), (void**)&RES));
+    WF_TRY(c.get(key + "part", (size_t)nb * SP::NPART * sizeof(double), (void**)&part));
+    WF_TRY(c.get(key + "sc", nb * sizeof(CgScal), (void**)&sc));
+    WF_TRY(c.get_pinned(key + "hsc", nb * sizeof(CgScal), (void**)&this->hsc));
+    for (int m = 0; m < nb; ++m) {
+      WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    WF_TRY(group_sums<N>(c, *this, SP::NPART, st));
+    // tables
+    const int TAB = SP::TAB;
+    std::vector<double> vc((size_t)nb * TAB), vm((size_t)nb * TAB), vs((size_t)nb * TAB);
+    unit_m = true;
+    for (int m = 0; m < nb; ++m) {
+      const bool pre = sys[m]->opts.precond != 0;
+      unit_m = unit_m && pre;
+      const double c0 = 1.0 / std::sqrt(sys[m]->nbar * this->sumw[m] * inv_vc);
+      make_tables(sys[m]->sinv, pre, c0, vc.data() + (size_t)m * TAB, vm.data() + (size_t)m * TAB);
+      std::copy(sys[m]->sinv.begin(), sys[m]->sinv.end(), vs.begin() + (size_t)m * TAB);
+    }
+    WF_TRY(upload_tables<double>(c, key + "tc", vc, &ct, st));
+    WF_TRY(upload_tables<double>(c, key + "tm", vm, &mt, st));
+    WF_TRY(upload_tables<double>(c, key + "ts", vs, &stab, st));
+    // scalars
+    h.assign(nb, CgScal{});
+    for (int m = 0; m < nb; ++m) {
+      h[m].nbar = sys[m]->nbar;
+      h[m].max_iter = sys[m]->opts.max_iter;
+      h[m].tol2 = sys[m]->opts.tol * sys[m]->opts.tol;
+      h[m].bb = bb0[m];
+    }
+    WF_TRY(this->push_scalars(st));
+    c.launch("make_D", 16.0 * V * nb, st, [&] { k_make_D<double><<<dim3(152 * 4, nb), 256, 0, st>>>(W, D, sc, inv_vc, V); });
+    WF_CUDA(cudaMemsetAsync(xh, 0, nb * SPEC * sizeof(ST), st));
+    rel.assign(nb, 1.0);
+    state.assign(nb, 0);
+    restarts.assign(nb, 0);
+    WF_TRY(start_cg(c, B, st));
+    phase = 1;
+    return WF_OK;
+  }
+  // r = C F(rhs) for every system; p = 0; reset the recurrences of the running systems
+  wf_status start_cg(Ctx& c, const double* rhs, cudaStream_t st) {
+    const size_t SPEC = SP::SPEC;
+    SP::zfwd(c, nb, rhs, T, tw, part, false, nullptr, st);
+    SP::ypass(c, nb, T, tw, nullptr, -1, st);
+    SP::template xmul<true, false, true>(c, nb, T, rh, ct, tw, part, nullptr, st);
+    const Bat b = SP::bat();
+    c.launch("fin", 0, st, [&] { k_fin_init<<<nb, 1024, 0, st>>>(part, SP::GXY, sc, b); });
+    WF_CUDA(cudaMemsetAsync(P0, 0, nb * SPEC * sizeof(ST), st));
+    WF_CUDA(cudaMemsetAsync(P1, 0, nb * SPEC * sizeof(ST), st));
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+  }
+  wf_status enqueue(Ctx& c, cudaStream_t st) override {
+    if (phase == 1) {
+      for (int i = 0; i < check_every<N>(); ++i)
+        SP::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, st);
+    } else if (phase == 2) {
+      const Bat b = SP::bat();
+      c.launch("axpy", 3 * SP::BS * nb, st,
+               [&] { k_axpy_final<<<dim3(152 * 4, nb), 256, 0, st>>>(xh, P0, P1, SP::SPEC, sc, b); });
+      SP::template xmul<false, true, false>(c, nb, xh, T, ct, tw, part, nullptr, st);
+      SP::ypass(c, nb, T, tw, nullptr, +1, st);
+      SP::template zinv<ZI_STORE>(c, nb, T, S, nullptr, nullptr, nullptr, inv_vc, tw, part, nullptr, st);
+      // residual b - A s
+      SP::zfwd(c, nb, S, T, tw, part, false, nullptr, st);
+      SP::ypass(c, nb, T, tw, nullptr, -1, st);
+      SP::template xmul<true, true, false>(c, nb, T, T2, stab, tw, part, nullptr, st);
+      SP::ypass(c, nb, T2, tw, nullptr, +1, st);
+      SP::template zinv<ZI_RESID>(c, nb, T2, RES, S, W, B, inv_vc, tw, part, sc, st);
+      c.launch("fin", 0, st, [&] { k_fin_sum<<<nb, 1024, 0, st>>>(part, SP::GZ, 0, sc, b); });
+    } else if (phase == 3) {
+      WF_TRY(this->push_scalars(st));
+      WF_TRY(start_cg(c, RES, st));
+      phase = 1;
+      for (int i = 0; i < check_every<N>(); ++i)
+        SP::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, st);
+    }
+    WF_CUDA(cudaGetLastError());
+    return this->pull_scalars(st);
+  }
+  wf_status advance(Ctx&) override {
+    this->read_scalars();
+    if (phase == 1) {
+      if (this->all_done()) phase = 2;
+      return WF_OK;
+    }
+    if (phase == 2) {
+      bool any = false;
+      for (int m = 0; m < nb; ++m) {
+        if (state[m]) {
+          h[m].done = 4;
+          continue;
+        }
+        rel[m] = bb0[m] > 0 ? std::sqrt(h[m].aux[0] / bb0[m]) : 0.0;
+        wf_status st = WF_OK;
+        bool fin = true;
+        if (bb0[m] == 0.0 || rel[m] <= sys[m]->opts.tol) st = WF_OK;
+        else if (h[m].done == 3) st = WF_ERR_BREAKDOWN;
+        else if (h[m].iter >= sys[m]->opts.max_iter || restarts[m] >= 8) st = WF_ERR_NOT_CONVERGED;
+        else fin = false;
+        if (fin) {
+          state[m] = 1;
+          h[m].done = 4;
+          if (info[m]) *info[m] = wf_solve_info{h[m].iter, restarts[m], rel[m], sys[m]->nbar, st};
+        } else {
+          restarts[m] += 1;
+          h[m].done = 0;
+          any = true;
+        }
+      }
+      phase = any ? 3 : 9;
+    }
+    return WF_OK;
+  }
+  bool done() const override { return phase == 9; }
+  wf_status finish(Ctx&, cudaStream_t st) override {
+    for (int m = 0; m < nb; ++m)
+      WF_CUDA(cudaMemcpyAsync(sys[m]->s_out, S + m * SP::V, SP::V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return WF_OK;
+  }
+};
+
+// ------------------------------------------------------------------------------------------
+// Mixed group: outer FP64 refinement x += e, inner CG on A e = res in FP32 spectra.
+// Phases: 0 inner start, 1 CG loop, 2 accumulate + FP64 residual, 9 done.
+// ------------------------------------------------------------------------------------------
+template <int N>
+struct GroupMixed : GroupCommon<N> {
   using SF = Spec<float, N>;
-  using SD = Spec<double, N>;
-  WF_CUDA(SF::attrs());
-  WF_CUDA(SD::attrs());
-  const size_t V = (size_t)N * N * N, SPEC = SF::SPEC;
-  const double inv_vc = 1.0 / (double)V;
-  const double2* tw;
-  WF_TRY(c.tw(N, &tw));
-  float2 *xh, *rh, *P[2], *qh, *T;
+  using SD = Spec<FP64Arith, N>;
+  using Base = GroupCommon<N>;
+  using Base::nb; using Base::sys; using Base::info; using Base::key; using Base::W; using Base::B;
+  using Base::S; using Base::RES; using Base::part; using Base::sc; using Base::tw; using Base::h;
+  using Base::phase; using Base::inv_vc; using Base::bb0; using Base::rel; using Base::state;
+  float2 *xh, *rh, *P0, *P1, *qh, *T;
   float* D;
   double2 *T64, *T64b;
-  double *res, *part;
-  CgScal* sc;
-  WF_TRY(c.get("m_x", SPEC * sizeof(float2), (void**)&xh));
-  WF_TRY(c.get("m_r", SPEC * sizeof(float2), (void**)&rh));
-  WF_TRY(c.get("m_p0", SPEC * sizeof(float2), (void**)&P[0]));
-  WF_TRY(c.get("m_p1", SPEC * sizeof(float2), (void**)&P[1]));
-  WF_TRY(c.get("m_q", SPEC * sizeof(float2), (void**)&qh));
-  WF_TRY(c.get("m_T", SPEC * sizeof(float2), (void**)&T));
-  WF_TRY(c.get("m_D", V * sizeof(float), (void**)&D));
-  WF_TRY(c.get("s_T", SPEC * sizeof(double2), (void**)&T64));
-  WF_TRY(c.get("s_T2", SPEC * sizeof(double2), (void**)&T64b));
-  WF_TRY(c.get("s_res", V * sizeof(double), (void**)&res));
-  // partials: the FP32 inner passes and the FP64 residual passes both write here
-  const size_t np = (size_t)std::max({SF::GXY, SF::GZ, 2 * SF::GU, SD::GXY, SD::GZ, 2 * SD::GU});
-  WF_TRY(c.get("s_part", np * sizeof(double), (void**)&part));
-  WF_TRY(c.get("s_sc", sizeof(CgScal), (void**)&sc));
+  float *ct, *mt;
+  double* stab;
+  std::vector<int> outer, iters;
+  bool unit_m = true;
+  static constexpr int NPART = SF::NPART > SD::NPART ? SF::NPART : SD::NPART;
 
-  CgScal init{};
-  WF_TRY(write_scal(c, sc, init, st));
-  c.launch("reduce", 8.0 * V, st, [&] { k_sum<<<SF::GU, 256, 0, st>>>(a.w, V, part); });
-  c.launch("fin", 0, st, [&] { k_fin_sum<<<1, 1024, 0, st>>>(part, SF::GU, 1, sc); });
-  WF_CUDA(cudaGetLastError());
-  CgScal h;
-  WF_TRY(read_scal(c, sc, &h, st));
-  const double sum_w = h.aux[1];
-  if (!(sum_w > 0.0)) return WF_ERR_ARG;
-  const double c0 = 1.0 / std::sqrt(a.nbar * sum_w * inv_vc);
-  std::vector<double> ct, mt;
-  make_tables(a.sinv, a.opts.precond != 0, c0, ct, mt);
-  const float *ctab, *mtab;
-  const double* stab;
-  WF_TRY(upload<float>(c, "tf_c", ct, &ctab, st));
-  WF_TRY(upload<float>(c, "tf_m", mt, &mtab, st));
-  WF_TRY(upload<double>(c, "t_s", a.sinv, &stab, st));
-  c.launch("scale_copy", 12.0 * V, st, [&] { k_scale_copy<float><<<SF::GU, 256, 0, st>>>(a.w, D, a.nbar * inv_vc, V); });
-  // x = s_out = 0; res = b; ||b||^2
-  double* x = a.s_out;
-  WF_CUDA(cudaMemsetAsync(x, 0, V * sizeof(double), st));
-  WF_CUDA(cudaMemcpyAsync(res, a.b, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  c.launch("reduce", 8.0 * V, st, [&] { k_sumsq<<<SF::GU, 256, 0, st>>>(a.b, V, part); });
-  c.launch("fin", 0, st, [&] { k_fin_sum<<<1, 1024, 0, st>>>(part, SF::GU, 0, sc); });
-  WF_CUDA(cudaGetLastError());
-  WF_TRY(read_scal(c, sc, &h, st));
-  const double bb = h.aux[0];
-  wf_status status = WF_OK;
-  int total_iters = 0, outer = 0;
-  double rel = 1.0;
-  const double inner_tol = a.opts.inner_tol > 0.0 ? a.opts.inner_tol : 1e-4;
-  if (bb == 0.0) rel = 0.0;
-  while (rel > a.opts.tol) {
-    if (outer >= 12 || total_iters >= a.opts.max_iter) {
-      status = WF_ERR_NOT_CONVERGED;
-      break;
+  wf_status prepare(Ctx& c, cudaStream_t st) override {
+    nb = (int)sys.size();
+    key = "mix_" + std::to_string(N) + "_";
+    WF_CUDA(SF::attrs());
+    WF_CUDA(SD::attrs());
+    const size_t SPEC = SF::SPEC, V = SF::V;
+    WF_TRY(c.tw(N, &tw));
+    const char* nm[6] = {"x", "r", "p0", "p1", "q", "T"};
+    float2** ptr[6] = {&xh, &rh, &P0, &P1, &qh, &T};
+    for (int i = 0; i < 6; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(float2), (void**)ptr[i]));
+    WF_TRY(c.get(key + "D", nb * V * sizeof(float), (void**)&D));
+    WF_TRY(c.get(key + "T64", nb * SPEC * sizeof(double2), (void**)&T64));
+    WF_TRY(c.get(key + "T64b", nb * SPEC * sizeof(double2), (void**)&T64b));
+    WF_TRY(c.get(key + "W", nb * V * sizeof(double), (void**)&W));
+    WF_TRY(c.get(key + "B", nb * V * sizeof(double), (void**)&B));
+    WF_TRY(c.get(key + "S", nb * V * sizeof(double), (void**)&S));
+    WF_TRY(c.get(key + "RES", nb * V * sizeof(double), (void**)&RES));
+    WF_TRY(c.get(key + "part", (size_t)nb * NPART * sizeof(double), (void**)&part));
+    WF_TRY(c.get(key + "sc", nb * sizeof(CgScal), (void**)&sc));
+    WF_TRY(c.get_pinned(key + "hsc", nb * sizeof(CgScal), (void**)&this->hsc));
+    for (int m = 0; m < nb; ++m) {
+      WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    ++outer;
-    const double target = std::max(inner_tol, 0.3 * a.opts.tol / rel);
-    // inner: r~ = C res (FP32), CG to ||res - A e|| <= target ||res||
-    CgScal in{};
-    in.max_iter = a.opts.max_iter - total_iters;
-    in.tol2 = target * target;
-    in.bb = rel * rel * bb;
-    WF_TRY(write_scal(c, sc, in, st));
-    SF::zfwd(c, res, T, tw, part, false, nullptr, st);
-    SF::ypass(c, T, tw, nullptr, -1, st);
-    SF::template xmul<true, false, true>(c, T, rh, ctab, tw, part, nullptr, st);
-    c.launch("fin", 0, st, [&] { k_fin_init<<<1, 1024, 0, st>>>(part, SF::GXY, sc); });
-    WF_CUDA(cudaMemsetAsync(P[0], 0, SPEC * sizeof(float2), st));
-    WF_CUDA(cudaMemsetAsync(P[1], 0, SPEC * sizeof(float2), st));
-    WF_CUDA(cudaMemsetAsync(xh, 0, SPEC * sizeof(float2), st));
-    WF_CUDA(cudaGetLastError());
-    CgScal fin;
-    WF_TRY(cg_loop<float, N>(c, rh, P, xh, T, qh, D, ctab, mtab, part, sc, &fin, st));
-    total_iters += fin.iter;
-    // x += C e (FP32 transform, FP64 accumulation)
-    SF::template xmul<false, true, false>(c, xh, T, ctab, tw, part, nullptr, st);
-    SF::ypass(c, T, tw, nullptr, +1, st);
-    SF::template zinv<ZI_ACCUM>(c, T, x, nullptr, nullptr, nullptr, 0.0, inv_vc, tw, part, nullptr, st);
-    WF_CUDA(cudaGetLastError());
-    // FP64 residual
-    double rr;
-    WF_TRY((residual<double, N>(c, x, a.w, a.b, a.nbar, stab, res, T64, T64b, part, sc, &rr, st)));
-    const double rel_new = std::sqrt(rr / bb);
-    if (!(rel_new < rel) && fin.done == 3) {
-      rel = rel_new;
-      status = WF_ERR_BREAKDOWN;
-      break;
+    WF_TRY(group_sums<N>(c, *this, NPART, st));
+    const int TAB = SF::TAB;
+    std::vector<double> vc((size_t)nb * TAB), vm((size_t)nb * TAB), vs((size_t)nb * TAB);
+    unit_m = true;
+    for (int m = 0; m < nb; ++m) {
+      const bool pre = sys[m]->opts.precond != 0;
+      unit_m = unit_m && pre;
+      const double c0 = 1.0 / std::sqrt(sys[m]->nbar * this->sumw[m] * inv_vc);
+      make_tables(sys[m]->sinv, pre, c0, vc.data() + (size_t)m * TAB, vm.data() + (size_t)m * TAB);
+      std::copy(sys[m]->sinv.begin(), sys[m]->sinv.end(), vs.begin() + (size_t)m * TAB);
     }
-    rel = rel_new;
+    WF_TRY(upload_tables<float>(c, key + "tc", vc, &ct, st));
+    WF_TRY(upload_tables<float>(c, key + "tm", vm, &mt, st));
+    WF_TRY(upload_tables<double>(c, key + "ts", vs, &stab, st));
+    h.assign(nb, CgScal{});
+    for (int m = 0; m < nb; ++m) h[m].nbar = sys[m]->nbar;
+    WF_TRY(this->push_scalars(st));
+    c.launch("make_D", 12.0 * V * nb, st, [&] { k_make_D<float><<<dim3(152 * 4, nb), 256, 0, st>>>(W, D, sc, inv_vc, V); });
+    // x = 0 (accumulated in S), res = b
+    WF_CUDA(cudaMemsetAsync(S, 0, nb * V * sizeof(double), st));
+    WF_CUDA(cudaMemcpyAsync(RES, B, nb * V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    rel.assign(nb, 1.0);
+    state.assign(nb, 0);
+    outer.assign(nb, 0);
+    iters.assign(nb, 0);
+    for (int m = 0; m < nb; ++m)
+      if (bb0[m] == 0.0) {
+        state[m] = 1;
+        rel[m] = 0.0;
+        if (info[m]) *info[m] = wf_solve_info{0, 0, 0.0, sys[m]->nbar, WF_OK};
+      }
+    phase = 0;
+    return WF_OK;
   }
-  if (info) {
-    info->iters = total_iters;
-    info->outer_iters = outer;
-    info->rel_residual = rel;
-    info->nbar = a.nbar;
-    info->status = status;
+  wf_status enqueue(Ctx& c, cudaStream_t st) override {
+    const Bat bf = SF::bat();
+    if (phase == 0) {
+      const double inner_tol_def = 1e-4;
+      for (int m = 0; m < nb; ++m) {
+        CgScal z{};
+        z.nbar = sys[m]->nbar;
+        if (state[m]) {
+          z.done = 4;
+        } else {
+          const double itol = sys[m]->opts.inner_tol > 0.0 ? sys[m]->opts.inner_tol : inner_tol_def;
+          const double target = std::max(itol, 0.3 * sys[m]->opts.tol / rel[m]);
+          z.tol2 = target * target;
+          z.bb = rel[m] * rel[m] * bb0[m];
+          z.max_iter = std::max(1, sys[m]->opts.max_iter - iters[m]);
+          outer[m] += 1;
+        }
+        h[m] = z;
+      }
+      WF_TRY(this->push_scalars(st));
+      const size_t SPEC = SF::SPEC;
+      SF::zfwd(c, nb, RES, T, tw, part, false, nullptr, st);
+      SF::ypass(c, nb, T, tw, nullptr, -1, st);
+      SF::template xmul<true, false, true>(c, nb, T, rh, ct, tw, part, nullptr, st);
+      c.launch("fin", 0, st, [&] { k_fin_init<<<nb, 1024, 0, st>>>(part, SF::GXY, sc, bf); });
+      WF_CUDA(cudaMemsetAsync(P0, 0, nb * SPEC * sizeof(float2), st));
+      WF_CUDA(cudaMemsetAsync(P1, 0, nb * SPEC * sizeof(float2), st));
+      WF_CUDA(cudaMemsetAsync(xh, 0, nb * SPEC * sizeof(float2), st));
+      phase = 1;
+    }
+    if (phase == 1) {
+      for (int i = 0; i < check_every<N>(); ++i)
+        SF::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, st);
+    } else if (phase == 2) {
+      c.launch("axpy", 3 * SF::BS * nb, st,
+               [&] { k_axpy_final<<<dim3(152 * 4, nb), 256, 0, st>>>(xh, P0, P1, SF::SPEC, sc, bf); });
+      // x += C e (FP32 transform, FP64 accumulation) for the systems that ran
+      SF::template xmul<false, true, false>(c, nb, xh, T, ct, tw, part, nullptr, st);
+      SF::ypass(c, nb, T, tw, nullptr, +1, st);
+      SF::template zinv<ZI_ACCUM>(c, nb, T, S, nullptr, nullptr, nullptr, inv_vc, tw, part, sc, st);
+      // FP64 residual res = b - A x
+      SD::zfwd(c, nb, S, T64, tw, part, false, nullptr, st);
+      SD::ypass(c, nb, T64, tw, nullptr, -1, st);
+      SD::template xmul<true, true, false>(c, nb, T64, T64b, stab, tw, part, nullptr, st);
+      SD::ypass(c, nb, T64b, tw, nullptr, +1, st);
+      SD::template zinv<ZI_RESID>(c, nb, T64b, RES, S, W, B, inv_vc, tw, part, sc, st);
+      const Bat bd = SD::bat();
+      c.launch("fin", 0, st, [&] { k_fin_sum<<<nb, 1024, 0, st>>>(part, SD::GZ, 0, sc, bd); });
+    }
+    WF_CUDA(cudaGetLastError());
+    return this->pull_scalars(st);
   }
-  return status;
-}
+  wf_status advance(Ctx&) override {
+    this->read_scalars();
+    if (phase == 1) {
+      if (this->all_done()) phase = 2;
+      return WF_OK;
+    }
+    if (phase == 2) {
+      bool any = false;
+      for (int m = 0; m < nb; ++m) {
+        if (state[m]) continue;
+        iters[m] += h[m].iter;
+        const double rn = std::sqrt(h[m].aux[0] / bb0[m]);
+        const bool broke = h[m].done == 3 && !(rn < rel[m]);
+        rel[m] = rn;
+        wf_status st = WF_OK;
+        bool fin = true;
+        if (rel[m] <= sys[m]->opts.tol) st = WF_OK;
+        else if (broke) st = WF_ERR_BREAKDOWN;
+        else if (outer[m] >= 12 || iters[m] >= sys[m]->opts.max_iter) st = WF_ERR_NOT_CONVERGED;
+        else fin = false;
+        if (fin) {
+          state[m] = 1;
+          if (info[m]) *info[m] = wf_solve_info{iters[m], outer[m], rel[m], sys[m]->nbar, st};
+        } else {
+          any = true;
+        }
+      }
+      phase = any ? 0 : 9;
+    }
+    return WF_OK;
+  }
+  bool done() const override { return phase == 9; }
+  wf_status finish(Ctx&, cudaStream_t st) override {
+    for (int m = 0; m < nb; ++m)
+      WF_CUDA(cudaMemcpyAsync(sys[m]->s_out, S + m * SF::V, SF::V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return WF_OK;
+  }
+};
 
 template <int N>
-wf_status solve_sized(Ctx& c, SolveArgs& a, wf_solve_info* info, cudaStream_t st) {
-  if (a.opts.prec == WF_MIXED) return solve_mixed<N>(c, a, info, st);
-  return solve_fp64<double, N>(c, a, info, st);
+Group* make_group(int prec) {
+  if (prec == WF_MIXED) return new GroupMixed<N>();
+  return new GroupFP64<FP64Arith, N>();
 }
 
 }  // namespace wf

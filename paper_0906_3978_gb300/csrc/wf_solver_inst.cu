@@ -7,5 +7,5 @@
 #endif
 
 namespace wf {
-template wf_status solve_sized<WF_N>(Ctx&, SolveArgs&, wf_solve_info*, cudaStream_t);
+template Group* make_group<WF_N>(int prec);
 }

@@ -20,12 +20,15 @@
 //   z turn      packed -> C2R -> multiply by a real diagonal -> R2C -> packed (one z line)
 //   z fwd/inv   real rows <-> packed spectrum rows, with epilogues
 #pragma once
+#include <type_traits>
+
 #include "wf_fft.cuh"
 
 namespace wf {
 
-// Device-resident CG scalars.  Written only by the single-CTA finisher kernels.
-struct CgScal {
+// Device-resident CG scalars of one system.  Written by the single-CTA finisher kernels (and by
+// the host between solves).  A batch keeps one per system, indexed by blockIdx.z.
+struct __align__(16) CgScal {
   double rr;          // <r, r> of the preconditioned residual
   double pq;          // <p, A p>
   double alpha;       // rr / pq of the last iteration
@@ -35,11 +38,22 @@ struct CgScal {
   double rc2;         // upper estimate of the canonical ||b - A s||^2 (real space)
   double tol2;        // stop when rc2 <= tol2 * bb
   double rr_stop;     // inner solves: stop when rc2 <= rr_stop (absolute)
+  double nbar;        // mean density of this system
   double aux[4];
-  int iter;
+  int iter;           // iterations since the solve began
   int max_iter;
-  int done;           // 1: converged (estimate); 2: iteration cap; 3: breakdown
+  int done;           // 0 running; 1 converged (estimate); 2 iteration cap; 3 breakdown; 4 idle
   int status;
+  int lit;            // iterations since the last reset of p: p_old = P[lit & 1]
+  int pad[3];
+};
+
+// Distances between consecutive systems of a batch (elements of each array type).
+struct Bat {
+  size_t spec;  // complex elements of a spectrum
+  size_t real;  // elements of a real-space field
+  int tab;      // entries of a Fourier table
+  int part;     // partial sums per system
 };
 
 template <class R> constexpr int tile_lines() { return 128 / (int)sizeof(cx<R>); }
@@ -67,34 +81,105 @@ WF_D void load_tw(cx<R>* tw, const double2* tab, int tid, int nt) {
 }
 
 // ------------------------------------------------------------------------------------------
-// y pass: complex FFT along y of every (x, kz) line; in place.
-// grid (N/2 / NL, N), block NL * TPL.
+// Geometry of the x / y passes: a tile is M = N rows (the transform axis) by NL consecutive
+// kz columns; each line is transformed by TPL threads holding E elements each, so the CTA
+// has exactly NL * TPL threads.  Tiles move between global and shared memory as 16-byte
+// vectors (VW elements), PER vectors per thread, fully unrolled so every load of a thread is
+// in flight at once.  The shared tile has a pad column (LD = NL + 1) that also holds the
+// partner line of column 0.
 // ------------------------------------------------------------------------------------------
-template <class R, int N, int DIR>
-__global__ void __launch_bounds__(xy_lines<R, N>() * tpl<R, N>())
-k_ypass(typename Store<R>::T* __restrict__ spec, const double2* __restrict__ twtab,
-        const CgScal* __restrict__ sc) {
+template <class R, int N>
+struct XYG {
   using ST = typename Store<R>::T;
-  constexpr int M = N, NH = N / 2, NL = xy_lines<R, N>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = NL * TPL;
+  static constexpr int M = N, NH = N / 2;
+  static constexpr int NL = xy_lines<R, N>();
+  static constexpr int E = sizeof(cx<R>) == 8 ? 32 : 16;
+  static constexpr int TPL = M / E >= 1 ? M / E : 1;
+  static constexpr int NT = NL * TPL;
+  static constexpr int LD = NL + 1;
+  static constexpr int VW = (sizeof(ST) == 8 && NL % 2 == 0) ? 2 : 1;
+  static constexpr int NV = NL / VW;
+  static constexpr int NVEC = M * NV;
+  static constexpr int PER = (NVEC + NT - 1) / NT;
+  static constexpr bool EVEN = NVEC % NT == 0;
+  using VT = typename std::conditional<VW == 2, float4, ST>::type;
+  static constexpr size_t SMEM = (size_t)(M * LD + M) * sizeof(cx<R>);
+};
+
+template <class G, class R>
+WF_D void vec_to_tile(cx<R>* tile, int i, int c0, const typename G::VT& v) {
+  if constexpr (G::VW == 2) {
+    const float4 f = *reinterpret_cast<const float4*>(&v);
+    tile[i * G::LD + c0] = cx<R>{RT<R>::from_f(f.x), RT<R>::from_f(f.y)};
+    tile[i * G::LD + c0 + 1] = cx<R>{RT<R>::from_f(f.z), RT<R>::from_f(f.w)};
+  } else {
+    tile[i * G::LD + c0] = ld_c<R>(&v);
+  }
+}
+template <class G, class R>
+WF_D typename G::VT tile_to_vec(const cx<R>* tile, int i, int c0) {
+  typename G::VT v;
+  if constexpr (G::VW == 2) {
+    const cx<R> a = tile[i * G::LD + c0], b = tile[i * G::LD + c0 + 1];
+    *reinterpret_cast<float4*>(&v) = make_float4(RT<R>::to_f(a.x), RT<R>::to_f(a.y), RT<R>::to_f(b.x), RT<R>::to_f(b.y));
+  } else {
+    st_c(&v, tile[i * G::LD + c0]);
+  }
+  return v;
+}
+
+// Load / store a whole tile whose element (i, l) is at g[i * rowstride + l].
+template <class G, class R>
+WF_D void tile_load(cx<R>* tile, const typename G::ST* g, size_t rowstride, int tid) {
+  using VT = typename G::VT;
+  VT buf[G::PER];
+#pragma unroll
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (G::EVEN || idx < G::NVEC) {
+      const int i = idx / G::NV, v = idx % G::NV;
+      buf[k] = *reinterpret_cast<const VT*>(g + (size_t)i * rowstride + v * G::VW);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (G::EVEN || idx < G::NVEC) vec_to_tile<G>(tile, idx / G::NV, (idx % G::NV) * G::VW, buf[k]);
+  }
+}
+template <class G, class R>
+WF_D void tile_store(const cx<R>* tile, typename G::ST* g, size_t rowstride, int tid) {
+  using VT = typename G::VT;
+#pragma unroll
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (G::EVEN || idx < G::NVEC) {
+      const int i = idx / G::NV, v = idx % G::NV;
+      *reinterpret_cast<VT*>(g + (size_t)i * rowstride + v * G::VW) = tile_to_vec<G>(tile, i, v * G::VW);
+    }
+  }
+}
+
+// y pass: complex FFT along y of every (x, kz) line; in place.  grid (N/2 / NL, N).
+template <class R, int N, int DIR>
+__global__ void __launch_bounds__(XYG<R, N>::NT)
+k_ypass(typename Store<R>::T* __restrict__ spec, const double2* __restrict__ twtab,
+        const CgScal* __restrict__ sc, Bat bt) {
+  using G = XYG<R, N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;
-  if (sc && sc->done) return;
+  cx<R>* tw = tile + G::M * G::LD;
+  const int z = blockIdx.z;
+  if (sc && sc[z].done) return;
+  spec += z * bt.spec;
   const int tid = threadIdx.x;
-  const int kz0 = blockIdx.x * NL, x = blockIdx.y;
-  load_tw<R, M, 2 * N>(tw, twtab, tid, NT);
-  ST* base = spec + (size_t)x * N * NH + kz0;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    tile[i * LD + l] = ld_c<R>(base + (size_t)i * NH + l);
-  }
+  const int kz0 = blockIdx.x * G::NL, x = blockIdx.y;
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
+  typename G::ST* base = spec + (size_t)x * N * G::NH + kz0;
+  tile_load<G>(tile, base, G::NH, tid);
   __syncthreads();
-  fft_line<R, M, TPL, LD, DIR>(tile + tid % NL, tid / NL, tw);
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    st_c(base + (size_t)i * NH + l, tile[i * LD + l]);
-  }
+  fft_line<R, G::M, G::TPL, G::LD, DIR>(tile + tid % G::NL, tid / G::NL, tw);
+  tile_store<G>(tile, base, G::NH, tid);
 }
 
 // Apply the packed-column multiplier pair to column 0 of a tile (slot 0) using the partner
@@ -117,142 +202,207 @@ WF_D void combine_col0(cx<R>* tile, int ky_s, const TAB* tab, int tid, int nt) {
   __syncthreads();
 }
 
+// Multiply every tile element except column 0 of the kz0 = 0 tile by tab[n2].
+template <class G, class R, class TAB>
+WF_D void tile_mul(cx<R>* tile, int kz0, int ky_s, const TAB* tab, int tid) {
+  for (int idx = tid; idx < G::M * G::NL; idx += G::NT) {
+    const int i = idx / G::NL, l = idx % G::NL, kz = kz0 + l;
+    if (kz == 0) continue;
+    const int kxs = sfreq(i, G::M);
+    tile[i * G::LD + l] = scale(tile[i * G::LD + l], RT<R>::c((double)tab[kxs * kxs + ky_s * ky_s + kz * kz]));
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // CG x pass 1 (start of A p):  p_new = r + beta p_old;  x += alpha_prev p_old;
-//                              T = IFFT_x( c (.) p_new )
-// grid (N/2 / NL, N), block (NL + 1) * TPL; slot NL holds the partner line (ky' = -ky) of
-// column 0 when kz0 == 0.
+//                              T = IFFT_x( c (.) p_new )                grid (N/2 / NL, N)
 // ------------------------------------------------------------------------------------------
 template <class R, int N>
-__global__ void __launch_bounds__((xy_lines<R, N>() + 1) * tpl<R, N>())
-k_cg_xinv(const typename Store<R>::T* __restrict__ r, const typename Store<R>::T* __restrict__ pold,
-          typename Store<R>::T* __restrict__ pnew, typename Store<R>::T* __restrict__ x,
-          typename Store<R>::T* __restrict__ T, const typename Store<R>::S* __restrict__ ctab,
-          const double2* __restrict__ twtab, const CgScal* __restrict__ sc) {
+__global__ void __launch_bounds__(XYG<R, N>::NT)
+k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, typename Store<R>::T* P1,
+          typename Store<R>::T* __restrict__ x, typename Store<R>::T* __restrict__ T,
+          const typename Store<R>::S* __restrict__ ctab, const double2* __restrict__ twtab,
+          const CgScal* __restrict__ sc, Bat bt) {
+  using G = XYG<R, N>;
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
-  constexpr int M = N, NH = N / 2, NL = xy_lines<R, N>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = (NL + 1) * TPL;
+  using VT = typename G::VT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;
+  cx<R>* tw = tile + G::M * G::LD;
+  const int z = blockIdx.z;
+  sc += z;
   if (sc->done) return;
+  // p_old / p_new alternate between P0 and P1 with this system's iteration count
+  const ST* __restrict__ pold = ((sc->lit & 1) ? P1 : P0) + z * bt.spec;
+  ST* __restrict__ pnew = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;
+  r += z * bt.spec;
+  x += z * bt.spec;
+  T += z * bt.spec;
+  ctab += z * bt.tab;
   const int tid = threadIdx.x;
-  const int kz0 = blockIdx.x * NL, ky = blockIdx.y;
+  const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
   const int ky_s = sfreq(ky, N);
   const SS beta = (SS)sc->beta, alpha_prev = (SS)sc->alpha_prev;
-  load_tw<R, M, 2 * N>(tw, twtab, tid, NT);
-  const size_t rowstride = (size_t)N * NH;
-  const size_t base = (size_t)ky * NH + kz0;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    const size_t e = base + (size_t)i * rowstride + l;
-    const ST rv = r[e], po = pold[e];
-    ST pn;
-    pn.x = rv.x + beta * po.x;
-    pn.y = rv.y + beta * po.y;
-    pnew[e] = pn;
-    ST xv = x[e];
-    xv.x += alpha_prev * po.x;
-    xv.y += alpha_prev * po.y;
-    x[e] = xv;
-    tile[i * LD + l] = ld_c<R>(&pn);
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
+  const size_t rowstride = (size_t)N * G::NH;
+  const size_t base = (size_t)ky * G::NH + kz0;
+  constexpr int CH = 4;  // vectors per thread whose three loads are in flight together
+  constexpr int SPV = sizeof(VT) / sizeof(SS);
+#pragma unroll
+  for (int k0 = 0; k0 < G::PER; k0 += CH) {
+    VT rv[CH], pv[CH], xv[CH];
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (G::EVEN || idx < G::NVEC) {
+        const size_t e = base + (size_t)(idx / G::NV) * rowstride + (idx % G::NV) * G::VW;
+        rv[k] = *reinterpret_cast<const VT*>(r + e);
+        pv[k] = *reinterpret_cast<const VT*>(pold + e);
+        xv[k] = *reinterpret_cast<const VT*>(x + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (G::EVEN || idx < G::NVEC) {
+        const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+        const size_t e = base + (size_t)i * rowstride + c0;
+        SS* rs = reinterpret_cast<SS*>(&rv[k]);
+        SS* ps = reinterpret_cast<SS*>(&pv[k]);
+        SS* xs = reinterpret_cast<SS*>(&xv[k]);
+        VT nv;
+        SS* ns = reinterpret_cast<SS*>(&nv);
+#pragma unroll
+        for (int q = 0; q < SPV; ++q) {
+          ns[q] = rs[q] + beta * ps[q];
+          xs[q] = xs[q] + alpha_prev * ps[q];
+        }
+        *reinterpret_cast<VT*>(pnew + e) = nv;
+        *reinterpret_cast<VT*>(x + e) = xv[k];
+        vec_to_tile<G>(tile, i, c0, nv);
+      }
+    }
   }
   if (kz0 == 0) {  // partner line of column 0: p_new at (kx, -ky, 0), recomputed from inputs
-    const size_t pb = (size_t)((N - ky) % N) * NH;
-    for (int i = tid; i < M; i += NT) {
+    const size_t pb = (size_t)((N - ky) % N) * G::NH;
+    for (int i = tid; i < G::M; i += G::NT) {
       const size_t e = pb + (size_t)i * rowstride;
       const ST rv = r[e], po = pold[e];
       ST pn;
       pn.x = rv.x + beta * po.x;
       pn.y = rv.y + beta * po.y;
-      tile[i * LD + NL] = ld_c<R>(&pn);
+      tile[i * G::LD + G::NL] = ld_c<R>(&pn);
     }
   }
   __syncthreads();
-  // multiplier c(k)
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    if (kz0 + l == 0) continue;
-    const int kxs = sfreq(i, N), kz = kz0 + l;
-    tile[i * LD + l] = scale(tile[i * LD + l], RT<R>::c((double)ctab[kxs * kxs + ky_s * ky_s + kz * kz]));
-  }
-  if (kz0 == 0) combine_col0<R, N, LD, NL>(tile, ky_s, ctab, tid, NT);
+  tile_mul<G>(tile, kz0, ky_s, ctab, tid);
+  if (kz0 == 0) combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
   else __syncthreads();
-  const int l = tid % (NL + 1), t = tid / (NL + 1);
-  fft_line<R, M, TPL, LD, +1>(tile + l, t, tw);
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, ll = idx % NL;
-    st_c(T + base + (size_t)i * rowstride + ll, tile[i * LD + ll]);
-  }
+  fft_line<R, G::M, G::TPL, G::LD, +1>(tile + tid % G::NL, tid / G::NL, tw);
+  tile_store<G>(tile, T + base, rowstride, tid);
 }
 
 // ------------------------------------------------------------------------------------------
 // CG x pass 2 (end of A p):  T^ = FFT_x(T);  q = m (.) p + c (.) T^;  partial <p, q>
+// UNIT_M: m = 1 at every k != 0 (the preconditioned system), so the m table is not read there.
 // ------------------------------------------------------------------------------------------
-template <class R, int N>
-__global__ void __launch_bounds__((xy_lines<R, N>() + 1) * tpl<R, N>())
-k_cg_xfwd(const typename Store<R>::T* __restrict__ T, const typename Store<R>::T* __restrict__ p,
-          typename Store<R>::T* __restrict__ q, const typename Store<R>::S* __restrict__ ctab,
-          const typename Store<R>::S* __restrict__ mtab, const double2* __restrict__ twtab,
-          double* __restrict__ partials, const CgScal* __restrict__ sc) {
+template <class R, int N, bool UNIT_M>
+__global__ void __launch_bounds__(XYG<R, N>::NT)
+k_cg_xfwd(const typename Store<R>::T* __restrict__ T, const typename Store<R>::T* P0,
+          const typename Store<R>::T* P1, typename Store<R>::T* __restrict__ q,
+          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
+          const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+          Bat bt) {
+  using G = XYG<R, N>;
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
-  constexpr int M = N, NH = N / 2, NL = xy_lines<R, N>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = (NL + 1) * TPL;
+  using VT = typename G::VT;
+  constexpr int NH = G::NH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;
+  cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
+  const int z = blockIdx.z;
+  sc += z;
   if (sc->done) return;
+  const ST* __restrict__ p = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;  // this iteration's p_new
+  T += z * bt.spec;
+  q += z * bt.spec;
+  ctab += z * bt.tab;
+  mtab += z * bt.tab;
+  partials += z * bt.part;
   const int tid = threadIdx.x;
-  const int kz0 = blockIdx.x * NL, ky = blockIdx.y;
+  const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
   const int ky_s = sfreq(ky, N);
   const int pky = (N - ky) % N;
-  load_tw<R, M, 2 * N>(tw, twtab, tid, NT);
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
   const size_t rowstride = (size_t)N * NH;
   const size_t base = (size_t)ky * NH + kz0;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    tile[i * LD + l] = ld_c<R>(T + base + (size_t)i * rowstride + l);
-  }
+  tile_load<G>(tile, T + base, rowstride, tid);
   if (kz0 == 0)
-    for (int i = tid; i < M; i += NT) tile[i * LD + NL] = ld_c<R>(T + (size_t)pky * NH + (size_t)i * rowstride);
+    for (int i = tid; i < G::M; i += G::NT) tile[i * G::LD + G::NL] = ld_c<R>(T + (size_t)pky * NH + (size_t)i * rowstride);
   __syncthreads();
-  {
-    const int l = tid % (NL + 1), t = tid / (NL + 1);
-    fft_line<R, M, TPL, LD, -1>(tile + l, t, tw);
+  fft_line<R, G::M, G::TPL, G::LD, -1>(tile + tid % G::NL, tid / G::NL, tw);
+  if (kz0 == 0) {  // transform the partner line too, then combine column 0
+    fft_line<R, G::M, G::TPL, G::LD, -1>(tile + G::NL, tid / G::NL, tw, tid % G::NL == 0);
+    combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
   }
-  if (kz0 == 0) combine_col0<R, N, LD, NL>(tile, ky_s, ctab, tid, NT);
   typename AccFor<SS>::T acc;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    const int kxs = sfreq(i, N), kz = kz0 + l;
-    const size_t e = base + (size_t)i * rowstride + l;
-    const ST pv = p[e];
-    cx<R> t = tile[i * LD + l];
-    ST qv;
-    if (kz == 0) {
-      // packed column: m-term combined with the partner element p(-kx, -ky, 0)
-      const int n2 = kxs * kxs + ky_s * ky_s;
-      const double m0 = (double)mtab[n2], mN = (double)mtab[n2 + NH * NH];
-      const ST pp = p[(size_t)((N - i) % N) * rowstride + (size_t)pky * NH];
-      const double a = 0.5 * (m0 + mN), b = 0.5 * (m0 - mN);
-      const double mx = a * (double)pv.x + b * (double)pp.x;
-      const double my = a * (double)pv.y - b * (double)pp.y;
-      qv.x = (SS)(mx + RT<R>::to_d(t.x));
-      qv.y = (SS)(my + RT<R>::to_d(t.y));
-    } else {
-      const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
-      const cx<R> ct = scale(t, RT<R>::c((double)ctab[n2]));
-      const SS m = mtab[n2];
-      qv.x = (SS)(m * pv.x + (SS)RT<R>::to_d(ct.x));
-      qv.y = (SS)(m * pv.y + (SS)RT<R>::to_d(ct.y));
+  // epilogue in chunks: the p vectors and table entries of a chunk are loaded together
+  constexpr int CH = 8;
+#pragma unroll
+  for (int k0 = 0; k0 < G::PER; k0 += CH) {
+    VT pv[CH];
+    SS cv[CH][G::VW], mv[CH][G::VW];
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (!(G::EVEN || idx < G::NVEC)) continue;
+      const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+      const int kxs = sfreq(i, N);
+      pv[k] = *reinterpret_cast<const VT*>(p + base + (size_t)i * rowstride + c0);
+#pragma unroll
+      for (int u = 0; u < G::VW; ++u) {
+        const int kz = kz0 + c0 + u;
+        const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
+        cv[k][u] = ctab[n2];
+        mv[k][u] = UNIT_M ? (SS)1 : mtab[n2];
+      }
     }
-    q[e] = qv;
-    const SS wgt = kz == 0 ? (SS)1 : (SS)2;
-    acc.add_prod(wgt * pv.x, qv.x);
-    acc.add_prod(wgt * pv.y, qv.y);
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (!(G::EVEN || idx < G::NVEC)) continue;
+      const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+      const int kxs = sfreq(i, N);
+      const size_t e = base + (size_t)i * rowstride + c0;
+      const SS* ps = reinterpret_cast<const SS*>(&pv[k]);
+      VT qv;
+      SS* qs = reinterpret_cast<SS*>(&qv);
+#pragma unroll
+      for (int u = 0; u < G::VW; ++u) {
+        const int kz = kz0 + c0 + u;
+        const cx<R> t = tile[i * G::LD + c0 + u];
+        if (kz == 0) {
+          // packed column: m-term combined with the partner element p(-kx, -ky, 0)
+          const int n2 = kxs * kxs + ky_s * ky_s;
+          const double m0 = (double)mtab[n2], mN = (double)mtab[n2 + NH * NH];
+          const ST pp = p[(size_t)((N - i) % N) * rowstride + (size_t)pky * NH];
+          const double a = 0.5 * (m0 + mN), b = 0.5 * (m0 - mN);
+          qs[2 * u] = (SS)(a * (double)ps[2 * u] + b * (double)pp.x + RT<R>::to_d(t.x));
+          qs[2 * u + 1] = (SS)(a * (double)ps[2 * u + 1] - b * (double)pp.y + RT<R>::to_d(t.y));
+        } else {
+          const cx<R> ct = scale(t, RT<R>::c((double)cv[k][u]));
+          qs[2 * u] = mv[k][u] * ps[2 * u] + (SS)RT<R>::to_d(ct.x);
+          qs[2 * u + 1] = mv[k][u] * ps[2 * u + 1] + (SS)RT<R>::to_d(ct.y);
+        }
+        const SS wgt = kz == 0 ? (SS)1 : (SS)2;
+        acc.add_prod(wgt * ps[2 * u], qs[2 * u]);
+        acc.add_prod(wgt * ps[2 * u + 1], qs[2 * u + 1]);
+      }
+      *reinterpret_cast<VT*>(q + e) = qv;
+    }
   }
   const double s = block_sum(acc.get(), red);
   if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
@@ -263,56 +413,54 @@ k_cg_xfwd(const typename Store<R>::T* __restrict__ T, const typename Store<R>::T
 // in != out (the partner line of column 0 is read from `in`).
 // ------------------------------------------------------------------------------------------
 template <class R, int N, bool FWD, bool INV, bool DOT>
-__global__ void __launch_bounds__((xy_lines<R, N>() + 1) * tpl<R, N>())
+__global__ void __launch_bounds__(XYG<R, N>::NT)
 k_xmul(const typename Store<R>::T* __restrict__ in, typename Store<R>::T* __restrict__ out,
        const typename Store<R>::S* __restrict__ tab, const double2* __restrict__ twtab,
-       double* __restrict__ partials, const CgScal* __restrict__ sc) {
+       double* __restrict__ partials, const CgScal* __restrict__ sc, Bat bt) {
+  using G = XYG<R, N>;
   using SS = typename Store<R>::S;
-  constexpr int M = N, NH = N / 2, NL = xy_lines<R, N>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = (NL + 1) * TPL;
+  constexpr int NH = G::NH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;
+  cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
-  if (sc && sc->done) return;
+  const int z = blockIdx.z;
+  if (sc && sc[z].done) return;
+  in += z * bt.spec;
+  out += z * bt.spec;
+  tab += z * bt.tab;
+  partials += z * bt.part;
   const int tid = threadIdx.x;
-  const int kz0 = blockIdx.x * NL, ky = blockIdx.y;
+  const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
   const int ky_s = sfreq(ky, N);
   const int pky = (N - ky) % N;
-  load_tw<R, M, 2 * N>(tw, twtab, tid, NT);
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
   const size_t rowstride = (size_t)N * NH;
   const size_t base = (size_t)ky * NH + kz0;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, l = idx % NL;
-    tile[i * LD + l] = ld_c<R>(in + base + (size_t)i * rowstride + l);
-  }
+  tile_load<G>(tile, in + base, rowstride, tid);
   if (kz0 == 0)
-    for (int i = tid; i < M; i += NT) tile[i * LD + NL] = ld_c<R>(in + (size_t)pky * NH + (size_t)i * rowstride);
+    for (int i = tid; i < G::M; i += G::NT) tile[i * G::LD + G::NL] = ld_c<R>(in + (size_t)pky * NH + (size_t)i * rowstride);
   __syncthreads();
-  const int l = tid % (NL + 1), t = tid / (NL + 1);
-  if constexpr (FWD) fft_line<R, M, TPL, LD, -1>(tile + l, t, tw);
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, ll = idx % NL;
-    if (kz0 + ll == 0) continue;
-    const int kxs = sfreq(i, N), kz = kz0 + ll;
-    tile[i * LD + ll] = scale(tile[i * LD + ll], RT<R>::c((double)tab[kxs * kxs + ky_s * ky_s + kz * kz]));
+  const int l = tid % G::NL, t = tid / G::NL;
+  if constexpr (FWD) {
+    fft_line<R, G::M, G::TPL, G::LD, -1>(tile + l, t, tw);
+    if (kz0 == 0) fft_line<R, G::M, G::TPL, G::LD, -1>(tile + G::NL, t, tw, l == 0);
   }
-  if (kz0 == 0) combine_col0<R, N, LD, NL>(tile, ky_s, tab, tid, NT);
+  tile_mul<G>(tile, kz0, ky_s, tab, tid);
+  if (kz0 == 0) combine_col0<R, N, G::LD, G::NL>(tile, ky_s, tab, tid, G::NT);
   else __syncthreads();
-  if constexpr (INV) fft_line<R, M, TPL, LD, +1>(tile + l, t, tw);
-  typename AccFor<SS>::T acc;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int i = idx / NL, ll = idx % NL;
-    const cx<R> v = tile[i * LD + ll];
-    st_c(out + base + (size_t)i * rowstride + ll, v);
-    if constexpr (DOT) {
+  if constexpr (INV) fft_line<R, G::M, G::TPL, G::LD, +1>(tile + l, t, tw);
+  tile_store<G>(tile, out + base, rowstride, tid);
+  if constexpr (DOT) {
+    typename AccFor<SS>::T acc;
+    for (int idx = tid; idx < G::M * G::NL; idx += G::NT) {
+      const int i = idx / G::NL, ll = idx % G::NL;
+      const cx<R> v = tile[i * G::LD + ll];
       const SS wgt = (kz0 + ll == 0) ? (SS)1 : (SS)2;
       const SS vx = (SS)RT<R>::to_d(v.x), vy = (SS)RT<R>::to_d(v.y);
       acc.add_prod(wgt * vx, vx);
       acc.add_prod(wgt * vy, vy);
     }
-  }
-  if constexpr (DOT) {
     const double s = block_sum(acc.get(), red);
     if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
@@ -366,89 +514,177 @@ WF_D void r2c_post(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
 }
 
 // ------------------------------------------------------------------------------------------
-// z turn (middle of A p): each (x, y) line: packed -> real (C2R), times D(x, y, z), -> packed.
-// D = nbar w / V_c carries the 1/V_c of the inverse transform.  grid (N*N / NL), block NL*TPL.
+// Geometry of the z passes: NL consecutive rows (x, y) per CTA, each a line of H = N/2
+// complex values; TPL threads per line with E elements each.  Rows are contiguous in memory,
+// so tiles move as 16-byte vectors along the row (VW elements each).
 // ------------------------------------------------------------------------------------------
 template <class R, int N>
-__global__ void __launch_bounds__(tile_lines<R>() * tpl<R, N / 2>())
-k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
-        const double2* __restrict__ twtab, const CgScal* __restrict__ sc) {
+struct ZG {
   using ST = typename Store<R>::T;
-  using SS = typename Store<R>::S;
-  constexpr int H = N / 2, M = H, NL = tile_lines<R>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = NL * TPL;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;  // 2N entries
-  if (sc && sc->done) return;
-  const int tid = threadIdx.x;
-  const size_t row0 = (size_t)blockIdx.x * NL;
-  for (int e = tid; e < 2 * N; e += NT) tw[e] = ld_c<R>(twtab + e);
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int l = idx / M, i = idx % M;
-    tile[i * LD + l] = ld_c<R>(spec + (row0 + l) * H + i);
+  static constexpr int H = N / 2, M = H;
+  static constexpr int NL = tile_lines<R>();
+  static constexpr int E = sizeof(cx<R>) == 8 ? 32 : 16;
+  static constexpr int TPL = M / E >= 1 ? M / E : 1;
+  static constexpr int NT = NL * TPL;
+  static constexpr int LD = NL + 1;
+  static constexpr int VW = (sizeof(ST) == 8 && M % 2 == 0) ? 2 : 1;
+  static constexpr int NV = M / VW;
+  static constexpr int NVEC = NL * NV;
+  static constexpr int PER = (NVEC + NT - 1) / NT;
+  static constexpr bool EVEN = NVEC % NT == 0;
+  using VT = typename std::conditional<VW == 2, float4, ST>::type;
+  static constexpr size_t SMEM = (size_t)(M * LD + 2 * N) * sizeof(cx<R>);
+};
+
+// rows [row0, row0 + NL) of a packed spectrum (H complex per row) <-> tile
+template <class G, class R>
+WF_D void zrows_load(cx<R>* tile, const typename G::ST* g, size_t row0, int tid) {
+  using VT = typename G::VT;
+  VT buf[G::PER];
+#pragma unroll
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (G::EVEN || idx < G::NVEC)
+      buf[k] = *reinterpret_cast<const VT*>(g + (row0 + idx / G::NV) * G::H + (idx % G::NV) * G::VW);
   }
-  __syncthreads();
-  const int l = tid % NL, t = tid / NL;
-  c2r_prep<R, N, LD>(tile + l, t, TPL, tw);
-  __syncthreads();
-  fft_line<R, M, TPL, LD, +1, 4>(tile + l, t, tw);
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int ll = idx / M, i = idx % M;
-    const ST dv = *reinterpret_cast<const ST*>(D + (row0 + ll) * N + 2 * i);
-    cx<R> v = tile[i * LD + ll];
-    v.x = v.x * RT<R>::c((double)dv.x);
-    v.y = v.y * RT<R>::c((double)dv.y);
-    tile[i * LD + ll] = v;
+#pragma unroll
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (!(G::EVEN || idx < G::NVEC)) continue;
+    const int l = idx / G::NV, i = (idx % G::NV) * G::VW;
+    if constexpr (G::VW == 2) {
+      const float4 f = *reinterpret_cast<const float4*>(&buf[k]);
+      tile[i * G::LD + l] = cx<R>{RT<R>::from_f(f.x), RT<R>::from_f(f.y)};
+      tile[(i + 1) * G::LD + l] = cx<R>{RT<R>::from_f(f.z), RT<R>::from_f(f.w)};
+    } else {
+      tile[i * G::LD + l] = ld_c<R>(&buf[k]);
+    }
   }
-  __syncthreads();
-  fft_line<R, M, TPL, LD, -1, 4>(tile + l, t, tw);
-  r2c_post<R, N, LD>(tile + l, t, TPL, tw);
-  __syncthreads();
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int ll = idx / M, i = idx % M;
-    st_c(spec + (row0 + ll) * H + i, tile[i * LD + ll]);
+}
+template <class G, class R>
+WF_D void zrows_store(const cx<R>* tile, typename G::ST* g, size_t row0, int tid) {
+  using VT = typename G::VT;
+#pragma unroll
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (!(G::EVEN || idx < G::NVEC)) continue;
+    const int l = idx / G::NV, i = (idx % G::NV) * G::VW;
+    VT v;
+    if constexpr (G::VW == 2) {
+      const cx<R> a = tile[i * G::LD + l], b = tile[(i + 1) * G::LD + l];
+      *reinterpret_cast<float4*>(&v) = make_float4(RT<R>::to_f(a.x), RT<R>::to_f(a.y), RT<R>::to_f(b.x), RT<R>::to_f(b.y));
+    } else {
+      st_c(&v, tile[i * G::LD + l]);
+    }
+    *reinterpret_cast<VT*>(g + (row0 + l) * G::H + i) = v;
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// z forward: real rows (FP64) -> packed spectrum rows.  Optional partial of sum(in^2).
-// grid (N*N / NL), block NL*TPL, shared (H*LD + 2N) complex.
+// z turn (middle of A p): each (x, y) line: packed -> real (C2R), times D(x, y, z), -> packed.
+// D = nbar w / V_c carries the 1/V_c of the inverse transform.  grid (N*N / NL).
 // ------------------------------------------------------------------------------------------
-template <class R, int N, bool SQ>
-__global__ void __launch_bounds__(tile_lines<R>() * tpl<R, N / 2>())
-k_zfwd(const double* __restrict__ in, typename Store<R>::T* __restrict__ out,
-       const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc) {
-  constexpr int H = N / 2, M = H, NL = tile_lines<R>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = NL * TPL;
+template <class R, int N>
+__global__ void __launch_bounds__(ZG<R, N>::NT)
+k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
+        const double2* __restrict__ twtab, const CgScal* __restrict__ sc, Bat bt) {
+  using G = ZG<R, N>;
+  using SS = typename Store<R>::S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;
-  __shared__ double red[32];
-  if (sc && sc->done) return;
+  cx<R>* tw = tile + G::M * G::LD;  // 2N entries
+  const int z = blockIdx.z;
+  if (sc && sc[z].done) return;
+  spec += z * bt.spec;
+  D += z * bt.real;
   const int tid = threadIdx.x;
-  const size_t row0 = (size_t)blockIdx.x * NL;
-  for (int e = tid; e < 2 * N; e += NT) tw[e] = ld_c<R>(twtab + e);
+  const size_t row0 = (size_t)blockIdx.x * G::NL;
+  for (int e = tid; e < 2 * N; e += G::NT) tw[e] = ld_c<R>(twtab + e);
+  zrows_load<G>(tile, spec, row0, tid);
+  __syncthreads();
+  const int l = tid % G::NL, t = tid / G::NL;
+  c2r_prep<R, N, G::LD>(tile + l, t, G::TPL, tw);
+  __syncthreads();
+  fft_line<R, G::M, G::TPL, G::LD, +1, 4>(tile + l, t, tw);
+  // real samples 2i, 2i+1 of line l sit in element i: multiply by D, VW elements at a time
+  using DV = typename std::conditional<G::VW == 2, float4, double2>::type;  // 2 VW reals of D
+#pragma unroll 4
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (!(G::EVEN || idx < G::NVEC)) continue;
+    const int ll = idx / G::NV, i = (idx % G::NV) * G::VW;
+    const SS* dp = D + (row0 + ll) * N + 2 * i;
+    if constexpr (G::VW == 2) {
+      const float4 d = *reinterpret_cast<const float4*>(dp);
+      cx<R> a = tile[i * G::LD + ll], b = tile[(i + 1) * G::LD + ll];
+      a.x = a.x * RT<R>::from_f(d.x);
+      a.y = a.y * RT<R>::from_f(d.y);
+      b.x = b.x * RT<R>::from_f(d.z);
+      b.y = b.y * RT<R>::from_f(d.w);
+      tile[i * G::LD + ll] = a;
+      tile[(i + 1) * G::LD + ll] = b;
+    } else {
+      const double2 d = *reinterpret_cast<const double2*>(dp);
+      cx<R> a = tile[i * G::LD + ll];
+      a.x = a.x * RT<R>::c(d.x);
+      a.y = a.y * RT<R>::c(d.y);
+      tile[i * G::LD + ll] = a;
+    }
+  }
+  (void)sizeof(DV);
+  __syncthreads();
+  fft_line<R, G::M, G::TPL, G::LD, -1, 4>(tile + l, t, tw);
+  r2c_post<R, N, G::LD>(tile + l, t, G::TPL, tw);
+  __syncthreads();
+  zrows_store<G>(tile, spec, row0, tid);
+}
+
+// ------------------------------------------------------------------------------------------
+// z forward: real rows (FP64) -> packed spectrum rows.  Optional partial of sum(in^2).
+// ------------------------------------------------------------------------------------------
+template <class R, int N, bool SQ>
+__global__ void __launch_bounds__(ZG<R, N>::NT)
+k_zfwd(const double* __restrict__ in, typename Store<R>::T* __restrict__ out,
+       const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+       Bat bt) {
+  using G = ZG<R, N>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* tw = tile + G::M * G::LD;
+  __shared__ double red[32];
+  const int z = blockIdx.z;
+  if (sc && sc[z].done) return;
+  in += z * bt.real;
+  out += z * bt.spec;
+  partials += z * bt.part;
+  const int tid = threadIdx.x;
+  const size_t row0 = (size_t)blockIdx.x * G::NL;
+  for (int e = tid; e < 2 * N; e += G::NT) tw[e] = ld_c<R>(twtab + e);
   const double2* in2 = reinterpret_cast<const double2*>(in);
   AccD acc;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int l = idx / M, i = idx % M;
-    const double2 v = in2[(row0 + l) * H + i];
-    tile[i * LD + l] = ld_c<R>(&v);
+  constexpr int NE = G::NL * G::M, PE = (NE + G::NT - 1) / G::NT;
+  double2 buf[PE];
+#pragma unroll
+  for (int k = 0; k < PE; ++k) {
+    const int idx = tid + k * G::NT;
+    if (NE % G::NT == 0 || idx < NE) buf[k] = in2[(row0 + idx / G::M) * G::H + idx % G::M];
+  }
+#pragma unroll
+  for (int k = 0; k < PE; ++k) {
+    const int idx = tid + k * G::NT;
+    if (!(NE % G::NT == 0 || idx < NE)) continue;
+    tile[(idx % G::M) * G::LD + idx / G::M] = ld_c<R>(&buf[k]);
     if constexpr (SQ) {
-      acc.add_prod(v.x, v.x);
-      acc.add_prod(v.y, v.y);
+      acc.add_prod(buf[k].x, buf[k].x);
+      acc.add_prod(buf[k].y, buf[k].y);
     }
   }
   __syncthreads();
-  const int l = tid % NL, t = tid / NL;
-  fft_line<R, M, TPL, LD, -1, 4>(tile + l, t, tw);
-  r2c_post<R, N, LD>(tile + l, t, TPL, tw);
+  const int l = tid % G::NL, t = tid / G::NL;
+  fft_line<R, G::M, G::TPL, G::LD, -1, 4>(tile + l, t, tw);
+  r2c_post<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int ll = idx / M, i = idx % M;
-    st_c(out + (row0 + ll) * H + i, tile[i * LD + ll]);
-  }
+  zrows_store<G>(tile, out, row0, tid);
   if constexpr (SQ) {
     const double s = block_sum(acc.get(), red);
     if (tid == 0) partials[blockIdx.x] = s;
@@ -463,36 +699,43 @@ k_zfwd(const double* __restrict__ in, typename Store<R>::T* __restrict__ out,
 // ------------------------------------------------------------------------------------------
 enum { ZI_STORE = 0, ZI_RESID = 1, ZI_ACCUM = 2 };
 template <class R, int N, int MODE>
-__global__ void __launch_bounds__(tile_lines<R>() * tpl<R, N / 2>())
+__global__ void __launch_bounds__(ZG<R, N>::NT)
 k_zinv(const typename Store<R>::T* __restrict__ in, double* __restrict__ out,
        const double* __restrict__ s, const double* __restrict__ w, const double* __restrict__ b,
-       double nbar, double scl, const double2* __restrict__ twtab, double* __restrict__ partials,
-       const CgScal* __restrict__ sc) {
-  constexpr int H = N / 2, M = H, NL = tile_lines<R>(), LD = NL + 1;
-  constexpr int TPL = tpl<R, M>(), NT = NL * TPL;
+       double scl, const double2* __restrict__ twtab, double* __restrict__ partials,
+       const CgScal* __restrict__ sc, Bat bt) {
+  using G = ZG<R, N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + M * LD;
+  cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
-  if (sc && sc->done) return;
+  const int z = blockIdx.z;
+  // RESID reads nbar from the system's scalars; the other modes skip idle systems (done = 4)
+  const double nbar = sc ? sc[z].nbar : 0.0;
+  if (MODE != ZI_RESID && sc && sc[z].done == 4) return;
+  in += z * bt.spec;
+  out += z * bt.real;
+  if (s) s += z * bt.real;
+  if (w) w += z * bt.real;
+  if (b) b += z * bt.real;
+  partials += z * bt.part;
   const int tid = threadIdx.x;
-  const size_t row0 = (size_t)blockIdx.x * NL;
-  for (int e = tid; e < 2 * N; e += NT) tw[e] = ld_c<R>(twtab + e);
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int l = idx / M, i = idx % M;
-    tile[i * LD + l] = ld_c<R>(in + (row0 + l) * H + i);
-  }
+  const size_t row0 = (size_t)blockIdx.x * G::NL;
+  for (int e = tid; e < 2 * N; e += G::NT) tw[e] = ld_c<R>(twtab + e);
+  zrows_load<G>(tile, in, row0, tid);
   __syncthreads();
-  const int l = tid % NL, t = tid / NL;
-  c2r_prep<R, N, LD>(tile + l, t, TPL, tw);
+  const int l = tid % G::NL, t = tid / G::NL;
+  c2r_prep<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
-  fft_line<R, M, TPL, LD, +1, 4>(tile + l, t, tw);
+  fft_line<R, G::M, G::TPL, G::LD, +1, 4>(tile + l, t, tw);
   double2* out2 = reinterpret_cast<double2*>(out);
   AccD acc;
-  for (int idx = tid; idx < M * NL; idx += NT) {
-    const int ll = idx / M, i = idx % M;
-    const size_t e = (row0 + ll) * H + i;
-    const cx<R> v = tile[i * LD + ll];
+  constexpr int NE = G::NL * G::M;
+#pragma unroll 4
+  for (int idx = tid; idx < NE; idx += G::NT) {
+    const int ll = idx / G::M, i = idx % G::M;
+    const size_t e = (row0 + ll) * G::H + i;
+    const cx<R> v = tile[i * G::LD + ll];
     double2 val = make_double2(RT<R>::to_d(v.x) * scl, RT<R>::to_d(v.y) * scl);
     if constexpr (MODE == ZI_RESID) {
       const double2 sv = reinterpret_cast<const double2*>(s)[e];
@@ -524,38 +767,54 @@ template <class R, int N>
 __global__ void __launch_bounds__(256)
 k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* __restrict__ q,
          const typename Store<R>::S* __restrict__ ctab, double* __restrict__ partials,
-         const CgScal* __restrict__ sc) {
+         const CgScal* __restrict__ sc, Bat bt) {
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
   constexpr int NH = N / 2;
+  constexpr int VW = sizeof(ST) == 8 ? 2 : 1;  // complex elements per 16-byte vector
+  using VT = typename std::conditional<VW == 2, float4, ST>::type;
   __shared__ double red[32];
+  const int z = blockIdx.y;
+  sc += z;
   if (sc->done) return;
+  r += z * bt.spec;
+  q += z * bt.spec;
+  ctab += z * bt.tab;
+  partials += z * bt.part;
   const SS alpha = (SS)sc->alpha;
-  const size_t total = (size_t)N * N * NH;
+  const size_t nvec = (size_t)N * N * NH / VW;
+  VT* r4 = reinterpret_cast<VT*>(r);
+  const VT* q4 = reinterpret_cast<const VT*>(q);
   typename AccFor<SS>::T a_rr, a_rc;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    ST rv = r[e];
-    const ST qv = q[e];
-    rv.x -= alpha * qv.x;
-    rv.y -= alpha * qv.y;
-    r[e] = rv;
-    const int kz = (int)(e % NH);
-    const int ky = (int)((e / NH) % N);
-    const int kx = (int)(e / ((size_t)N * NH));
+#pragma unroll 4
+  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec; v += (size_t)gridDim.x * blockDim.x) {
+    VT rv = r4[v];
+    const VT qv = q4[v];
+    SS* rs = reinterpret_cast<SS*>(&rv);
+    const SS* qs = reinterpret_cast<const SS*>(&qv);
+#pragma unroll
+    for (int u = 0; u < 2 * VW; ++u) rs[u] -= alpha * qs[u];
+    r4[v] = rv;
+    const size_t e0 = v * VW;
+    const int ky = (int)((e0 / NH) % N);
+    const int kx = (int)(e0 / ((size_t)N * NH));
     const int kxs = sfreq(kx, N), kys = sfreq(ky, N);
-    const int n2 = kxs * kxs + kys * kys + kz * kz;
-    SS c = ctab[n2];
-    SS ic2 = (SS)1 / (c * c);
-    if (kz == 0) {
-      const SS cN = ctab[n2 + NH * NH];
-      const SS i2 = (SS)1 / (cN * cN);
-      ic2 = ic2 > i2 ? ic2 : i2;
+#pragma unroll
+    for (int u = 0; u < VW; ++u) {
+      const int kz = (int)((e0 + u) % NH);
+      const int n2 = kxs * kxs + kys * kys + kz * kz;
+      const SS c = ctab[n2];
+      SS ic2 = (SS)1 / (c * c);
+      if (kz == 0) {
+        const SS cN = ctab[n2 + NH * NH];
+        const SS i2 = (SS)1 / (cN * cN);
+        ic2 = ic2 > i2 ? ic2 : i2;
+      }
+      const SS wgt = kz == 0 ? (SS)1 : (SS)2;
+      const SS m2 = rs[2 * u] * rs[2 * u] + rs[2 * u + 1] * rs[2 * u + 1];
+      a_rr.add_prod(wgt, m2);
+      a_rc.add_prod(wgt * ic2, m2);
     }
-    const SS wgt = kz == 0 ? (SS)1 : (SS)2;
-    const SS m2 = rv.x * rv.x + rv.y * rv.y;
-    a_rr.add_prod(wgt, m2);
-    a_rc.add_prod(wgt * ic2, m2);
   }
   const double s1 = block_sum(a_rr.get(), red);
   const double s2 = block_sum(a_rc.get(), red);
@@ -565,10 +824,16 @@ k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* __res
   }
 }
 
-// x += alpha_prev p (applies the last alpha after the loop ends); alpha_prev is then cleared
+// x += alpha_prev p_last after the loop ends (p_last = P[lit & 1], the last direction);
+// grid (., systems).  Systems whose alpha_prev is 0 (nothing pending) skip the sweep.
 template <class ST>
-__global__ void k_axpy_final(ST* __restrict__ x, const ST* __restrict__ p, size_t n, CgScal* sc) {
+__global__ void k_axpy_final(ST* __restrict__ x, const ST* P0, const ST* P1, size_t n, const CgScal* sc, Bat bt) {
+  const int z = blockIdx.y;
+  sc += z;
   const double a = sc->alpha_prev;
+  if (a == 0.0) return;
+  const ST* __restrict__ p = ((sc->lit & 1) ? P1 : P0) + z * bt.spec;
+  x += z * bt.spec;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     ST xv = x[e];
     const ST pv = p[e];
@@ -585,25 +850,30 @@ WF_D double sum_partials(const double* p, int n, int stride, int off, double* re
   return block_sum(v, red);
 }
 
-// After the initial r = C b (k_xmul with DOT): rr = <r, r>; reset the recurrences.
-static __global__ void k_fin_init(const double* __restrict__ partials, int n, CgScal* sc) {
+// After the initial r = C b (k_xmul with DOT): rr = <r, r>; reset the recurrences.  Systems
+// marked idle (done = 4) stay idle.  grid = systems.
+static __global__ void k_fin_init(const double* __restrict__ partials, int n, CgScal* sc, Bat bt) {
   __shared__ double red[32];
-  const double rr = sum_partials(partials, n, 1, 0, red);
+  sc += blockIdx.x;
+  if (sc->done == 4) return;
+  const double rr = sum_partials(partials + blockIdx.x * bt.part, n, 1, 0, red);
   if (threadIdx.x == 0) {
     sc->rr = rr;
     sc->beta = 0.0;
     sc->alpha = 0.0;
     sc->alpha_prev = 0.0;
+    sc->lit = 0;
     sc->rc2 = sc->bb;
     sc->done = (rr == 0.0 || sc->bb == 0.0) ? 1 : 0;
     sc->status = 0;
   }
 }
 
-static __global__ void k_fin_alpha(const double* __restrict__ partials, int n, CgScal* sc) {
+static __global__ void k_fin_alpha(const double* __restrict__ partials, int n, CgScal* sc, Bat bt) {
   __shared__ double red[32];
+  sc += blockIdx.x;
   if (sc->done) return;
-  const double pq = sum_partials(partials, n, 1, 0, red);
+  const double pq = sum_partials(partials + blockIdx.x * bt.part, n, 1, 0, red);
   if (threadIdx.x == 0) {
     sc->pq = pq;
     if (!(pq > 0.0) || !isfinite(pq)) {
@@ -617,9 +887,11 @@ static __global__ void k_fin_alpha(const double* __restrict__ partials, int n, C
 }
 
 // stop rule: rc2 * inv_vc <= max(tol2 * bb, rr_stop)
-static __global__ void k_fin_beta(const double* __restrict__ partials, int n, double inv_vc, CgScal* sc) {
+static __global__ void k_fin_beta(const double* __restrict__ partials, int n, double inv_vc, CgScal* sc, Bat bt) {
   __shared__ double red[32];
+  sc += blockIdx.x;
   if (sc->done) return;
+  partials += blockIdx.x * bt.part;
   const double rr = sum_partials(partials, n, 2, 0, red);
   const double rc = sum_partials(partials, n, 2, 1, red);
   if (threadIdx.x == 0) {
@@ -629,6 +901,7 @@ static __global__ void k_fin_beta(const double* __restrict__ partials, int n, do
     sc->rc2 = rc2;
     sc->alpha_prev = sc->alpha;
     sc->iter += 1;
+    sc->lit += 1;
     const double lim = fmax(sc->tol2 * sc->bb, sc->rr_stop);
     if (!isfinite(rr) || !isfinite(rc2)) sc->done = 3;
     else if (rc2 <= lim) sc->done = 1;
@@ -636,10 +909,12 @@ static __global__ void k_fin_beta(const double* __restrict__ partials, int n, do
   }
 }
 
-// sum of partials into sc->aux[slot] (slot >= 0, host reads it) or into sc->bb (slot < 0)
-static __global__ void k_fin_sum(const double* __restrict__ partials, int n, int slot, CgScal* sc) {
+// sum of partials into sc->aux[slot] (slot >= 0, host reads it) or into sc->bb (slot < 0);
+// grid = systems
+static __global__ void k_fin_sum(const double* __restrict__ partials, int n, int slot, CgScal* sc, Bat bt) {
   __shared__ double red[32];
-  const double v = sum_partials(partials, n, 1, 0, red);
+  sc += blockIdx.x;
+  const double v = sum_partials(partials + blockIdx.x * bt.part, n, 1, 0, red);
   if (threadIdx.x == 0) {
     if (slot >= 0) sc->aux[slot] = v;
     else sc->bb = v;

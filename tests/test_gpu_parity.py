@@ -272,3 +272,52 @@ def test_fixed_iterations_large_grid(ctx, n):
     s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=3, precond=0, check=False)
     assert info.iters == 3
     assert rl2(host(s), ref) <= 1e-11
+
+
+# ------------------------------------------------------------------------ batched solves
+def _mock(n, seed, box_per_cell=1.953):
+    """A small mock of the batched workload: LCDM prior, SDSS-like selection, its own seed."""
+    pr = synth.problem("c2", n_override=n, cache=False)
+    rng = np.random.default_rng(seed)
+    box = n * box_per_cell
+    sel = synth.selection_sdss_like(box, seed)
+    pos = synth.lognormal_catalogue(n, box, pr.pk_k, pr.pk_p, sel, float(rng.uniform(2e3, 2e4)), seed)
+    return box, sel, pos, pr.pk_k, pr.pk_p
+
+
+@pytest.mark.parametrize("prec", [wf.FP64, wf.MIXED])
+def test_batch_equals_individual_solves(ctx, prec):
+    """Systems of uneven sizes solved in one batch give the same result as solved alone."""
+    probs, singles = [], []
+    for i, n in enumerate([32, 48, 32, 64, 48, 24]):
+        box, sel, pos, k, p = _mock(n, 2000 + i)
+        nobs = ctx.grid_assign(gpu(pos), n, box, wf.TSC, 2)
+        w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box)
+        probs.append(dict(w=w, nbar=nbar, b=b, box=box, pk_k=k, pk_p=p, tol=1e-8, prec=prec))
+        s, info = ctx.solve(w, nbar, b, box, k, p, tol=1e-8, prec=prec)
+        singles.append((host(s).copy(), info.iters))
+    st, outs, infos = ctx.solve_batch(probs)
+    assert st == wf.OK
+    for (ref, it), s, info in zip(singles, outs, infos):
+        assert info.status == wf.OK and info.rel_residual <= 1e-8
+        tol = 1e-12 if prec == wf.FP64 else 1e-6
+        assert rl2(host(s), ref) <= tol
+        if prec == wf.FP64:
+            assert info.iters == it                        # same iterates, same count
+
+
+def test_batch_matches_oracle(ctx):
+    probs, refs = [], []
+    for i, n in enumerate([24, 32]):
+        box, sel, pos, k, p = _mock(n, 2100 + i)
+        fine = oracle.assign(pos, n, box, 2, 2)
+        nobs = oracle.lowpass(fine, n, 2)
+        w = oracle.window(sel, n, box)
+        d, b, nbar = oracle.build_noise(nobs, w, pos.shape[0])
+        tab = oracle.sinv_table(n, box, k, p)
+        refs.append(oracle.cg(tab, nbar, w, b, tol=1e-12)[0])
+        probs.append(dict(w=gpu(w), nbar=nbar, b=gpu(b), box=box, pk_k=k, pk_p=p, tol=1e-12, max_iter=20000))
+    st, outs, infos = ctx.solve_batch(probs)
+    assert st == wf.OK
+    for ref, s in zip(refs, outs):
+        assert rl2(host(s), ref) <= 1e-10
