@@ -104,6 +104,7 @@ typedef struct {
   double rel_residual; /* ||b - A s|| / ||b|| recomputed from the returned s in FP64 */
   double nbar;         /* nbar the solve used */
   wf_status status;
+  double latency_s;    /* wf_poll results: seconds from wf_submit to completion (else 0) */
 } wf_solve_info;
 
 /* ---- context ------------------------------------------------------------------------ */
@@ -213,9 +214,14 @@ wf_status wf_solve_batch(wf_ctx* ctx, int count, const wf_grid* grids, const wf_
 
 /* Queue one solve.  w and b are HOST double [n^3] arrays copied before return (the caller
  * may free them); the power table is copied too.  *request_id receives a handle.
- * The request is admitted when its device footprint fits the context's HBM budget and a
- * slot is free; admitted requests stay resident and their iterations are interleaved.
- * Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED, WF_ERR_BUSY (queue full). */
+ * A scheduler thread of the context (started by the first wf_submit) admits queued requests
+ * in arrival order while their device footprint fits the HBM budget (the context's budget,
+ * or 80% of the device memory free when the scheduler starts) and fewer than 64 systems are
+ * resident.  Requests admitted together are batched by grid size and precision; the batches
+ * run interleaved with those already resident, each keeping its CG state on the device until
+ * it finishes, and a finished request's memory is released at once.  A result does not
+ * depend on which requests shared the device with it.
+ * Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED, WF_ERR_BUSY (more than 4096 queued). */
 wf_status wf_submit(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const double* w,
                     double nbar, const double* b, const wf_solve_opts* opts,
                     uint64_t* request_id);

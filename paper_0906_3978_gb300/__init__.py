@@ -57,7 +57,7 @@ class SolveOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iters", c_int), ("outer_iters", c_int), ("rel_residual", c_double),
-                ("nbar", c_double), ("status", c_int)]
+                ("nbar", c_double), ("status", c_int), ("latency_s", c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -99,6 +99,26 @@ wf_status Ctx::stream(int i, cudaStream_t* out) {
   return WF_OK;
 }
 
+void Ctx::release_prefix(const std::string& prefix) {
+  for (auto it = bufs.begin(); it != bufs.end();) {
+    if (it->first.compare(0, prefix.size(), prefix) == 0) {
+      if (it->second.ptr) cudaFree(it->second.ptr);
+      held -= it->second.bytes;
+      it = bufs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  for (auto it = pinned.begin(); it != pinned.end();) {
+    if (it->first.compare(0, prefix.size(), prefix) == 0) {
+      if (it->second.ptr) cudaFreeHost(it->second.ptr);
+      it = pinned.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 void Ctx::release_all() {
   for (auto& kv : bufs)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
@@ -142,7 +162,11 @@ wf_status build_sinv_table(const wf_grid& g, const wf_power& pw, std::vector<dou
   return WF_OK;
 }
 
-static Group* make_group_n(int n, int prec) {
+}  // namespace wf
+#include "wf_solver_group.h"
+namespace wf {
+
+Group* make_group_n(int n, int prec) {
   switch (n) {
 #define WF_CASE(N) \
   case N:          \
@@ -154,9 +178,13 @@ static Group* make_group_n(int n, int prec) {
   }
 }
 
-}  // namespace wf
-#include "wf_solver_group.h"
-namespace wf {
+// Device bytes of a group (the buffers GroupFP64 / GroupMixed allocate, tables excluded).
+size_t Group::footprint(int n, int prec, int count) {
+  const double V = (double)n * n * n, spec = V / 2;
+  const double per = prec == WF_MIXED ? 6 * spec * 8 + 2 * spec * 16 + 4 * V + 4 * 8 * V
+                                      : 7 * spec * 16 + 5 * 8 * V;
+  return (size_t)(per * count) + (size_t)count * (3 * (n / 2) * (n / 2) + 1) * 24 + (64u << 10);
+}
 
 wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_info*>& infos, cudaStream_t st) {
   std::map<std::pair<int, int>, std::unique_ptr<Group>> groups;

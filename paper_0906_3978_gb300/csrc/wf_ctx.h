@@ -130,6 +130,8 @@ struct Ctx {
   wf_status get_pinned(const std::string& name, size_t bytes, void** out);
   // i-th library-owned non-blocking stream.
   wf_status stream(int i, cudaStream_t* out);
+  // Free every device and pinned buffer whose name starts with `prefix`.
+  void release_prefix(const std::string& prefix);
   void release_all();
 };
 

@@ -1,14 +1,272 @@
-// wf_serve.cu -- serving loop (wf_submit / wf_poll).
+// wf_serve.cu -- serving loop behind wf_submit / wf_poll: continuous batching of Wiener solves.
+//
+// A scheduler thread per context owns a FIFO of submitted requests and a list of resident
+// groups (systems of one grid size and precision advanced together by the batched kernels).
+// Each tick it (1) admits queued requests in arrival order while the device footprint of the
+// resident systems plus theirs fits the HBM budget and fewer than kMaxResident systems are
+// resident, forming new groups from the admitted requests; (2) enqueues one block of work for
+// every resident group on its own stream; (3) synchronises and advances each group; (4) copies
+// the solutions of finished groups to the requests' host buffers, releases their device memory
+// and wakes the pollers.  Work of groups admitted at different times overlaps on the device.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+
 #include "wf_ctx.h"
+#include "wf_solver_group.h"
 
 namespace wf {
-void serve_shutdown(Ctx&) {}
+
+wf_status prepare_solve(const wf_grid* grid, const wf_power* power, const double* w, double nbar,
+                        const double* b, const wf_solve_opts* opts, double* s_out, SolveArgs& a);
+
+namespace {
+constexpr int kMaxResident = 64;
+constexpr size_t kMaxQueued = 4096;
+constexpr int kFirstStream = 8;  // library streams 0..7 belong to wf_solve_batch
+using Clock = std::chrono::steady_clock;
+}  // namespace
+
+struct Request {
+  uint64_t id = 0;
+  std::vector<double> w, b, k, p, s;  // host copies; s receives the solution
+  SolveArgs args;
+  wf_solve_info info{};
+  wf_status status = WF_PENDING;
+  Clock::time_point t_submit;
+  size_t footprint = 0;
+};
+
+struct ResidentGroup {
+  std::unique_ptr<Group> g;
+  std::vector<std::shared_ptr<Request>> reqs;
+  cudaStream_t stream = nullptr;
+  int stream_idx = 0;
+  size_t footprint = 0;
+  bool prepared = false;
+};
+
+struct Server {
+  Ctx* ctx = nullptr;
+  std::thread th;
+  std::mutex mu;                  // guards queue, requests, stop
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Request>> queue;
+  std::map<uint64_t, std::shared_ptr<Request>> requests;
+  std::vector<ResidentGroup> resident;  // touched by the scheduler thread only
+  std::vector<int> free_streams;
+  uint64_t next_id = 1;
+  uint64_t next_group = 1;
+  int next_stream = kFirstStream;
+  bool stop = false;
+  size_t budget = 0, used = 0;
+  int resident_systems = 0;
+
+  void run();
+  void complete(ResidentGroup& rg, wf_status st);
+};
+
+void Server::complete(ResidentGroup& rg, wf_status st) {
+  const auto now = Clock::now();
+  std::lock_guard<std::mutex> lk(mu);
+  for (size_t i = 0; i < rg.reqs.size(); ++i) {
+    auto& r = rg.reqs[i];
+    r->status = st != WF_OK ? st : r->info.status;
+    r->info.status = r->status;
+    r->info.latency_s = std::chrono::duration<double>(now - r->t_submit).count();
+  }
+  cv_done.notify_all();
+}
+
+void Server::run() {
+  Ctx& c = *ctx;
+  for (;;) {
+    // ---- admission -----------------------------------------------------------------------
+    std::vector<std::shared_ptr<Request>> admit;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      if (resident.empty())
+        cv_work.wait(lk, [&] { return stop || !queue.empty(); });
+      if (stop) break;
+      while (!queue.empty() && resident_systems + (int)admit.size() < kMaxResident) {
+        auto& r = queue.front();
+        if (used + r->footprint > budget && !(resident.empty() && admit.empty())) break;
+        used += r->footprint;
+        admit.push_back(r);
+        queue.pop_front();
+      }
+    }
+    {
+      std::lock_guard<std::mutex> ck(c.mu);
+      DeviceGuard dg(c.device);
+      // group the admitted requests by (size, precision)
+      std::map<std::pair<int, int>, std::vector<std::shared_ptr<Request>>> by;
+      for (auto& r : admit) by[{r->args.grid.n, (int)r->args.opts.prec}].push_back(r);
+      for (auto& kv : by) {
+        ResidentGroup rg;
+        rg.g.reset(make_group_n(kv.first.first, kv.first.second));
+        rg.g->tag = "srv" + std::to_string(next_group++) + "_";
+        for (auto& r : kv.second) {
+          rg.g->sys.push_back(&r->args);
+          rg.g->info.push_back(&r->info);
+          rg.footprint += r->footprint;
+        }
+        rg.reqs = kv.second;
+        if (free_streams.empty()) free_streams.push_back(next_stream++);
+        rg.stream_idx = free_streams.back();
+        free_streams.pop_back();
+        wf_status st = c.stream(rg.stream_idx, &rg.stream);
+        if (st == WF_OK) st = rg.g->prepare(c, rg.stream);
+        if (st == WF_OK) {
+          cudaError_t e = cudaStreamSynchronize(rg.stream);
+          if (e != cudaSuccess) st = WF_ERR_CUDA;
+        }
+        resident_systems += (int)rg.reqs.size();
+        rg.prepared = st == WF_OK;
+        if (st != WF_OK) {
+          complete(rg, st);
+          c.release_prefix(rg.g->tag);
+          std::lock_guard<std::mutex> lk(mu);
+          used -= rg.footprint;
+          resident_systems -= (int)rg.reqs.size();
+          free_streams.push_back(rg.stream_idx);
+          continue;
+        }
+        resident.push_back(std::move(rg));
+      }
+      // ---- one block of work for every resident group -------------------------------------
+      std::vector<wf_status> sts(resident.size(), WF_OK);
+      for (size_t i = 0; i < resident.size(); ++i) sts[i] = resident[i].g->enqueue(c, resident[i].stream);
+      for (size_t i = 0; i < resident.size(); ++i) {
+        if (sts[i] == WF_OK && cudaStreamSynchronize(resident[i].stream) != cudaSuccess) sts[i] = WF_ERR_CUDA;
+        if (sts[i] == WF_OK) sts[i] = resident[i].g->advance(c);
+      }
+      // ---- finished groups -----------------------------------------------------------------
+      for (size_t i = 0; i < resident.size();) {
+        ResidentGroup& rg = resident[i];
+        if (sts[i] == WF_OK && !rg.g->done()) {
+          ++i;
+          continue;
+        }
+        wf_status st = sts[i];
+        if (st == WF_OK) st = rg.g->finish(c, rg.stream);
+        if (st == WF_OK && cudaStreamSynchronize(rg.stream) != cudaSuccess) st = WF_ERR_CUDA;
+        complete(rg, st);
+        c.release_prefix(rg.g->tag);
+        {
+          std::lock_guard<std::mutex> lk(mu);
+          used -= rg.footprint;
+          resident_systems -= (int)rg.reqs.size();
+        }
+        free_streams.push_back(rg.stream_idx);
+        resident.erase(resident.begin() + i);
+        sts.erase(sts.begin() + i);
+      }
+    }
+  }
+  // shutdown: fail whatever is still queued or resident
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& r : queue) r->status = WF_ERR_TIMEOUT;
+  for (auto& rg : resident)
+    for (auto& r : rg.reqs) r->status = WF_ERR_TIMEOUT;
+  cv_done.notify_all();
+}
+
+void serve_shutdown(Ctx& c) {
+  Server* s = c.server;
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv_work.notify_all();
+  if (s->th.joinable()) s->th.join();
+  {
+    std::lock_guard<std::mutex> ck(c.mu);
+    for (auto& rg : s->resident) c.release_prefix(rg.g->tag);
+  }
+  delete s;
+  c.server = nullptr;
+}
+
+static Server* server_of(Ctx& c) {
+  if (!c.server) {
+    Server* s = new Server();
+    s->ctx = &c;
+    size_t fr = 0, tot = 0;
+    {
+      DeviceGuard dg(c.device);
+      cudaMemGetInfo(&fr, &tot);
+    }
+    s->budget = c.budget ? c.budget : (size_t)(0.8 * (double)fr);
+    c.server = s;
+    s->th = std::thread([s] { s->run(); });
+  }
+  return c.server;
+}
+
 }  // namespace wf
 
+using namespace wf;
+
 extern "C" {
-wf_status wf_submit(wf_ctx*, const wf_grid*, const wf_power*, const double*, double, const double*,
-                    const wf_solve_opts*, uint64_t*) {
-  return WF_ERR_UNSUPPORTED;
+
+wf_status wf_submit(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const double* w, double nbar,
+                    const double* b, const wf_solve_opts* opts, uint64_t* request_id) {
+  if (!ctx || !request_id || !grid || !power || !w || !b || !opts) return WF_ERR_ARG;
+  if (!supported_size(grid->n)) return WF_ERR_UNSUPPORTED;
+  if (!power->k || !power->p || power->n < 2) return WF_ERR_ARG;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  auto r = std::make_shared<Request>();
+  const size_t V = (size_t)grid->n * grid->n * grid->n;
+  r->w.assign(w, w + V);
+  r->b.assign(b, b + V);
+  r->k.assign(power->k, power->k + power->n);
+  r->p.assign(power->p, power->p + power->n);
+  r->s.assign(V, 0.0);
+  wf_power pw{r->k.data(), r->p.data(), power->n};
+  wf_status st = prepare_solve(grid, &pw, r->w.data(), nbar, r->b.data(), opts, r->s.data(), r->args);
+  if (st != WF_OK) return st;
+  r->footprint = Group::footprint(grid->n, (int)opts->prec, 1);
+  r->t_submit = Clock::now();
+  Server* s = server_of(c);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->queue.size() >= kMaxQueued) return WF_ERR_BUSY;
+    r->id = s->next_id++;
+    s->requests[r->id] = r;
+    s->queue.push_back(r);
+    *request_id = r->id;
+  }
+  s->cv_work.notify_one();
+  return WF_OK;
 }
-wf_status wf_poll(wf_ctx*, uint64_t, int, double*, wf_solve_info*) { return WF_ERR_UNSUPPORTED; }
+
+wf_status wf_poll(wf_ctx* ctx, uint64_t request_id, int timeout_ms, double* s_out, wf_solve_info* info) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  Server* s = c.server;
+  if (!s) return WF_ERR_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->requests.find(request_id);
+  if (it == s->requests.end()) return WF_ERR_ARG;
+  std::shared_ptr<Request> r = it->second;
+  auto ready = [&] { return r->status != WF_PENDING; };
+  if (!ready()) {
+    if (timeout_ms < 0) s->cv_done.wait(lk, ready);
+    else if (timeout_ms > 0) s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+  }
+  if (!ready()) return WF_PENDING;
+  if (s_out) std::memcpy(s_out, r->s.data(), r->s.size() * sizeof(double));
+  if (info) *info = r->info;
+  const wf_status st = r->status;
+  s->requests.erase(it);
+  return st;
 }
+
+}  // extern "C"

@@ -1,6 +1,7 @@
 // wf_solver_group.h -- the host-side interface of a group of systems solved together
 // (implemented per grid size in wf_solver_impl.cuh).
 #pragma once
+#include <string>
 #include <vector>
 
 #include "wf_ctx.h"
@@ -17,6 +18,11 @@ struct Group {
   std::vector<SolveArgs*> sys;
   std::vector<wf_solve_info*> info;
   int nb = 0;
+  std::string tag;  // prefix of this group's workspace names ("" = shared, reused across calls)
+  // Device bytes a group of `count` systems of size n and precision prec holds.
+  static size_t footprint(int n, int prec, int count);
 };
+
+Group* make_group_n(int n, int prec);
 
 }  // namespace wf

@@ -286,7 +286,7 @@ struct GroupFP64 : GroupCommon<N> {
 
   wf_status prepare(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
-    key = "f64_" + std::to_string(N) + "_";
+    key = this->tag + "f64_" + std::to_string(N) + "_";
     WF_CUDA(SP::attrs());
     const size_t SPEC = SP::SPEC, V = SP::V;
     WF_TRY(c.tw(N, &tw));
@@ -302,8 +302,8 @@ struct GroupFP64 : GroupCommon<N> {
     WF_TRY(c.get(key + "sc", nb * sizeof(CgScal), (void**)&sc));
     WF_TRY(c.get_pinned(key + "hsc", nb * sizeof(CgScal), (void**)&this->hsc));
     for (int m = 0; m < nb; ++m) {
-      WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDefault, st));
+      WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDefault, st));
     }
     WF_TRY(group_sums<N>(c, *this, SP::NPART, st));
     // tables
@@ -416,7 +416,7 @@ struct GroupFP64 : GroupCommon<N> {
   bool done() const override { return phase == 9; }
   wf_status finish(Ctx&, cudaStream_t st) override {
     for (int m = 0; m < nb; ++m)
-      WF_CUDA(cudaMemcpyAsync(sys[m]->s_out, S + m * SP::V, SP::V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      WF_CUDA(cudaMemcpyAsync(sys[m]->s_out, S + m * SP::V, SP::V * sizeof(double), cudaMemcpyDefault, st));
     return WF_OK;
   }
 };
@@ -444,7 +444,7 @@ struct GroupMixed : GroupCommon<N> {
 
   wf_status prepare(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
-    key = "mix_" + std::to_string(N) + "_";
+    key = this->tag + "mix_" + std::to_string(N) + "_";
     WF_CUDA(SF::attrs());
     WF_CUDA(SD::attrs());
     const size_t SPEC = SF::SPEC, V = SF::V;
@@ -463,8 +463,8 @@ struct GroupMixed : GroupCommon<N> {
     WF_TRY(c.get(key + "sc", nb * sizeof(CgScal), (void**)&sc));
     WF_TRY(c.get_pinned(key + "hsc", nb * sizeof(CgScal), (void**)&this->hsc));
     for (int m = 0; m < nb; ++m) {
-      WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDefault, st));
+      WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDefault, st));
     }
     WF_TRY(group_sums<N>(c, *this, NPART, st));
     const int TAB = SF::TAB;
@@ -586,7 +586,7 @@ struct GroupMixed : GroupCommon<N> {
   bool done() const override { return phase == 9; }
   wf_status finish(Ctx&, cudaStream_t st) override {
     for (int m = 0; m < nb; ++m)
-      WF_CUDA(cudaMemcpyAsync(sys[m]->s_out, S + m * SF::V, SF::V * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      WF_CUDA(cudaMemcpyAsync(sys[m]->s_out, S + m * SF::V, SF::V * sizeof(double), cudaMemcpyDefault, st));
     return WF_OK;
   }
 };

@@ -321,3 +321,55 @@ def test_batch_matches_oracle(ctx):
     assert st == wf.OK
     for ref, s in zip(refs, outs):
         assert rl2(host(s), ref) <= 1e-10
+
+
+# ------------------------------------------------------------------------ serving
+def _serve_inputs(n, seed):
+    box, sel, pos, k, p = _mock(n, seed)
+    c = wf.Context(0)
+    nobs = c.grid_assign(gpu(pos), n, box, wf.TSC, 2)
+    w, d, b, nbar = c.build_noise(sel, nobs, pos.shape[0], box)
+    out = (host(w).copy(), host(b).copy(), nbar, box, k, p)
+    c.close()
+    return out
+
+
+def test_serving_results_same_alone_and_in_mix():
+    """Requests of mixed sizes and precisions, some submitted while others run, give the same
+    solution as the same request solved alone."""
+    wf.build()
+    reqs = [(32, 3000, wf.FP64), (48, 3001, wf.MIXED), (64, 3002, wf.FP64), (32, 3003, wf.MIXED),
+            (64, 3004, wf.MIXED), (24, 3005, wf.FP64)]
+    inputs = [_serve_inputs(n, seed) for n, seed, _ in reqs]
+    with wf.Context(0) as ctx:
+        ids = []
+        for i, ((n, seed, prec), (w, b, nbar, box, k, p)) in enumerate(zip(reqs, inputs)):
+            ids.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-8, prec=prec))
+            if i == 2:  # the first requests are resident while the rest arrive
+                st, _ = ctx.poll(ids[0], timeout_ms=0)
+                assert st in (wf.PENDING, wf.OK)
+        results = []
+        for rid, (n, _, _) in zip(ids, reqs):
+            s = np.empty(n ** 3)
+            st, info = ctx.poll(rid, timeout_ms=-1, s_out=s)
+            assert st == wf.OK and info.rel_residual <= 1e-8 and info.latency_s > 0
+            results.append(s.reshape(n, n, n))
+        for (n, seed, prec), (w, b, nbar, box, k, p), s in zip(reqs, inputs, results):
+            alone, info = ctx.solve(gpu(w), nbar, gpu(b), box, k, p, tol=1e-8, prec=prec)
+            assert rl2(s, host(alone)) <= (1e-12 if prec == wf.FP64 else 1e-6)
+
+
+def test_serving_errors():
+    wf.build()
+    w, b, nbar, box, k, p = _serve_inputs(16, 3010)
+    with wf.Context(0) as ctx:
+        with pytest.raises(wf.WfError) as e:
+            ctx.submit(w, -1.0, b, box, k, p)
+        assert e.value.status == wf.ERR_ARG
+        st, _ = ctx.poll(12345, timeout_ms=0)
+        assert st == wf.ERR_ARG
+        rid = ctx.submit(w, nbar, b, box, k, p, tol=1e-6)
+        st, info = ctx.poll(rid, timeout_ms=-1)
+        assert st == wf.OK
+        st, _ = ctx.poll(rid, timeout_ms=0)          # released after the final poll
+        assert st == wf.ERR_ARG
