@@ -33,7 +33,10 @@ WORKLOADS = {
 }
 # DRAM traffic of the dominant kernel per launch from one ncu capture, valid while the kernel
 # sources hash to `src`; scaled from the captured size by the units processed (bytes ~ N^3).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/cg_kernels_f32_256_full.md: 213.9 + 147.8 MB at 256^3, x 8 for 512^3
+    ("cg_xinv", 512): {"bytes": 361.7e6 * 8, "src": "0776abeef5ffe458"},
+}
 
 
 def kernel_src_hash():
@@ -256,6 +259,10 @@ def gpu_arm(args):
     e2e_s = time.perf_counter() - t0
     e2e_s = barrier_max(ws, e2e_s)
 
+    extra = {}
+    if not args.no_forms:
+        extra["batch"] = bench_batch(ctx, dev)
+        extra["serving"] = bench_serving(ctx, dev)
     if rank != 0:
         return 0
     k = args.steps
@@ -290,9 +297,143 @@ def gpu_arm(args):
         "gpu_launches": prof["launches"],
         "clocks": clk.summary(),
     }
+    line.update(extra)
     print(json.dumps(line))
     ctx.close()
     return 0
+
+
+# ------------------------------------------------------------------------------------------
+# Batched form: 96 mocks of uneven size in one wf_solve_batch call
+# ------------------------------------------------------------------------------------------
+def batch_mocks(count=96, seed=2000):
+    """Seeded mocks of the batched workload: N from {64, 96, 128, 192}, L = 1.953 N Mpc/h,
+    1e4-1e5 galaxies (log-uniform), LCDM prior, SDSS-like selection with per-mock holes."""
+    import numpy as np
+    import synth
+    rng = np.random.default_rng(seed)
+    k, p = synth.lcdm_table()
+    out = []
+    for i in range(count):
+        n = int(rng.choice([64, 96, 128, 192]))
+        box = 1.953 * n
+        ng = float(np.exp(rng.uniform(np.log(1e4), np.log(1e5))))
+        sel = synth.selection_sdss_like(box, seed + i)
+        pos = synth._cached_catalogue("batch_n%d_s%d_g%d" % (n, seed + i, int(ng)),
+                                      lambda: synth.lognormal_catalogue(n, box, k, p, sel, ng, seed + i))
+        out.append((n, box, sel, pos, k, p))
+    return out
+
+
+def bench_batch(ctx, dev):
+    import torch
+    import paper_0906_3978_gb300 as wf
+    mocks = batch_mocks()
+    pos_d = [torch.from_numpy(m[3]).to(dev) for m in mocks]
+
+    def prepare():
+        probs = []
+        for (n, box, sel, pos, k, p), pd in zip(mocks, pos_d):
+            nobs = ctx.grid_assign(pd, n, box, wf.TSC, 2)
+            w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
+            probs.append(dict(w=w, nbar=nbar, b=b, box=box, pk_k=k, pk_p=p, tol=1e-6, max_iter=20000,
+                              prec=wf.MIXED))
+        return probs
+
+    probs = prepare()
+    ctx.solve_batch(probs)            # warm-up (workspaces, tables)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    probs = prepare()
+    st, outs, infos = ctx.solve_batch(probs)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    # the same systems, one plain FP64 solve after another, same tolerance
+    t0 = time.perf_counter()
+    iters64 = 0
+    for pr in probs:
+        s, info = ctx.solve(pr["w"], pr["nbar"], pr["b"], pr["box"], pr["pk_k"], pr["pk_p"], tol=1e-6,
+                            max_iter=20000, prec=wf.FP64)
+        iters64 += info.iters
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    sizes = {}
+    for m in mocks:
+        sizes[m[0]] = sizes.get(m[0], 0) + 1
+    return {"workload": "96 mocks, N in {64,96,128,192} (counts %s), L = 1.953 N Mpc/h, 1e4-1e5 galaxies; "
+                        "gridding + window/noise + one wf_solve_batch (mixed, FP32 inner / FP64 refinement) "
+                        "to 1e-6" % sizes,
+            "value": len(mocks) / t_batch, "unit": "solves/s", "status": st,
+            "max_rel_residual": max(i.rel_residual for i in infos),
+            "fp64_sequential": {"value": len(mocks) / t_seq, "unit": "solves/s",
+                                "note": "plain FP64 wf_solve one system at a time, same tolerance, solve only"}}
+
+
+# ------------------------------------------------------------------------------------------
+# Served form: Poisson stream of requests through wf_submit / wf_poll
+# ------------------------------------------------------------------------------------------
+SERVE_SIZES = [64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384]
+
+
+def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
+    import numpy as np
+    import torch
+    import paper_0906_3978_gb300 as wf
+    import synth
+    rng = np.random.default_rng(seed)
+    k, p = synth.lcdm_table()
+    pool = {}
+    for i, n in enumerate(SERVE_SIZES):     # one problem per size, shared by that size's requests
+        box = 1.953 * n
+        sel = synth.selection_sdss_like(box, seed + i, half_angle_deg=float(rng.uniform(20, 45)),
+                                        r_peak=float(rng.uniform(100, 200)) * box / 500.0)
+        ng = 0.009 * n ** 3 * float(rng.uniform(0.5, 1.5))
+        pos = synth._cached_catalogue("serve_n%d_s%d" % (n, seed + i),
+                                      lambda: synth.lognormal_catalogue(n, box, k, p, sel, ng, seed + i))
+        nobs = ctx.grid_assign(torch.from_numpy(pos).to(dev), n, box, wf.TSC, 2)
+        w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
+        pool[n] = (w.cpu().numpy().copy(), b.cpu().numpy().copy(), nbar, box)
+    sizes = rng.choice(SERVE_SIZES, size=n_req)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    # FP64 comparison: service time of one plain FP64 solve per size
+    t64 = {}
+    for n in SERVE_SIZES:
+        w, b, nbar, box = pool[n]
+        wd, bd = torch.from_numpy(w).to(dev), torch.from_numpy(b).to(dev)
+        ctx.solve(wd, nbar, bd, box, k, p, tol=1e-6, max_iter=20000, prec=wf.FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve(wd, nbar, bd, box, k, p, tol=1e-6, max_iter=20000, prec=wf.FP64)
+        torch.cuda.synchronize()
+        t64[n] = time.perf_counter() - t0
+    # warm the serving path once per size
+    for n in SERVE_SIZES:
+        w, b, nbar, box = pool[n]
+        ctx.poll(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED), timeout_ms=-1)
+    lat, stats = [], []
+    t_start = time.perf_counter()
+    submitted = []
+    for i in range(n_req):
+        target = t_start + float(np.sum(gaps[:i + 1]))
+        now = time.perf_counter()
+        if target > now:
+            time.sleep(target - now)
+        w, b, nbar, box = pool[int(sizes[i])]
+        submitted.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED))
+    for rid in submitted:
+        st, info = ctx.poll(rid, timeout_ms=-1)
+        stats.append(st)
+        lat.append(info.latency_s)
+    t_total = time.perf_counter() - t_start
+    lat = np.array(lat)
+    mean64 = float(np.mean([t64[int(n)] for n in sizes]))
+    return {"workload": "%d requests, Poisson arrivals at %.0f/s, N uniform over %s, L = 1.953 N Mpc/h, "
+                        "0.009 N^3 x U(0.5,1.5) galaxies, random cone 20-45 deg and radial peak; mixed "
+                        "precision to 1e-6 through wf_submit/wf_poll" % (n_req, rate, SERVE_SIZES),
+            "value": n_req / t_total, "unit": "solves/s", "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "ok": int(sum(1 for s in stats if s == 0)),
+            "fp64_sequential": {"value": 1.0 / mean64, "unit": "solves/s",
+                                "note": "1 / mean service time of one plain FP64 wf_solve over the same size mix"}}
 
 
 def read_profile(ctx):
@@ -306,6 +447,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wf", choices=["wf", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-forms", dest="no_forms", action="store_true",
+                    help="leave out the batched and served forms (reported after the timed 512^3 steps)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

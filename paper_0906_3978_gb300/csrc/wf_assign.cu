@@ -111,10 +111,19 @@ k_lowpass(const IN* __restrict__ in, double* __restrict__ out, double in_scale,
   // ---- load 2N reals per line as N complex
   if constexpr (AXIS == 0) {
     const size_t r0 = (size_t)blockIdx.x * NL;
+    int nonzero = 0;
     for (int idx = tid; idx < M * NL; idx += NT) {
       const int l = idx / M, m = idx % M;
       const IN* src = in + (r0 + l) * (2 * N) + 2 * m;
+      nonzero |= (src[0] != 0) | (src[1] != 0);
       tile[m * LD + l] = cx<R>{RT<R>::from_d(to_real(src[0], in_scale)), RT<R>::from_d(to_real(src[1], in_scale))};
+    }
+    // rows the survey never reaches are all zero: their filtered output is exactly zero
+    if (!__syncthreads_or(nonzero)) {
+      double2* o2 = reinterpret_cast<double2*>(out);
+      for (int idx = tid; idx < (M / 2) * NL; idx += NT)
+        o2[(r0 + idx / (M / 2)) * (N / 2) + idx % (M / 2)] = make_double2(0.0, 0.0);
+      return;
     }
   } else {
     const int z0 = blockIdx.x * NL, c = blockIdx.y;

@@ -518,12 +518,13 @@ WF_D void r2c_post(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
 // complex values; TPL threads per line with E elements each.  Rows are contiguous in memory,
 // so tiles move as 16-byte vectors along the row (VW elements each).
 // ------------------------------------------------------------------------------------------
-template <class R, int N>
+template <class R> constexpr int z_elems() { return sizeof(cx<R>) == 8 ? 32 : 16; }
+template <class R, int N, int EZ = z_elems<R>()>
 struct ZG {
   using ST = typename Store<R>::T;
   static constexpr int H = N / 2, M = H;
   static constexpr int NL = tile_lines<R>();
-  static constexpr int E = sizeof(cx<R>) == 8 ? 32 : 16;
+  static constexpr int E = EZ;
   static constexpr int TPL = M / E >= 1 ? M / E : 1;
   static constexpr int NT = NL * TPL;
   static constexpr int LD = NL + 1;
@@ -584,11 +585,11 @@ WF_D void zrows_store(const cx<R>* tile, typename G::ST* g, size_t row0, int tid
 // z turn (middle of A p): each (x, y) line: packed -> real (C2R), times D(x, y, z), -> packed.
 // D = nbar w / V_c carries the 1/V_c of the inverse transform.  grid (N*N / NL).
 // ------------------------------------------------------------------------------------------
-template <class R, int N>
-__global__ void __launch_bounds__(ZG<R, N>::NT)
+template <class R, int N, int EZ = z_elems<R>()>
+__global__ void __launch_bounds__(ZG<R, N, EZ>::NT)
 k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
         const double2* __restrict__ twtab, const CgScal* __restrict__ sc, Bat bt) {
-  using G = ZG<R, N>;
+  using G = ZG<R, N, EZ>;
   using SS = typename Store<R>::S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
