@@ -93,7 +93,8 @@ typedef struct {
   double tol;         /* stop when ||b - A s||_2 / ||b||_2 <= tol (recomputed from s) */
   int max_iter;       /* cap on CG iterations (inner iterations summed for WF_MIXED) */
   wf_precision prec;
-  double inner_tol;   /* WF_MIXED: relative reduction asked of each inner solve (<= 0: 1e-4) */
+  double inner_tol;   /* WF_MIXED: largest relative reduction asked of one inner solve (<= 0:
+                         1e-4; each step asks for half the remaining reduction, at most this) */
   int precond;        /* 1: CG in Fourier variables split-preconditioned by S^(1/2)
                          (same canonical system and residual); 0: plain CG on A */
 } wf_solve_opts;

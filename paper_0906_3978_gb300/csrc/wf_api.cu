@@ -99,6 +99,12 @@ wf_status Ctx::stream(int i, cudaStream_t* out) {
   return WF_OK;
 }
 
+wf_status Ctx::capture_stream(cudaStream_t* out) {
+  if (!cap_stream) WF_CUDA(cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking));
+  *out = cap_stream;
+  return WF_OK;
+}
+
 void Ctx::release_prefix(const std::string& prefix) {
   for (auto it = bufs.begin(); it != bufs.end();) {
     if (it->first.compare(0, prefix.size(), prefix) == 0) {
@@ -131,6 +137,8 @@ void Ctx::release_all() {
   pinned.clear();
   for (auto s : streams) cudaStreamDestroy(s);
   streams.clear();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  cap_stream = nullptr;
 }
 
 // P(k) by log-log linear interpolation in the table (end segments extrapolated);

@@ -102,6 +102,7 @@ struct Ctx {
   std::map<int, double2*> twiddles;  // per N: exp(-2 pi i e / (2N)), e < 2N
   std::map<std::string, DevBuf> pinned;  // page-locked host buffers (scalar staging)
   std::vector<cudaStream_t> streams;     // non-blocking streams for interleaved groups
+  cudaStream_t cap_stream = nullptr;     // stream on which CG blocks are captured as graphs
   void* host_pinned = nullptr;       // small pinned staging area for scalars
   struct Server* server = nullptr;   // serving loop, created on first wf_submit
   Prof prof;
@@ -130,6 +131,7 @@ struct Ctx {
   wf_status get_pinned(const std::string& name, size_t bytes, void** out);
   // i-th library-owned non-blocking stream.
   wf_status stream(int i, cudaStream_t* out);
+  wf_status capture_stream(cudaStream_t* out);
   // Free every device and pinned buffer whose name starts with `prefix`.
   void release_prefix(const std::string& prefix);
   void release_all();

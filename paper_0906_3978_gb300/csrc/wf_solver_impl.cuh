@@ -221,6 +221,43 @@ struct GroupCommon : Group {
   std::vector<int> state;      // 0 running, 1 finished
   int phase = 0;
   double inv_vc = 1.0 / (double)V;
+  // CUDA graph of one block of CG iterations (kernel arguments are fixed for the group)
+  cudaGraphExec_t gexec = nullptr;
+  long long glaunches = 0;
+
+  ~GroupCommon() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+  }
+  // Enqueue `body(stream)` on st: directly while the profiler times launches, otherwise as a
+  // graph captured on the first call (on the context's capture stream) and replayed.
+  template <class F>
+  wf_status run_block(Ctx& c, cudaStream_t st, F&& body) {
+    if (c.prof.on) {
+      body(st);
+      return WF_OK;
+    }
+    if (!gexec) {
+      cudaStream_t cs;
+      WF_TRY(c.capture_stream(&cs));
+      const long long before = c.prof.launches;
+      WF_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      body(cs);
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      glaunches = c.prof.launches - before;
+      c.prof.launches = before;
+      if (e != cudaSuccess) {
+        gexec = nullptr;
+        set_last_error("graph capture of the CG block", e);
+        return WF_ERR_CUDA;
+      }
+    }
+    WF_CUDA(cudaGraphLaunch(gexec, st));
+    c.prof.launches += glaunches;
+    return WF_OK;
+  }
 
   wf_status push_scalars(cudaStream_t st) {
     for (int m = 0; m < nb; ++m) hsc[m] = h[m];
@@ -351,10 +388,15 @@ struct GroupFP64 : GroupCommon<N> {
     WF_CUDA(cudaGetLastError());
     return WF_OK;
   }
+  wf_status block(Ctx& c, cudaStream_t st) {
+    return this->run_block(c, st, [&](cudaStream_t s2) {
+      for (int i = 0; i < check_every<N>(); ++i)
+        SP::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, s2);
+    });
+  }
   wf_status enqueue(Ctx& c, cudaStream_t st) override {
     if (phase == 1) {
-      for (int i = 0; i < check_every<N>(); ++i)
-        SP::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, st);
+      WF_TRY(block(c, st));
     } else if (phase == 2) {
       const Bat b = SP::bat();
       c.launch("axpy", 3 * SP::BS * nb, st,
@@ -373,8 +415,7 @@ struct GroupFP64 : GroupCommon<N> {
       WF_TRY(this->push_scalars(st));
       WF_TRY(start_cg(c, RES, st));
       phase = 1;
-      for (int i = 0; i < check_every<N>(); ++i)
-        SP::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, st);
+      WF_TRY(block(c, st));
     }
     WF_CUDA(cudaGetLastError());
     return this->pull_scalars(st);
@@ -503,6 +544,11 @@ struct GroupMixed : GroupCommon<N> {
   wf_status enqueue(Ctx& c, cudaStream_t st) override {
     const Bat bf = SF::bat();
     if (phase == 0) {
+      // Each inner solve aims at the remaining reduction (half of it, for margin) but at most
+      // inner_tol (1e-4 by default) per step, so at least two FP64 refinement steps run for
+      // tol <= 1e-6: the second removes the FP32 rounding error the first leaves in the
+      // low-eigenvalue directions (at 512^3 a single step to 1e-6 saves ~6% of the iterations but
+      // leaves the solution 3.6e-5 from the converged one, two steps 5e-7).
       const double inner_tol_def = 1e-4;
       for (int m = 0; m < nb; ++m) {
         CgScal z{};
@@ -511,7 +557,7 @@ struct GroupMixed : GroupCommon<N> {
           z.done = 4;
         } else {
           const double itol = sys[m]->opts.inner_tol > 0.0 ? sys[m]->opts.inner_tol : inner_tol_def;
-          const double target = std::max(itol, 0.3 * sys[m]->opts.tol / rel[m]);
+          const double target = std::max(itol, 0.5 * sys[m]->opts.tol / rel[m]);
           z.tol2 = target * target;
           z.bb = rel[m] * rel[m] * bb0[m];
           z.max_iter = std::max(1, sys[m]->opts.max_iter - iters[m]);
@@ -531,8 +577,10 @@ struct GroupMixed : GroupCommon<N> {
       phase = 1;
     }
     if (phase == 1) {
-      for (int i = 0; i < check_every<N>(); ++i)
-        SF::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, st);
+      WF_TRY(this->run_block(c, st, [&](cudaStream_t s2) {
+        for (int i = 0; i < check_every<N>(); ++i)
+          SF::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, s2);
+      }));
     } else if (phase == 2) {
       c.launch("axpy", 3 * SF::BS * nb, st,
                [&] { k_axpy_final<<<dim3(152 * 4, nb), 256, 0, st>>>(xh, P0, P1, SF::SPEC, sc, bf); });

@@ -88,12 +88,19 @@ WF_D void load_tw(cx<R>* tw, const double2* tab, int tid, int nt) {
 // in flight at once.  The shared tile has a pad column (LD = NL + 1) that also holds the
 // partner line of column 0.
 // ------------------------------------------------------------------------------------------
+// Elements per thread: 32 (FP32) / 16 (16-byte types) on long lines, fewer on short ones so that
+// a CTA still has about 128 threads.
+template <class R> constexpr int max_elems() { return sizeof(cx<R>) == 8 ? 32 : 16; }
+template <class R> constexpr int elems_for(int M, int NL) {
+  return div_le(M, M * NL / 128 >= max_elems<R>() ? max_elems<R>() : (M * NL / 128 >= 4 ? M * NL / 128 : 4));
+}
+
 template <class R, int N>
 struct XYG {
   using ST = typename Store<R>::T;
   static constexpr int M = N, NH = N / 2;
   static constexpr int NL = xy_lines<R, N>();
-  static constexpr int E = sizeof(cx<R>) == 8 ? 32 : 16;
+  static constexpr int E = elems_for<R>(M, NL);
   static constexpr int TPL = M / E >= 1 ? M / E : 1;
   static constexpr int NT = NL * TPL;
   static constexpr int LD = NL + 1;
@@ -518,8 +525,8 @@ WF_D void r2c_post(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
 // complex values; TPL threads per line with E elements each.  Rows are contiguous in memory,
 // so tiles move as 16-byte vectors along the row (VW elements each).
 // ------------------------------------------------------------------------------------------
-template <class R> constexpr int z_elems() { return sizeof(cx<R>) == 8 ? 32 : 16; }
-template <class R, int N, int EZ = z_elems<R>()>
+template <class R, int N> constexpr int z_elems() { return elems_for<R>(N / 2, tile_lines<R>()); }
+template <class R, int N, int EZ = z_elems<R, N>()>
 struct ZG {
   using ST = typename Store<R>::T;
   static constexpr int H = N / 2, M = H;
@@ -585,7 +592,7 @@ WF_D void zrows_store(const cx<R>* tile, typename G::ST* g, size_t row0, int tid
 // z turn (middle of A p): each (x, y) line: packed -> real (C2R), times D(x, y, z), -> packed.
 // D = nbar w / V_c carries the 1/V_c of the inverse transform.  grid (N*N / NL).
 // ------------------------------------------------------------------------------------------
-template <class R, int N, int EZ = z_elems<R>()>
+template <class R, int N, int EZ = z_elems<R, N>()>
 __global__ void __launch_bounds__(ZG<R, N, EZ>::NT)
 k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
         const double2* __restrict__ twtab, const CgScal* __restrict__ sc, Bat bt) {
