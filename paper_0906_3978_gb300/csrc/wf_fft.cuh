@@ -18,14 +18,20 @@
 
 namespace wf {
 
-// ---- radix plan: 8s first, then 4, 2, then 3s -------------------------------------------
-constexpr int pick_radix(int rem) {
-  return rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 3 == 0 ? 3 : rem;
+// ---- radix plan: the largest power-of-two radix up to RMAX first, then 3s ----------------
+// RMAX (32, 16 or 8) is the largest radix whose butterfly fits in one thread's elements.
+constexpr int pick_radix(int rem, int rmax) {
+  return (rmax >= 32 && rem % 32 == 0) ? 32
+         : (rmax >= 16 && rem % 16 == 0) ? 16
+         : rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : rem % 2 == 0 ? 2 : rem % 3 == 0 ? 3 : rem;
 }
-constexpr int radix_at(int M, int s) {
+constexpr int radix_at(int M, int s, int rmax) {
   int rem = M;
-  for (int i = 0; i < s; ++i) rem /= pick_radix(rem);
-  return pick_radix(rem);
+  for (int i = 0; i < s; ++i) rem /= pick_radix(rem, rmax);
+  return pick_radix(rem, rmax);
+}
+constexpr int rmax_for(int M, int TPL) {
+  return M / TPL >= 32 ? 32 : (M / TPL >= 16 ? 16 : 8);
 }
 
 // ---- small DFTs in registers -------------------------------------------------------------
@@ -70,11 +76,125 @@ template <int DIR, class R> WF_D void dft8(cx<R>* v) {
   v[3] = e[3] + o3;
   v[7] = e[3] - o3;
 }
-template <int RAD, int DIR, class R> WF_D void dft(cx<R>* v) {
+template <int RAD, int DIR, class R> WF_D void dft_small(cx<R>* v) {
   if constexpr (RAD == 2) dft2<DIR>(v);
   else if constexpr (RAD == 3) dft3<DIR>(v);
   else if constexpr (RAD == 4) dft4<DIR>(v);
   else dft8<DIR>(v);
+}
+// cos and sin of 2 pi m / RR at compile time (Taylor series after reduction to the first octant
+// by symmetry), used for the internal twiddles of the composite radices.
+constexpr double k_pi = 3.14159265358979323846;
+constexpr double taylor_sin(double x) {
+  double term = x, sum = x;
+  for (int n = 1; n < 12; ++n) {
+    term *= -x * x / ((2 * n) * (2 * n + 1));
+    sum += term;
+  }
+  return sum;
+}
+constexpr double taylor_cos(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int n = 1; n < 12; ++n) {
+    term *= -x * x / ((2 * n - 1) * (2 * n));
+    sum += term;
+  }
+  return sum;
+}
+// (cos, sin) of 2 pi m / RR, m in [0, RR)
+constexpr double cw_cos(int m, int RR) {
+  m = ((m % RR) + RR) % RR;
+  if (4 * m == RR || 4 * m == 3 * RR) return 0.0;
+  if (2 * m == RR) return -1.0;
+  if (m == 0) return 1.0;
+  if (4 * m > RR && 4 * m < 3 * RR) return -cw_cos(m + RR / 2, RR);  // cos(x) = -cos(x + pi)
+  if (4 * m >= 3 * RR) return cw_cos(RR - m, RR);
+  if (8 * m > RR) return taylor_sin(2.0 * k_pi * (double)(RR / 4 - m) / RR);  // cos(x) = sin(pi/2 - x)
+  return taylor_cos(2.0 * k_pi * (double)m / RR);
+}
+constexpr double cw_sin(int m, int RR) { return cw_cos(m - RR / 4 + RR, RR); }  // sin(x) = cos(x - pi/2)
+
+// v * exp(DIR 2 pi i m / RR) with a compile-time m: exact for quarter turns
+template <int M_, int RR, int DIR, class R>
+WF_D cx<R> twiddle_const(cx<R> v) {
+  constexpr int m = M_ % RR;
+  if constexpr (m == 0) return v;
+  else if constexpr (4 * m == RR) return mul_si<DIR>(v);
+  else if constexpr (2 * m == RR) return cx<R>{-v.x, -v.y};
+  else if constexpr (4 * m == 3 * RR) return mul_si<-DIR>(v);
+  else {
+    const R c = RT<R>::c(cw_cos(m, RR)), sn = RT<R>::c(DIR * cw_sin(m, RR));
+    return cx<R>{v.x * c - v.y * sn, v.x * sn + v.y * c};
+  }
+}
+
+template <int N2, int R1, int R2, int DIR, class R>
+WF_D void comp_column(cx<R>* v) {
+  cx<R> c[R1];
+#pragma unroll
+  for (int n1 = 0; n1 < R1; ++n1) c[n1] = v[R2 * n1 + N2];
+  dft_small<R1, DIR>(c);
+  v[N2] = c[0];
+  if constexpr (R1 > 1) v[R2 * 1 + N2] = twiddle_const<N2 * 1, R1 * R2, DIR>(c[1]);
+  if constexpr (R1 > 2) v[R2 * 2 + N2] = twiddle_const<N2 * 2, R1 * R2, DIR>(c[2]);
+  if constexpr (R1 > 3) v[R2 * 3 + N2] = twiddle_const<N2 * 3, R1 * R2, DIR>(c[3]);
+  if constexpr (N2 + 1 < R2) comp_column<N2 + 1, R1, R2, DIR>(v);
+}
+
+// Radix R1*R2 butterfly (R1 <= 4) as a two-level Cooley-Tukey in registers:
+//   X[k1 + R1 k2] = sum_n2 W_R2^(n2 k2) W_R1R2^(n2 k1) sum_n1 x[R2 n1 + n2] W_R1^(n1 k1)
+// with the internal twiddles W_R1R2^(n2 k1) as compile-time constants.
+template <int R1, int R2, int DIR, class R>
+WF_D void dft_comp(cx<R>* v, const cx<R>*, int) {
+  constexpr int RR = R1 * R2;
+  comp_column<0, R1, R2, DIR>(v);
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) dft_small<R2, DIR>(v + R2 * k1);
+  cx<R> o[RR];
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = v[R2 * k1 + k2];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) v[r] = o[r];
+}
+
+// (previous table-driven form kept out of the build)
+template <int R1, int R2, int DIR, class R>
+WF_D void dft_comp_table(cx<R>* v, const cx<R>* tw, int tstep) {
+  constexpr int RR = R1 * R2;
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    cx<R> c[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) c[n1] = v[R2 * n1 + n2];
+    dft_small<R1, DIR>(c);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      cx<R> t = c[k1];
+      if (n2 * k1 != 0) {
+        cx<R> w = tw[tstep * ((n2 * k1) % RR)];
+        if constexpr (DIR > 0) w = conj(w);
+        t = t * w;
+      }
+      v[R2 * k1 + n2] = t;
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) dft_small<R2, DIR>(v + R2 * k1);
+  cx<R> o[RR];
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = v[R2 * k1 + k2];
+#pragma unroll
+  for (int r = 0; r < RR; ++r) v[r] = o[r];
+}
+// tstep: table stride of W_RAD^1 (only the composite radices use the table)
+template <int RAD, int DIR, class R> WF_D void dft(cx<R>* v, const cx<R>* tw, int tstep) {
+  if constexpr (RAD == 32) dft_comp<4, 8, DIR>(v, tw, tstep);
+  else if constexpr (RAD == 16) dft_comp<4, 4, DIR>(v, tw, tstep);
+  else dft_small<RAD, DIR>(v);
 }
 
 // ---- one Stockham pass -------------------------------------------------------------------
@@ -105,7 +225,7 @@ WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw, bool act) {
           v[m][r] = v[m][r] * w;
         }
       }
-      dft<RAD, DIR>(v[m]);
+      dft<RAD, DIR>(v[m], tw, TWS * (M / RAD));
       const int base = (j / NS) * NS * RAD + k;
 #pragma unroll
       for (int r = 0; r < RAD; ++r) col[(base + r * NS) * LD] = v[m][r];
@@ -114,22 +234,24 @@ WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw, bool act) {
   __syncthreads();
 }
 
-template <class R, int M, int S, int NS, int TPL, int LD, int DIR, int TWS>
+template <class R, int M, int S, int NS, int TPL, int LD, int DIR, int TWS, int RMAX>
 WF_D void fft_passes(cx<R>* col, int t, const cx<R>* tw, bool act) {
   if constexpr (NS < M) {
-    constexpr int RAD = radix_at(M, S);
+    constexpr int RAD = radix_at(M, S, RMAX);
     fft_pass<R, M, RAD, NS, TPL, LD, DIR, TWS>(col, t, tw, act);
-    fft_passes<R, M, S + 1, NS * RAD, TPL, LD, DIR, TWS>(col, t, tw, act);
+    fft_passes<R, M, S + 1, NS * RAD, TPL, LD, DIR, TWS, RMAX>(col, t, tw, act);
   }
 }
 
 // Transform column `col` (stride LD) of length M with TPL threads (thread index t in
 // [0, TPL)).  Every thread of the CTA must call this (it synchronises the CTA); threads with
 // act = false only take part in the barriers.  The twiddle table holds
-// exp(-2 pi i e / (M TWS)), so W_M^e = tw[TWS e].
-template <class R, int M, int TPL, int LD, int DIR, int TWS = 1>
+// exp(-2 pi i e / (M TWS)), so W_M^e = tw[TWS e].  RMAX caps the radix: 8 keeps every
+// butterfly in the small kernels; 16 or 32 allows the composite butterflies (fewer shared
+// memory round trips, more registers), which measured faster only for the z passes.
+template <class R, int M, int TPL, int LD, int DIR, int TWS = 1, int RMAX = 8>
 WF_D void fft_line(cx<R>* col, int t, const cx<R>* tw, bool act = true) {
-  fft_passes<R, M, 0, 1, TPL, LD, DIR, TWS>(col, t, tw, act);
+  fft_passes<R, M, 0, 1, TPL, LD, DIR, TWS, RMAX>(col, t, tw, act);
 }
 
 // Threads per line for a line of length M: one radix-8-or-smaller butterfly group per thread

@@ -613,7 +613,7 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
   const int l = tid % G::NL, t = tid / G::NL;
   c2r_prep<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
-  fft_line<R, G::M, G::TPL, G::LD, +1, 4>(tile + l, t, tw);
+  fft_line<R, G::M, G::TPL, G::LD, +1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
   // real samples 2i, 2i+1 of line l sit in element i: multiply by D, VW elements at a time
   using DV = typename std::conditional<G::VW == 2, float4, double2>::type;  // 2 VW reals of D
 #pragma unroll 4
@@ -641,7 +641,7 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
   }
   (void)sizeof(DV);
   __syncthreads();
-  fft_line<R, G::M, G::TPL, G::LD, -1, 4>(tile + l, t, tw);
+  fft_line<R, G::M, G::TPL, G::LD, -1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
   r2c_post<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
   zrows_store<G>(tile, spec, row0, tid);
@@ -689,7 +689,7 @@ k_zfwd(const double* __restrict__ in, typename Store<R>::T* __restrict__ out,
   }
   __syncthreads();
   const int l = tid % G::NL, t = tid / G::NL;
-  fft_line<R, G::M, G::TPL, G::LD, -1, 4>(tile + l, t, tw);
+  fft_line<R, G::M, G::TPL, G::LD, -1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
   r2c_post<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
   zrows_store<G>(tile, out, row0, tid);
@@ -735,7 +735,7 @@ k_zinv(const typename Store<R>::T* __restrict__ in, double* __restrict__ out,
   const int l = tid % G::NL, t = tid / G::NL;
   c2r_prep<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
-  fft_line<R, G::M, G::TPL, G::LD, +1, 4>(tile + l, t, tw);
+  fft_line<R, G::M, G::TPL, G::LD, +1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
   double2* out2 = reinterpret_cast<double2*>(out);
   AccD acc;
   constexpr int NE = G::NL * G::M;
