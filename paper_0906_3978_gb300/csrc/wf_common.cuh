@@ -35,6 +35,7 @@ WF_D void fast_two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   e = __fsub_rn(b, __fsub_rn(s, a));
 }
+// accurate double-float sum (relative error ~2^-46 even under cancellation)
 WF_D df32 operator+(df32 a, df32 b) {
   float s, e, t, f;
   two_sum(a.hi, b.hi, s, e);

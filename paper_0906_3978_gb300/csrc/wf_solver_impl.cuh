@@ -219,6 +219,7 @@ struct GroupCommon : Group {
   std::vector<CgScal> h;       // host copy of the scalars
   std::vector<double> bb0, sumw, rel;
   std::vector<int> state;      // 0 running, 1 finished
+  std::vector<int> bad;        // 1: rejected input (status already set)
   int phase = 0;
   double inv_vc = 1.0 / (double)V;
   // CUDA graph of one block of CG iterations (kernel arguments are fixed for the group)
@@ -293,10 +294,17 @@ static wf_status group_sums(Ctx& c, GroupCommon<N>& g, int npart, cudaStream_t s
   g.read_scalars();
   g.sumw.resize(g.nb);
   g.bb0.resize(g.nb);
+  g.bad.assign(g.nb, 0);
   for (int m = 0; m < g.nb; ++m) {
     g.sumw[m] = g.h[m].aux[0];
     g.bb0[m] = g.h[m].aux[1];
-    if (!(g.sumw[m] > 0.0)) return WF_ERR_ARG;
+    // an empty window or a non-finite w or b is this system's argument error, not the batch's
+    if (!(g.sumw[m] > 0.0) || !std::isfinite(g.sumw[m]) || !std::isfinite(g.bb0[m])) {
+      g.bad[m] = 1;
+      g.sumw[m] = 1.0;
+      g.bb0[m] = 0.0;
+      if (g.info[m]) *g.info[m] = wf_solve_info{0, 0, 0.0, g.sys[m]->nbar, WF_ERR_ARG};
+    }
   }
   return WF_OK;
 }
@@ -364,12 +372,13 @@ struct GroupFP64 : GroupCommon<N> {
       h[m].max_iter = sys[m]->opts.max_iter;
       h[m].tol2 = sys[m]->opts.tol * sys[m]->opts.tol;
       h[m].bb = bb0[m];
+      if (this->bad[m]) h[m].done = 4;
     }
     WF_TRY(this->push_scalars(st));
     c.launch("make_D", 16.0 * V * nb, st, [&] { k_make_D<double><<<dim3(152 * 4, nb), 256, 0, st>>>(W, D, sc, inv_vc, V); });
     WF_CUDA(cudaMemsetAsync(xh, 0, nb * SPEC * sizeof(ST), st));
     rel.assign(nb, 1.0);
-    state.assign(nb, 0);
+    state.assign(this->bad.begin(), this->bad.end());
     restarts.assign(nb, 0);
     WF_TRY(start_cg(c, B, st));
     phase = 1;
@@ -529,11 +538,11 @@ struct GroupMixed : GroupCommon<N> {
     WF_CUDA(cudaMemsetAsync(S, 0, nb * V * sizeof(double), st));
     WF_CUDA(cudaMemcpyAsync(RES, B, nb * V * sizeof(double), cudaMemcpyDeviceToDevice, st));
     rel.assign(nb, 1.0);
-    state.assign(nb, 0);
+    state.assign(this->bad.begin(), this->bad.end());
     outer.assign(nb, 0);
     iters.assign(nb, 0);
     for (int m = 0; m < nb; ++m)
-      if (bb0[m] == 0.0) {
+      if (bb0[m] == 0.0 && !state[m]) {
         state[m] = 1;
         rel[m] = 0.0;
         if (info[m]) *info[m] = wf_solve_info{0, 0, 0.0, sys[m]->nbar, WF_OK};

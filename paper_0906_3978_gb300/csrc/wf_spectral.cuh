@@ -95,12 +95,12 @@ template <class R> constexpr int elems_for(int M, int NL) {
   return div_le(M, M * NL / 128 >= max_elems<R>() ? max_elems<R>() : (M * NL / 128 >= 4 ? M * NL / 128 : 4));
 }
 
-template <class R, int N>
+template <class R, int N, int EX = elems_for<R>(N, xy_lines<R, N>())>
 struct XYG {
   using ST = typename Store<R>::T;
   static constexpr int M = N, NH = N / 2;
   static constexpr int NL = xy_lines<R, N>();
-  static constexpr int E = elems_for<R>(M, NL);
+  static constexpr int E = EX;
   static constexpr int TPL = M / E >= 1 ? M / E : 1;
   static constexpr int NT = NL * TPL;
   static constexpr int LD = NL + 1;
@@ -168,11 +168,11 @@ WF_D void tile_store(const cx<R>* tile, typename G::ST* g, size_t rowstride, int
 }
 
 // y pass: complex FFT along y of every (x, kz) line; in place.  grid (N/2 / NL, N).
-template <class R, int N, int DIR>
-__global__ void __launch_bounds__(XYG<R, N>::NT)
+template <class R, int N, int DIR, int EX = elems_for<R>(N, xy_lines<R, N>())>
+__global__ void __launch_bounds__(XYG<R, N, EX>::NT)
 k_ypass(typename Store<R>::T* __restrict__ spec, const double2* __restrict__ twtab,
         const CgScal* __restrict__ sc, Bat bt) {
-  using G = XYG<R, N>;
+  using G = XYG<R, N, EX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;

@@ -373,3 +373,55 @@ def test_serving_errors():
         assert st == wf.OK
         st, _ = ctx.poll(rid, timeout_ms=0)          # released after the final poll
         assert st == wf.ERR_ARG
+
+
+# ------------------------------------------------------------------------ failure handling
+def test_budget_exceeded_is_reported():
+    """A context whose HBM budget cannot hold the workspaces returns WF_ERR_OOM, and a
+    following call on a context with room succeeds."""
+    wf.build()
+    pr, w, b, nbar, tab = _solve_inputs("c1", 32)
+    with wf.Context(0, hbm_budget=1 << 20) as small:
+        s, info = small.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8, check=False)
+        assert info.status == wf.ERR_OOM
+    with wf.Context(0) as c:
+        s, info = c.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8)
+        assert info.status == wf.OK
+
+
+def test_serving_admission_under_tight_budget():
+    """With room for about two systems at a time, requests queue and are admitted a few at a time,
+    and all complete."""
+    wf.build()
+    w, b, nbar, box, k, p = _serve_inputs(32, 3020)
+    one = 32 ** 3 * 8 * 20
+    with wf.Context(0, hbm_budget=one) as ctx:
+        ids = [ctx.submit(w, nbar, b, box, k, p, tol=1e-8, prec=wf.MIXED) for _ in range(4)]
+        outs = []
+        for rid in ids:
+            s = np.empty(32 ** 3)
+            st, info = ctx.poll(rid, timeout_ms=-1, s_out=s)
+            assert st == wf.OK
+            outs.append(s)
+        for s in outs[1:]:
+            assert np.array_equal(s, outs[0])
+
+
+@pytest.mark.parametrize("prec", [wf.FP64, wf.MIXED])
+def test_non_finite_input_is_rejected(prec):
+    """A NaN in b or w is that system's argument error; batch-mates still solve."""
+    pr, w, b, nbar, tab = _solve_inputs("c1", 16)
+    bn = b.copy()
+    bn[3, 4, 5] = np.nan
+    wn = w.copy()
+    wn[1, 2, 3] = np.inf
+    with wf.Context(0) as c:
+        s, info = c.solve(gpu(w), nbar, gpu(bn), pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=prec, check=False)
+        assert info.status == wf.ERR_ARG
+        probs = [dict(w=gpu(w), nbar=nbar, b=gpu(bn), box=pr.box, pk_k=pr.pk_k, pk_p=pr.pk_p, prec=prec),
+                 dict(w=gpu(wn), nbar=nbar, b=gpu(b), box=pr.box, pk_k=pr.pk_k, pk_p=pr.pk_p, prec=prec),
+                 dict(w=gpu(w), nbar=nbar, b=gpu(b), box=pr.box, pk_k=pr.pk_k, pk_p=pr.pk_p, prec=prec, tol=1e-8)]
+        st, outs, infos = c.solve_batch(probs)
+        assert st == wf.ERR_ARG
+        assert [i.status for i in infos] == [wf.ERR_ARG, wf.ERR_ARG, wf.OK]
+        assert infos[2].rel_residual <= 1e-8
