@@ -125,6 +125,17 @@ const char* wf_status_string(wf_status s);
 /* Text of the last CUDA error seen by this thread (empty string if none). */
 const char* wf_last_error(void);
 
+/* Choose how the FP32 transforms of a CG iteration (the mixed-precision inner solves) run
+ * between the two x passes (Sec. 2.5.1: the data term applied between the inverse and forward
+ * transforms of the signal).  on = 0 (the default): three passes (inverse y, the real z
+ * transforms with the multiplication by nbar w in between, forward y).  on = 1: where the grid
+ * size allows (n = 128, 192, 256, 384, 512), one kernel per x-plane on a thread-block cluster
+ * does all three, holding the plane in the cluster's distributed shared memory (fewer HBM
+ * bytes, but on GB300 it measures slower than the three passes).  Both compute the same
+ * operator with the same arithmetic; the choice affects speed and, where the radix plans
+ * differ, the FP32 rounding.  Applies to solves started after the call. */
+wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
+
 /* ---- tracing ------------------------------------------------------------------------ */
 
 /* Reset the context's launch counters and enable (1) or disable (0) per-kernel timing.

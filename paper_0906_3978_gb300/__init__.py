@@ -95,11 +95,13 @@ def lib():
         L.wf_submit.argtypes = [c_void_p, P(Grid), P(Power), c_void_p, c_double, c_void_p, P(SolveOpts), P(c_uint64)]
         L.wf_poll.argtypes = [c_void_p, c_uint64, c_int, c_void_p, P(SolveInfo)]
         L.wf_profile.argtypes = [c_void_p, c_int]
+        L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
         L.wf_profile_read.argtypes = [c_void_p, P(c_int64), P(c_int)]
         L.wf_profile_class.argtypes = [c_void_p, c_int, ctypes.c_char_p, c_int, P(c_int64), P(c_double),
                                        P(c_double)]
         for name in ("wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve", "wf_solve_batch",
-                     "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class"):
+                     "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
+                     "wf_set_fused_planes"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -284,6 +286,14 @@ class Context:
         return st, outs, list(infos)
 
     # ---- tracing ------------------------------------------------------------------------
+    def set_fused_planes(self, on: bool = True):
+        """FP32 y / z / y transforms as one cluster kernel per x-plane (True) or as three
+        separate passes (False, the default), for solves started afterwards
+        (wf_set_fused_planes)."""
+        st = lib().wf_set_fused_planes(self._h, 1 if on else 0)
+        if st != OK:
+            raise WfError(st, "wf_set_fused_planes")
+
     def profile(self, enable: bool = True):
         """Reset launch counters; enable/disable per-kernel CUDA-event timing (wf_profile)."""
         st = lib().wf_profile(self._h, 1 if enable else 0)

@@ -384,6 +384,14 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   return s;
 }
 
+wf_status wf_set_fused_planes(wf_ctx* ctx, int on) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  c->fused_planes = on != 0;
+  return WF_OK;
+}
+
 wf_status wf_profile(wf_ctx* ctx, int enable) {
   if (!ctx) return WF_ERR_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);

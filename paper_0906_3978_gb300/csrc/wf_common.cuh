@@ -69,6 +69,12 @@ WF_D df32 df_from_double(double v) {
 }
 WF_D double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
 
+// Ask L2 to fetch [p, p + bytes) from HBM ahead of its use (a bulk prefetch: no registers or
+// shared memory held, no completion to wait for).  p and bytes must be multiples of 16.
+WF_D void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // ------------------------------------------------------------------------------------------
 // real-type traits: constants and conversion to/from the FP64 / FP32 storage types
 // ------------------------------------------------------------------------------------------
@@ -136,7 +142,9 @@ template <> struct Store<float> { using T = float2; using S = float; };
 // ------------------------------------------------------------------------------------------
 // dot-product accumulation.  For FP32 data the products are formed exactly (two-product) and
 // accumulated in double-float; for FP64 data in FP64.  Either way the per-thread partial is
-// returned as a double and the cross-thread sums are FP64.
+// returned as a double and the cross-thread sums are FP64.  Sums whose terms are all >= 0 (norms,
+// <p, m p>, sum D T^2) add a 16-byte vector's few terms in the storage type first and pass that
+// partial to add(): no cancellation, so the relative error stays a few units of FP32 rounding.
 // ------------------------------------------------------------------------------------------
 struct AccD {
   double s = 0.0;

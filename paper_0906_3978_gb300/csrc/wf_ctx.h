@@ -105,6 +105,7 @@ struct Ctx {
   cudaStream_t cap_stream = nullptr;     // stream on which CG blocks are captured as graphs
   void* host_pinned = nullptr;       // small pinned staging area for scalars
   struct Server* server = nullptr;   // serving loop, created on first wf_submit
+  bool fused_planes = false;         // FP32 y / z / y passes as one cluster kernel where possible
   Prof prof;
 
   // Launch `f` (which enqueues one kernel on st), counting it and, when profiling, timing it.

@@ -159,37 +159,6 @@ WF_D void dft_comp(cx<R>* v, const cx<R>*, int) {
   for (int r = 0; r < RR; ++r) v[r] = o[r];
 }
 
-// (previous table-driven form kept out of the build)
-template <int R1, int R2, int DIR, class R>
-WF_D void dft_comp_table(cx<R>* v, const cx<R>* tw, int tstep) {
-  constexpr int RR = R1 * R2;
-#pragma unroll
-  for (int n2 = 0; n2 < R2; ++n2) {
-    cx<R> c[R1];
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) c[n1] = v[R2 * n1 + n2];
-    dft_small<R1, DIR>(c);
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) {
-      cx<R> t = c[k1];
-      if (n2 * k1 != 0) {
-        cx<R> w = tw[tstep * ((n2 * k1) % RR)];
-        if constexpr (DIR > 0) w = conj(w);
-        t = t * w;
-      }
-      v[R2 * k1 + n2] = t;
-    }
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < R1; ++k1) dft_small<R2, DIR>(v + R2 * k1);
-  cx<R> o[RR];
-#pragma unroll
-  for (int k1 = 0; k1 < R1; ++k1)
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = v[R2 * k1 + k2];
-#pragma unroll
-  for (int r = 0; r < RR; ++r) v[r] = o[r];
-}
 // tstep: table stride of W_RAD^1 (only the composite radices use the table)
 template <int RAD, int DIR, class R> WF_D void dft(cx<R>* v, const cx<R>* tw, int tstep) {
   if constexpr (RAD == 32) dft_comp<4, 8, DIR>(v, tw, tstep);
@@ -197,9 +166,16 @@ template <int RAD, int DIR, class R> WF_D void dft(cx<R>* v, const cx<R>* tw, in
   else dft_small<RAD, DIR>(v);
 }
 
+// ---- element addressing ------------------------------------------------------------------
+// A line's element i lives at col[map(i)]: Strided<LD> for the side-by-side tiles above, other
+// maps for swizzled or blocked tiles.
+template <int LD> struct Strided {
+  WF_D int operator()(int i) const { return i * LD; }
+};
+
 // ---- one Stockham pass -------------------------------------------------------------------
-template <class R, int M, int RAD, int NS, int TPL, int LD, int DIR, int TWS>
-WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw, bool act) {
+template <class R, int M, int RAD, int NS, int TPL, int DIR, int TWS, class MAP>
+WF_D void fft_pass(cx<R>* col, const MAP& map, int t, const cx<R>* tw, bool act) {
   constexpr int NB = M / RAD;
   constexpr int PER = (NB + TPL - 1) / TPL;
   cx<R> v[PER][RAD];
@@ -208,7 +184,7 @@ WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw, bool act) {
     const int j = t + m * TPL;
     if (act && ((NB % TPL) == 0 || j < NB)) {
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) v[m][r] = col[(j + r * NB) * LD];
+      for (int r = 0; r < RAD; ++r) v[m][r] = col[map(j + r * NB)];
     }
   }
   __syncthreads();
@@ -228,30 +204,35 @@ WF_D void fft_pass(cx<R>* col, int t, const cx<R>* tw, bool act) {
       dft<RAD, DIR>(v[m], tw, TWS * (M / RAD));
       const int base = (j / NS) * NS * RAD + k;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) col[(base + r * NS) * LD] = v[m][r];
+      for (int r = 0; r < RAD; ++r) col[map(base + r * NS)] = v[m][r];
     }
   }
   __syncthreads();
 }
 
-template <class R, int M, int S, int NS, int TPL, int LD, int DIR, int TWS, int RMAX>
-WF_D void fft_passes(cx<R>* col, int t, const cx<R>* tw, bool act) {
+template <class R, int M, int S, int NS, int TPL, int DIR, int TWS, int RMAX, class MAP>
+WF_D void fft_passes(cx<R>* col, const MAP& map, int t, const cx<R>* tw, bool act) {
   if constexpr (NS < M) {
     constexpr int RAD = radix_at(M, S, RMAX);
-    fft_pass<R, M, RAD, NS, TPL, LD, DIR, TWS>(col, t, tw, act);
-    fft_passes<R, M, S + 1, NS * RAD, TPL, LD, DIR, TWS, RMAX>(col, t, tw, act);
+    fft_pass<R, M, RAD, NS, TPL, DIR, TWS>(col, map, t, tw, act);
+    fft_passes<R, M, S + 1, NS * RAD, TPL, DIR, TWS, RMAX>(col, map, t, tw, act);
   }
 }
 
-// Transform column `col` (stride LD) of length M with TPL threads (thread index t in
-// [0, TPL)).  Every thread of the CTA must call this (it synchronises the CTA); threads with
-// act = false only take part in the barriers.  The twiddle table holds
+// Transform the line whose element i is at col[map(i)], of length M, with TPL threads (thread
+// index t in [0, TPL)).  Every thread of the CTA must call this (it synchronises the CTA);
+// threads with act = false only take part in the barriers.  The twiddle table holds
 // exp(-2 pi i e / (M TWS)), so W_M^e = tw[TWS e].  RMAX caps the radix: 8 keeps every
 // butterfly in the small kernels; 16 or 32 allows the composite butterflies (fewer shared
 // memory round trips, more registers), which measured faster only for the z passes.
+template <class R, int M, int TPL, int DIR, int TWS = 1, int RMAX = 8, class MAP>
+WF_D void fft_line_map(cx<R>* col, const MAP& map, int t, const cx<R>* tw, bool act = true) {
+  fft_passes<R, M, 0, 1, TPL, DIR, TWS, RMAX>(col, map, t, tw, act);
+}
+// the same for the line col[i * LD]
 template <class R, int M, int TPL, int LD, int DIR, int TWS = 1, int RMAX = 8>
 WF_D void fft_line(cx<R>* col, int t, const cx<R>* tw, bool act = true) {
-  fft_passes<R, M, 0, 1, TPL, LD, DIR, TWS, RMAX>(col, t, tw, act);
+  fft_passes<R, M, 0, 1, TPL, DIR, TWS, RMAX>(col, Strided<LD>{}, t, tw, act);
 }
 
 // Threads per line for a line of length M: one radix-8-or-smaller butterfly group per thread

@@ -18,6 +18,8 @@
 //   z turn  : IFFT_z, times D / V_c, FFT_z
 //   y pass  : FFT_y
 //   x pass 2: FFT_x, q = m p + c T, <p, q>
+// (for FP32 at the sizes plane_cs() lists, the three middle passes run as one thread-block
+// cluster kernel per x-plane, k_plane_turn)
 //   finisher: alpha;  update: r -= alpha q, <r, r>, ||C^-1 r||^2;  finisher: beta, stop test
 #pragma once
 #include <algorithm>
@@ -26,6 +28,7 @@
 
 #include "wf_ctx.h"
 #include "wf_solver_group.h"
+#include "wf_plane.cuh"
 #include "wf_spectral.cuh"
 
 namespace wf {
@@ -61,7 +64,9 @@ struct Spec {
   static constexpr size_t SPEC = (size_t)N * N * NH;  // complex elements of a spectrum
   static constexpr size_t V = (size_t)N * N * N;
   static constexpr int TAB = 3 * (N / 2) * (N / 2) + 1;
-  static constexpr int NPART = GXY > GZ ? (GXY > 2 * GU ? GXY : 2 * GU) : (GZ > 2 * GU ? GZ : 2 * GU);
+  // partial sums per system: the largest of GXY + (z-turn or plane-kernel blocks), GZ, 2 GU
+  static constexpr int NMID = GZ > N * 8 ? GZ : N * 8;
+  static constexpr int NPART = GXY + NMID > 2 * GU ? GXY + NMID : 2 * GU;
   static dim3 gxy(int nb) { return dim3(NH / NLxy, N, nb); }
   static dim3 gz(int nb) { return dim3(GZ, 1, nb); }
   static Bat bat() { return Bat{SPEC, V, TAB, NPART}; }
@@ -69,6 +74,8 @@ struct Spec {
   // algorithmic bytes of one launch per system (DRAM traffic the pass cannot avoid)
   static constexpr double BS = (double)SPEC * sizeof(ST);
   static constexpr double BV = (double)V;
+  // cluster size of the fused y / z / y plane kernel (0: not available at this size)
+  static constexpr int PCS = plane_cs<R, N>(), PE = plane_e<R, N>();
 
   static cudaError_t attrs() {
     static bool done = false;
@@ -77,13 +84,14 @@ struct Spec {
 #define WF_A(k, b) if (e == cudaSuccess) e = set_smem(k, b)
     WF_A((k_ypass<R, N, -1>), SMxy);
     WF_A((k_ypass<R, N, +1>), SMxy);
-    WF_A((k_cg_xinv<R, N>), SMxy);
-    WF_A((k_cg_xfwd<R, N, true>), SMxy);
-    WF_A((k_cg_xfwd<R, N, false>), SMxy);
+    WF_A((k_cg_xinv<R, N, true>), SMxy);
+    WF_A((k_cg_xinv<R, N, false>), SMxy);
+    WF_A((k_cg_xfwd<R, N>), SMxy);
     WF_A((k_xmul<R, N, true, false, true>), SMxy);
     WF_A((k_xmul<R, N, false, true, false>), SMxy);
     WF_A((k_xmul<R, N, true, true, false>), SMxy);
     WF_A((k_zturn<R, N>), SMz);
+    if constexpr (PCS > 0) WF_A((k_plane_turn<R, N, PCS, PE>), (PlaneG<R, N, PCS, PE>::SMEM));
     WF_A((k_zfwd<R, N, true>), SMz);
     WF_A((k_zfwd<R, N, false>), SMz);
     WF_A((k_zinv<R, N, ZI_STORE>), SMz);
@@ -127,19 +135,32 @@ struct Spec {
                         const SS* mtab, bool unit_m, const double2* tw, double* part, CgScal* sc, double inv_vc,
                         cudaStream_t st) {
     const Bat b = bat();
-    c.launch("cg_xinv", 6 * BS * nb, st,
-             [&] { k_cg_xinv<R, N><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, tw, sc, b); });
-    c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
-    c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st,
-             [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, sc, b); });
-    c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
-    c.launch("cg_xfwd", 3 * BS * nb, st, [&] {
-      if (unit_m) k_cg_xfwd<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(T, P0, P1, q, ctab, mtab, tw, part, sc, b);
-      else k_cg_xfwd<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(T, P0, P1, q, ctab, mtab, tw, part, sc, b);
+    c.launch("cg_xinv", 6 * BS * nb, st, [&] {
+      if (unit_m) k_cg_xinv<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, b);
+      else k_cg_xinv<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, b);
     });
-    c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, GXY, sc, b); });
-    c.launch("cg_update", 3 * BS * nb, st,
-             [&] { k_update<R, N><<<dim3(GU, nb), 256, 0, st>>>(r, q, ctab, part, sc, b); });
+    int nmid = GZ;  // blocks that sum the data term of <p, A p> into part[GXY ...]
+    bool fused = false;
+    if constexpr (PCS > 0) {
+      if (c.fused_planes) {
+        c.launch("plane_turn", (2 * BS + sizeof(SS) * BV) * nb, st,
+                 [&] { plane_turn_launch<R, N, PCS, PE>(T, D, tw, part + GXY, sc, b, nb, st); });
+        nmid = N * PCS;
+        fused = true;
+      }
+    }
+    if (!fused) {
+      c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
+      c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st,
+               [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, part + GXY, sc, b); });
+      c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
+    }
+    c.launch("cg_xfwd", 2 * BS * nb, st, [&] { k_cg_xfwd<R, N><<<gxy(nb), NTx, SMxy, st>>>(T, q, ctab, tw, sc, b); });
+    c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, GXY, nmid, sc, b); });
+    c.launch("cg_update", 4 * BS * nb, st, [&] {
+      if (unit_m) k_update<R, N, true><<<dim3(GU, nb), 256, 0, st>>>(r, P0, P1, q, ctab, mtab, part, sc, b);
+      else k_update<R, N, false><<<dim3(GU, nb), 256, 0, st>>>(r, P0, P1, q, ctab, mtab, part, sc, b);
+    });
     c.launch("fin", 0, st, [&] { k_fin_beta<<<nb, 1024, 0, st>>>(part, GU, inv_vc, sc, b); });
   }
 };

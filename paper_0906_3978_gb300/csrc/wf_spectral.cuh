@@ -222,21 +222,29 @@ WF_D void tile_mul(cx<R>* tile, int kz0, int ky_s, const TAB* tab, int tid) {
 
 // ------------------------------------------------------------------------------------------
 // CG x pass 1 (start of A p):  p_new = r + beta p_old;  x += alpha_prev p_old;
-//                              T = IFFT_x( c (.) p_new )                grid (N/2 / NL, N)
+//                              T = IFFT_x( c (.) p_new );  partial of <p_new, m p_new>
+// grid (N/2 / NL, N).  <p, A p> = <p, m p> + <c p, D (c p)>: the first term is summed here,
+// where p_new is formed, the second by the z turn, where the real field of c p is at hand.
+// For the packed column the m term is m0 |P0|^2 + mN |PN|^2 of the two planes it holds,
+// P0 = (Z + conj Z(-k)) / 2 and PN = (Z - conj Z(-k)) / 2i (Z(-k) from the partner line).
+// UNIT_M: m = 1 at every k != 0 (the preconditioned system), so m is read only on column 0.
 // ------------------------------------------------------------------------------------------
-template <class R, int N>
+template <class R, int N, bool UNIT_M>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
 k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, typename Store<R>::T* P1,
           typename Store<R>::T* __restrict__ x, typename Store<R>::T* __restrict__ T,
-          const typename Store<R>::S* __restrict__ ctab, const double2* __restrict__ twtab,
-          const CgScal* __restrict__ sc, Bat bt) {
+          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
+          const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+          Bat bt) {
   using G = XYG<R, N>;
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
   using VT = typename G::VT;
+  constexpr int NH = G::NH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
+  __shared__ double red[32];
   const int z = blockIdx.z;
   sc += z;
   if (sc->done) return;
@@ -247,26 +255,39 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
   x += z * bt.spec;
   T += z * bt.spec;
   ctab += z * bt.tab;
+  mtab += z * bt.tab;
+  partials += z * bt.part;
   const int tid = threadIdx.x;
   const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
   const int ky_s = sfreq(ky, N);
   const SS beta = (SS)sc->beta, alpha_prev = (SS)sc->alpha_prev;
   load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
-  const size_t rowstride = (size_t)N * G::NH;
-  const size_t base = (size_t)ky * G::NH + kz0;
+  const size_t rowstride = (size_t)N * NH;
+  const size_t base = (size_t)ky * NH + kz0;
+  typename AccFor<SS>::T acc;  // <p_new, m p_new> over the columns kz != 0 (weight 2)
   constexpr int CH = 4;  // vectors per thread whose three loads are in flight together
   constexpr int SPV = sizeof(VT) / sizeof(SS);
 #pragma unroll
   for (int k0 = 0; k0 < G::PER; k0 += CH) {
     VT rv[CH], pv[CH], xv[CH];
+    SS cv[CH][G::VW], mv[CH][G::VW];
 #pragma unroll
     for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
       const int idx = tid + (k0 + k) * G::NT;
       if (G::EVEN || idx < G::NVEC) {
-        const size_t e = base + (size_t)(idx / G::NV) * rowstride + (idx % G::NV) * G::VW;
+        const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+        const size_t e = base + (size_t)i * rowstride + c0;
         rv[k] = *reinterpret_cast<const VT*>(r + e);
         pv[k] = *reinterpret_cast<const VT*>(pold + e);
         xv[k] = *reinterpret_cast<const VT*>(x + e);
+        const int kxs = sfreq(i, N);
+#pragma unroll
+        for (int u = 0; u < G::VW; ++u) {
+          const int kz = kz0 + c0 + u;
+          const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
+          cv[k][u] = ctab[n2];
+          mv[k][u] = UNIT_M ? (SS)1 : mtab[n2];
+        }
       }
     }
 #pragma unroll
@@ -287,12 +308,24 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
         }
         *reinterpret_cast<VT*>(pnew + e) = nv;
         *reinterpret_cast<VT*>(x + e) = xv[k];
+        // the tile gets c (.) p_new; column kz = 0 stays raw for the packed-column combine.  The
+        // terms of <p, m p> are >= 0, so a vector's few terms are summed in the storage type
+        // before entering the accumulator.
+        SS part = 0;
+#pragma unroll
+        for (int u = 0; u < G::VW; ++u)
+          if (kz0 + c0 + u != 0) {
+            part += (SS)2 * mv[k][u] * (ns[2 * u] * ns[2 * u] + ns[2 * u + 1] * ns[2 * u + 1]);
+            ns[2 * u] *= cv[k][u];
+            ns[2 * u + 1] *= cv[k][u];
+          }
+        acc.add(part);
         vec_to_tile<G>(tile, i, c0, nv);
       }
     }
   }
   if (kz0 == 0) {  // partner line of column 0: p_new at (kx, -ky, 0), recomputed from inputs
-    const size_t pb = (size_t)((N - ky) % N) * G::NH;
+    const size_t pb = (size_t)((N - ky) % N) * NH;
     for (int i = tid; i < G::M; i += G::NT) {
       const size_t e = pb + (size_t)i * rowstride;
       const ST rv = r[e], po = pold[e];
@@ -303,42 +336,50 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
     }
   }
   __syncthreads();
-  tile_mul<G>(tile, kz0, ky_s, ctab, tid);
-  if (kz0 == 0) combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
-  else __syncthreads();
+  if (kz0 == 0) {
+    // m term of the packed column (weight 1), from the raw column and its partner line
+    for (int kx = tid; kx < N; kx += G::NT) {
+      const int kxs = sfreq(kx, N);
+      const int n2 = kxs * kxs + ky_s * ky_s;
+      const cx<R> zc = tile[kx * G::LD];
+      const cx<R> zp = tile[((N - kx) % N) * G::LD + G::NL];
+      const SS zr = (SS)RT<R>::to_d(zc.x), zi = (SS)RT<R>::to_d(zc.y);
+      const SS pr = (SS)RT<R>::to_d(zp.x), pi = (SS)RT<R>::to_d(zp.y);
+      const SS h = (SS)0.5;
+      const SS a0 = h * (zr + pr), b0 = h * (zi - pi);  // P0
+      const SS aN = h * (zi + pi), bN = h * (pr - zr);  // PN
+      const SS m0 = mtab[n2], mN = mtab[n2 + NH * NH];
+      acc.add(m0 * (a0 * a0 + b0 * b0) + mN * (aN * aN + bN * bN));
+    }
+    combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
+  }
   fft_line<R, G::M, G::TPL, G::LD, +1>(tile + tid % G::NL, tid / G::NL, tw);
   tile_store<G>(tile, T + base, rowstride, tid);
+  const double sum = block_sum(acc.get(), red);
+  if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sum;
 }
 
 // ------------------------------------------------------------------------------------------
-// CG x pass 2 (end of A p):  T^ = FFT_x(T);  q = m (.) p + c (.) T^;  partial <p, q>
-// UNIT_M: m = 1 at every k != 0 (the preconditioned system), so the m table is not read there.
+// CG x pass 2 (end of A p):  out = FFT_x(T), with c applied to the packed column only (it needs
+// the partner line); the update applies c to the other columns, where it reads c(k) anyway,
+// and forms q = m p + c T^.  grid (N/2 / NL, N).  out != T: the partner line is read from T.
 // ------------------------------------------------------------------------------------------
-template <class R, int N, bool UNIT_M>
+template <class R, int N>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
-k_cg_xfwd(const typename Store<R>::T* __restrict__ T, const typename Store<R>::T* P0,
-          const typename Store<R>::T* P1, typename Store<R>::T* __restrict__ q,
-          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
-          const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
-          Bat bt) {
+k_cg_xfwd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ out,
+          const typename Store<R>::S* __restrict__ ctab, const double2* __restrict__ twtab,
+          const CgScal* __restrict__ sc, Bat bt) {
   using G = XYG<R, N>;
-  using ST = typename Store<R>::T;
-  using SS = typename Store<R>::S;
-  using VT = typename G::VT;
   constexpr int NH = G::NH;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
-  __shared__ double red[32];
   const int z = blockIdx.z;
   sc += z;
   if (sc->done) return;
-  const ST* __restrict__ p = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;  // this iteration's p_new
   T += z * bt.spec;
-  q += z * bt.spec;
+  out += z * bt.spec;
   ctab += z * bt.tab;
-  mtab += z * bt.tab;
-  partials += z * bt.part;
   const int tid = threadIdx.x;
   const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
   const int ky_s = sfreq(ky, N);
@@ -351,68 +392,11 @@ k_cg_xfwd(const typename Store<R>::T* __restrict__ T, const typename Store<R>::T
     for (int i = tid; i < G::M; i += G::NT) tile[i * G::LD + G::NL] = ld_c<R>(T + (size_t)pky * NH + (size_t)i * rowstride);
   __syncthreads();
   fft_line<R, G::M, G::TPL, G::LD, -1>(tile + tid % G::NL, tid / G::NL, tw);
-  if (kz0 == 0) {  // transform the partner line too, then combine column 0
+  if (kz0 == 0) {  // transform the partner line too, then apply c to column 0 as a packed pair
     fft_line<R, G::M, G::TPL, G::LD, -1>(tile + G::NL, tid / G::NL, tw, tid % G::NL == 0);
     combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
   }
-  typename AccFor<SS>::T acc;
-  // epilogue in chunks: the p vectors and table entries of a chunk are loaded together
-  constexpr int CH = 8;
-#pragma unroll
-  for (int k0 = 0; k0 < G::PER; k0 += CH) {
-    VT pv[CH];
-    SS cv[CH][G::VW], mv[CH][G::VW];
-#pragma unroll
-    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
-      const int idx = tid + (k0 + k) * G::NT;
-      if (!(G::EVEN || idx < G::NVEC)) continue;
-      const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
-      const int kxs = sfreq(i, N);
-      pv[k] = *reinterpret_cast<const VT*>(p + base + (size_t)i * rowstride + c0);
-#pragma unroll
-      for (int u = 0; u < G::VW; ++u) {
-        const int kz = kz0 + c0 + u;
-        const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
-        cv[k][u] = ctab[n2];
-        mv[k][u] = UNIT_M ? (SS)1 : mtab[n2];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
-      const int idx = tid + (k0 + k) * G::NT;
-      if (!(G::EVEN || idx < G::NVEC)) continue;
-      const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
-      const int kxs = sfreq(i, N);
-      const size_t e = base + (size_t)i * rowstride + c0;
-      const SS* ps = reinterpret_cast<const SS*>(&pv[k]);
-      VT qv;
-      SS* qs = reinterpret_cast<SS*>(&qv);
-#pragma unroll
-      for (int u = 0; u < G::VW; ++u) {
-        const int kz = kz0 + c0 + u;
-        const cx<R> t = tile[i * G::LD + c0 + u];
-        if (kz == 0) {
-          // packed column: m-term combined with the partner element p(-kx, -ky, 0)
-          const int n2 = kxs * kxs + ky_s * ky_s;
-          const double m0 = (double)mtab[n2], mN = (double)mtab[n2 + NH * NH];
-          const ST pp = p[(size_t)((N - i) % N) * rowstride + (size_t)pky * NH];
-          const double a = 0.5 * (m0 + mN), b = 0.5 * (m0 - mN);
-          qs[2 * u] = (SS)(a * (double)ps[2 * u] + b * (double)pp.x + RT<R>::to_d(t.x));
-          qs[2 * u + 1] = (SS)(a * (double)ps[2 * u + 1] - b * (double)pp.y + RT<R>::to_d(t.y));
-        } else {
-          const cx<R> ct = scale(t, RT<R>::c((double)cv[k][u]));
-          qs[2 * u] = mv[k][u] * ps[2 * u] + (SS)RT<R>::to_d(ct.x);
-          qs[2 * u + 1] = mv[k][u] * ps[2 * u + 1] + (SS)RT<R>::to_d(ct.y);
-        }
-        const SS wgt = kz == 0 ? (SS)1 : (SS)2;
-        acc.add_prod(wgt * ps[2 * u], qs[2 * u]);
-        acc.add_prod(wgt * ps[2 * u + 1], qs[2 * u + 1]);
-      }
-      *reinterpret_cast<VT*>(q + e) = qv;
-    }
-  }
-  const double s = block_sum(acc.get(), red);
-  if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+  tile_store<G>(tile, out + base, rowstride, tid);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -478,46 +462,55 @@ k_xmul(const typename Store<R>::T* __restrict__ in, typename Store<R>::T* __rest
 // through a complex FFT of length h on z_m = x_2m + i x_2m+1.  tw holds exp(-2 pi i e/(2N)),
 // e < 2N (so W_N^k = tw[2k] and the length-h FFT uses stride 4).
 // ------------------------------------------------------------------------------------------
-// C2R pre-step on one line (stride LD): X (packed) -> Z with z = IFFT_h(Z) the real samples.
-template <class R, int N, int LD>
-WF_D void c2r_prep(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
+// C2R pre-step on one line (element k at col[map(k)]): X (packed) -> Z with z = IFFT_h(Z) the
+// real samples.
+template <class R, int N, class MAP>
+WF_D void c2r_prep_map(cx<R>* col, const MAP& map, int t, int tpl_, const cx<R>* tw) {
   constexpr int H = N / 2;
   for (int k = t; k <= H / 2; k += tpl_) {
     if (k == 0) {
-      const cx<R> v = col[0];
-      col[0] = cx<R>{v.x + v.y, v.x - v.y};
+      const cx<R> v = col[map(0)];
+      col[map(0)] = cx<R>{v.x + v.y, v.x - v.y};
     } else {
       const int k2 = H - k;
-      const cx<R> a = col[k * LD], b = col[k2 * LD];
+      const cx<R> a = col[map(k)], b = col[map(k2)];
       // Z_k = (X_k + conj X_{h-k}) + i W_N^{+k} (X_k - conj X_{h-k})
       const cx<R> s1 = a + conj(b), d1 = a - conj(b);
       const cx<R> s2 = b + conj(a), d2 = b - conj(a);
       const cx<R> w1 = conj(tw[2 * k]), w2 = conj(tw[2 * k2]);
-      col[k * LD] = s1 + mul_i(w1 * d1);
-      if (k2 != k) col[k2 * LD] = s2 + mul_i(w2 * d2);
+      col[map(k)] = s1 + mul_i(w1 * d1);
+      if (k2 != k) col[map(k2)] = s2 + mul_i(w2 * d2);
     }
   }
 }
 // R2C post-step on one line: Z = FFT_h(z) -> packed X (X_0, X_h in element 0).
-template <class R, int N, int LD>
-WF_D void r2c_post(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
+template <class R, int N, class MAP>
+WF_D void r2c_post_map(cx<R>* col, const MAP& map, int t, int tpl_, const cx<R>* tw) {
   constexpr int H = N / 2;
   const R half = RT<R>::c(0.5);
   for (int k = t; k <= H / 2; k += tpl_) {
     if (k == 0) {
-      const cx<R> v = col[0];
-      col[0] = cx<R>{v.x + v.y, v.x - v.y};
+      const cx<R> v = col[map(0)];
+      col[map(0)] = cx<R>{v.x + v.y, v.x - v.y};
     } else {
       const int k2 = H - k;
-      const cx<R> a = col[k * LD], b = col[k2 * LD];
+      const cx<R> a = col[map(k)], b = col[map(k2)];
       // X_k = (Z_k + conj Z_{h-k})/2 - (i/2) W_N^{-k} (Z_k - conj Z_{h-k})
       const cx<R> s1 = a + conj(b), d1 = a - conj(b);
       const cx<R> s2 = b + conj(a), d2 = b - conj(a);
       const cx<R> w1 = tw[2 * k], w2 = tw[2 * k2];
-      col[k * LD] = scale(s1 - mul_i(w1 * d1), half);
-      if (k2 != k) col[k2 * LD] = scale(s2 - mul_i(w2 * d2), half);
+      col[map(k)] = scale(s1 - mul_i(w1 * d1), half);
+      if (k2 != k) col[map(k2)] = scale(s2 - mul_i(w2 * d2), half);
     }
   }
+}
+template <class R, int N, int LD>
+WF_D void c2r_prep(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
+  c2r_prep_map<R, N>(col, Strided<LD>{}, t, tpl_, tw);
+}
+template <class R, int N, int LD>
+WF_D void r2c_post(cx<R>* col, int t, int tpl_, const cx<R>* tw) {
+  r2c_post_map<R, N>(col, Strided<LD>{}, t, tpl_, tw);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -595,18 +588,23 @@ WF_D void zrows_store(const cx<R>* tile, typename G::ST* g, size_t row0, int tid
 template <class R, int N, int EZ = z_elems<R, N>()>
 __global__ void __launch_bounds__(ZG<R, N, EZ>::NT)
 k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
-        const double2* __restrict__ twtab, const CgScal* __restrict__ sc, Bat bt) {
+        const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+        Bat bt) {
   using G = ZG<R, N, EZ>;
   using SS = typename Store<R>::S;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;  // 2N entries
+  __shared__ double red[32];
   const int z = blockIdx.z;
   if (sc && sc[z].done) return;
   spec += z * bt.spec;
   D += z * bt.real;
+  partials += z * bt.part;
   const int tid = threadIdx.x;
   const size_t row0 = (size_t)blockIdx.x * G::NL;
+  // the D rows go to L2 while the rows are transformed
+  if (tid < G::NL) prefetch_l2(D + (row0 + tid) * N, N * sizeof(SS));
   for (int e = tid; e < 2 * N; e += G::NT) tw[e] = ld_c<R>(twtab + e);
   zrows_load<G>(tile, spec, row0, tid);
   __syncthreads();
@@ -614,8 +612,10 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
   c2r_prep<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
   fft_line<R, G::M, G::TPL, G::LD, +1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
-  // real samples 2i, 2i+1 of line l sit in element i: multiply by D, VW elements at a time
+  // real samples 2i, 2i+1 of line l sit in element i: multiply by D, VW elements at a time,
+  // and sum D T^2 (the <c p, D (c p)> term of <p, A p>)
   using DV = typename std::conditional<G::VW == 2, float4, double2>::type;  // 2 VW reals of D
+  typename AccFor<SS>::T acc;
 #pragma unroll 4
   for (int k = 0; k < G::PER; ++k) {
     const int idx = tid + k * G::NT;
@@ -625,17 +625,22 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
     if constexpr (G::VW == 2) {
       const float4 d = *reinterpret_cast<const float4*>(dp);
       cx<R> a = tile[i * G::LD + ll], b = tile[(i + 1) * G::LD + ll];
+      const cx<R> a0 = a, b0 = b;
       a.x = a.x * RT<R>::from_f(d.x);
       a.y = a.y * RT<R>::from_f(d.y);
       b.x = b.x * RT<R>::from_f(d.z);
       b.y = b.y * RT<R>::from_f(d.w);
+      // D T^2 >= 0: the vector's four terms are summed first
+      acc.add((SS)RT<R>::to_d(a.x * a0.x + a.y * a0.y + b.x * b0.x + b.y * b0.y));
       tile[i * G::LD + ll] = a;
       tile[(i + 1) * G::LD + ll] = b;
     } else {
       const double2 d = *reinterpret_cast<const double2*>(dp);
       cx<R> a = tile[i * G::LD + ll];
+      const cx<R> a0 = a;
       a.x = a.x * RT<R>::c(d.x);
       a.y = a.y * RT<R>::c(d.y);
+      acc.add((SS)RT<R>::to_d(a.x * a0.x + a.y * a0.y));
       tile[i * G::LD + ll] = a;
     }
   }
@@ -645,6 +650,8 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
   r2c_post<R, N, G::LD>(tile + l, t, G::TPL, tw);
   __syncthreads();
   zrows_store<G>(tile, spec, row0, tid);
+  const double sum = block_sum(acc.get(), red);
+  if (tid == 0) partials[blockIdx.x] = sum;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -767,14 +774,16 @@ k_zinv(const typename Store<R>::T* __restrict__ in, double* __restrict__ out,
 }
 
 // ------------------------------------------------------------------------------------------
-// CG update: r -= alpha q; partials [2 per block]: <r, r> (packed weights, without 1/V_c) and
-// an upper estimate of V_c ||C^-1 r||^2 (the canonical residual): on column 0 the larger of
-// the two planes' 1/c^2 is used.  Grid-stride; fixed grid size.
+// CG update: q = m p + c T^ (column 0: T^ already carries c, and the m term is combined with the
+// partner element p(-kx, -ky, 0)); r -= alpha q; partials [2 per block]: <r, r> (packed
+// weights, without 1/V_c) and an upper estimate of V_c ||C^-1 r||^2 (the canonical residual):
+// on column 0 the larger of the two planes' 1/c^2 is used.  Grid-stride; fixed grid size.
 // ------------------------------------------------------------------------------------------
-template <class R, int N>
+template <class R, int N, bool UNIT_M>
 __global__ void __launch_bounds__(256)
-k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* __restrict__ q,
-         const typename Store<R>::S* __restrict__ ctab, double* __restrict__ partials,
+k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* P0, const typename Store<R>::T* P1,
+         const typename Store<R>::T* __restrict__ tq, const typename Store<R>::S* __restrict__ ctab,
+         const typename Store<R>::S* __restrict__ mtab, double* __restrict__ partials,
          const CgScal* __restrict__ sc, Bat bt) {
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
@@ -785,44 +794,66 @@ k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* __res
   const int z = blockIdx.y;
   sc += z;
   if (sc->done) return;
+  const ST* __restrict__ p = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;  // this iteration's p_new
   r += z * bt.spec;
-  q += z * bt.spec;
+  tq += z * bt.spec;
   ctab += z * bt.tab;
+  mtab += z * bt.tab;
   partials += z * bt.part;
   const SS alpha = (SS)sc->alpha;
-  const size_t nvec = (size_t)N * N * NH / VW;
+  // 32-bit indices: N^3 / 2 elements fit for every supported N (<= 512)
+  constexpr unsigned NVR = NH / VW;  // vectors per (kx, ky) row
+  constexpr unsigned nvec = (unsigned)N * N * NVR;
+  static_assert((unsigned long long)N * N * NH < (1ull << 31), "32-bit spectrum indices");
   VT* r4 = reinterpret_cast<VT*>(r);
-  const VT* q4 = reinterpret_cast<const VT*>(q);
+  const VT* q4 = reinterpret_cast<const VT*>(tq);
+  const VT* p4 = reinterpret_cast<const VT*>(p);
   typename AccFor<SS>::T a_rr, a_rc;
 #pragma unroll 4
-  for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec; v += (size_t)gridDim.x * blockDim.x) {
+  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += gridDim.x * blockDim.x) {
     VT rv = r4[v];
-    const VT qv = q4[v];
+    const VT qv = q4[v], pv = p4[v];
     SS* rs = reinterpret_cast<SS*>(&rv);
     const SS* qs = reinterpret_cast<const SS*>(&qv);
-#pragma unroll
-    for (int u = 0; u < 2 * VW; ++u) rs[u] -= alpha * qs[u];
-    r4[v] = rv;
-    const size_t e0 = v * VW;
-    const int ky = (int)((e0 / NH) % N);
-    const int kx = (int)(e0 / ((size_t)N * NH));
+    const SS* ps = reinterpret_cast<const SS*>(&pv);
+    const unsigned row = v / NVR, kz0 = (v % NVR) * VW;
+    const int ky = (int)(row % N), kx = (int)(row / N);
     const int kxs = sfreq(kx, N), kys = sfreq(ky, N);
+    SS s_rr = 0, s_rc = 0;
 #pragma unroll
     for (int u = 0; u < VW; ++u) {
-      const int kz = (int)((e0 + u) % NH);
+      const int kz = (int)kz0 + u;
       const int n2 = kxs * kxs + kys * kys + kz * kz;
       const SS c = ctab[n2];
       SS ic2 = (SS)1 / (c * c);
+      SS q0, q1;  // q = m p + c T^ (tq holds T^, with c already applied on column 0)
       if (kz == 0) {
+        // packed column: m-term combined with the partner element p(-kx, -ky, 0)
         const SS cN = ctab[n2 + NH * NH];
         const SS i2 = (SS)1 / (cN * cN);
         ic2 = ic2 > i2 ? ic2 : i2;
+        const double m0 = (double)mtab[n2], mN = (double)mtab[n2 + NH * NH];
+        const double a = 0.5 * (m0 + mN), b = 0.5 * (m0 - mN);
+        ST pp = ST{};
+        if (b != 0.0) pp = p[((size_t)((N - kx) % N) * N + (size_t)((N - ky) % N)) * NH];
+        q0 = (SS)(a * (double)ps[2 * u] + b * (double)pp.x + (double)qs[2 * u]);
+        q1 = (SS)(a * (double)ps[2 * u + 1] - b * (double)pp.y + (double)qs[2 * u + 1]);
+      } else {
+        const SS m = UNIT_M ? (SS)1 : mtab[n2];
+        q0 = m * ps[2 * u] + c * qs[2 * u];
+        q1 = m * ps[2 * u + 1] + c * qs[2 * u + 1];
       }
+      rs[2 * u] -= alpha * q0;
+      rs[2 * u + 1] -= alpha * q1;
       const SS wgt = kz == 0 ? (SS)1 : (SS)2;
-      const SS m2 = rs[2 * u] * rs[2 * u] + rs[2 * u + 1] * rs[2 * u + 1];
-      a_rr.add_prod(wgt, m2);
-      a_rc.add_prod(wgt * ic2, m2);
+      const SS m2 = wgt * (rs[2 * u] * rs[2 * u] + rs[2 * u + 1] * rs[2 * u + 1]);
+      s_rr += m2;
+      s_rc += ic2 * m2;
     }
+    r4[v] = rv;
+    // the terms are >= 0: a vector's terms are summed in the storage type first
+    a_rr.add(s_rr);
+    a_rc.add(s_rc);
   }
   const double s1 = block_sum(a_rr.get(), red);
   const double s2 = block_sum(a_rc.get(), red);
@@ -877,11 +908,15 @@ static __global__ void k_fin_init(const double* __restrict__ partials, int n, Cg
   }
 }
 
-static __global__ void k_fin_alpha(const double* __restrict__ partials, int n, CgScal* sc, Bat bt) {
+// <p, A p> = partials [0, n1) (the m term, from the x pass) + [n1, n1 + n2) (the data term,
+// from the z turn); alpha = rr / <p, A p>.
+static __global__ void k_fin_alpha(const double* __restrict__ partials, int n1, int n2, CgScal* sc, Bat bt) {
   __shared__ double red[32];
   sc += blockIdx.x;
   if (sc->done) return;
-  const double pq = sum_partials(partials + blockIdx.x * bt.part, n, 1, 0, red);
+  const double pm = sum_partials(partials + blockIdx.x * bt.part, n1, 1, 0, red);
+  const double pd = sum_partials(partials + blockIdx.x * bt.part + n1, n2, 1, 0, red);
+  const double pq = pm + pd;
   if (threadIdx.x == 0) {
     sc->pq = pq;
     if (!(pq > 0.0) || !isfinite(pq)) {

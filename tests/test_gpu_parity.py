@@ -274,6 +274,31 @@ def test_fixed_iterations_large_grid(ctx, n):
     assert rl2(host(s), ref) <= 1e-11
 
 
+@pytest.mark.parametrize("n", [128, 192, 256, 384])
+def test_fused_planes_match_separate_passes(n):
+    """The cluster kernel for the y / z / y transforms (clusters of 2, 3, 4, 6 CTAs at these
+    sizes) and the three separate passes apply the same FP32 operator: a few inner iterations
+    give the same iterate, and a solve with the cluster kernel meets the FP64 residual."""
+    pr = synth.problem("c2", n_override=n, cache=False)
+    with wf.Context(0) as c:
+        nobs = c.grid_assign(gpu(pr.pos), pr.n, pr.box, pr.scheme, 2)
+        w, d, b, nbar = c.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+        out, its = [], []
+        for fused in (False, True):
+            c.set_fused_planes(fused)
+            s, info = c.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=6, prec=wf.MIXED,
+                              check=False)
+            out.append(host(s).copy())
+            its.append(info.iters)
+        assert its[0] == its[1] and 0 < its[0] <= 6
+        assert rl2(out[1], out[0]) <= 1e-5
+        s, info = c.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED)
+        assert info.status == wf.OK and info.rel_residual <= 1e-8
+        c.set_fused_planes(False)
+        s0, info0 = c.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED)
+        assert rl2(host(s), host(s0)) <= 1e-6
+
+
 # ------------------------------------------------------------------------ batched solves
 def _mock(n, seed, box_per_cell=1.953):
     """A small mock of the batched workload: LCDM prior, SDSS-like selection, its own seed."""
