@@ -71,6 +71,26 @@ wf_status Ctx::tw(int n, const double2** out) {
   return WF_OK;
 }
 
+wf_status Ctx::tw32(int n, const float2** out) {
+  auto it = twiddles32.find(n);
+  if (it != twiddles32.end()) {
+    *out = it->second;
+    return WF_OK;
+  }
+  std::vector<float2> h((size_t)2 * n);
+  const double pi = 3.14159265358979323846;
+  for (int e = 0; e < 2 * n; ++e) {
+    const double ang = 2.0 * pi * (double)e / (2.0 * n);
+    h[e] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+  }
+  float2* d = nullptr;
+  WF_CUDA(cudaMalloc(&d, h.size() * sizeof(float2)));
+  WF_CUDA(cudaMemcpy(d, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  twiddles32[n] = d;
+  *out = d;
+  return WF_OK;
+}
+
 wf_status Ctx::get_pinned(const std::string& name, size_t bytes, void** out) {
   if (bytes == 0) bytes = 16;
   DevBuf& b = pinned[name];
@@ -132,6 +152,8 @@ void Ctx::release_all() {
   held = 0;
   for (auto& kv : twiddles) cudaFree(kv.second);
   twiddles.clear();
+  for (auto& kv : twiddles32) cudaFree(kv.second);
+  twiddles32.clear();
   for (auto& kv : pinned)
     if (kv.second.ptr) cudaFreeHost(kv.second.ptr);
   pinned.clear();

@@ -100,6 +100,7 @@ struct Ctx {
   std::mutex mu;            // serialises synchronous API calls on this context
   std::map<std::string, DevBuf> bufs;
   std::map<int, double2*> twiddles;  // per N: exp(-2 pi i e / (2N)), e < 2N
+  std::map<int, float2*> twiddles32; // the same rounded to FP32 (for the FP32 kernels)
   std::map<std::string, DevBuf> pinned;  // page-locked host buffers (scalar staging)
   std::vector<cudaStream_t> streams;     // non-blocking streams for interleaved groups
   cudaStream_t cap_stream = nullptr;     // stream on which CG blocks are captured as graphs
@@ -128,6 +129,7 @@ struct Ctx {
   // Device buffer `name` with at least `bytes` bytes (contents not preserved on growth).
   wf_status get(const std::string& name, size_t bytes, void** out);
   wf_status tw(int n, const double2** out);
+  wf_status tw32(int n, const float2** out);
   // Page-locked host buffer `name` with at least `bytes` bytes.
   wf_status get_pinned(const std::string& name, size_t bytes, void** out);
   // i-th library-owned non-blocking stream.

@@ -206,7 +206,7 @@ WF_D double plane_zturn(cx<R>* tile, const typename G::SS* __restrict__ Drow0, c
 template <class R, int N, int CS, int E, int MINB = 1>
 __global__ void __launch_bounds__(PlaneG<R, N, CS, E>::NT, MINB)
 k_plane_turn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
-             const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+             const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
              Bat bt) {
   using G = PlaneG<R, N, CS, E>;
   namespace cg = cooperative_groups;
@@ -243,7 +243,8 @@ k_plane_turn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S
 // Launch k_plane_turn over nb systems on stream st with the cluster shape (CS, 1, 1).  The
 // caller has raised the kernel's dynamic shared-memory limit to PlaneG::SMEM.
 template <class R, int N, int CS, int E, int MINB = 1>
-static cudaError_t plane_turn_launch(typename Store<R>::T* spec, const typename Store<R>::S* D, const double2* tw,
+static cudaError_t plane_turn_launch(typename Store<R>::T* spec, const typename Store<R>::S* D,
+                                     const typename Store<R>::T* tw,
                                      double* partials, const CgScal* sc, Bat bt, int nb, cudaStream_t st) {
   using G = PlaneG<R, N, CS, E>;
   cudaLaunchConfig_t cfg = {};

@@ -102,7 +102,7 @@ struct Spec {
     return e;
   }
 
-  static void ypass(Ctx& c, int nb, ST* t, const double2* tw, const CgScal* sc, int dir, cudaStream_t st) {
+  static void ypass(Ctx& c, int nb, ST* t, const ST* tw, const CgScal* sc, int dir, cudaStream_t st) {
     c.launch("ypass", 2 * BS * nb, st, [&] {
       if (dir < 0) k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(t, tw, sc, bat());
       else k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(t, tw, sc, bat());
@@ -110,12 +110,12 @@ struct Spec {
   }
   // out = [IFFT_x] tab (.) [FFT_x] in
   template <bool FWD, bool INV, bool DOT>
-  static void xmul(Ctx& c, int nb, const ST* in, ST* out, const SS* tab, const double2* tw, double* part,
+  static void xmul(Ctx& c, int nb, const ST* in, ST* out, const SS* tab, const ST* tw, double* part,
                    const CgScal* sc, cudaStream_t st) {
     c.launch("xmul", 2 * BS * nb, st,
              [&] { k_xmul<R, N, FWD, INV, DOT><<<gxy(nb), NTx, SMxy, st>>>(in, out, tab, tw, part, sc, bat()); });
   }
-  static void zfwd(Ctx& c, int nb, const double* in, ST* out, const double2* tw, double* part, bool sq,
+  static void zfwd(Ctx& c, int nb, const double* in, ST* out, const ST* tw, double* part, bool sq,
                    const CgScal* sc, cudaStream_t st) {
     c.launch("zfwd", (BS + 8 * BV) * nb, st, [&] {
       if (sq) k_zfwd<R, N, true><<<gz(nb), NTz, SMz, st>>>(in, out, tw, part, sc, bat());
@@ -124,7 +124,7 @@ struct Spec {
   }
   template <int MODE>
   static void zinv(Ctx& c, int nb, const ST* in, double* out, const double* s, const double* w, const double* b,
-                   double scl, const double2* tw, double* part, const CgScal* sc, cudaStream_t st) {
+                   double scl, const ST* tw, double* part, const CgScal* sc, cudaStream_t st) {
     const double vb = MODE == ZI_RESID ? 4 : (MODE == ZI_ACCUM ? 2 : 1);
     c.launch("zinv", (BS + 8 * vb * BV) * nb, st,
              [&] { k_zinv<R, N, MODE><<<gz(nb), NTz, SMz, st>>>(in, out, s, w, b, scl, tw, part, sc, bat()); });
@@ -132,7 +132,7 @@ struct Spec {
 
   // One CG iteration of every unfinished system (no host synchronisation).
   static void iteration(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, ST* q, const SS* D, const SS* ctab,
-                        const SS* mtab, bool unit_m, const double2* tw, double* part, CgScal* sc, double inv_vc,
+                        const SS* mtab, bool unit_m, const ST* tw, double* part, CgScal* sc, double inv_vc,
                         cudaStream_t st) {
     const Bat b = bat();
     c.launch("cg_xinv", 6 * BS * nb, st, [&] {
@@ -507,6 +507,7 @@ struct GroupMixed : GroupCommon<N> {
   float2 *xh, *rh, *P0, *P1, *qh, *T;
   float* D;
   double2 *T64, *T64b;
+  const float2* tw32 = nullptr;  // FP32 copy of the twiddle table for the FP32 passes
   float *ct, *mt;
   double* stab;
   std::vector<int> outer, iters;
@@ -520,6 +521,7 @@ struct GroupMixed : GroupCommon<N> {
     WF_CUDA(SD::attrs());
     const size_t SPEC = SF::SPEC, V = SF::V;
     WF_TRY(c.tw(N, &tw));
+    WF_TRY(c.tw32(N, &tw32));
     const char* nm[6] = {"x", "r", "p0", "p1", "q", "T"};
     float2** ptr[6] = {&xh, &rh, &P0, &P1, &qh, &T};
     for (int i = 0; i < 6; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(float2), (void**)ptr[i]));
@@ -597,9 +599,9 @@ struct GroupMixed : GroupCommon<N> {
       }
       WF_TRY(this->push_scalars(st));
       const size_t SPEC = SF::SPEC;
-      SF::zfwd(c, nb, RES, T, tw, part, false, nullptr, st);
-      SF::ypass(c, nb, T, tw, nullptr, -1, st);
-      SF::template xmul<true, false, true>(c, nb, T, rh, ct, tw, part, nullptr, st);
+      SF::zfwd(c, nb, RES, T, tw32, part, false, nullptr, st);
+      SF::ypass(c, nb, T, tw32, nullptr, -1, st);
+      SF::template xmul<true, false, true>(c, nb, T, rh, ct, tw32, part, nullptr, st);
       c.launch("fin", 0, st, [&] { k_fin_init<<<nb, 1024, 0, st>>>(part, SF::GXY, sc, bf); });
       WF_CUDA(cudaMemsetAsync(P0, 0, nb * SPEC * sizeof(float2), st));
       WF_CUDA(cudaMemsetAsync(P1, 0, nb * SPEC * sizeof(float2), st));
@@ -609,15 +611,15 @@ struct GroupMixed : GroupCommon<N> {
     if (phase == 1) {
       WF_TRY(this->run_block(c, st, [&](cudaStream_t s2) {
         for (int i = 0; i < check_every<N>(); ++i)
-          SF::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, s2);
+          SF::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw32, part, sc, inv_vc, s2);
       }));
     } else if (phase == 2) {
       c.launch("axpy", 3 * SF::BS * nb, st,
                [&] { k_axpy_final<<<dim3(152 * 4, nb), 256, 0, st>>>(xh, P0, P1, SF::SPEC, sc, bf); });
       // x += C e (FP32 transform, FP64 accumulation) for the systems that ran
-      SF::template xmul<false, true, false>(c, nb, xh, T, ct, tw, part, nullptr, st);
-      SF::ypass(c, nb, T, tw, nullptr, +1, st);
-      SF::template zinv<ZI_ACCUM>(c, nb, T, S, nullptr, nullptr, nullptr, inv_vc, tw, part, sc, st);
+      SF::template xmul<false, true, false>(c, nb, xh, T, ct, tw32, part, nullptr, st);
+      SF::ypass(c, nb, T, tw32, nullptr, +1, st);
+      SF::template zinv<ZI_ACCUM>(c, nb, T, S, nullptr, nullptr, nullptr, inv_vc, tw32, part, sc, st);
       // FP64 residual res = b - A x
       SD::zfwd(c, nb, S, T64, tw, part, false, nullptr, st);
       SD::ypass(c, nb, T64, tw, nullptr, -1, st);

@@ -71,12 +71,20 @@ constexpr int div_le(int n, int cap) {
 // lines per CTA of the x / y passes: consecutive kz columns, a divisor of N/2
 template <class R, int N> constexpr int xy_lines() { return div_le(N / 2, tile_lines<R>()); }
 
+// a table entry in the arithmetic type (no FP64 round trip when the types agree)
+template <class R, class T> WF_D R tab_to(T v) {
+  if constexpr (std::is_same<R, T>::value) return v;
+  else return RT<R>::c((double)v);
+}
+
 // signed frequency of an index on an axis of length n
 WF_D int sfreq(int j, int n) { return j <= (n >> 1) ? j : j - n; }
 
-// Load the length-M twiddles exp(-2 pi i e / M) from a length-TN FP64 table into shared memory.
-template <class R, int M, int TN>
-WF_D void load_tw(cx<R>* tw, const double2* tab, int tid, int nt) {
+// Load the length-M twiddles exp(-2 pi i e / M) from a length-TN table into shared memory.  The
+// table has the kernel's storage type (FP32 kernels read an FP32 copy: converting FP64 entries would
+// put the start of every CTA on GB300's 1/64-rate FP64 unit).
+template <class R, int M, int TN, class TT>
+WF_D void load_tw(cx<R>* tw, const TT* tab, int tid, int nt) {
   for (int e = tid; e < M; e += nt) tw[e] = ld_c<R>(tab + e * (TN / M));
 }
 
@@ -170,7 +178,7 @@ WF_D void tile_store(const cx<R>* tile, typename G::ST* g, size_t rowstride, int
 // y pass: complex FFT along y of every (x, kz) line; in place.  grid (N/2 / NL, N).
 template <class R, int N, int DIR, int EX = elems_for<R>(N, xy_lines<R, N>())>
 __global__ void __launch_bounds__(XYG<R, N, EX>::NT)
-k_ypass(typename Store<R>::T* __restrict__ spec, const double2* __restrict__ twtab,
+k_ypass(typename Store<R>::T* __restrict__ spec, const typename Store<R>::T* __restrict__ twtab,
         const CgScal* __restrict__ sc, Bat bt) {
   using G = XYG<R, N, EX>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -198,8 +206,8 @@ WF_D void combine_col0(cx<R>* tile, int ky_s, const TAB* tab, int tid, int nt) {
   for (int kx = tid; kx < N; kx += nt) {
     const int kxs = sfreq(kx, N);
     const int n2 = kxs * kxs + ky_s * ky_s;
-    const R m0 = RT<R>::c((double)tab[n2]);
-    const R mN = RT<R>::c((double)tab[n2 + NH * NH]);
+    const R m0 = tab_to<R>(tab[n2]);
+    const R mN = tab_to<R>(tab[n2 + NH * NH]);
     const R h = RT<R>::c(0.5);
     const R a = (m0 + mN) * h, b = (m0 - mN) * h;
     const cx<R> z = tile[kx * LD];
@@ -216,7 +224,7 @@ WF_D void tile_mul(cx<R>* tile, int kz0, int ky_s, const TAB* tab, int tid) {
     const int i = idx / G::NL, l = idx % G::NL, kz = kz0 + l;
     if (kz == 0) continue;
     const int kxs = sfreq(i, G::M);
-    tile[i * G::LD + l] = scale(tile[i * G::LD + l], RT<R>::c((double)tab[kxs * kxs + ky_s * ky_s + kz * kz]));
+    tile[i * G::LD + l] = scale(tile[i * G::LD + l], tab_to<R>(tab[kxs * kxs + ky_s * ky_s + kz * kz]));
   }
 }
 
@@ -234,13 +242,14 @@ __global__ void __launch_bounds__(XYG<R, N>::NT)
 k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, typename Store<R>::T* P1,
           typename Store<R>::T* __restrict__ x, typename Store<R>::T* __restrict__ T,
           const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
-          const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+          const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
           Bat bt) {
   using G = XYG<R, N>;
   using ST = typename Store<R>::T;
   using SS = typename Store<R>::S;
   using VT = typename G::VT;
   constexpr int NH = G::NH;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
@@ -343,8 +352,7 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
       const int n2 = kxs * kxs + ky_s * ky_s;
       const cx<R> zc = tile[kx * G::LD];
       const cx<R> zp = tile[((N - kx) % N) * G::LD + G::NL];
-      const SS zr = (SS)RT<R>::to_d(zc.x), zi = (SS)RT<R>::to_d(zc.y);
-      const SS pr = (SS)RT<R>::to_d(zp.x), pi = (SS)RT<R>::to_d(zp.y);
+      const SS zr = (SS)zc.x, zi = (SS)zc.y, pr = (SS)zp.x, pi = (SS)zp.y;  // R is the storage type
       const SS h = (SS)0.5;
       const SS a0 = h * (zr + pr), b0 = h * (zi - pi);  // P0
       const SS aN = h * (zi + pi), bN = h * (pr - zr);  // PN
@@ -367,7 +375,7 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
 template <class R, int N>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
 k_cg_xfwd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ out,
-          const typename Store<R>::S* __restrict__ ctab, const double2* __restrict__ twtab,
+          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::T* __restrict__ twtab,
           const CgScal* __restrict__ sc, Bat bt) {
   using G = XYG<R, N>;
   constexpr int NH = G::NH;
@@ -406,7 +414,7 @@ k_cg_xfwd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __re
 template <class R, int N, bool FWD, bool INV, bool DOT>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
 k_xmul(const typename Store<R>::T* __restrict__ in, typename Store<R>::T* __restrict__ out,
-       const typename Store<R>::S* __restrict__ tab, const double2* __restrict__ twtab,
+       const typename Store<R>::S* __restrict__ tab, const typename Store<R>::T* __restrict__ twtab,
        double* __restrict__ partials, const CgScal* __restrict__ sc, Bat bt) {
   using G = XYG<R, N>;
   using SS = typename Store<R>::S;
@@ -588,10 +596,11 @@ WF_D void zrows_store(const cx<R>* tile, typename G::ST* g, size_t row0, int tid
 template <class R, int N, int EZ = z_elems<R, N>()>
 __global__ void __launch_bounds__(ZG<R, N, EZ>::NT)
 k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
-        const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+        const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
         Bat bt) {
   using G = ZG<R, N, EZ>;
   using SS = typename Store<R>::S;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;  // 2N entries
@@ -630,8 +639,8 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
       a.y = a.y * RT<R>::from_f(d.y);
       b.x = b.x * RT<R>::from_f(d.z);
       b.y = b.y * RT<R>::from_f(d.w);
-      // D T^2 >= 0: the vector's four terms are summed first
-      acc.add((SS)RT<R>::to_d(a.x * a0.x + a.y * a0.y + b.x * b0.x + b.y * b0.y));
+      // D T^2 >= 0: the vector's four terms are summed first (in R = the storage type)
+      acc.add((SS)(a.x * a0.x + a.y * a0.y + b.x * b0.x + b.y * b0.y));
       tile[i * G::LD + ll] = a;
       tile[(i + 1) * G::LD + ll] = b;
     } else {
@@ -640,7 +649,7 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
       const cx<R> a0 = a;
       a.x = a.x * RT<R>::c(d.x);
       a.y = a.y * RT<R>::c(d.y);
-      acc.add((SS)RT<R>::to_d(a.x * a0.x + a.y * a0.y));
+      acc.add((SS)(a.x * a0.x + a.y * a0.y));
       tile[i * G::LD + ll] = a;
     }
   }
@@ -660,7 +669,7 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
 template <class R, int N, bool SQ>
 __global__ void __launch_bounds__(ZG<R, N>::NT)
 k_zfwd(const double* __restrict__ in, typename Store<R>::T* __restrict__ out,
-       const double2* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
+       const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
        Bat bt) {
   using G = ZG<R, N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -717,7 +726,7 @@ template <class R, int N, int MODE>
 __global__ void __launch_bounds__(ZG<R, N>::NT)
 k_zinv(const typename Store<R>::T* __restrict__ in, double* __restrict__ out,
        const double* __restrict__ s, const double* __restrict__ w, const double* __restrict__ b,
-       double scl, const double2* __restrict__ twtab, double* __restrict__ partials,
+       double scl, const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials,
        const CgScal* __restrict__ sc, Bat bt) {
   using G = ZG<R, N>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -832,12 +841,14 @@ k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* P0, c
         const SS cN = ctab[n2 + NH * NH];
         const SS i2 = (SS)1 / (cN * cN);
         ic2 = ic2 > i2 ? ic2 : i2;
-        const double m0 = (double)mtab[n2], mN = (double)mtab[n2 + NH * NH];
-        const double a = 0.5 * (m0 + mN), b = 0.5 * (m0 - mN);
+        // (in the storage type: FP64 here would run on GB300's 1/64-rate unit for every warp
+        // that holds a column-0 lane)
+        const SS m0 = mtab[n2], mN = mtab[n2 + NH * NH];
+        const SS a = (SS)0.5 * (m0 + mN), b = (SS)0.5 * (m0 - mN);
         ST pp = ST{};
-        if (b != 0.0) pp = p[((size_t)((N - kx) % N) * N + (size_t)((N - ky) % N)) * NH];
-        q0 = (SS)(a * (double)ps[2 * u] + b * (double)pp.x + (double)qs[2 * u]);
-        q1 = (SS)(a * (double)ps[2 * u + 1] - b * (double)pp.y + (double)qs[2 * u + 1]);
+        if (b != (SS)0) pp = p[((size_t)((N - kx) % N) * N + (size_t)((N - ky) % N)) * NH];
+        q0 = a * ps[2 * u] + b * pp.x + qs[2 * u];
+        q1 = a * ps[2 * u + 1] - b * pp.y + qs[2 * u + 1];
       } else {
         const SS m = UNIT_M ? (SS)1 : mtab[n2];
         q0 = m * ps[2 * u] + c * qs[2 * u];
