@@ -1,0 +1,121 @@
+"""CPU FP64 oracle of the evaluation steps applied to a reconstruction (Kitaura et al. 2009,
+arXiv:0906.3978, Sec. 5.1 "Statistical correlation measures" and Sec. 6.2 "Statistical
+analysis"): Gaussian smoothing, the correlation coefficient r, the Euclidean distance D_Euc, the
+normalised Kullback-Leibler distance D_KL, and binned density statistics (counts in 1+delta bins
+per radial shell and observed / unobserved region; mean, central moments, skewness, kurtosis,
+Pearson's skewness).
+
+Test infrastructure only (tests, ``__graft_entry__.smoke()``, the benchmark's CPU leg); the
+library never imports it.  Each function is the plain definition, in FP64, with the oracle's own
+FFT (``oracle.fft3d``) as the only library step.  Readings where the paper is silent or garbled:
+
+  * eq:GAUSS prints exp(+|r|^2 / 2 r_S^2); the kernel is read as the normalised Gaussian
+    exp(-|r|^2 / 2 r_S^2) / ((2 pi)^(3/2) r_S^3), applied on the periodic grid as the multiplier
+    exp(-|k|^2 r_S^2 / 2) of the DFT (k = 2 pi m / L, m the signed index in (-N/2, N/2]).
+  * D_KL takes log(x) only where both 1 + delta are > 0; other cells are left out of the sum
+    (the 1 / N_cells normalisation keeps all cells) and counted.
+  * The density bins are [lo + i width, lo + (i + 1) width) in 1 + delta, bin index
+    floor(((1 + delta) - lo) / width) in FP64; values below bin 0 or above the last bin are
+    counted apart and do not enter the moments.  Moments use the bin centres (the paper's
+    "density at the center of the bins"); Pearson's mode is the first bin of largest count.
+  * A node lies in shell [r_lo, r_hi) when r_lo <= r < r_hi, r = |i H - o| (nodes at i H, no
+    periodic wrap, as for the window); observed means w > 0.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import fft3d
+
+
+def gaussian_multiplier(n: int, box: float, r_s: float) -> np.ndarray:
+    """exp(-|k|^2 r_S^2 / 2) on the full [n, n, n] DFT grid (Sec. 6.2, eq:GAUSS as read above)."""
+    m = np.fft.fftfreq(n, 1.0 / n)
+    m[n // 2] = n // 2  # the Nyquist index as +N/2 (its square is the same)
+    k2 = (2.0 * np.pi / box) ** 2 * (m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2)
+    return np.exp(-0.5 * k2 * r_s * r_s)
+
+
+def smooth(field, box: float, r_s: float) -> np.ndarray:
+    """Field convolved with the normalised Gaussian of radius r_s on the periodic grid."""
+    f = np.asarray(field, dtype=np.float64)
+    n = f.shape[0]
+    spec = fft3d(f.astype(np.complex128), -1)
+    out = fft3d(spec * gaussian_multiplier(n, box, r_s), +1)
+    return np.real(out) / float(n) ** 3
+
+
+def compare(rec, true) -> dict:
+    """Sec. 5.1: r = sum(t r) / sqrt(sum t^2 sum r^2); D_Euc = sqrt(mean (r - t)^2);
+    D_KL = (1 / N_cells) sum (1 + r) log((1 + r) / (1 + t)) over the cells where both 1 + delta > 0."""
+    r = np.asarray(rec, dtype=np.float64).ravel()
+    t = np.asarray(true, dtype=np.float64).ravel()
+    nc = r.size
+    corr = np.sum(t * r) / (np.sqrt(np.sum(t * t)) * np.sqrt(np.sum(r * r)))
+    d_euc = np.sqrt(np.sum((r - t) ** 2) / nc)
+    a, b = 1.0 + r, 1.0 + t
+    ok = (a > 0.0) & (b > 0.0)
+    d_kl = np.sum(a[ok] * np.log(a[ok] / b[ok])) / nc
+    return {"r": float(corr), "d_euc": float(d_euc), "d_kl": float(d_kl), "kl_excluded": int(nc - np.count_nonzero(ok))}
+
+
+def node_radius(n: int, box: float, observer) -> np.ndarray:
+    """|i H - o| at every node, in the same operation order as the window: ((dx dx + dy dy) + dz dz)."""
+    h = box / n
+    i = np.arange(n, dtype=np.float64) * h
+    dx = (i - float(observer[0]))[:, None, None]
+    dy = (i - float(observer[1]))[None, :, None]
+    dz = (i - float(observer[2]))[None, None, :]
+    return np.sqrt((dx * dx + dy * dy) + dz * dz)
+
+
+def density_hist(delta, w, box: float, observer, shells, lo: float, width: float, n_bins: int):
+    """Counts of 1 + delta in n_bins bins of `width` from `lo`, per shell (rows of `shells`:
+    r_lo, r_hi) and region (0: w > 0, 1: w = 0).  Returns (hist [S, 2, n_bins], under [S, 2],
+    over [S, 2]) as int64."""
+    d = np.asarray(delta, dtype=np.float64)
+    n = d.shape[0]
+    r = node_radius(n, box, observer).ravel()
+    obs = (np.asarray(w, dtype=np.float64).ravel() > 0.0)
+    b = np.floor(((1.0 + d.ravel()) - lo) / width)
+    shells = np.asarray(shells, dtype=np.float64).reshape(-1, 2)
+    S = shells.shape[0]
+    hist = np.zeros((S, 2, n_bins), dtype=np.int64)
+    under = np.zeros((S, 2), dtype=np.int64)
+    over = np.zeros((S, 2), dtype=np.int64)
+    for s, (r_lo, r_hi) in enumerate(shells):
+        ins = (r >= r_lo) & (r < r_hi)
+        for g, sel in enumerate((obs, ~obs)):
+            bb = b[ins & sel]
+            under[s, g] = np.count_nonzero(bb < 0)
+            over[s, g] = np.count_nonzero(bb >= n_bins)
+            inr = bb[(bb >= 0) & (bb < n_bins)].astype(np.int64)
+            hist[s, g] = np.bincount(inr, minlength=n_bins)
+    return hist, under, over
+
+
+MOMENT_FIELDS = ("n_cells", "mean", "mu2", "mu3", "mu4", "skewness", "kurtosis", "pearson")
+
+
+def density_moments(hist, lo: float, width: float) -> np.ndarray:
+    """Sec. 6.2 from the bin counts f_i at the bin centres delta_i = lo + (i + 1/2) width - 1:
+    N = sum f, mean, mu_n = sum f (delta - mean)^n / N, s = mu3 / sigma^3, k = mu4 / sigma^4 - 3,
+    s_P = (mean - delta_mode) / sigma.  Returns [..., 8] in MOMENT_FIELDS order (NaN if N = 0)."""
+    h = np.asarray(hist, dtype=np.int64)
+    nb = h.shape[-1]
+    c = lo + (np.arange(nb) + 0.5) * width - 1.0
+    flat = h.reshape(-1, nb)
+    out = np.full((flat.shape[0], 8), np.nan)
+    for j, f in enumerate(flat):
+        N = int(f.sum())
+        out[j, 0] = N
+        if N == 0:
+            continue
+        ff = f.astype(np.float64)
+        mean = float(np.sum(ff * c)) / N
+        dev = c - mean
+        mu2, mu3, mu4 = (float(np.sum(ff * dev ** p)) / N for p in (2, 3, 4))
+        sig = np.sqrt(mu2)
+        mode = c[int(np.argmax(f))]
+        out[j, 1:] = (mean, mu2, mu3, mu4, mu3 / sig ** 3, mu4 / sig ** 4 - 3.0, (mean - mode) / sig)
+    return out.reshape(h.shape[:-1] + (8,))

@@ -299,6 +299,43 @@ def test_fused_planes_match_separate_passes(n):
         assert rl2(host(s), host(s0)) <= 1e-6
 
 
+def test_full_size_workload(ctx):
+    """The 512^3 workload the benchmark times (1024^3 fine grid, TSC, the same launches): the
+    fine grid bit for bit against the oracle's, the window's membership decisions exactly and
+    its values to 1e-14, n_obs at sampled nodes against the oracle's direct low-pass sum, and
+    the mixed solve's residual recomputed by the oracle's own operator."""
+    pr = synth.problem("c3")
+    n, nf = pr.n, 2 * pr.n
+    fine_d = torch.empty(nf ** 3, dtype=torch.int64, device=DEV)
+    nobs = ctx.grid_assign(gpu(pr.pos), n, pr.box, pr.scheme, 2, fine_out=fine_d)
+    fine = fine_host(fine_d, (nf, nf, nf))
+    del fine_d
+    ref = oracle.assign(pr.pos, n, pr.box, pr.scheme, 2)
+    assert np.array_equal(fine, ref)
+    del fine
+    nobs_h = host(nobs)
+    pts = [tuple(int(v) for v in np.unravel_index(i, (n, n, n)))
+           for i in np.argsort(nobs_h, axis=None)[-3:]]
+    rng = np.random.default_rng(5)
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(3)] + [(0, 0, 0)]
+    vals = [oracle.lowpass_point(ref, n, 2, j) for j in pts]
+    scale = max(1.0, max(abs(v) for v in vals))
+    for j, v in zip(pts, vals):
+        assert abs(nobs_h[j] - v) <= 1e-11 * scale, (j, nobs_h[j], v)
+    del ref
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box, want_d=False)
+    wh, w_ref = host(w), oracle.window(pr.sel, n, pr.box)
+    assert np.array_equal(wh > 0, w_ref > 0)
+    assert rl2(wh, w_ref) <= 1e-14
+    assert abs(nbar - pr.n_gal / w_ref.sum()) <= 1e-12 * nbar
+    s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=pr.tol, prec=wf.MIXED)
+    assert info.status == wf.OK and info.rel_residual <= pr.tol
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    bh = host(b)
+    res = bh - oracle.matvec(tab, nbar, wh, host(s))
+    assert np.linalg.norm(res) <= 1.0001 * pr.tol * np.linalg.norm(bh)
+
+
 # ------------------------------------------------------------------------ batched solves
 def _mock(n, seed, box_per_cell=1.953):
     """A small mock of the batched workload: LCDM prior, SDSS-like selection, its own seed."""

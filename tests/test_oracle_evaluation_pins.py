@@ -1,0 +1,114 @@
+"""Pins of the evaluation oracle (Sec. 5.1 and Sec. 6.2: Gaussian smoothing, correlation and
+distance measures, binned density statistics) against closed forms and hand-worked cases."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import evaluation as ev
+
+
+def test_smoothing_plane_wave_closed_form():
+    """A plane wave is an eigenfunction: it is scaled by exp(-|k|^2 r_S^2 / 2)."""
+    n, box, rs = 16, 40.0, 3.0
+    x = np.arange(n) * box / n
+    m = (1, 2, 3)
+    f = np.cos(2 * np.pi * (m[0] * x[:, None, None] + m[1] * x[None, :, None] + m[2] * x[None, None, :]) / box)
+    k2 = (2 * np.pi / box) ** 2 * sum(v * v for v in m)
+    got = ev.smooth(f + 2.0, box, rs)
+    assert np.max(np.abs(got - (2.0 + math.exp(-0.5 * k2 * rs * rs) * f))) <= 1e-13
+
+
+def test_smoothing_impulse_is_the_normalised_gaussian():
+    """The response to a unit impulse at the origin is the normalised Gaussian sampled at the
+    nodes (r_S = 2.5 cells: the multiplier is negligible at the Nyquist frequency and the
+    periodic images are negligible at the centre region)."""
+    n, box = 32, 32.0
+    rs = 2.5
+    f = np.zeros((n, n, n))
+    f[0, 0, 0] = 1.0
+    got = ev.smooth(f, box, rs)
+    i = np.fft.fftfreq(n, 1.0 / n)  # signed offsets (H = 1)
+    r2 = i[:, None, None] ** 2 + i[None, :, None] ** 2 + i[None, None, :] ** 2
+    want = np.exp(-0.5 * r2 / rs ** 2) / ((2 * np.pi) ** 1.5 * rs ** 3)
+    near = r2 <= 36
+    assert np.max(np.abs(got[near] - want[near])) <= 1e-12 * want.max()
+    assert abs(got.sum() - 1.0) <= 1e-12
+
+
+def test_smoothing_keeps_the_mean_and_zero_radius_is_identity():
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((12, 12, 12))
+    assert abs(ev.smooth(f, 50.0, 7.0).mean() - f.mean()) <= 1e-14
+    assert np.max(np.abs(ev.smooth(f, 50.0, 0.0) - f)) <= 1e-13
+
+
+def test_compare_identities():
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-0.5, 2.0, (8, 8, 8))
+    same = ev.compare(x, x)
+    assert abs(same["r"] - 1.0) <= 1e-15 and same["d_euc"] == 0.0 and same["d_kl"] == 0.0
+    assert abs(ev.compare(2.5 * x, x)["r"] - 1.0) <= 1e-15
+    assert abs(ev.compare(-x, x)["r"] + 1.0) <= 1e-15
+    assert abs(ev.compare(x + 0.25, x)["d_euc"] - 0.25) <= 1e-15
+
+
+def test_compare_hand_worked():
+    rec = np.array([0.0, 1.0, -2.0, 3.0])  # 1 + delta = 1, 2, -1, 4
+    true = np.array([0.0, 0.0, 0.0, -1.0])  # 1 + delta = 1, 1, 1, 0
+    got = ev.compare(rec, true)
+    assert got["kl_excluded"] == 2
+    assert abs(got["d_kl"] - (2.0 * math.log(2.0)) / 4.0) <= 1e-16
+    assert abs(got["r"] - (-3.0) / (1.0 * math.sqrt(14.0))) <= 1e-15
+    assert abs(got["d_euc"] - math.sqrt((0 + 1 + 4 + 16) / 4.0)) <= 1e-15
+
+
+def test_histogram_bins_edges_and_overflow():
+    """Exact edges (width 0.25) go to the upper bin; values outside are counted apart."""
+    d = np.array([-0.75, -0.5, -0.26, 0.0, 0.24999, 1.9, 5.0, -3.0]).reshape(2, 2, 2)
+    w = np.array([1, 1, 1, 1, 0, 0, 0, 0], float).reshape(2, 2, 2)
+    # 1 + delta = 0.25, 0.5, 0.74, 1.0 | 1.24999, 2.9, 6.0, -2.0 ; bins of 0.25 from lo = 0
+    hist, under, over = ev.density_hist(d, w, 2.0, (0.0, 0.0, 0.0), [[0.0, 1e9]], 0.0, 0.25, 8)
+    assert hist[0, 0].tolist() == [0, 1, 2, 0, 1, 0, 0, 0]  # 0.25 | 0.5, 0.74 | 1.0
+    assert hist[0, 1].tolist() == [0, 0, 0, 0, 1, 0, 0, 0]
+    assert under[0].tolist() == [0, 1] and over[0].tolist() == [0, 2]
+
+
+def test_histogram_shells():
+    """Node (1, 0, 0) at distance H = 1 from the origin is in [1, 2), not in [0, 1)."""
+    n, box = 4, 4.0
+    d = np.zeros((n, n, n))
+    w = np.ones((n, n, n))
+    hist, _, _ = ev.density_hist(d, w, box, (0.0, 0.0, 0.0), [[0.0, 1.0], [1.0, 2.0]], 0.0, 0.5, 4)
+    r = ev.node_radius(n, box, (0.0, 0.0, 0.0))
+    assert hist[0, 0].sum() == np.count_nonzero(r < 1.0) == 1
+    assert hist[1, 0].sum() == np.count_nonzero((r >= 1.0) & (r < 2.0))
+
+
+def test_moments_discrete_uniform_closed_form():
+    """Equal counts in m bins: s = 0, k = -6 (m^2 + 1) / (5 (m^2 - 1)), s_P from the first bin."""
+    m, width, lo = 7, 0.03, 0.4
+    mom = ev.density_moments(np.full((1, 1, m), 5, dtype=np.int64), lo, width)[0, 0]
+    sigma = width * math.sqrt((m * m - 1) / 12.0)
+    assert mom[0] == 5 * m
+    assert abs(mom[1] - (lo + (m / 2.0) * width - 1.0)) <= 1e-14
+    assert abs(mom[2] - sigma ** 2) <= 1e-15
+    assert abs(mom[5]) <= 1e-10
+    assert abs(mom[6] + 6.0 * (m * m + 1) / (5.0 * (m * m - 1))) <= 1e-12
+    assert abs(mom[7] - ((m - 1) / 2.0) * width / sigma) <= 1e-12
+
+
+def test_moments_two_point_skewness():
+    """Counts p q in two bins one width apart: skewness (q - p) / sqrt(pq) with weights p, q."""
+    p, q = 3, 1
+    h = np.zeros((1, 1, 5), dtype=np.int64)
+    h[0, 0, 1], h[0, 0, 2] = p, q
+    mom = ev.density_moments(h, 0.0, 1.0)[0, 0]
+    P, Q = p / (p + q), q / (p + q)
+    assert abs(mom[5] - (P - Q) / math.sqrt(P * Q)) <= 1e-12
+    assert abs(mom[6] - (1 - 6 * P * Q) / (P * Q)) <= 1e-12  # excess kurtosis of a two-point law
+
+
+def test_moments_empty_region_is_nan():
+    mom = ev.density_moments(np.zeros((1, 1, 4), dtype=np.int64), 0.0, 0.1)[0, 0]
+    assert mom[0] == 0 and np.all(np.isnan(mom[1:]))
