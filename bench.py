@@ -251,7 +251,7 @@ def gpu_arm(args):
     nref = torch.linalg.norm(s_ref)
     err_mixed = float(torch.linalg.norm(s_mixed - s_ref) / nref)
     err_fp64 = float(torch.linalg.norm(s_fp64 - s_ref) / nref)
-    del s_ref, w_r, b_r, nobs_r
+    del s_ref, b_r, nobs_r
     # ---- e2e through the C ABI with host buffers (positions in, solution out)
     pos_h = torch.from_numpy(pr.pos).pin_memory()
     s_h = torch.empty((n, n, n), dtype=torch.float64).pin_memory()
@@ -271,6 +271,7 @@ def gpu_arm(args):
 
     extra = {}
     if not args.no_forms:
+        extra["postproc"] = bench_postproc(ctx, pr, s_mixed, s_fp64, w_r)
         extra["batch"] = bench_batch(ctx, dev)
         extra["serving"] = bench_serving(ctx, dev)
     if rank != 0:
@@ -335,6 +336,45 @@ def batch_mocks(count=96, seed=2000):
         pos = synth._cached_catalogue("batch_n%d_s%d_g%d" % (n, seed + i, int(ng)),
                                       lambda: synth.lognormal_catalogue(n, box, k, p, sel, ng, seed + i))
         out.append((n, box, sel, pos, k, p))
+    return out
+
+
+def bench_postproc(ctx, pr, s_rec, s_ref, w):
+    """Sec. 5.1 / 6.2 evaluation of the 512^3 reconstruction: Gaussian smoothing at r_S = 10, 20,
+    30 Mpc/h (FP64 transforms, FP64-ALU-bound), the quality measures of the mixed solution
+    against the FP64 one, and the density statistics of the r_S = 10 field in the paper's radial
+    shells and observed / unobserved regions (1 + delta bins of 0.03 from -1)."""
+    import torch
+    n, box = pr.n, pr.box
+
+    def timed(f, reps=3):
+        f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = f()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    out = {"workload": "the 512^3 mixed-precision solution s (as delta), its FP64 counterpart as the "
+                       "reference; smoothing radii 10/20/30 Mpc/h; shells [0,200), [200,400), [400,inf), "
+                       "[0,600) Mpc/h from the observer; 200 bins of 0.03 in 1 + delta from -1"}
+    sm = torch.empty_like(s_rec)
+    for rs in (10.0, 20.0, 30.0):
+        ms, _ = timed(lambda: ctx.smooth(s_rec, box, rs, out=sm))
+        out["smooth_r%d_ms" % int(rs)] = ms
+    ms, q = timed(lambda: ctx.compare(s_rec, s_ref))
+    out["compare"] = {"ms": ms, "gbs": 16.0 * n ** 3 / (ms * 1e6), **q}
+    ctx.smooth(s_rec, box, 10.0, out=sm)
+    shells = [[0.0, 200.0], [200.0, 400.0], [400.0, float("inf")], [0.0, 600.0]]
+    obs = pr.sel.observer
+    ms, (hist, mom) = timed(lambda: ctx.density_stats(sm, w, box, obs, shells, -1.0, 0.03, 200))
+    out["density"] = {"ms": ms, "gbs": 16.0 * n ** 3 / (ms * 1e6),
+                      "r10_skewness_obs_unobs": [[round(float(mom[s, g, 5]), 4) for g in (0, 1)] for s in range(4)],
+                      "r10_kurtosis_obs_unobs": [[round(float(mom[s, g, 6]), 4) for g in (0, 1)] for s in range(4)],
+                      "r10_pearson_obs_unobs": [[round(float(mom[s, g, 7]), 4) for g in (0, 1)] for s in range(4)]}
     return out
 
 

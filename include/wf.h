@@ -136,6 +136,59 @@ const char* wf_last_error(void);
  * differ, the FP32 rounding.  Applies to solves started after the call. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
+/* ---- evaluation of a reconstruction (Sec. 5.1 and Sec. 6.2) ------------------------------ */
+
+/* Gaussian smoothing (Sec. 6.2, eq:GAUSS): out = the field convolved on the periodic grid with
+ * the normalised Gaussian of radius r_s, i.e. its DFT multiplied by exp(-|k|^2 r_s^2 / 2) with
+ * k = 2 pi m / box and m the signed index in (-n/2, n/2].  The paper prints the kernel as
+ * exp(+|r|^2 / 2 r_S^2); the decaying Gaussian is the reading taken.  FP64 transforms.
+ *   in, out  dev double [n^3] (row-major [x][y][z]; out may equal in)
+ *   r_s      smoothing radius in box units, >= 0 (0 returns the field through the transforms)
+ * Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED (n not compiled in), WF_ERR_OOM, WF_ERR_CUDA.
+ * Stream-ordered on `stream` (NULL: the context's stream). */
+wf_status wf_smooth(wf_ctx* ctx, const wf_grid* grid, const double* in, double r_s, double* out,
+                    void* stream);
+
+typedef struct {
+  double r;             /* correlation coefficient sum(t r) / (sqrt(sum t^2) sqrt(sum r^2)) */
+  double d_euc;         /* Euclidean distance sqrt(sum (r - t)^2 / N_cells) */
+  double d_kl;          /* (1 / N_cells) sum (1 + r) log((1 + r) / (1 + t)), over the cells where
+                           both 1 + r > 0 and 1 + t > 0 (the log is undefined elsewhere) */
+  int64_t kl_excluded;  /* cells left out of d_kl */
+} wf_compare_result;
+
+/* Sec. 5.1 quality measures between a reconstructed overdensity `rec` and a reference `truth`
+ * (dev double [n_cells] each, any layout): correlation coefficient, Euclidean distance and
+ * normalised Kullback-Leibler distance.  Sums are FP64 and deterministic.  Result on the host;
+ * waits for completion.  Errors: WF_ERR_ARG, WF_ERR_OOM, WF_ERR_CUDA. */
+wf_status wf_compare(wf_ctx* ctx, int64_t n_cells, const double* rec, const double* truth,
+                     wf_compare_result* out, void* stream);
+
+typedef struct {
+  double n_cells, mean, mu2, mu3, mu4, skewness, kurtosis, pearson;
+} wf_density_moments;
+
+/* Sec. 6.2 density statistics.  Counts of 1 + delta in n_bins bins [lo + i width, lo + (i + 1)
+ * width) per radial shell (shells[2 s] <= r < shells[2 s + 1], r = |i H - observer| at node i H,
+ * no periodic wrap) and region (0: w > 0, 1: w = 0); the bin index is floor(((1 + delta) - lo) /
+ * width) in FP64.  For each (shell, region), from the bin centres delta_i = lo + (i + 1/2) width
+ * - 1: N = sum f, the mean, the central moments mu_2..mu_4, skewness mu_3 / sigma^3, kurtosis
+ * mu_4 / sigma^4 - 3 and Pearson's skewness (mean - delta_mode) / sigma with the mode the first
+ * bin of largest count.  Values outside the bins are counted apart and do not enter the moments.
+ *   delta, w   dev double [n^3]
+ *   observer   host double[3], shells host double [n_shells][2]
+ *   hist       host int64 [n_shells][2][n_bins + 2]: the bins, then the below- and above-range
+ *              counts
+ *   moments    host wf_density_moments [n_shells][2]; every field but n_cells is NaN when a
+ *              region is empty
+ * Limits: n_shells >= 1, n_bins >= 1, n_shells (n_bins + 2) <= 6144, width > 0.  Counts are
+ * exact (integer atomics).  Waits for completion.
+ * Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED, WF_ERR_OOM, WF_ERR_CUDA. */
+wf_status wf_density_stats(wf_ctx* ctx, const wf_grid* grid, const double* delta, const double* w,
+                           const double* observer, int n_shells, const double* shells, double lo,
+                           double width, int n_bins, int64_t* hist, wf_density_moments* moments,
+                           void* stream);
+
 /* ---- tracing ------------------------------------------------------------------------ */
 
 /* Reset the context's launch counters and enable (1) or disable (0) per-kernel timing.

@@ -50,6 +50,15 @@ class Power(ctypes.Structure):
     _fields_ = [("k", dp), ("p", dp), ("n", c_int)]
 
 
+class CompareResult(ctypes.Structure):
+    _fields_ = [("r", c_double), ("d_euc", c_double), ("d_kl", c_double), ("kl_excluded", c_int64)]
+
+
+class DensityMoments(ctypes.Structure):
+    _fields_ = [("n_cells", c_double), ("mean", c_double), ("mu2", c_double), ("mu3", c_double),
+                ("mu4", c_double), ("skewness", c_double), ("kurtosis", c_double), ("pearson", c_double)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("prec", c_int), ("inner_tol", c_double),
                 ("precond", c_int)]
@@ -96,12 +105,16 @@ def lib():
         L.wf_poll.argtypes = [c_void_p, c_uint64, c_int, c_void_p, P(SolveInfo)]
         L.wf_profile.argtypes = [c_void_p, c_int]
         L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
+        L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
+        L.wf_compare.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, P(CompareResult), c_void_p]
+        L.wf_density_stats.argtypes = [c_void_p, P(Grid), c_void_p, c_void_p, P(c_double), c_int, P(c_double),
+                                       c_double, c_double, c_int, P(c_int64), P(DensityMoments), c_void_p]
         L.wf_profile_read.argtypes = [c_void_p, P(c_int64), P(c_int)]
         L.wf_profile_class.argtypes = [c_void_p, c_int, ctypes.c_char_p, c_int, P(c_int64), P(c_double),
                                        P(c_double)]
         for name in ("wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve", "wf_solve_batch",
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
-                     "wf_set_fused_planes"):
+                     "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -286,6 +299,45 @@ class Context:
         return st, outs, list(infos)
 
     # ---- tracing ------------------------------------------------------------------------
+    # ---- Sec. 5.1 and 6.2: evaluation of a reconstruction ---------------------------------
+    def smooth(self, field, box: float, r_s: float, out=None, stream=None):
+        """Field convolved with the normalised Gaussian of radius r_s (box units) on the periodic
+        grid (wf_smooth); FP64 [n,n,n] device tensors, out may be field."""
+        import torch
+        if out is None:
+            out = torch.empty_like(field)
+        g = Grid(int(field.shape[0]), float(box), 1)
+        st = lib().wf_smooth(self._h, ctypes.byref(g), _ptr(field), float(r_s), _ptr(out), _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_smooth")
+        return out
+
+    def compare(self, rec, truth, stream=None) -> dict:
+        """{"r", "d_euc", "d_kl", "kl_excluded"} of rec against truth (wf_compare)."""
+        res = CompareResult()
+        st = lib().wf_compare(self._h, int(rec.numel()), _ptr(rec), _ptr(truth), ctypes.byref(res), _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_compare")
+        return {f: getattr(res, f) for f, _ in res._fields_}
+
+    def density_stats(self, delta, w, box: float, observer, shells, lo: float, width: float, n_bins: int,
+                      stream=None):
+        """(hist [S, 2, n_bins + 2] int64 with the below/above-range counts last, moments [S, 2, 8]
+        in DensityMoments order) of 1 + delta per shell and region (wf_density_stats)."""
+        shells = np.ascontiguousarray(np.asarray(shells, dtype=np.float64).reshape(-1, 2))
+        S = shells.shape[0]
+        obs = (c_double * 3)(*[float(v) for v in observer])
+        hist = np.zeros((S, 2, n_bins + 2), dtype=np.int64)
+        mom = (DensityMoments * (2 * S))()
+        g = Grid(int(delta.shape[0]), float(box), 1)
+        st = lib().wf_density_stats(self._h, ctypes.byref(g), _ptr(delta), _ptr(w), obs, S,
+                                    shells.ctypes.data_as(ctypes.POINTER(c_double)), float(lo), float(width),
+                                    int(n_bins), hist.ctypes.data_as(ctypes.POINTER(c_int64)), mom, _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_density_stats")
+        m = np.array([[getattr(x, f) for f, _ in DensityMoments._fields_] for x in mom]).reshape(S, 2, 8)
+        return hist, m
+
     def set_fused_planes(self, on: bool = True):
         """FP32 y / z / y transforms as one cluster kernel per x-plane (True) or as three
         separate passes (False, the default), for solves started afterwards

@@ -406,6 +406,36 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   return s;
 }
 
+wf_status wf_smooth(wf_ctx* ctx, const wf_grid* grid, const double* in, double r_s, double* out, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return smooth_run(*c, *grid, in, r_s, out, (cudaStream_t)stream);
+}
+
+wf_status wf_compare(wf_ctx* ctx, int64_t n_cells, const double* rec, const double* truth, wf_compare_result* out,
+                     void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return compare_run(*c, n_cells, rec, truth, out, (cudaStream_t)stream);
+}
+
+wf_status wf_density_stats(wf_ctx* ctx, const wf_grid* grid, const double* delta, const double* w,
+                           const double* observer, int n_shells, const double* shells, double lo, double width,
+                           int n_bins, int64_t* hist, wf_density_moments* moments, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return density_run(*c, *grid, delta, w, observer, n_shells, shells, lo, width, n_bins, hist, moments,
+                     (cudaStream_t)stream);
+}
+
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on) {
   if (!ctx) return WF_ERR_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);

@@ -168,6 +168,13 @@ inline int supported_size(int n) {
 // ---- entry points of the compute modules (defined in the .cu files) ----------------------
 wf_status assign_run(Ctx& c, const wf_grid& g, int scheme, const double* pos, int64_t n_gal,
                      uint64_t* fine_out, double* n_obs, cudaStream_t st);
+// evaluation of a reconstruction (wf_post.cu)
+wf_status smooth_run(Ctx& c, const wf_grid& g, const double* in, double r_s, double* out, cudaStream_t st);
+wf_status compare_run(Ctx& c, int64_t n_cells, const double* rec, const double* truth, wf_compare_result* out,
+                      cudaStream_t st);
+wf_status density_run(Ctx& c, const wf_grid& g, const double* delta, const double* w, const double* observer,
+                      int n_shells, const double* shells, double lo, double width, int n_bins, int64_t* hist,
+                      wf_density_moments* moments, cudaStream_t st);
 wf_status noise_run(Ctx& c, const wf_grid& g, const wf_selection& sel, const double* n_obs,
                     int64_t n_gal, double* w, double* d, double* b, double* nbar, cudaStream_t st);
 

@@ -25,4 +25,8 @@ struct Group {
 
 Group* make_group_n(int n, int prec);
 
+// Gaussian smoothing of one field of size N (instantiated with the solve drivers of each size).
+template <int N>
+wf_status smooth_n(Ctx& c, const double* in, double* out, double box, double r_s, cudaStream_t st);
+
 }  // namespace wf

@@ -671,6 +671,36 @@ struct GroupMixed : GroupCommon<N> {
   }
 };
 
+// Gaussian smoothing of one FP64 field (Sec. 6.2, eq:GAUSS read as the decaying Gaussian):
+// out = F^-1 [exp(-|k|^2 r_s^2 / 2) F in] on the periodic grid, k = 2 pi m / box.  The multiplier
+// depends on n2 = |m|^2 only, so the x pass applies it from an n2-indexed table, as it does the
+// prior; the transforms are the solver's FP64 passes.
+template <int N>
+wf_status smooth_n(Ctx& c, const double* in, double* out, double box, double r_s, cudaStream_t st) {
+  using SD = Spec<FP64Arith, N>;
+  WF_CUDA(SD::attrs());
+  const double2* tw;
+  WF_TRY(c.tw(N, &tw));
+  double2 *T, *T2;
+  double* part;
+  WF_TRY(c.get("sm_T", SD::SPEC * sizeof(double2), (void**)&T));
+  WF_TRY(c.get("sm_T2", SD::SPEC * sizeof(double2), (void**)&T2));
+  WF_TRY(c.get("sm_part", (size_t)SD::NPART * sizeof(double), (void**)&part));
+  std::vector<double> g(SD::TAB);
+  const double kf = 2.0 * 3.14159265358979323846 / box;
+  for (int n2 = 0; n2 < SD::TAB; ++n2) g[n2] = std::exp(-0.5 * kf * kf * (double)n2 * r_s * r_s);
+  double* gt;
+  WF_TRY(upload_tables<double>(c, "sm_g", g, &gt, st));
+  SD::zfwd(c, 1, in, T, tw, part, false, nullptr, st);
+  SD::ypass(c, 1, T, tw, nullptr, -1, st);
+  SD::template xmul<true, true, false>(c, 1, T, T2, gt, tw, part, nullptr, st);
+  SD::ypass(c, 1, T2, tw, nullptr, +1, st);
+  SD::template zinv<ZI_STORE>(c, 1, T2, out, nullptr, nullptr, nullptr, 1.0 / (double)SD::V, tw, part, nullptr,
+                              st);
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
 template <int N>
 Group* make_group(int prec) {
   if (prec == WF_MIXED) return new GroupMixed<N>();

@@ -1,0 +1,130 @@
+"""GPU evaluation steps (Sec. 5.1 quality measures, Sec. 6.2 smoothing and density statistics)
+against the evaluation oracle, through the C ABI, on seeded synthetic fields.
+
+Tolerances: smoothing relative L2 1e-13 (FP64 transforms on both sides, different orders); the
+measures 1e-12 relative (FP64 sums in different orders, log to an ulp); histogram counts bit for
+bit (the bin and shell decisions are the same FP64 operations on both sides); moments 1e-11
+relative (from identical counts, sums in different orders).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import evaluation as ev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_0906_3978_gb300 as wf  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    wf.build()
+    c = wf.Context(0)
+    yield c
+    c.close()
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def rl2(a, r):
+    return float(np.linalg.norm(np.asarray(a) - r) / np.linalg.norm(r))
+
+
+@pytest.mark.parametrize("n,box,rs", [(16, 40.0, 0.0), (24, 50.0, 3.0), (48, 100.0, 5.5), (108, 211.0, 9.0),
+                                      (128, 250.0, 10.0)])
+def test_smoothing_matches_oracle(ctx, n, box, rs):
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal((n, n, n))
+    got = host(ctx.smooth(gpu(f), box, rs))
+    assert rl2(got, ev.smooth(f, box, rs)) <= 1e-13
+
+
+def test_smoothing_in_place_and_plane_wave(ctx):
+    n, box, rs = 32, 64.0, 4.0
+    x = np.arange(n) * box / n
+    f = 1.0 + np.cos(2 * np.pi * (3 * x[:, None, None] + 1 * x[None, :, None] + 2 * x[None, None, :]) / box)
+    t = gpu(f)
+    ctx.smooth(t, box, rs, out=t)
+    k2 = (2 * np.pi / box) ** 2 * 14
+    want = 1.0 + math.exp(-0.5 * k2 * rs * rs) * (f - 1.0)
+    assert np.max(np.abs(host(t) - want)) <= 1e-13
+
+
+def test_compare_matches_oracle(ctx):
+    rng = np.random.default_rng(7)
+    true = rng.normal(0.0, 0.8, (40, 40, 40))
+    rec = 0.7 * true + rng.normal(0.0, 0.3, true.shape)
+    rec[:3, :, :5] = -1.5   # 1 + delta < 0: left out of D_KL
+    true[5, 5, :] = -1.0    # 1 + delta = 0: left out too
+    got = ctx.compare(gpu(rec), gpu(true))
+    ref = ev.compare(rec, true)
+    assert got["kl_excluded"] == ref["kl_excluded"] > 0
+    for k in ("r", "d_euc", "d_kl"):
+        assert abs(got[k] - ref[k]) <= 1e-12 * abs(ref[k]), k
+
+
+def test_compare_identities(ctx):
+    x = np.random.default_rng(8).uniform(-0.5, 2.0, (16, 16, 16))
+    got = ctx.compare(gpu(x), gpu(x))
+    assert abs(got["r"] - 1.0) <= 1e-15 and got["d_euc"] == 0.0 and got["d_kl"] == 0.0 and got["kl_excluded"] == 0
+
+
+def _density_case(n, seed):
+    rng = np.random.default_rng(seed)
+    delta = np.exp(rng.normal(0.0, 0.45, (n, n, n))) - 1.1
+    delta.ravel()[rng.integers(0, n ** 3, 20)] = 9.0       # above the bins
+    delta.ravel()[rng.integers(0, n ** 3, 5)] = np.nan     # in no bin
+    w = np.where(rng.uniform(size=(n, n, n)) > 0.4, rng.uniform(size=(n, n, n)), 0.0)
+    return delta, w
+
+
+@pytest.mark.parametrize("n,box", [(24, 50.0), (48, 100.0), (128, 600.0)])
+def test_density_stats_match_oracle(ctx, n, box):
+    delta, w = _density_case(n, n)
+    obs = (0.0, box / 2, 0.04 * box)
+    shells = [[0.0, box / 3], [box / 3, 2 * box / 3], [2 * box / 3, np.inf], [0.0, 1.2 * box]]
+    lo, width, nb = -0.2, 0.03, 150
+    hist, mom = ctx.density_stats(gpu(delta), gpu(w), box, obs, shells, lo, width, nb)
+    h_ref, under, over = ev.density_hist(delta, w, box, obs, shells, lo, width, nb)
+    assert np.array_equal(hist[..., :nb], h_ref)
+    assert np.array_equal(hist[..., nb], under) and np.array_equal(hist[..., nb + 1], over)
+    m_ref = ev.density_moments(h_ref, lo, width)
+    assert np.allclose(mom, m_ref, rtol=1e-11, atol=1e-13, equal_nan=True)
+
+
+def test_density_exact_edges_and_empty_region(ctx):
+    """Values on bin edges (width 0.25, exact in binary) fall in the upper bin on both sides; a
+    region with no cell has NaN moments."""
+    n, box = 8, 8.0
+    vals = np.array([-1.0, -0.75, -0.5, 0.0, 0.25, 1.0, 1.75])
+    delta = vals[np.arange(n ** 3) % len(vals)].reshape(n, n, n)
+    w = np.ones((n, n, n))
+    hist, mom = ctx.density_stats(gpu(delta), gpu(w), box, (0.0, 0.0, 0.0), [[0.0, np.inf]], 0.0, 0.25, 10)
+    h_ref, under, over = ev.density_hist(delta, w, box, (0.0, 0.0, 0.0), [[0.0, np.inf]], 0.0, 0.25, 10)
+    assert np.array_equal(hist[..., :10], h_ref)
+    assert mom[0, 1, 0] == 0 and np.all(np.isnan(mom[0, 1, 1:]))
+
+
+def test_evaluation_argument_errors(ctx):
+    d = gpu(np.zeros((8, 8, 8)))
+    for kw in [dict(width=0.0), dict(shells=[[0.0, 1.0]] * 9), dict(nb=6000)]:
+        a = dict(width=0.03, shells=[[0.0, 10.0]], nb=10)
+        a.update(kw)
+        with pytest.raises(wf.WfError) as e:
+            ctx.density_stats(d, d, 8.0, (0.0, 0.0, 0.0), a["shells"], 0.0, a["width"], a["nb"])
+        assert e.value.status == wf.ERR_ARG
+    with pytest.raises(wf.WfError) as e:
+        ctx.smooth(d, 8.0, -1.0)
+    assert e.value.status == wf.ERR_ARG
