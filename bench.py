@@ -360,13 +360,18 @@ def bench_postproc(ctx, pr, s_rec, s_ref, w):
 
     out = {"workload": "the 512^3 mixed-precision solution s (as delta), its FP64 counterpart as the "
                        "reference; smoothing radii 10/20/30 Mpc/h; shells [0,200), [200,400), [400,inf), "
-                       "[0,600) Mpc/h from the observer; 200 bins of 0.03 in 1 + delta from -1"}
+                       "[0,600) Mpc/h from the observer; 200 bins of 0.03 in 1 + delta from -1; the "
+                       "inverse-weighting grid of the same catalogue"}
     sm = torch.empty_like(s_rec)
     for rs in (10.0, 20.0, 30.0):
         ms, _ = timed(lambda: ctx.smooth(s_rec, box, rs, out=sm))
         out["smooth_r%d_ms" % int(rs)] = ms
     ms, q = timed(lambda: ctx.compare(s_rec, s_ref))
     out["compare"] = {"ms": ms, "gbs": 16.0 * n ** 3 / (ms * 1e6), **q}
+    pos = torch.from_numpy(pr.pos).to(s_rec.device)
+    ms, _ = timed(lambda: ctx.grid_assign_weighted(pos, ctx.selection_eval(pr.sel, pos, reciprocal=True), n, box,
+                                                   pr.scheme, 2))
+    out["inverse_weighting_ms"] = ms  # masses 1 / w at the galaxies, 1024^3 fine grid, low-pass
     ctx.smooth(s_rec, box, 10.0, out=sm)
     shells = [[0.0, 200.0], [200.0, 400.0], [400.0, float("inf")], [0.0, 600.0]]
     obs = pr.sel.observer

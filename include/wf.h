@@ -136,6 +136,30 @@ const char* wf_last_error(void);
  * differ, the FP32 rounding.  Applies to solves started after the call. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
+/* ---- inverse-weighting estimator (Sec. 5, Eq. def:ngrid with galaxy mass 1/w) ------------- */
+
+/* The selection w (Sec. 2.3: cone x holes x radial law, the same formula and operation order as
+ * the window of wf_build_noise) at arbitrary positions, e.g. the completeness at each galaxy.
+ * reciprocal = 1 returns 1 / w instead (0 where w = 0): the galaxy masses of the
+ * inverse-weighting estimator.
+ *   pos  dev double [n_pts][3], out dev double [n_pts]
+ * Errors: WF_ERR_ARG, WF_ERR_OOM, WF_ERR_CUDA.  Waits for completion. */
+wf_status wf_selection_eval(wf_ctx* ctx, const wf_selection* sel, const double* pos, int64_t n_pts,
+                            int reciprocal, double* out, void* stream);
+
+/* Supersampled assignment with per-galaxy masses (the inverse-weighting estimator of Sec. 5
+ * takes mass 1 / w(x_g)), then the same ideal low-pass as wf_grid_assign.  Each node's
+ * contribution is its Q48 fixed-point weight times wgt[g], rounded once to the nearest Q32 unit,
+ * so the fine grid is exact and independent of the order of the atomics.
+ *   pos      dev double [n_gal][3];  wgt dev double [n_gal], each in [0, 2^32)
+ *   fine_out dev uint64 [(s n)^3] or NULL: the fine grid in units of 2^-32 weighted galaxies
+ *   n_obs    dev double [n^3]: the low-passed weighted counts
+ * Errors: WF_ERR_ARG (bad position or weight), WF_ERR_OVERFLOW (a cell beyond 2^64 units),
+ * WF_ERR_UNSUPPORTED, WF_ERR_OOM, WF_ERR_CUDA.  Waits for completion. */
+wf_status wf_grid_assign_weighted(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const double* pos,
+                                  const double* wgt, int64_t n_gal, uint64_t* fine_out, double* n_obs,
+                                  void* stream);
+
 /* ---- evaluation of a reconstruction (Sec. 5.1 and Sec. 6.2) ------------------------------ */
 
 /* Gaussian smoothing (Sec. 6.2, eq:GAUSS): out = the field convolved on the periodic grid with

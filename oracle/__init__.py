@@ -7,6 +7,8 @@ Each function follows the paper (Kitaura et al. 2009, arXiv:0906.3978):
   assign      Sec. 2.2 "Supersampling step", Eq. def:ngrid (fixed-point CIC/TSC)
   lowpass     Sec. 2.2, supersampling step 2 (ideal low-pass, sampling at target grid)
   window      Sec. 2.3 (3D mask w <= 1; analytic cone x holes x radial law)
+  window_at, assign_weighted
+              Sec. 5, Eq. def:ngrid with galaxy mass 1/w (the inverse-weighting estimator)
   build_noise Sec. 2.4, Eqs. eq:datamodel, eq:nmean, eq:noiseav
   sinv_table  Sec. 2.5.1, Fourier-diagonal prior S
   matvec/cg   Sec. 2.5.1, Eq. eq:WF, by a Krylov (CG) inversion
@@ -53,6 +55,9 @@ def lib():
         i, d, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
         L.oracle_assign.argtypes = [i, d, i, i, dp, i64, u64p]
         L.oracle_lowpass.argtypes = [i, i, u64p, dp]
+        L.oracle_lowpass_scaled.argtypes = [i, i, u64p, d, dp]
+        L.oracle_assign_weighted.argtypes = [i, d, i, i, dp, dp, i64, u64p]
+        L.oracle_window_at.argtypes = [i64, dp, dp, dp, d, i, dp, i, dp, dp]
         L.oracle_lowpass_point.argtypes = [i, i, u64p, i, i, i]
         L.oracle_lowpass_point.restype = d
         L.oracle_window.argtypes = [i, d, dp, dp, d, i, dp, i, dp, dp]
@@ -111,6 +116,41 @@ def lowpass_point(fine, n: int, ss: int, j) -> float:
     """One output node of the low-pass by the direct sum over the fine grid."""
     fine = np.ascontiguousarray(fine, dtype=np.uint64)
     return float(lib().oracle_lowpass_point(n, ss, _u64p(fine), int(j[0]), int(j[1]), int(j[2])))
+
+
+def lowpass_scaled(fine, n: int, ss: int, unit: float) -> np.ndarray:
+    """The low-pass of a fine grid holding fine * unit galaxies per cell (2^-32 for
+    ``assign_weighted``)."""
+    fine = np.ascontiguousarray(fine, dtype=np.uint64)
+    out = np.empty(n ** 3, dtype=np.float64)
+    _check(lib().oracle_lowpass_scaled(n, ss, _u64p(fine), float(unit), _dp(out)), "lowpass_scaled")
+    return out.reshape(n, n, n)
+
+
+def assign_weighted(pos, wgt, n: int, box: float, scheme: int, ss: int = 2) -> np.ndarray:
+    """Fine grid [(ss n)^3] uint64 in Q32 units of weighted galaxies: each node contribution is
+    rint(Q48 weight * wgt * 2^-16) (Sec. 5, Eq. def:ngrid with galaxy mass wgt)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    wgt = np.ascontiguousarray(wgt, dtype=np.float64).ravel()
+    nf = ss * n
+    fine = np.empty(nf ** 3, dtype=np.uint64)
+    _check(lib().oracle_assign_weighted(n, box, ss, scheme, _dp(pos), _dp(wgt), pos.shape[0], _u64p(fine)),
+           "assign_weighted")
+    return fine.reshape(nf, nf, nf)
+
+
+def window_at(sel, pts) -> np.ndarray:
+    """The selection w at arbitrary positions pts [m, 3] (Sec. 2.3, the completeness at a galaxy)."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+    obs = np.ascontiguousarray(sel.observer, dtype=np.float64)
+    ax = np.ascontiguousarray(sel.axis, dtype=np.float64)
+    holes = np.ascontiguousarray(np.asarray(sel.holes, dtype=np.float64).reshape(-1, 4))
+    rp = np.ascontiguousarray(np.resize(np.asarray(sel.radial_params, dtype=np.float64), 4))
+    w = np.empty(pts.shape[0], dtype=np.float64)
+    _check(lib().oracle_window_at(pts.shape[0], _dp(pts), _dp(obs), _dp(ax), float(sel.half_angle),
+                                  holes.shape[0], _dp(holes), int(sel.radial_kind), _dp(rp), _dp(w)),
+           "window_at")
+    return w
 
 
 def window(sel, n: int, box: float) -> np.ndarray:

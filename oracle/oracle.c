@@ -127,6 +127,42 @@ int oracle_assign(int n, double box, int ss, int scheme, const double* pos, int6
   return overflow ? OR_ERR_OVERFLOW : OR_OK;
 }
 
+/* Weighted assignment for the inverse-weighting estimator (Sec. 5, Eq. def:ngrid with the
+ * galaxy mass 1/w): galaxy g carries weight wgt[g] >= 0.  Each node's contribution is its Q48
+ * fixed-point weight (as in oracle_assign) times wgt[g], rounded once to the nearest Q32 unit:
+ * rint(double(q48) * wgt[g] * 2^-16).  The grid is then exact and independent of the order of
+ * the galaxies; a cell holds fine[i] * 2^-32 weighted galaxies. */
+int oracle_assign_weighted(int n, double box, int ss, int scheme, const double* pos, const double* wgt,
+                           int64_t n_gal, uint64_t* fine) {
+  if (n <= 0 || ss < 1 || !(box > 0) || (scheme != 1 && scheme != 2) || n_gal < 0) return OR_ERR_ARG;
+  int64_t nf = (int64_t)ss * n;
+  size_t nfine = (size_t)nf * nf * nf;
+  memset(fine, 0, nfine * sizeof(uint64_t));
+  double scale = ((double)nf * 65536.0) / box;
+  int overflow = 0;
+  for (int64_t g = 0; g < n_gal; ++g) {
+    if (!(wgt[g] >= 0.0) || !(wgt[g] < 4294967296.0)) return OR_ERR_ARG; /* < 2^32 */
+    int64_t nd[3][3];
+    uint64_t wt[3][3];
+    int cnt = 0;
+    for (int a = 0; a < 3; ++a) {
+      cnt = axis_weights(pos[3 * g + a], scale, nf, scheme, nd[a], wt[a]);
+      if (cnt < 0) return OR_ERR_ARG;
+    }
+    for (int i = 0; i < cnt; ++i)
+      for (int j = 0; j < cnt; ++j)
+        for (int k = 0; k < cnt; ++k) {
+          double q = (double)(wt[0][i] * wt[1][j] * wt[2][k]);
+          uint64_t add = (uint64_t)rint(q * wgt[g] * (1.0 / 65536.0));
+          size_t idx = ((size_t)nd[0][i] * nf + (size_t)nd[1][j]) * nf + (size_t)nd[2][k];
+          uint64_t old = fine[idx];
+          fine[idx] = old + add;
+          if (fine[idx] < old) overflow = 1;
+        }
+  }
+  return overflow ? OR_ERR_OVERFLOW : OR_OK;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* 2. Plain complex DFT: recursive decimation in time, radix = smallest prime factor    */
 /* ------------------------------------------------------------------------------------ */
@@ -237,10 +273,16 @@ static long sfreq(long j, long n) { return j <= n / 2 ? j : j - n; }
  * coarse indices satisfy |k| < n/2 (the coarse Nyquist planes are dropped, which keeps
  * the result real and alias-free); place them in an n^3 spectrum and return
  * (1/n^3) * inverse DFT.  The k = 0 mode is kept, so sum(n_obs) = sum(fine)/2^48. */
+int oracle_lowpass_scaled(int n, int ss, const uint64_t* fine, double unit, double* n_obs);
 int oracle_lowpass(int n, int ss, const uint64_t* fine, double* n_obs) {
+  return oracle_lowpass_scaled(n, ss, fine, 1.0 / 281474976710656.0 /* 2^-48 */, n_obs);
+}
+/* The same for a fine grid in other fixed-point units: a cell holds fine[i] * unit galaxies
+ * (2^-48 for oracle_assign, 2^-32 for oracle_assign_weighted). */
+int oracle_lowpass_scaled(int n, int ss, const uint64_t* fine, double unit, double* n_obs) {
   if (n <= 0 || ss < 1 || (n % 2) != 0) return OR_ERR_ARG;
   size_t N = (size_t)n, V = N * N * N;
-  const double q48 = 1.0 / 281474976710656.0; /* 2^-48 */
+  const double q48 = unit;
   if (ss == 1) {
     for (size_t i = 0; i < V; ++i) n_obs[i] = (double)fine[i] * q48;
     return OR_OK;
@@ -319,6 +361,49 @@ double oracle_lowpass_point(int n, int ss, const uint64_t* fine, int jx, int jy,
  * written here.  axis and the hole directions must be unit vectors.
  * holes[4*h] = (hx, hy, hz, rho_h).  radial_kind 0: f = 1; 1: f = exp(-(r/p0)^2);
  * 2: f = (r/p0)^p1 * exp(p1 * (1 - r/p0)) (peak 1 at r = p0). */
+static double window_value(double dx, double dy, double dz, const double* axis, double cos_half,
+                           int n_holes, const double* holes, const double* cos_h, int radial_kind,
+                           const double* rp) {
+  double r = sqrt(dx * dx + dy * dy + dz * dz);
+  double val = 0.0;
+  if (r > 0.0) {
+    int inside = (dx * axis[0] + dy * axis[1] + dz * axis[2]) >= cos_half * r;
+    for (int h = 0; h < n_holes && inside; ++h) {
+      const double* hv = holes + 4 * h;
+      if ((dx * hv[0] + dy * hv[1] + dz * hv[2]) > cos_h[h] * r) inside = 0;
+    }
+    if (inside) {
+      if (radial_kind == 0) {
+        val = 1.0;
+      } else if (radial_kind == 1) {
+        double t = r / rp[0];
+        val = exp(-(t * t));
+      } else {
+        double t = r / rp[0];
+        val = pow(t, rp[1]) * exp(rp[1] * (1.0 - t));
+      }
+    }
+  }
+  return val;
+}
+
+/* The same selection at arbitrary positions pts[3 i] (the completeness at a galaxy, for the
+ * inverse-weighting estimator of Sec. 5). */
+int oracle_window_at(int64_t n_pts, const double* pts, const double* obs, const double* axis,
+                     double half_angle, int n_holes, const double* holes, int radial_kind,
+                     const double* rp, double* w) {
+  if (n_pts < 0 || n_holes < 0 || radial_kind < 0 || radial_kind > 2) return OR_ERR_ARG;
+  double cos_half = cos(half_angle);
+  double* cos_h = (double*)malloc((size_t)(n_holes > 0 ? n_holes : 1) * sizeof(double));
+  if (!cos_h) return OR_ERR_OOM;
+  for (int h = 0; h < n_holes; ++h) cos_h[h] = cos(holes[4 * h + 3]);
+  for (int64_t i = 0; i < n_pts; ++i)
+    w[i] = window_value(pts[3 * i] - obs[0], pts[3 * i + 1] - obs[1], pts[3 * i + 2] - obs[2], axis, cos_half,
+                        n_holes, holes, cos_h, radial_kind, rp);
+  free(cos_h);
+  return OR_OK;
+}
+
 int oracle_window(int n, double box, const double* obs, const double* axis, double half_angle,
                   int n_holes, const double* holes, int radial_kind, const double* rp,
                   double* w) {
@@ -335,27 +420,8 @@ int oracle_window(int n, double box, const double* obs, const double* axis, doub
         double dx = (double)ix * H - obs[0];
         double dy = (double)iy * H - obs[1];
         double dz = (double)iz * H - obs[2];
-        double r = sqrt(dx * dx + dy * dy + dz * dz);
-        double val = 0.0;
-        if (r > 0.0) {
-          int inside = (dx * axis[0] + dy * axis[1] + dz * axis[2]) >= cos_half * r;
-          for (int h = 0; h < n_holes && inside; ++h) {
-            const double* hv = holes + 4 * h;
-            if ((dx * hv[0] + dy * hv[1] + dz * hv[2]) > cos_h[h] * r) inside = 0;
-          }
-          if (inside) {
-            if (radial_kind == 0) {
-              val = 1.0;
-            } else if (radial_kind == 1) {
-              double t = r / rp[0];
-              val = exp(-(t * t));
-            } else {
-              double t = r / rp[0];
-              val = pow(t, rp[1]) * exp(rp[1] * (1.0 - t));
-            }
-          }
-        }
-        w[(ix * N + iy) * N + iz] = val;
+        w[(ix * N + iy) * N + iz] =
+            window_value(dx, dy, dz, axis, cos_half, n_holes, holes, cos_h, radial_kind, rp);
       }
   free(cos_h);
   return OR_OK;

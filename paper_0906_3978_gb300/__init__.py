@@ -106,6 +106,9 @@ def lib():
         L.wf_profile.argtypes = [c_void_p, c_int]
         L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
         L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
+        L.wf_selection_eval.argtypes = [c_void_p, P(SelectionC), c_void_p, c_int64, c_int, c_void_p, c_void_p]
+        L.wf_grid_assign_weighted.argtypes = [c_void_p, P(Grid), c_int, c_void_p, c_void_p, c_int64, c_void_p,
+                                              c_void_p, c_void_p]
         L.wf_compare.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, P(CompareResult), c_void_p]
         L.wf_density_stats.argtypes = [c_void_p, P(Grid), c_void_p, c_void_p, P(c_double), c_int, P(c_double),
                                        c_double, c_double, c_int, P(c_int64), P(DensityMoments), c_void_p]
@@ -114,7 +117,8 @@ def lib():
                                        P(c_double)]
         for name in ("wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve", "wf_solve_batch",
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
-                     "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats"):
+                     "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
+                     "wf_selection_eval", "wf_grid_assign_weighted"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -248,6 +252,36 @@ class Context:
         if check and st != OK:
             raise WfError(st, "wf_build_noise")
         return (w, d, b, nb.value) if check else (st, w, d, b, nb.value)
+
+    # ---- Sec. 5: the inverse-weighting estimator -----------------------------------------
+    def selection_eval(self, sel, pos, reciprocal=False, stream=None):
+        """w (or 1 / w, 0 where w = 0) at positions pos [m, 3] (device FP64) with the window's
+        formula (wf_selection_eval)."""
+        import torch
+        m = int(pos.shape[0])
+        w = torch.empty(m, dtype=torch.float64, device=pos.device)
+        s, keep = make_selection(sel)
+        st = lib().wf_selection_eval(self._h, ctypes.byref(s), _ptr(pos), m, 1 if reciprocal else 0, _ptr(w),
+                                     _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_selection_eval")
+        return w
+
+    def grid_assign_weighted(self, pos, wgt, n: int, box: float, scheme: int = TSC, supersample: int = 2,
+                             fine_out=None, n_obs=None, stream=None, check=True):
+        """Low-passed counts of galaxies with masses wgt (e.g. 1 / w for inverse weighting),
+        [n, n, n] FP64 on the device (wf_grid_assign_weighted)."""
+        import torch
+        if n_obs is None:
+            n_obs = torch.empty((n, n, n), dtype=torch.float64, device=pos.device)
+        g = Grid(n, float(box), supersample)
+        ngal = int(pos.shape[0])
+        st = lib().wf_grid_assign_weighted(self._h, ctypes.byref(g), scheme, _ptr(pos) if ngal else None,
+                                           _ptr(wgt) if ngal else None, ngal, _ptr(fine_out), _ptr(n_obs),
+                                           _stream(stream))
+        if check and st != OK:
+            raise WfError(st, "wf_grid_assign_weighted")
+        return n_obs if check else (st, n_obs)
 
     # ---- Sec. 2.5.1 ---------------------------------------------------------------------
     def solve(self, w, nbar: float, b, box: float, pk_k, pk_p, tol=1e-6, max_iter=5000, prec=FP64,

@@ -406,6 +406,26 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   return s;
 }
 
+wf_status wf_selection_eval(wf_ctx* ctx, const wf_selection* sel, const double* pos, int64_t n_pts,
+                            int reciprocal, double* w, void* stream) {
+  if (!ctx || !sel) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return selection_at_run(*c, *sel, pos, n_pts, reciprocal != 0, w, (cudaStream_t)stream);
+}
+
+wf_status wf_grid_assign_weighted(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const double* pos,
+                                  const double* wgt, int64_t n_gal, uint64_t* fine_out, double* n_obs,
+                                  void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return assign_weighted_run(*c, *grid, (int)scheme, pos, wgt, n_gal, fine_out, n_obs, (cudaStream_t)stream);
+}
+
 wf_status wf_smooth(wf_ctx* ctx, const wf_grid* grid, const double* in, double r_s, double* out, void* stream) {
   if (!ctx) return WF_ERR_ARG;
   WF_TRY(check_grid(grid));

@@ -76,9 +76,48 @@ k_assign(const double* __restrict__ pos, long long n_gal, long long nf, double s
     }
 }
 
-__global__ void k_q48_to_double(const unsigned long long* __restrict__ fine, double* __restrict__ out, size_t n) {
+// Weighted assignment for the inverse-weighting estimator (Sec. 5, Eq. def:ngrid with galaxy
+// mass wgt[g], e.g. 1 / w): each node contribution is the Q48 weight times wgt[g], rounded once
+// to the nearest Q32 unit, so the grid is exact and independent of the order of the atomics.
+__global__ void __launch_bounds__(256)
+k_assign_weighted(const double* __restrict__ pos, const double* __restrict__ wgt, long long n_gal, long long nf,
+                  double scale, int scheme, unsigned long long* __restrict__ fine, int* __restrict__ err) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (g >= n_gal) return;
+  const double wg = wgt[g];
+  if (!(wg >= 0.0) || !(wg < 4294967296.0)) {  // [0, 2^32): a contribution stays below 2^64
+    atomicOr(err, 1);
+    return;
+  }
+  long long nd[3][3];
+  unsigned long long wt[3][3];
+  int cnt = 0;
+  for (int a = 0; a < 3; ++a) {
+    cnt = axis_nodes(pos[3 * g + a], scale, nf, scheme, nd[a], wt[a]);
+    if (cnt < 0) {
+      atomicOr(err, 1);
+      return;
+    }
+  }
+  for (int i = 0; i < cnt; ++i)
+    for (int j = 0; j < cnt; ++j) {
+      const size_t rowb = ((size_t)nd[0][i] * nf + (size_t)nd[1][j]) * nf;
+      const unsigned long long wij = wt[0][i] * wt[1][j];
+      for (int k = 0; k < cnt; ++k) {
+        const double q = __ull2double_rn(wij * wt[2][k]);  // exact: < 2^49
+        const unsigned long long add = __double2ull_rn(__dmul_rn(__dmul_rn(q, wg), 1.0 / 65536.0));
+        if (add == 0) continue;
+        const unsigned long long old = atomicAdd(fine + rowb + nd[2][k], add);
+        if (old + add < old) atomicOr(err, 2);
+      }
+    }
+}
+
+// fine grid in fixed-point units (2^-48 galaxies, 2^-32 weighted galaxies) -> FP64 counts
+__global__ void k_q48_to_double(const unsigned long long* __restrict__ fine, double* __restrict__ out, size_t n,
+                                double unit) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = __ull2double_rn(fine[i]) * 3.5527136788005009e-15;  // 2^-48
+    out[i] = __ull2double_rn(fine[i]) * unit;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -201,7 +240,8 @@ static cudaError_t smem_attr(K kernel, size_t bytes) {
 }
 
 template <class R, int N>
-static wf_status lowpass_sized(Ctx& c, const unsigned long long* fine, double* n_obs, cudaStream_t st) {
+static wf_status lowpass_sized(Ctx& c, const unsigned long long* fine, double* n_obs, double unit,
+                               cudaStream_t st) {
   constexpr int NL = lp_lines<R, N>();
   const size_t smem = (size_t)(N * (NL + 1) + 2 * N) * sizeof(cx<R>);
   const int nt = lp_threads<R, N>();
@@ -213,7 +253,7 @@ static wf_status lowpass_sized(Ctx& c, const unsigned long long* fine, double* n
   WF_CUDA(smem_attr(k_lowpass<R, N, 0, unsigned long long>, smem));
   WF_CUDA(smem_attr(k_lowpass<R, N, 1, double>, smem));
   WF_CUDA(smem_attr(k_lowpass<R, N, 2, double>, smem));
-  const double q48 = 3.5527136788005009e-15;
+  const double q48 = unit;
   const double V = (double)N * N * N;
   c.launch("lowpass_z", 8 * (8 * V + 4 * V), st, [&] {
     k_lowpass<R, N, 0, unsigned long long><<<(unsigned)((size_t)4 * N * N / NL), nt, smem, st>>>(fine, t1, q48, tw);
@@ -228,8 +268,23 @@ static wf_status lowpass_sized(Ctx& c, const unsigned long long* fine, double* n
   return WF_OK;
 }
 
+static wf_status assign_any(Ctx& c, const wf_grid& g, int scheme, const double* pos, const double* wgt,
+                            int64_t n_gal, uint64_t* fine_out, double* n_obs, cudaStream_t st);
+
 wf_status assign_run(Ctx& c, const wf_grid& g, int scheme, const double* pos, int64_t n_gal,
                      uint64_t* fine_out, double* n_obs, cudaStream_t st) {
+  return assign_any(c, g, scheme, pos, nullptr, n_gal, fine_out, n_obs, st);
+}
+
+wf_status assign_weighted_run(Ctx& c, const wf_grid& g, int scheme, const double* pos, const double* wgt,
+                              int64_t n_gal, uint64_t* fine_out, double* n_obs, cudaStream_t st) {
+  if (n_gal > 0 && !wgt) return WF_ERR_ARG;
+  return assign_any(c, g, scheme, pos, wgt, n_gal, fine_out, n_obs, st);
+}
+
+// wgt == nullptr: unit masses in Q48; else masses wgt[g] in Q32.
+static wf_status assign_any(Ctx& c, const wf_grid& g, int scheme, const double* pos, const double* wgt,
+                            int64_t n_gal, uint64_t* fine_out, double* n_obs, cudaStream_t st) {
   const int n = g.n, ss = g.supersample;
   if (!supported_size(n)) return WF_ERR_UNSUPPORTED;
   if (!(g.box > 0.0) || !(g.box < 1e300) || (ss != 1 && ss != 2) || (scheme != WF_CIC && scheme != WF_TSC) ||
@@ -245,21 +300,26 @@ wf_status assign_run(Ctx& c, const wf_grid& g, int scheme, const double* pos, in
   WF_CUDA(cudaMemsetAsync(fine, 0, nfine * sizeof(uint64_t), st));  // counted as a launch below
   c.prof.launches += 1;
   const double scale = ((double)nf * 65536.0) / g.box;
+  const double unit = wgt ? 2.3283064365386963e-10 /* 2^-32 */ : 3.5527136788005009e-15 /* 2^-48 */;
   if (n_gal > 0) {
     c.launch("assign", 24.0 * n_gal + 16.0 * 27 * n_gal, st, [&] {
-      k_assign<<<(unsigned)((n_gal + 255) / 256), 256, 0, st>>>(pos, (long long)n_gal, nf, scale, scheme, fine, err);
+      if (wgt)
+        k_assign_weighted<<<(unsigned)((n_gal + 255) / 256), 256, 0, st>>>(pos, wgt, (long long)n_gal, nf, scale,
+                                                                           scheme, fine, err);
+      else
+        k_assign<<<(unsigned)((n_gal + 255) / 256), 256, 0, st>>>(pos, (long long)n_gal, nf, scale, scheme, fine, err);
     });
     WF_CUDA(cudaGetLastError());
   }
   if (ss == 1) {
-    c.launch("q48", 16.0 * nfine, st, [&] { k_q48_to_double<<<1216, 256, 0, st>>>(fine, n_obs, nfine); });
+    c.launch("q48", 16.0 * nfine, st, [&] { k_q48_to_double<<<1216, 256, 0, st>>>(fine, n_obs, nfine, unit); });
     WF_CUDA(cudaGetLastError());
   } else {
     wf_status s = WF_ERR_UNSUPPORTED;
     switch (n) {
 #define WF_CASE(N) \
   case N:          \
-    s = lowpass_sized<double, N>(c, fine, n_obs, st); \
+    s = lowpass_sized<double, N>(c, fine, n_obs, unit, st); \
     break;
       WF_SIZES(WF_CASE)
 #undef WF_CASE

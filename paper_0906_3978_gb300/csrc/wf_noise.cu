@@ -8,6 +8,7 @@
 // The cone and hole tests are decisions taken in floating point; they are evaluated with
 // explicitly rounded IEEE operations in a fixed order (no contraction), so the decision is the
 // one the plain definition gives.
+#include <algorithm>
 #include <map>
 #include <mutex>
 
@@ -26,6 +27,34 @@ struct SelParams {
   int n_holes;
 };
 
+// The selection at offset (dx, dy, dz) from the observer: cone x holes x radial law, w = 0 at
+// the observer; every operation explicitly rounded, in the order of the definition.
+WF_D double sel_value(const SelParams& s, const double4* __restrict__ holes, double dx, double dy, double dz) {
+  const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+  double val = 0.0;
+  if (r > 0.0) {
+    bool inside = __dadd_rn(__dadd_rn(__dmul_rn(dx, s.ax), __dmul_rn(dy, s.ay)), __dmul_rn(dz, s.az)) >=
+                  __dmul_rn(s.cos_half, r);
+    for (int h = 0; h < s.n_holes && inside; ++h) {
+      const double4 hv = holes[h];
+      if (__dadd_rn(__dadd_rn(__dmul_rn(dx, hv.x), __dmul_rn(dy, hv.y)), __dmul_rn(dz, hv.z)) > __dmul_rn(hv.w, r))
+        inside = false;
+    }
+    if (inside) {
+      if (s.kind == 0) {
+        val = 1.0;
+      } else if (s.kind == 1) {
+        const double t = __ddiv_rn(r, s.p0);
+        val = exp(-__dmul_rn(t, t));
+      } else {
+        const double t = __ddiv_rn(r, s.p0);
+        val = __dmul_rn(pow(t, s.p1), exp(__dmul_rn(s.p1, __dsub_rn(1.0, t))));
+      }
+    }
+  }
+  return val;
+}
+
 __global__ void __launch_bounds__(256)
 k_window(int n, SelParams s, const double4* __restrict__ holes, double* __restrict__ w,
          double* __restrict__ partials) {
@@ -34,36 +63,26 @@ k_window(int n, SelParams s, const double4* __restrict__ holes, double* __restri
   AccD acc;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < V; e += (size_t)gridDim.x * blockDim.x) {
     const int iz = (int)(e % n), iy = (int)((e / n) % n), ix = (int)(e / ((size_t)n * n));
-    const double dx = __dsub_rn(__dmul_rn((double)ix, s.H), s.ox);
-    const double dy = __dsub_rn(__dmul_rn((double)iy, s.H), s.oy);
-    const double dz = __dsub_rn(__dmul_rn((double)iz, s.H), s.oz);
-    const double r = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
-    double val = 0.0;
-    if (r > 0.0) {
-      bool inside = __dadd_rn(__dadd_rn(__dmul_rn(dx, s.ax), __dmul_rn(dy, s.ay)), __dmul_rn(dz, s.az)) >=
-                    __dmul_rn(s.cos_half, r);
-      for (int h = 0; h < s.n_holes && inside; ++h) {
-        const double4 hv = holes[h];
-        if (__dadd_rn(__dadd_rn(__dmul_rn(dx, hv.x), __dmul_rn(dy, hv.y)), __dmul_rn(dz, hv.z)) > __dmul_rn(hv.w, r))
-          inside = false;
-      }
-      if (inside) {
-        if (s.kind == 0) {
-          val = 1.0;
-        } else if (s.kind == 1) {
-          const double t = __ddiv_rn(r, s.p0);
-          val = exp(-__dmul_rn(t, t));
-        } else {
-          const double t = __ddiv_rn(r, s.p0);
-          val = __dmul_rn(pow(t, s.p1), exp(__dmul_rn(s.p1, __dsub_rn(1.0, t))));
-        }
-      }
-    }
+    const double val = sel_value(s, holes, __dsub_rn(__dmul_rn((double)ix, s.H), s.ox),
+                                 __dsub_rn(__dmul_rn((double)iy, s.H), s.oy),
+                                 __dsub_rn(__dmul_rn((double)iz, s.H), s.oz));
     w[e] = val;
     acc.add(val);
   }
   const double sum = block_sum(acc.get(), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+}
+
+// The selection at arbitrary positions pos[3 i] (the completeness at a galaxy), or its
+// reciprocal (0 where w = 0), the galaxy mass of the inverse-weighting estimator.
+__global__ void __launch_bounds__(256)
+k_window_at(const double* __restrict__ pos, long long n_pts, SelParams s, const double4* __restrict__ holes,
+            bool reciprocal, double* __restrict__ w) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pts; i += (long long)gridDim.x * blockDim.x) {
+    const double v = sel_value(s, holes, __dsub_rn(pos[3 * i], s.ox), __dsub_rn(pos[3 * i + 1], s.oy),
+                               __dsub_rn(pos[3 * i + 2], s.oz));
+    w[i] = reciprocal ? (v > 0.0 ? __drcp_rn(v) : 0.0) : v;
+  }
 }
 
 // scal[0] = sum(w), scal[1] = nbar, scal[2] = 1/nbar
@@ -94,6 +113,40 @@ k_data(const double* __restrict__ n_obs, const double* __restrict__ w, const dou
     if (d) reinterpret_cast<double2*>(d)[e] = dv;
     reinterpret_cast<double2*>(b)[e] = bv;
   }
+}
+
+wf_status selection_at_run(Ctx& c, const wf_selection& sel, const double* pos, int64_t n_pts, bool reciprocal,
+                          double* w, cudaStream_t st) {
+  if (n_pts < 0 || (n_pts > 0 && (!pos || !w)) || sel.n_holes < 0 || (sel.n_holes > 0 && !sel.holes) ||
+      sel.radial_kind < 0 || sel.radial_kind > 2)
+    return WF_ERR_ARG;
+  if (sel.radial_kind > 0 && !(sel.radial_params[0] > 0.0)) return WF_ERR_ARG;
+  if (n_pts == 0) return WF_OK;
+  SelParams s;
+  s.ox = sel.observer[0];
+  s.oy = sel.observer[1];
+  s.oz = sel.observer[2];
+  s.ax = sel.axis[0];
+  s.ay = sel.axis[1];
+  s.az = sel.axis[2];
+  s.cos_half = cos(sel.half_angle);
+  s.H = 0.0;
+  s.p0 = sel.radial_params[0];
+  s.p1 = sel.radial_params[1];
+  s.kind = sel.radial_kind;
+  s.n_holes = sel.n_holes;
+  std::vector<double4> hh((size_t)(sel.n_holes > 0 ? sel.n_holes : 1));
+  for (int h = 0; h < sel.n_holes; ++h)
+    hh[h] = make_double4(sel.holes[4 * h], sel.holes[4 * h + 1], sel.holes[4 * h + 2], cos(sel.holes[4 * h + 3]));
+  double4* dh;
+  WF_TRY(c.get("holes_at", hh.size() * sizeof(double4), (void**)&dh));
+  WF_CUDA(cudaMemcpyAsync(dh, hh.data(), hh.size() * sizeof(double4), cudaMemcpyHostToDevice, st));
+  const unsigned grid = (unsigned)std::min<int64_t>((n_pts + 255) / 256, 152 * 16);
+  c.launch("window_at", 32.0 * (double)n_pts, st, [&] { k_window_at<<<grid, 256, 0, st>>>(pos, (long long)n_pts, s, dh, reciprocal, w); });
+  WF_CUDA(cudaGetLastError());
+  // the host copy of the hole table must outlive the copy
+  WF_CUDA(cudaStreamSynchronize(st));
+  return WF_OK;
 }
 
 wf_status noise_run(Ctx& c, const wf_grid& g, const wf_selection& sel, const double* n_obs, int64_t n_gal,

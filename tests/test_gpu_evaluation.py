@@ -107,7 +107,7 @@ def test_density_stats_match_oracle(ctx, n, box):
 def test_density_exact_edges_and_empty_region(ctx):
     """Values on bin edges (width 0.25, exact in binary) fall in the upper bin on both sides; a
     region with no cell has NaN moments."""
-    n, box = 8, 8.0
+    n, box = 16, 16.0
     vals = np.array([-1.0, -0.75, -0.5, 0.0, 0.25, 1.0, 1.75])
     delta = vals[np.arange(n ** 3) % len(vals)].reshape(n, n, n)
     w = np.ones((n, n, n))
@@ -118,13 +118,70 @@ def test_density_exact_edges_and_empty_region(ctx):
 
 
 def test_evaluation_argument_errors(ctx):
-    d = gpu(np.zeros((8, 8, 8)))
+    d = gpu(np.zeros((16, 16, 16)))
     for kw in [dict(width=0.0), dict(shells=[[0.0, 1.0]] * 9), dict(nb=6000)]:
         a = dict(width=0.03, shells=[[0.0, 10.0]], nb=10)
         a.update(kw)
         with pytest.raises(wf.WfError) as e:
-            ctx.density_stats(d, d, 8.0, (0.0, 0.0, 0.0), a["shells"], 0.0, a["width"], a["nb"])
+            ctx.density_stats(d, d, 16.0, (0.0, 0.0, 0.0), a["shells"], 0.0, a["width"], a["nb"])
         assert e.value.status == wf.ERR_ARG
     with pytest.raises(wf.WfError) as e:
-        ctx.smooth(d, 8.0, -1.0)
+        ctx.smooth(d, 16.0, -1.0)
     assert e.value.status == wf.ERR_ARG
+    with pytest.raises(wf.WfError) as e:
+        ctx.smooth(gpu(np.zeros((8, 8, 8))), 8.0, 1.0)
+    assert e.value.status == wf.ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ inverse weighting (Sec. 5)
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+def _iw_case(n):
+    pr = synth.problem("c2", n_override=n, cache=False)
+    return pr, oracle.window_at(pr.sel, pr.pos)
+
+
+@pytest.mark.parametrize("n", [16, 48])
+def test_selection_at_galaxies_matches_oracle(ctx, n):
+    pr, w_ref = _iw_case(n)
+    got = host(ctx.selection_eval(pr.sel, gpu(pr.pos)))
+    assert np.array_equal(got > 0, w_ref > 0)
+    assert rl2(got, w_ref) <= 1e-14
+
+
+@pytest.mark.parametrize("n,scheme", [(16, wf.CIC), (24, wf.TSC), (64, wf.TSC)])
+def test_weighted_grid_bit_exact(ctx, n, scheme):
+    """Same weights on both sides (1 / w from the oracle's selection): the fine grid in Q32
+    units matches bit for bit, and the low-passed counts to FP64 rounding."""
+    pr, w_ref = _iw_case(n)
+    wgt = 1.0 / w_ref
+    fine_d = torch.empty((2 * n) ** 3, dtype=torch.int64, device=DEV)
+    nobs = ctx.grid_assign_weighted(gpu(pr.pos), gpu(wgt), n, pr.box, scheme, 2, fine_out=fine_d)
+    ref = oracle.assign_weighted(pr.pos, wgt, n, pr.box, scheme, 2)
+    assert np.array_equal(host(fine_d).view(np.uint64).reshape(ref.shape), ref)
+    assert rl2(host(nobs), oracle.lowpass_scaled(ref, n, 2, 2.0 ** -32)) <= 1e-13
+
+
+def test_inverse_weighting_end_to_end(ctx):
+    """The estimator through the library alone (selection at the galaxies, 1 / w, weighted
+    gridding, smoothing) against the oracle's; pow / exp may differ by an ulp between the two
+    math libraries, which can move a contribution by one Q32 unit."""
+    n = 32
+    pr, w_ref = _iw_case(n)
+    pos = gpu(pr.pos)
+    wgt = ctx.selection_eval(pr.sel, pos, reciprocal=True)
+    assert rl2(host(wgt), 1.0 / w_ref) <= 1e-14
+    nobs = ctx.grid_assign_weighted(pos, wgt, n, pr.box, wf.TSC, 2)
+    got = host(ctx.smooth(nobs, pr.box, 3.0 * pr.box / n))
+    ref = ev.smooth(oracle.lowpass_scaled(oracle.assign_weighted(pr.pos, 1.0 / w_ref, n, pr.box, 2, 2), n, 2,
+                                          2.0 ** -32), pr.box, 3.0 * pr.box / n)
+    assert rl2(got, ref) <= 1e-9
+
+
+def test_weighted_grid_rejects_bad_weights(ctx):
+    pos = gpu(np.array([[1.0, 2.0, 3.0], [4.0, 5.0, 6.0]]))
+    for bad in (-1.0, 2.0 ** 32, np.nan):
+        st, _ = ctx.grid_assign_weighted(pos, gpu(np.array([1.0, bad])), 16, 16.0, wf.TSC, 2, check=False)
+        assert st == wf.ERR_ARG

@@ -112,3 +112,61 @@ def test_moments_two_point_skewness():
 def test_moments_empty_region_is_nan():
     mom = ev.density_moments(np.zeros((1, 1, 4), dtype=np.int64), 0.0, 0.1)[0, 0]
     assert mom[0] == 0 and np.all(np.isnan(mom[1:]))
+
+
+# ---------------------------------------------------------------- inverse weighting (Sec. 5)
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+
+def test_weighted_assignment_power_of_two_weight_is_exact():
+    """Weight 2^16 turns a Q48 contribution into the same integer in Q32 units: no rounding."""
+    pr = synth.problem("c1", n_override=16, cache=False)
+    for scheme in (1, 2):
+        f = oracle.assign(pr.pos, 16, pr.box, scheme, 2)
+        fw = oracle.assign_weighted(pr.pos, np.full(len(pr.pos), 65536.0), 16, pr.box, scheme, 2)
+        assert np.array_equal(f, fw)
+        assert np.array_equal(oracle.lowpass_scaled(fw, 16, 2, 2.0 ** -32), oracle.lowpass(f, 16, 2) * 65536.0)
+
+
+def test_weighted_assignment_rounding_bound_and_mass():
+    """Unit weights: each contribution is the Q48 weight rounded to Q32, so a cell is within
+    half a unit per contribution of the unweighted cell / 2^16, and the mass within half a unit
+    per node of N_gal 2^32."""
+    rng = np.random.default_rng(6)
+    pos = rng.uniform(0.0, 30.0, (500, 3))
+    f = oracle.assign(pos, 8, 30.0, 2, 2).astype(np.float64) / 65536.0
+    fw = oracle.assign_weighted(pos, np.ones(500), 8, 30.0, 2, 2).astype(np.float64)
+    assert np.max(np.abs(fw - f)) <= 0.5 * 27 * 500
+    assert abs(fw.sum() - 500 * 2.0 ** 32) <= 0.5 * 27 * 500
+
+
+def test_weighted_assignment_hand_worked():
+    """One CIC galaxy at fine coordinate (1.25, 0.5, 0) cells of weight 3: node weights
+    (3/4, 1/4) x (1/2, 1/2) x (1, 0) of 2^48, times 3, in Q32 units."""
+    box, n = 8.0, 4  # fine cell = 1
+    fw = oracle.assign_weighted(np.array([[1.25, 0.5, 0.0]]), np.array([3.0]), n, box, 1, 2)
+    want = {(1, 0, 0): 0.75 * 0.5, (2, 0, 0): 0.25 * 0.5, (1, 1, 0): 0.75 * 0.5, (2, 1, 0): 0.25 * 0.5}
+    for idx, frac in want.items():
+        assert fw[idx] == round(frac * 3.0 * 2.0 ** 32)
+    assert np.count_nonzero(fw) == 4
+
+
+def test_window_at_nodes_equals_window():
+    """The selection at node positions i H is the window itself, value for value."""
+    pr = synth.problem("c2", n_override=16, cache=False)
+    n, h = 16, pr.box / 16
+    i = np.arange(n) * h
+    pts = np.stack(np.meshgrid(i, i, i, indexing="ij"), axis=-1).reshape(-1, 3)
+    assert np.array_equal(oracle.window_at(pr.sel, pts), oracle.window(pr.sel, n, pr.box).ravel())
+
+
+def test_inverse_weighting_uniform_selection():
+    """With a uniform completeness c the inverse-weighted grid is the plain grid / c (up to the
+    Q32 rounding of each contribution)."""
+    rng = np.random.default_rng(9)
+    pos = rng.uniform(0.0, 20.0, (300, 3))
+    c = 0.37
+    f = oracle.lowpass(oracle.assign(pos, 8, 20.0, 2, 2), 8, 2)
+    fw = oracle.lowpass_scaled(oracle.assign_weighted(pos, np.full(300, 1.0 / c), 8, 20.0, 2, 2), 8, 2, 2.0 ** -32)
+    assert np.max(np.abs(fw - f / c)) <= 1e-8
