@@ -34,8 +34,8 @@ WORKLOADS = {
 # DRAM traffic of the dominant kernel per launch from one ncu capture, valid while the kernel
 # sources hash to `src`; scaled from the captured size by the units processed (bytes ~ N^3).
 NCU_TRAFFIC = {
-    # profiles/cg_kernels_f32_256_full.md: 213.9 + 147.2 MB at 256^3, x 8 for 512^3
-    ("cg_xinv", 512): {"bytes": 361.1e6 * 8, "src": "aa62f2c04f40f055"},
+    # profiles/cg_kernels_f32_256_full.md: 214.0 + 147.9 MB at 256^3, x 8 for 512^3
+    ("cg_xinv", 512): {"bytes": 361.9e6 * 8, "src": "6fb7caeb20dbde08"},
 }
 
 
