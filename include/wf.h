@@ -160,6 +160,26 @@ wf_status wf_grid_assign_weighted(wf_ctx* ctx, const wf_grid* grid, wf_scheme sc
                                   const double* wgt, int64_t n_gal, uint64_t* fine_out, double* n_obs,
                                   void* stream);
 
+/* ---- redshift distortions and the deconvolution (Sec. 3, Eq. eq:DEC) --------------------- */
+
+/* <K D>_mu(k): the mean over mu in [0, 1] of the Kaiser factor (1 + beta mu^2)^2 times the
+ * Lorentzian damping 1 / (1 + k^2 sigma_v^2 mu^2 / 2) (Sec. 3, "Redshift distortion operator").
+ * The redshift-space power spectrum is P^r(k) times this factor (build wf_power tables from it);
+ * its square root is the operator Z.  Closed form (power series for k^2 sigma_v^2 < 1).  Host
+ * arrays, no context, no device work.
+ *   k, out  host double [n_k]; k >= 0 in the inverse units of sigma_v (h/Mpc with sigma_v in
+ *           Mpc/h: the paper's 500 km/s / H0 is 5 Mpc/h)
+ * Errors: WF_ERR_ARG (negative or non-finite k, sigma_v < 0, non-finite beta). */
+wf_status wf_rsd_factor(int64_t n_k, const double* k, double beta, double sigma_v, double* out);
+
+/* Eq. eq:DEC with a constant bias b: the matter field in real space from the galaxy field in
+ * redshift space, B^-1 Z^-1 applied as the Fourier multiplier 1 / (b sqrt(<K D>_mu(|k|))) with
+ * k = 2 pi m / box.  FP64 transforms.
+ *   in, out  dev double [n^3] (out may equal in); bias > 0; sigma_v >= 0
+ * Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED, WF_ERR_OOM, WF_ERR_CUDA. */
+wf_status wf_deconvolve(wf_ctx* ctx, const wf_grid* grid, const double* in, double beta, double sigma_v,
+                        double bias, double* out, void* stream);
+
 /* ---- evaluation of a reconstruction (Sec. 5.1 and Sec. 6.2) ------------------------------ */
 
 /* Gaussian smoothing (Sec. 6.2, eq:GAUSS): out = the field convolved on the periodic grid with

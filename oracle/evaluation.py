@@ -1,6 +1,7 @@
-"""CPU FP64 oracle of the evaluation steps applied to a reconstruction (Kitaura et al. 2009,
-arXiv:0906.3978, Sec. 5.1 "Statistical correlation measures" and Sec. 6.2 "Statistical
-analysis"): Gaussian smoothing, the correlation coefficient r, the Euclidean distance D_Euc, the
+"""CPU FP64 oracle of the steps around the solve (Kitaura et al. 2009, arXiv:0906.3978): the
+redshift-distortion factor and the deconvolution B^-1 Z^-1 of Sec. 3 (Eq. eq:DEC), and the
+evaluation of a reconstruction of Sec. 5.1 "Statistical correlation measures" and Sec. 6.2
+"Statistical analysis": Gaussian smoothing, the correlation coefficient r, the Euclidean distance D_Euc, the
 normalised Kullback-Leibler distance D_KL, and binned density statistics (counts in 1+delta bins
 per radial shell and observed / unobserved region; mean, central moments, skewness, kurtosis,
 Pearson's skewness).
@@ -119,3 +120,33 @@ def density_moments(hist, lo: float, width: float) -> np.ndarray:
         mode = c[int(np.argmax(f))]
         out[j, 1:] = (mean, mu2, mu3, mu4, mu3 / sig ** 3, mu4 / sig ** 4 - 3.0, (mean - mode) / sig)
     return out.reshape(h.shape[:-1] + (8,))
+
+
+# ---------------------------------------------------------------- redshift distortions (Sec. 3)
+def rsd_factor(k, beta: float, sigma_v: float) -> np.ndarray:
+    """<K D>_mu: the mean over mu in [0, 1] of the Kaiser factor (1 + beta mu^2)^2 times the
+    Lorentzian damping 1 / (1 + k^2 sigma_v^2 mu^2 / 2) (Sec. 3, "Redshift distortion operator"),
+    by adaptive quadrature of the definition.  The real-space power spectrum times this factor is
+    the redshift-space one; its square root is the operator Z."""
+    from scipy.integrate import quad
+    out = []
+    for kk in np.atleast_1d(np.asarray(k, dtype=np.float64)):
+        a = 0.5 * (kk * sigma_v) ** 2
+        val, _ = quad(lambda m: (1.0 + beta * m * m) ** 2 / (1.0 + a * m * m), 0.0, 1.0,
+                      epsabs=1e-16, epsrel=2e-14, limit=400)
+        out.append(val)
+    return np.array(out)
+
+
+def deconvolve(field, box: float, beta: float, sigma_v: float, bias: float) -> np.ndarray:
+    """Eq. eq:DEC with a constant bias b: the galaxy field in redshift space mapped to the matter
+    field in real space, B^-1 Z^-1, i.e. the DFT multiplied by 1 / (b sqrt(<K D>_mu(|k|)))."""
+    f = np.asarray(field, dtype=np.float64)
+    n = f.shape[0]
+    m = np.fft.fftfreq(n, 1.0 / n)
+    m[n // 2] = n // 2
+    n2 = (m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2).astype(np.int64)
+    u, inv = np.unique(n2, return_inverse=True)
+    mult = 1.0 / (bias * np.sqrt(rsd_factor(2.0 * np.pi * np.sqrt(u) / box, beta, sigma_v)))
+    spec = fft3d(f.astype(np.complex128), -1) * mult[inv].reshape(n2.shape)
+    return np.real(fft3d(spec, +1)) / float(n) ** 3

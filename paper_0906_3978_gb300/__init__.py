@@ -106,6 +106,8 @@ def lib():
         L.wf_profile.argtypes = [c_void_p, c_int]
         L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
         L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
+        L.wf_rsd_factor.argtypes = [c_int64, P(c_double), c_double, c_double, P(c_double)]
+        L.wf_deconvolve.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_double, c_double, c_void_p, c_void_p]
         L.wf_selection_eval.argtypes = [c_void_p, P(SelectionC), c_void_p, c_int64, c_int, c_void_p, c_void_p]
         L.wf_grid_assign_weighted.argtypes = [c_void_p, P(Grid), c_int, c_void_p, c_void_p, c_int64, c_void_p,
                                               c_void_p, c_void_p]
@@ -118,11 +120,22 @@ def lib():
         for name in ("wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve", "wf_solve_batch",
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
-                     "wf_selection_eval", "wf_grid_assign_weighted"):
+                     "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
     return _lib
+
+
+def rsd_factor(k, beta: float, sigma_v: float) -> np.ndarray:
+    """<K D>_mu at wavenumbers k (wf_rsd_factor; host arrays, no GPU)."""
+    k = np.ascontiguousarray(np.atleast_1d(np.asarray(k, dtype=np.float64)))
+    out = np.empty_like(k)
+    st = lib().wf_rsd_factor(k.size, k.ctypes.data_as(ctypes.POINTER(c_double)), float(beta), float(sigma_v),
+                             out.ctypes.data_as(ctypes.POINTER(c_double)))
+    if st != OK:
+        raise WfError(st, "wf_rsd_factor")
+    return out
 
 
 class WfError(RuntimeError):
@@ -344,6 +357,18 @@ class Context:
         st = lib().wf_smooth(self._h, ctypes.byref(g), _ptr(field), float(r_s), _ptr(out), _stream(stream))
         if st != OK:
             raise WfError(st, "wf_smooth")
+        return out
+
+    def deconvolve(self, field, box: float, beta: float, sigma_v: float, bias: float, out=None, stream=None):
+        """Matter field in real space from a galaxy field in redshift space, B^-1 Z^-1 (wf_deconvolve)."""
+        import torch
+        if out is None:
+            out = torch.empty_like(field)
+        g = Grid(int(field.shape[0]), float(box), 1)
+        st = lib().wf_deconvolve(self._h, ctypes.byref(g), _ptr(field), float(beta), float(sigma_v), float(bias),
+                                 _ptr(out), _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_deconvolve")
         return out
 
     def compare(self, rec, truth, stream=None) -> dict:

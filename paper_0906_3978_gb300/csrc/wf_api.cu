@@ -426,6 +426,26 @@ wf_status wf_grid_assign_weighted(wf_ctx* ctx, const wf_grid* grid, wf_scheme sc
   return assign_weighted_run(*c, *grid, (int)scheme, pos, wgt, n_gal, fine_out, n_obs, (cudaStream_t)stream);
 }
 
+wf_status wf_rsd_factor(int64_t n_k, const double* k, double beta, double sigma_v, double* out) {
+  if (n_k < 0 || (n_k > 0 && (!k || !out)) || !std::isfinite(beta) || !(sigma_v >= 0.0) || !std::isfinite(sigma_v))
+    return WF_ERR_ARG;
+  for (int64_t i = 0; i < n_k; ++i) {
+    if (!(k[i] >= 0.0) || !std::isfinite(k[i])) return WF_ERR_ARG;
+    out[i] = rsd_factor(k[i], beta, sigma_v);
+  }
+  return WF_OK;
+}
+
+wf_status wf_deconvolve(wf_ctx* ctx, const wf_grid* grid, const double* in, double beta, double sigma_v,
+                        double bias, double* out, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return deconvolve_run(*c, *grid, in, beta, sigma_v, bias, out, (cudaStream_t)stream);
+}
+
 wf_status wf_smooth(wf_ctx* ctx, const wf_grid* grid, const double* in, double r_s, double* out, void* stream) {
   if (!ctx) return WF_ERR_ARG;
   WF_TRY(check_grid(grid));

@@ -172,7 +172,10 @@ wf_status assign_weighted_run(Ctx& c, const wf_grid& g, int scheme, const double
                               int64_t n_gal, uint64_t* fine_out, double* n_obs, cudaStream_t st);
 wf_status selection_at_run(Ctx& c, const wf_selection& sel, const double* pos, int64_t n_pts, bool reciprocal,
                           double* w, cudaStream_t st);
-// evaluation of a reconstruction (wf_post.cu)
+// the steps around the solve (wf_post.cu)
+double rsd_factor(double k, double beta, double sigma_v);
+wf_status deconvolve_run(Ctx& c, const wf_grid& g, const double* in, double beta, double sigma_v, double bias,
+                         double* out, cudaStream_t st);
 wf_status smooth_run(Ctx& c, const wf_grid& g, const double* in, double r_s, double* out, cudaStream_t st);
 wf_status compare_run(Ctx& c, int64_t n_cells, const double* rec, const double* truth, wf_compare_result* out,
                       cudaStream_t st);

@@ -1,6 +1,8 @@
-// wf_post.cu -- evaluation of a reconstruction (Kitaura et al. 2009, Sec. 5.1 "Statistical
-// correlation measures" and Sec. 6.2 "Statistical analysis"): Gaussian smoothing (dispatch to
-// the per-size FP64 transform passes), the correlation coefficient, Euclidean and normalised
+// wf_post.cu -- the steps around the solve (Kitaura et al. 2009): the redshift-distortion factor
+// and the deconvolution B^-1 Z^-1 of Sec. 3 (Eq. eq:DEC), and the evaluation of a reconstruction of
+// Sec. 5.1 "Statistical correlation measures" and Sec. 6.2 "Statistical analysis": Gaussian
+// smoothing (both Fourier multipliers dispatch to the per-size FP64 transform passes), the
+// correlation coefficient, Euclidean and normalised
 // Kullback-Leibler distances, and binned density statistics per radial shell and observed /
 // unobserved region with their moments.
 //
@@ -176,17 +178,65 @@ k_density_moments(const unsigned long long* __restrict__ hist, int n_bins, doubl
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
-wf_status smooth_run(Ctx& c, const wf_grid& g, const double* in, double r_s, double* out, cudaStream_t st) {
-  if (!in || !out || !(r_s >= 0.0) || !std::isfinite(r_s)) return WF_ERR_ARG;
-  switch (g.n) {
+static wf_status multiply_run(Ctx& c, int n, const double* in, double* out, const std::vector<double>& table,
+                              cudaStream_t st) {
+  switch (n) {
 #define WF_CASE(N) \
   case N:          \
-    return smooth_n<N>(c, in, out, g.box, r_s, st);
+    return fourier_multiply_n<N>(c, in, out, table, st);
     WF_SIZES(WF_CASE)
 #undef WF_CASE
     default:
       return WF_ERR_UNSUPPORTED;
   }
+}
+
+// table index n2 = |m|^2 of the signed DFT index m, up to 3 (n/2)^2; |k| = 2 pi sqrt(n2) / box
+static inline size_t n2_entries(int n) { return (size_t)3 * (n / 2) * (n / 2) + 1; }
+
+wf_status smooth_run(Ctx& c, const wf_grid& g, const double* in, double r_s, double* out, cudaStream_t st) {
+  if (!in || !out || !(r_s >= 0.0) || !std::isfinite(r_s)) return WF_ERR_ARG;
+  std::vector<double> t(n2_entries(g.n));
+  const double kf = 2.0 * 3.14159265358979323846 / g.box;
+  for (size_t n2 = 0; n2 < t.size(); ++n2) t[n2] = std::exp(-0.5 * kf * kf * (double)n2 * r_s * r_s);
+  return multiply_run(c, g.n, in, out, t, st);
+}
+
+// <K D>_mu of Sec. 3 ("Redshift distortion operator"): the mean over mu in [0, 1] of
+// (1 + beta mu^2)^2 / (1 + a mu^2), a = k^2 sigma_v^2 / 2.  Dividing the numerator by 1 + a mu^2
+// gives beta^2 / (3a) + 2 beta / a - beta^2 / a^2 + (1 - beta / a)^2 atan(sqrt a) / sqrt a; for
+// a < 1/2, where those terms cancel, the power series sum_j (-a)^j (1/(2j+1) + 2 beta/(2j+3) +
+// beta^2/(2j+5)) is summed instead.
+double rsd_factor(double k, double beta, double sigma_v) {
+  const double a = 0.5 * (k * sigma_v) * (k * sigma_v);
+  if (a < 0.5) {
+    double sum = 0.0, p = 1.0;
+    for (int j = 0; j < 200; ++j) {
+      const double term = p * (1.0 / (2 * j + 1) + 2.0 * beta / (2 * j + 3) + beta * beta / (2 * j + 5));
+      sum += term;
+      if (std::fabs(term) <= 1e-18 * std::fabs(sum)) break;
+      p *= -a;
+    }
+    return sum;
+  }
+  const double sa = std::sqrt(a), u = 1.0 - beta / a;
+  return beta * beta / (3.0 * a) + 2.0 * beta / a - beta * beta / (a * a) + u * u * std::atan(sa) / sa;
+}
+
+wf_status deconvolve_run(Ctx& c, const wf_grid& g, const double* in, double beta, double sigma_v, double bias,
+                         double* out, cudaStream_t st) {
+  if (!in || !out || !std::isfinite(beta) || !(sigma_v >= 0.0) || !std::isfinite(sigma_v) || !(bias > 0.0) ||
+      !std::isfinite(bias))
+    return WF_ERR_ARG;
+  std::vector<double> t(n2_entries(g.n));
+  const double kf = 2.0 * 3.14159265358979323846 / g.box;
+  for (size_t n2 = 0; n2 < t.size(); ++n2) {
+    const double f = rsd_factor(kf * std::sqrt((double)n2), beta, sigma_v);
+    if (!(f > 0.0)) return WF_ERR_ARG;  // (1 + beta mu^2)^2 vanishing on all of [0, 1] is impossible;
+                                        // a non-positive mean only comes from a non-finite input
+    t[n2] = 1.0 / (bias * std::sqrt(f));
+  }
+  return multiply_run(c, g.n, in, out, t, st);
 }
 
 wf_status compare_run(Ctx& c, int64_t n_cells, const double* rec, const double* truth, wf_compare_result* out,

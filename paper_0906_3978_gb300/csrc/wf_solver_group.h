@@ -25,8 +25,10 @@ struct Group {
 
 Group* make_group_n(int n, int prec);
 
-// Gaussian smoothing of one field of size N (instantiated with the solve drivers of each size).
+// out = F^-1 [table(|m|^2) F in] for one field of size N (instantiated with the solve drivers of
+// each size); table has 3 (N/2)^2 + 1 entries.
 template <int N>
-wf_status smooth_n(Ctx& c, const double* in, double* out, double box, double r_s, cudaStream_t st);
+wf_status fourier_multiply_n(Ctx& c, const double* in, double* out, const std::vector<double>& table,
+                             cudaStream_t st);
 
 }  // namespace wf

@@ -671,13 +671,14 @@ struct GroupMixed : GroupCommon<N> {
   }
 };
 
-// Gaussian smoothing of one FP64 field (Sec. 6.2, eq:GAUSS read as the decaying Gaussian):
-// out = F^-1 [exp(-|k|^2 r_s^2 / 2) F in] on the periodic grid, k = 2 pi m / box.  The multiplier
-// depends on n2 = |m|^2 only, so the x pass applies it from an n2-indexed table, as it does the
-// prior; the transforms are the solver's FP64 passes.
+// out = F^-1 [g(|m|^2) F in] for one FP64 field, with the multiplier given as a table over
+// n2 = |m|^2 (3 (N/2)^2 + 1 entries): the Gaussian smoothing of Sec. 6.2 and the deconvolution
+// B^-1 Z^-1 of Eq. eq:DEC.  The x pass applies the table as it applies the prior; the transforms
+// are the solver's FP64 passes.  in may equal out.
 template <int N>
-wf_status smooth_n(Ctx& c, const double* in, double* out, double box, double r_s, cudaStream_t st) {
+wf_status fourier_multiply_n(Ctx& c, const double* in, double* out, const std::vector<double>& table, cudaStream_t st) {
   using SD = Spec<FP64Arith, N>;
+  if ((int)table.size() != SD::TAB) return WF_ERR_ARG;
   WF_CUDA(SD::attrs());
   const double2* tw;
   WF_TRY(c.tw(N, &tw));
@@ -686,11 +687,8 @@ wf_status smooth_n(Ctx& c, const double* in, double* out, double box, double r_s
   WF_TRY(c.get("sm_T", SD::SPEC * sizeof(double2), (void**)&T));
   WF_TRY(c.get("sm_T2", SD::SPEC * sizeof(double2), (void**)&T2));
   WF_TRY(c.get("sm_part", (size_t)SD::NPART * sizeof(double), (void**)&part));
-  std::vector<double> g(SD::TAB);
-  const double kf = 2.0 * 3.14159265358979323846 / box;
-  for (int n2 = 0; n2 < SD::TAB; ++n2) g[n2] = std::exp(-0.5 * kf * kf * (double)n2 * r_s * r_s);
   double* gt;
-  WF_TRY(upload_tables<double>(c, "sm_g", g, &gt, st));
+  WF_TRY(upload_tables<double>(c, "sm_g", table, &gt, st));
   SD::zfwd(c, 1, in, T, tw, part, false, nullptr, st);
   SD::ypass(c, 1, T, tw, nullptr, -1, st);
   SD::template xmul<true, true, false>(c, 1, T, T2, gt, tw, part, nullptr, st);

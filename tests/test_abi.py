@@ -28,7 +28,7 @@ def test_header_declares_boundary():
     for required in ["wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve",
                      "wf_solve_batch", "wf_submit", "wf_poll", "wf_status_string", "wf_set_fused_planes",
                      "wf_smooth", "wf_compare", "wf_density_stats", "wf_selection_eval",
-                     "wf_grid_assign_weighted"]:
+                     "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve"]:
         assert required in names
 
 
@@ -49,3 +49,20 @@ def test_supported_sizes(lib):
         assert wf.supported_size(n)
     for n in [0, 8, 20, 100, 1000, 1024, -4]:
         assert not wf.supported_size(n)
+
+
+def test_rsd_factor_matches_oracle():
+    """The library's closed form (host code) against the oracle's quadrature of the definition,
+    across the switch between the power series and the arctan form (k^2 sigma_v^2 / 2 = 1/2)."""
+    import numpy as np
+    import paper_0906_3978_gb300 as wf
+    from oracle import evaluation as ev
+    k = np.concatenate([[0.0, 1e-4], np.linspace(0.01, 0.5, 30), [0.1999, 0.2, 0.2001], np.linspace(0.6, 6.0, 20)])
+    for beta in (0.0, 0.42, 1.3):
+        got, ref = wf.rsd_factor(k, beta, 5.0), ev.rsd_factor(k, beta, 5.0)
+        assert np.max(np.abs(got - ref) / ref) <= 5e-14
+    for bad in (dict(k=[-1.0]), dict(k=[np.nan]), dict(sigma_v=-1.0)):
+        a = dict(k=[0.1], beta=0.4, sigma_v=5.0)
+        a.update(bad)
+        with pytest.raises(wf.WfError):
+            wf.rsd_factor(a["k"], a["beta"], a["sigma_v"])

@@ -119,7 +119,7 @@ def test_density_exact_edges_and_empty_region(ctx):
 
 def test_evaluation_argument_errors(ctx):
     d = gpu(np.zeros((16, 16, 16)))
-    for kw in [dict(width=0.0), dict(shells=[[0.0, 1.0]] * 9), dict(nb=6000)]:
+    for kw in [dict(width=0.0), dict(shells=[[0.0, 1.0]] * 9), dict(nb=7000)]:  # 1 x 7002 > 6144 slots
         a = dict(width=0.03, shells=[[0.0, 10.0]], nb=10)
         a.update(kw)
         with pytest.raises(wf.WfError) as e:
@@ -185,3 +185,22 @@ def test_weighted_grid_rejects_bad_weights(ctx):
     for bad in (-1.0, 2.0 ** 32, np.nan):
         st, _ = ctx.grid_assign_weighted(pos, gpu(np.array([1.0, bad])), 16, 16.0, wf.TSC, 2, check=False)
         assert st == wf.ERR_ARG
+
+
+# ------------------------------------------------------------------ deconvolution (Sec. 3, eq:DEC)
+@pytest.mark.parametrize("n,box,beta,sv,b", [(16, 64.0, 0.42, 5.0, 1.0), (24, 47.0, 0.6, 3.0, 1.3),
+                                            (48, 94.0, 0.42, 5.0, 0.8)])
+def test_deconvolution_matches_oracle(ctx, n, box, beta, sv, b):
+    f = np.random.default_rng(n + 1).standard_normal((n, n, n))
+    got = host(ctx.deconvolve(gpu(f), box, beta, sv, b))
+    assert rl2(got, ev.deconvolve(f, box, beta, sv, b)) <= 1e-13
+
+
+def test_deconvolution_errors(ctx):
+    d = gpu(np.zeros((16, 16, 16)))
+    for kw in (dict(bias=0.0), dict(sigma_v=-1.0), dict(beta=np.nan)):
+        a = dict(beta=0.4, sigma_v=5.0, bias=1.0)
+        a.update(kw)
+        with pytest.raises(wf.WfError) as e:
+            ctx.deconvolve(d, 16.0, a["beta"], a["sigma_v"], a["bias"])
+        assert e.value.status == wf.ERR_ARG

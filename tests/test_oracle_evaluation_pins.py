@@ -170,3 +170,33 @@ def test_inverse_weighting_uniform_selection():
     f = oracle.lowpass(oracle.assign(pos, 8, 20.0, 2, 2), 8, 2)
     fw = oracle.lowpass_scaled(oracle.assign_weighted(pos, np.full(300, 1.0 / c), 8, 20.0, 2, 2), 8, 2, 2.0 ** -32)
     assert np.max(np.abs(fw - f / c)) <= 1e-8
+
+
+# ---------------------------------------------------------------- redshift distortions (Sec. 3)
+@pytest.mark.parametrize("beta", [0.0, 0.42, 1.0])
+def test_rsd_factor_limits(beta):
+    """k = 0 or sigma_v = 0: the angle-averaged Kaiser factor 1 + 2 beta / 3 + beta^2 / 5;
+    beta = 0: the averaged Lorentzian arctan(sqrt(a)) / sqrt(a), a = k^2 sigma_v^2 / 2."""
+    kaiser = 1.0 + 2.0 * beta / 3.0 + beta * beta / 5.0
+    assert abs(ev.rsd_factor(0.0, beta, 5.0)[0] - kaiser) <= 1e-14
+    assert abs(ev.rsd_factor(0.3, beta, 0.0)[0] - kaiser) <= 1e-14
+    k = np.array([0.05, 0.3, 2.0])
+    a = 0.5 * (k * 5.0) ** 2
+    lor = np.arctan(np.sqrt(a)) / np.sqrt(a)
+    assert np.max(np.abs(ev.rsd_factor(k, 0.0, 5.0) - lor) / lor) <= 1e-13
+
+
+def test_rsd_factor_decreases_with_k():
+    f = ev.rsd_factor(np.linspace(0.0, 5.0, 40), 0.42, 5.0)
+    assert np.all(np.diff(f) < 0.0)
+
+
+def test_deconvolution_plane_wave_and_bias():
+    n, box, beta, sv, b = 16, 64.0, 0.42, 5.0, 1.7
+    x = np.arange(n) * box / n
+    f = np.cos(2 * np.pi * (1 * x[:, None, None] + 2 * x[None, :, None] + 2 * x[None, None, :]) / box)
+    k = 2 * np.pi * 3.0 / box  # |m| = 3
+    want = f / (b * math.sqrt(ev.rsd_factor(k, beta, sv)[0]))
+    assert np.max(np.abs(ev.deconvolve(f, box, beta, sv, b) - want)) <= 1e-13
+    g = np.random.default_rng(2).standard_normal((8, 8, 8))
+    assert np.max(np.abs(ev.deconvolve(g, 30.0, 0.0, 0.0, 2.0) - g / 2.0)) <= 1e-14
