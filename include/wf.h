@@ -136,6 +136,30 @@ const char* wf_last_error(void);
  * differ, the FP32 rounding.  Applies to solves started after the call. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
+/* ---- signal-dependent noise (Eq. eq:noisecov; flat-prior and Jackknife-like estimators) ---- */
+
+/* The data terms of the signal-dependent-noise Wiener filter.  With N^SD = w lambda / nbar^2 per
+ * cell (Eq. eq:noisecov, lambda the expected counts of the complete sample):
+ *   D = R^T N^-1 R = nbar^2 w / lambda,   b = R^T N^-1 d = nbar^2 d / lambda,   d = n_obs / nbar - w,
+ * and 0, 0 where w = 0 or lambda <= 0 (no data term, as for unobserved cells).  Solve with
+ * wf_solve(w = D, nbar = 1, b); the LSQ filter is the case lambda = nbar.
+ *   n_obs, w   dev double [n_cells];  lambda dev double [n_cells] or NULL: the flat-prior mean
+ *              estimator (n_obs + 1) / w (Sec. "flat prior"); nbar > 0 as from wf_build_noise
+ *   D, b       dev double [n_cells]
+ * Errors: WF_ERR_ARG, WF_ERR_CUDA.  Stream-ordered. */
+wf_status wf_sd_noise(wf_ctx* ctx, int64_t n_cells, const double* n_obs, const double* w, const double* lambda,
+                      double nbar, double* D, double* b, void* stream);
+
+/* The Jackknife-like subsample of Eq. eq:selfunc as galaxy masses: galaxy g is kept when
+ * u[g] < alpha / w_gal[g] and then carries mass 1 / alpha (else 0, and 0 where w_gal = 0).
+ * Gridding these masses with wf_grid_assign_weighted gives N'' = N' / alpha, an unbiased estimate
+ * of the complete counts lambda.  The uniform numbers u in [0, 1) are the caller's (one fresh
+ * set per subsample); w_gal is the completeness at each galaxy (wf_selection_eval).
+ *   w_gal, u, out  dev double [n_gal];  0 < alpha <= 1 (the paper uses alpha = 1e-3 < min w)
+ * Errors: WF_ERR_ARG, WF_ERR_CUDA.  Stream-ordered. */
+wf_status wf_jackknife_masses(wf_ctx* ctx, int64_t n_gal, const double* w_gal, const double* u, double alpha,
+                              double* out, void* stream);
+
 /* ---- inverse-weighting estimator (Sec. 5, Eq. def:ngrid with galaxy mass 1/w) ------------- */
 
 /* The selection w (Sec. 2.3: cone x holes x radial law, the same formula and operation order as

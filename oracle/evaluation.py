@@ -150,3 +150,41 @@ def deconvolve(field, box: float, beta: float, sigma_v: float, bias: float) -> n
     mult = 1.0 / (bias * np.sqrt(rsd_factor(2.0 * np.pi * np.sqrt(u) / box, beta, sigma_v)))
     spec = fft3d(f.astype(np.complex128), -1) * mult[inv].reshape(n2.shape)
     return np.real(fft3d(spec, +1)) / float(n) ** 3
+
+
+# ---------------------------------------------------------------- signal-dependent noise (Sec. 2.4.2, App. A)
+def lambda_mean(n_obs, w) -> np.ndarray:
+    """Flat-prior mean estimator of the underlying counts, lambda_mean = (N^o + 1) / w, on w > 0
+    (0 elsewhere) (Sec. "flat prior": the posterior mean of a Poisson intensity)."""
+    n = np.asarray(n_obs, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    out = np.zeros_like(n)
+    ok = w > 0.0
+    out[ok] = (n[ok] + 1.0) / w[ok]
+    return out
+
+
+def jackknife_masses(w_gal, u, alpha: float) -> np.ndarray:
+    """Eq. eq:selfunc: a galaxy is kept with probability alpha / w(x_g) (u_g < alpha / w_g with
+    u_g uniform in [0, 1), drawn by the caller) and then carries mass 1 / alpha, so that the
+    gridded subsample is N'' = N' / alpha, an unbiased estimate of lambda."""
+    w = np.asarray(w_gal, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    keep = (w > 0.0) & (u < alpha / np.where(w > 0.0, w, 1.0))
+    return np.where(keep, 1.0 / alpha, 0.0)
+
+
+def sd_noise(n_obs, w, lam, nbar: float):
+    """Eq. eq:noisecov, N^SD = w lambda / nbar^2 (per cell): the solve's diagonal
+    R^T N^-1 R = nbar^2 w / lambda and right-hand side R^T N^-1 d = nbar^2 d / lambda with
+    d = n_obs / nbar - w.  Cells with w = 0 or lambda <= 0 carry no data term (0, 0).  The LSQ
+    noise is the case lambda = nbar.  Returns (D, b)."""
+    n = np.asarray(n_obs, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    lam = np.asarray(lam, dtype=np.float64)
+    d = n / nbar - w
+    ok = (w > 0.0) & (lam > 0.0)
+    nb2 = nbar * nbar
+    D = np.where(ok, nb2 * w / np.where(ok, lam, 1.0), 0.0)
+    b = np.where(ok, nb2 * d / np.where(ok, lam, 1.0), 0.0)
+    return D, b

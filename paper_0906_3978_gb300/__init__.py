@@ -106,6 +106,9 @@ def lib():
         L.wf_profile.argtypes = [c_void_p, c_int]
         L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
         L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
+        L.wf_sd_noise.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
+                                  c_void_p]
+        L.wf_jackknife_masses.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_double, c_void_p, c_void_p]
         L.wf_rsd_factor.argtypes = [c_int64, P(c_double), c_double, c_double, P(c_double)]
         L.wf_deconvolve.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_double, c_double, c_void_p, c_void_p]
         L.wf_selection_eval.argtypes = [c_void_p, P(SelectionC), c_void_p, c_int64, c_int, c_void_p, c_void_p]
@@ -120,7 +123,8 @@ def lib():
         for name in ("wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve", "wf_solve_batch",
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
-                     "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve"):
+                     "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve",
+                     "wf_sd_noise", "wf_jackknife_masses"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -265,6 +269,29 @@ class Context:
         if check and st != OK:
             raise WfError(st, "wf_build_noise")
         return (w, d, b, nb.value) if check else (st, w, d, b, nb.value)
+
+    # ---- signal-dependent noise -----------------------------------------------------------
+    def sd_noise(self, n_obs, w, nbar: float, lam=None, stream=None):
+        """(D, b): nbar^2 w / lambda and nbar^2 d / lambda (lambda None: the flat-prior mean
+        (n_obs + 1) / w); solve with solve(D, 1.0, b, ...) (wf_sd_noise)."""
+        import torch
+        D, b = torch.empty_like(n_obs), torch.empty_like(n_obs)
+        st = lib().wf_sd_noise(self._h, int(n_obs.numel()), _ptr(n_obs), _ptr(w), _ptr(lam), float(nbar), _ptr(D),
+                               _ptr(b), _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_sd_noise")
+        return D, b
+
+    def jackknife_masses(self, w_gal, u, alpha: float, stream=None):
+        """Galaxy masses of a Jackknife-like subsample: 1 / alpha where u < alpha / w, else 0
+        (wf_jackknife_masses)."""
+        import torch
+        out = torch.empty_like(w_gal)
+        st = lib().wf_jackknife_masses(self._h, int(w_gal.numel()), _ptr(w_gal), _ptr(u), float(alpha), _ptr(out),
+                                       _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_jackknife_masses")
+        return out
 
     # ---- Sec. 5: the inverse-weighting estimator -----------------------------------------
     def selection_eval(self, sel, pos, reciprocal=False, stream=None):

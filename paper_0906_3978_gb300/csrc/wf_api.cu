@@ -406,6 +406,24 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   return s;
 }
 
+wf_status wf_sd_noise(wf_ctx* ctx, int64_t n_cells, const double* n_obs, const double* w, const double* lambda,
+                      double nbar, double* D, double* b, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return sd_noise_run(*c, n_cells, n_obs, w, lambda, nbar, D, b, (cudaStream_t)stream);
+}
+
+wf_status wf_jackknife_masses(wf_ctx* ctx, int64_t n_gal, const double* w_gal, const double* u, double alpha,
+                              double* out, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return jackknife_run(*c, n_gal, w_gal, u, alpha, out, (cudaStream_t)stream);
+}
+
 wf_status wf_selection_eval(wf_ctx* ctx, const wf_selection* sel, const double* pos, int64_t n_pts,
                             int reciprocal, double* w, void* stream) {
   if (!ctx || !sel) return WF_ERR_ARG;

@@ -172,6 +172,10 @@ wf_status assign_weighted_run(Ctx& c, const wf_grid& g, int scheme, const double
                               int64_t n_gal, uint64_t* fine_out, double* n_obs, cudaStream_t st);
 wf_status selection_at_run(Ctx& c, const wf_selection& sel, const double* pos, int64_t n_pts, bool reciprocal,
                           double* w, cudaStream_t st);
+wf_status sd_noise_run(Ctx& c, int64_t n_cells, const double* n_obs, const double* w, const double* lambda,
+                       double nbar, double* D, double* b, cudaStream_t st);
+wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double* u, double alpha, double* out,
+                        cudaStream_t st);
 // the steps around the solve (wf_post.cu)
 double rsd_factor(double k, double beta, double sigma_v);
 wf_status deconvolve_run(Ctx& c, const wf_grid& g, const double* in, double beta, double sigma_v, double bias,

@@ -115,6 +115,62 @@ k_data(const double* __restrict__ n_obs, const double* __restrict__ w, const dou
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// Signal-dependent noise (Eq. eq:noisecov, N^SD = w lambda / nbar^2): the solve's diagonal
+// nbar^2 w / lambda and right-hand side nbar^2 d / lambda, d = n_obs / nbar - w; lambda given, or
+// the flat-prior mean (n_obs + 1) / w.  Cells with w = 0 or lambda <= 0 carry no data term.
+// Every operation explicitly rounded in the order of the definition.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_sd_noise(const double* __restrict__ n_obs, const double* __restrict__ w, const double* __restrict__ lam,
+           double nbar, size_t n, double* __restrict__ D, double* __restrict__ b) {
+  const double nb2 = __dmul_rn(nbar, nbar);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    const double nv = n_obs[e], wv = w[e];
+    const double l = lam ? lam[e] : (wv > 0.0 ? __ddiv_rn(__dadd_rn(nv, 1.0), wv) : 0.0);
+    if (wv > 0.0 && l > 0.0) {
+      const double d = __dsub_rn(__ddiv_rn(nv, nbar), wv);
+      D[e] = __ddiv_rn(__dmul_rn(nb2, wv), l);
+      b[e] = __ddiv_rn(__dmul_rn(nb2, d), l);
+    } else {
+      D[e] = 0.0;
+      b[e] = 0.0;
+    }
+  }
+}
+
+// Eq. eq:selfunc: galaxy g kept when u_g < alpha / w_g, then mass 1 / alpha (else 0).
+__global__ void __launch_bounds__(256)
+k_jackknife_masses(const double* __restrict__ w, const double* __restrict__ u, double alpha, long long n,
+                   double* __restrict__ out) {
+  const double inv = __drcp_rn(alpha);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double wv = w[i];
+    out[i] = (wv > 0.0 && u[i] < __ddiv_rn(alpha, wv)) ? inv : 0.0;
+  }
+}
+
+wf_status sd_noise_run(Ctx& c, int64_t n_cells, const double* n_obs, const double* w, const double* lambda,
+                       double nbar, double* D, double* b, cudaStream_t st) {
+  if (n_cells <= 0 || !n_obs || !w || !D || !b || !(nbar > 0.0) || !std::isfinite(nbar)) return WF_ERR_ARG;
+  c.launch("sd_noise", (lambda ? 40.0 : 32.0) * (double)n_cells, st, [&] {
+    k_sd_noise<<<152 * 4, 256, 0, st>>>(n_obs, w, lambda, nbar, (size_t)n_cells, D, b);
+  });
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
+wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double* u, double alpha, double* out,
+                        cudaStream_t st) {
+  if (n_gal < 0 || (n_gal > 0 && (!w_gal || !u || !out)) || !(alpha > 0.0) || !(alpha <= 1.0)) return WF_ERR_ARG;
+  if (n_gal == 0) return WF_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>((n_gal + 255) / 256, 152 * 16);
+  c.launch("jackknife", 24.0 * (double)n_gal, st,
+           [&] { k_jackknife_masses<<<grid, 256, 0, st>>>(w_gal, u, alpha, (long long)n_gal, out); });
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
 wf_status selection_at_run(Ctx& c, const wf_selection& sel, const double* pos, int64_t n_pts, bool reciprocal,
                           double* w, cudaStream_t st) {
   if (n_pts < 0 || (n_pts > 0 && (!pos || !w)) || sel.n_holes < 0 || (sel.n_holes > 0 && !sel.holes) ||

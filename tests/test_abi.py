@@ -28,7 +28,8 @@ def test_header_declares_boundary():
     for required in ["wf_create", "wf_destroy", "wf_grid_assign", "wf_build_noise", "wf_solve",
                      "wf_solve_batch", "wf_submit", "wf_poll", "wf_status_string", "wf_set_fused_planes",
                      "wf_smooth", "wf_compare", "wf_density_stats", "wf_selection_eval",
-                     "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve"]:
+                     "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve", "wf_sd_noise",
+                     "wf_jackknife_masses"]:
         assert required in names
 
 

@@ -204,3 +204,66 @@ def test_deconvolution_errors(ctx):
         with pytest.raises(wf.WfError) as e:
             ctx.deconvolve(d, 16.0, a["beta"], a["sigma_v"], a["bias"])
         assert e.value.status == wf.ERR_ARG
+
+
+# ------------------------------------------------------------------ signal-dependent noise (eq:noisecov)
+def _sd_inputs(n):
+    pr = synth.problem("c2", n_override=n, cache=False)
+    nobs = oracle.lowpass(oracle.assign(pr.pos, n, pr.box, pr.scheme, 2), n, 2)
+    w = oracle.window(pr.sel, n, pr.box)
+    d, b, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+    return pr, nobs, w, nbar
+
+
+def test_sd_noise_bit_exact(ctx):
+    """The same explicitly rounded FP64 operations on both sides: D and b bit for bit, with the
+    flat-prior lambda and with a given lambda (zeros included: no data term there)."""
+    pr, nobs, w, nbar = _sd_inputs(32)
+    lam = np.random.default_rng(3).uniform(0.0, 2.0, w.shape)
+    lam.ravel()[::3] = 0.0
+    for given in (None, lam):
+        D, b = ctx.sd_noise(gpu(nobs), gpu(w), nbar, lam=None if given is None else gpu(given))
+        Dr, br = ev.sd_noise(nobs, w, ev.lambda_mean(nobs, w) if given is None else given, nbar)
+        assert np.array_equal(host(D), Dr) and np.array_equal(host(b), br)
+
+
+def test_jackknife_masses_bit_exact(ctx):
+    rng = np.random.default_rng(31)
+    w = rng.uniform(0.0, 1.0, 5000)
+    w[::7] = 0.0
+    u = rng.uniform(size=5000)
+    assert np.array_equal(host(ctx.jackknife_masses(gpu(w), gpu(u), 0.05)), ev.jackknife_masses(w, u, 0.05))
+    with pytest.raises(wf.WfError):
+        ctx.jackknife_masses(gpu(w), gpu(u), 0.0)
+
+
+def test_jackknife_subsample_grid(ctx):
+    """N'' = the gridded subsample of masses 1 / alpha: the fine grid bit for bit against the
+    oracle's with the same completeness and uniform numbers."""
+    n = 24
+    pr = synth.problem("c2", n_override=n, cache=False)
+    w_gal = oracle.window_at(pr.sel, pr.pos)
+    u = np.random.default_rng(45).uniform(size=len(pr.pos))
+    alpha = 0.9 * w_gal.min()
+    m = ctx.jackknife_masses(gpu(w_gal), gpu(u), alpha)
+    fine_d = torch.empty((2 * n) ** 3, dtype=torch.int64, device=DEV)
+    ctx.grid_assign_weighted(gpu(pr.pos), m, n, pr.box, wf.TSC, 2, fine_out=fine_d)
+    ref = oracle.assign_weighted(pr.pos, ev.jackknife_masses(w_gal, u, alpha), n, pr.box, 2, 2)
+    assert np.array_equal(host(fine_d).view(np.uint64).reshape(ref.shape), ref)
+
+
+def test_sd_wiener_filter_flat_prior_end_to_end(ctx):
+    """The signal-dependent-noise filter with the flat-prior lambda, through the library (gridding,
+    window, SD terms, solve with nbar = 1 and w = D) against the oracle's textbook CG on the same
+    diagonal."""
+    n = 32
+    pr, nobs_o, w_o, nbar_o = _sd_inputs(n)
+    nobs = ctx.grid_assign(gpu(pr.pos), n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+    D, bsd = ctx.sd_noise(nobs, w, nbar)
+    s, info = ctx.solve(D, 1.0, bsd, pr.box, pr.pk_k, pr.pk_p, tol=1e-12, max_iter=20000)
+    assert info.status == wf.OK
+    D_o, b_o = ev.sd_noise(nobs_o, w_o, ev.lambda_mean(nobs_o, w_o), nbar_o)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    ref = oracle.cg(tab, 1.0, D_o, b_o, tol=1e-12)[0]
+    assert rl2(host(s), ref) <= 1e-10

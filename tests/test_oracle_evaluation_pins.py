@@ -200,3 +200,42 @@ def test_deconvolution_plane_wave_and_bias():
     assert np.max(np.abs(ev.deconvolve(f, box, beta, sv, b) - want)) <= 1e-13
     g = np.random.default_rng(2).standard_normal((8, 8, 8))
     assert np.max(np.abs(ev.deconvolve(g, 30.0, 0.0, 0.0, 2.0) - g / 2.0)) <= 1e-14
+
+
+# ---------------------------------------------------------------- signal-dependent noise
+def test_sd_noise_reduces_to_the_lsq_noise():
+    """lambda = nbar everywhere: the diagonal is nbar w and the right-hand side nbar d, the LSQ
+    Wiener filter's (Sec. 2.4, eq:noiseav)."""
+    pr = synth.problem("c1", n_override=16, cache=False)
+    nobs = oracle.lowpass(oracle.assign(pr.pos, 16, pr.box, pr.scheme, 2), 16, 2)
+    w = oracle.window(pr.sel, 16, pr.box)
+    d, b, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+    D, bsd = ev.sd_noise(nobs, w, np.full_like(w, nbar), nbar)
+    assert np.max(np.abs(D - nbar * w)) <= 1e-14 * nbar
+    assert np.max(np.abs(bsd - b)) <= 1e-12 * np.max(np.abs(b))
+
+
+def test_sd_noise_hand_worked_and_unobserved_cells():
+    n_obs = np.array([2.0, 0.0, 5.0, 1.0])
+    w = np.array([0.5, 0.25, 0.0, 1.0])
+    lam = ev.lambda_mean(n_obs, w)
+    assert lam.tolist() == [6.0, 4.0, 0.0, 2.0]
+    D, b = ev.sd_noise(n_obs, w, lam, 2.0)
+    assert D.tolist() == [4 * 0.5 / 6.0, 4 * 0.25 / 4.0, 0.0, 4 * 1.0 / 2.0]
+    assert b.tolist() == [4 * (1.0 - 0.5) / 6.0, 4 * (0.0 - 0.25) / 4.0, 0.0, 4 * (0.5 - 1.0) / 2.0]
+
+
+def test_jackknife_masses_rule_and_unbiasedness():
+    """Kept when u < alpha / w, mass 1 / alpha; over many draws the total mass averages
+    sum_g 1 / w_g, the number of galaxies of the complete sample the observed one was selected
+    from (Sec. "Jackknife-like scheme": <N''> = lambda, not the observed counts)."""
+    w = np.array([0.5, 0.01, 0.0, 1.0])
+    m = ev.jackknife_masses(w, np.array([0.0199, 0.5, 0.0, 0.0101]), 0.01)
+    assert m.tolist() == [100.0, 100.0, 0.0, 0.0]
+    rng = np.random.default_rng(12)
+    wg = rng.uniform(0.2, 1.0, 2000)
+    alpha = 0.1
+    tot = np.array([ev.jackknife_masses(wg, rng.uniform(size=2000), alpha).sum() for _ in range(400)])
+    p = alpha / wg
+    sigma = math.sqrt(np.sum(p * (1 - p)) / alpha ** 2 / 400)
+    assert abs(tot.mean() - np.sum(1.0 / wg)) <= 4 * sigma
