@@ -136,6 +136,26 @@ const char* wf_last_error(void);
  * differ, the FP32 rounding.  Applies to solves started after the call. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
+/* ---- the 3D mask from a sky completeness map (Sec. 2.3) ------------------------------------ */
+
+/* Projects a sky completeness map and a radial completeness table onto the grid along rays from
+ * the observer (Sec. 2.3 with Eq. eq:transf).  Sky pixel (i, j) of an equidistant alpha x delta
+ * map has its centre at alpha_i = alpha0 + (i + 1/2) dalpha, delta_j = delta0 + (j + 1/2) ddelta
+ * (radians); its ray is sampled at r_k = (k + 1/2) dr, k < n_r, at the point
+ * o + r_k (cos delta cos alpha, cos delta sin alpha, sin delta).  Each sample inside the box
+ * [0, box)^3 goes to its nearest-grid-point cell floor(x / H).  Per cell, the sky values and
+ * the radial values wr[k] of its samples are averaged; the mask is the product of the two
+ * averages (w <= 1), and 0 in cells no sample reached.  The sums are Q32 fixed point with integer
+ * atomics, so the result is exact and independent of the order of the samples.
+ *   sky       dev double [n_delta][n_alpha], values in [0, 1]
+ *   observer  host double[3] (box units); wr host double [n_r], values in [0, 1]
+ *   w         dev double [n^3];  counts dev int64 [n^3] (samples per cell) or NULL
+ * Errors: WF_ERR_ARG (bad geometry, a value outside [0, 1]), WF_ERR_UNSUPPORTED, WF_ERR_OOM,
+ * WF_ERR_CUDA.  Waits for completion. */
+wf_status wf_project_mask(wf_ctx* ctx, const wf_grid* grid, const double* sky, int n_alpha, int n_delta,
+                          double alpha0, double dalpha, double delta0, double ddelta, const double* observer,
+                          double dr, int n_r, const double* wr, double* w, int64_t* counts, void* stream);
+
 /* ---- signal-dependent noise (Eq. eq:noisecov; flat-prior and Jackknife-like estimators) ---- */
 
 /* The data terms of the signal-dependent-noise Wiener filter.  With N^SD = w lambda / nbar^2 per

@@ -7,6 +7,9 @@ Each function follows the paper (Kitaura et al. 2009, arXiv:0906.3978):
   assign      Sec. 2.2 "Supersampling step", Eq. def:ngrid (fixed-point CIC/TSC)
   lowpass     Sec. 2.2, supersampling step 2 (ideal low-pass, sampling at target grid)
   window      Sec. 2.3 (3D mask w <= 1; analytic cone x holes x radial law)
+  project_mask
+              Sec. 2.3, projection of a sky completeness map and a radial completeness table
+              along rays (Eq. eq:transf), NGP-assigned and averaged per cell
   window_at, assign_weighted
               Sec. 5, Eq. def:ngrid with galaxy mass 1/w (the inverse-weighting estimator)
   build_noise Sec. 2.4, Eqs. eq:datamodel, eq:nmean, eq:noiseav
@@ -58,6 +61,8 @@ def lib():
         L.oracle_lowpass_scaled.argtypes = [i, i, u64p, d, dp]
         L.oracle_assign_weighted.argtypes = [i, d, i, i, dp, dp, i64, u64p]
         L.oracle_window_at.argtypes = [i64, dp, dp, dp, d, i, dp, i, dp, dp]
+        L.oracle_project_mask.argtypes = [i, d, dp, i, i, d, d, d, d, dp, d, i, dp, dp,
+                                          ctypes.POINTER(ctypes.c_int64)]
         L.oracle_lowpass_point.argtypes = [i, i, u64p, i, i, i]
         L.oracle_lowpass_point.restype = d
         L.oracle_window.argtypes = [i, d, dp, dp, d, i, dp, i, dp, dp]
@@ -151,6 +156,21 @@ def window_at(sel, pts) -> np.ndarray:
                                   holes.shape[0], _dp(holes), int(sel.radial_kind), _dp(rp), _dp(w)),
            "window_at")
     return w
+
+
+def project_mask(sky, n: int, box: float, alpha0: float, dalpha: float, delta0: float, ddelta: float,
+                 observer, dr: float, wr):
+    """(w [n, n, n], counts [n, n, n]): the 3D mask from the sky map sky [n_delta, n_alpha] and the
+    radial completeness wr [n_r] at r_k = (k + 1/2) dr, projected along rays (Sec. 2.3)."""
+    sky = np.ascontiguousarray(sky, dtype=np.float64)
+    wr = np.ascontiguousarray(wr, dtype=np.float64).ravel()
+    obs = np.ascontiguousarray(observer, dtype=np.float64)
+    w = np.empty(n ** 3, dtype=np.float64)
+    cnt = np.empty(n ** 3, dtype=np.int64)
+    _check(lib().oracle_project_mask(n, box, _dp(sky), sky.shape[1], sky.shape[0], alpha0, dalpha, delta0, ddelta,
+                                     _dp(obs), dr, wr.size, _dp(wr), _dp(w),
+                                     cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "project_mask")
+    return w.reshape(n, n, n), cnt.reshape(n, n, n)
 
 
 def window(sel, n: int, box: float) -> np.ndarray:

@@ -427,6 +427,63 @@ int oracle_window(int n, double box, const double* obs, const double* axis, doub
   return OR_OK;
 }
 
+/* Projection of a sky completeness map onto the grid (Sec. 2.3): sky pixel (i, j) of an
+ * equidistant alpha x delta map has centre alpha_i = alpha0 + (i + 1/2) dalpha, delta_j =
+ * delta0 + (j + 1/2) ddelta; its ray from the observer is sampled at r_k = (k + 1/2) dr,
+ * k < n_r, at x = o + r_k (cos delta cos alpha, cos delta sin alpha, sin delta) (Eq. eq:transf);
+ * each sample inside the box goes to its nearest-grid-point cell floor(x / H).  Per cell the sky
+ * values and the radial completeness values wr[k] of the samples are summed in Q32 fixed point
+ * (rint(v 2^32), exact and order-independent) and counted; the mask is
+ * (S_sky 2^-32 / count) * (S_r 2^-32 / count), 0 where no sample fell.  sky[j * n_alpha + i],
+ * values in [0, 1]; counts may be NULL. */
+int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n_delta, double alpha0,
+                        double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
+                        const double* wr, double* w, int64_t* counts) {
+  if (n <= 0 || !(box > 0) || n_alpha <= 0 || n_delta <= 0 || !(dr > 0) || n_r <= 0) return OR_ERR_ARG;
+  size_t V = (size_t)n * n * n;
+  uint64_t* ss = (uint64_t*)calloc(V, sizeof(uint64_t));
+  uint64_t* sr = (uint64_t*)calloc(V, sizeof(uint64_t));
+  int64_t* cnt = (int64_t*)calloc(V, sizeof(int64_t));
+  if (!ss || !sr || !cnt) {
+    free(ss);
+    free(sr);
+    free(cnt);
+    return OR_ERR_OOM;
+  }
+  const double H = box / (double)n, q32 = 4294967296.0;
+  for (int k = 0; k < n_r; ++k)
+    if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return OR_ERR_ARG;
+  for (int j = 0; j < n_delta; ++j) {
+    const double de = delta0 + ((double)j + 0.5) * ddelta;
+    const double cd = cos(de), sd = sin(de);
+    for (int i = 0; i < n_alpha; ++i) {
+      const double v = sky[(size_t)j * n_alpha + i];
+      if (!(v >= 0.0 && v <= 1.0)) return OR_ERR_ARG;
+      const double al = alpha0 + ((double)i + 0.5) * dalpha;
+      const double ux = cd * cos(al), uy = cd * sin(al), uz = sd;
+      const uint64_t qs = (uint64_t)rint(v * q32);
+      for (int k = 0; k < n_r; ++k) {
+        const double r = ((double)k + 0.5) * dr;
+        const double fx = floor((obs[0] + r * ux) / H), fy = floor((obs[1] + r * uy) / H),
+                     fz = floor((obs[2] + r * uz) / H);
+        if (!(fx >= 0.0 && fx < n && fy >= 0.0 && fy < n && fz >= 0.0 && fz < n)) continue;
+        const size_t c = ((size_t)fx * n + (size_t)fy) * n + (size_t)fz;
+        ss[c] += qs;
+        sr[c] += (uint64_t)rint(wr[k] * q32);
+        cnt[c] += 1;
+      }
+    }
+  }
+  for (size_t c = 0; c < V; ++c) {
+    w[c] = cnt[c] ? ((double)ss[c] / q32 / (double)cnt[c]) * ((double)sr[c] / q32 / (double)cnt[c]) : 0.0;
+    if (counts) counts[c] = cnt[c];
+  }
+  free(ss);
+  free(sr);
+  free(cnt);
+  return OR_OK;
+}
+
 /* ------------------------------------------------------------------------------------ */
 /* 5. Data and noise (Sec. 2.4: eq:datamodel, eq:nmean, eq:noiseav)                     */
 /* ------------------------------------------------------------------------------------ */

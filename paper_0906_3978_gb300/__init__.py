@@ -106,6 +106,9 @@ def lib():
         L.wf_profile.argtypes = [c_void_p, c_int]
         L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
         L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
+        L.wf_project_mask.argtypes = [c_void_p, P(Grid), c_void_p, c_int, c_int, c_double, c_double, c_double,
+                                      c_double, P(c_double), c_double, c_int, P(c_double), c_void_p, c_void_p,
+                                      c_void_p]
         L.wf_sd_noise.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_double, c_void_p, c_void_p,
                                   c_void_p]
         L.wf_jackknife_masses.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_double, c_void_p, c_void_p]
@@ -124,7 +127,7 @@ def lib():
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
                      "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve",
-                     "wf_sd_noise", "wf_jackknife_masses"):
+                     "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -269,6 +272,25 @@ class Context:
         if check and st != OK:
             raise WfError(st, "wf_build_noise")
         return (w, d, b, nb.value) if check else (st, w, d, b, nb.value)
+
+    # ---- Sec. 2.3: the 3D mask from a sky map ---------------------------------------------
+    def project_mask(self, sky, n: int, box: float, alpha0: float, dalpha: float, delta0: float, ddelta: float,
+                     observer, dr: float, wr, want_counts=False, stream=None):
+        """The 3D mask [n, n, n] from the sky map sky [n_delta, n_alpha] (device FP64) and the radial
+        table wr (host) along rays (wf_project_mask); with want_counts also the samples per cell."""
+        import torch
+        w = torch.empty((n, n, n), dtype=torch.float64, device=sky.device)
+        cnt = torch.empty((n, n, n), dtype=torch.int64, device=sky.device) if want_counts else None
+        wr = np.ascontiguousarray(np.asarray(wr, dtype=np.float64).ravel())
+        obs = (c_double * 3)(*[float(v) for v in observer])
+        g = Grid(int(n), float(box), 1)
+        st = lib().wf_project_mask(self._h, ctypes.byref(g), _ptr(sky), int(sky.shape[1]), int(sky.shape[0]),
+                                   float(alpha0), float(dalpha), float(delta0), float(ddelta), obs, float(dr),
+                                   wr.size, wr.ctypes.data_as(ctypes.POINTER(c_double)), _ptr(w), _ptr(cnt),
+                                   _stream(stream))
+        if st != OK:
+            raise WfError(st, "wf_project_mask")
+        return (w, cnt) if want_counts else w
 
     # ---- signal-dependent noise -----------------------------------------------------------
     def sd_noise(self, n_obs, w, nbar: float, lam=None, stream=None):

@@ -406,6 +406,18 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   return s;
 }
 
+wf_status wf_project_mask(wf_ctx* ctx, const wf_grid* grid, const double* sky, int n_alpha, int n_delta,
+                          double alpha0, double dalpha, double delta0, double ddelta, const double* observer,
+                          double dr, int n_r, const double* wr, double* w, int64_t* counts, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  return project_mask_run(*c, *grid, sky, n_alpha, n_delta, alpha0, dalpha, delta0, ddelta, observer, dr, n_r, wr,
+                          w, counts, (cudaStream_t)stream);
+}
+
 wf_status wf_sd_noise(wf_ctx* ctx, int64_t n_cells, const double* n_obs, const double* w, const double* lambda,
                       double nbar, double* D, double* b, void* stream) {
   if (!ctx) return WF_ERR_ARG;

@@ -171,6 +171,118 @@ wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double
   return WF_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Projection of a sky completeness map along rays (Sec. 2.3, Eq. eq:transf): sample (j, i, k) is
+// the point o + r_k u_ij, r_k = (k + 1/2) dr, u = (cos d cos a, cos d sin a, sin d) with the
+// pixel-centre cosines and sines from the host; its nearest-grid-point cell receives the pixel's
+// sky value and the radial table's value in Q32 fixed point (integer atomics: exact, any order)
+// and one count.  Every operation explicitly rounded in the order of the definition.
+// ------------------------------------------------------------------------------------------
+struct MaskArgs {
+  int n, n_alpha, n_delta, n_r;
+  double H, ox, oy, oz, dr;
+};
+
+__global__ void __launch_bounds__(256)
+k_project_mask(const double* __restrict__ sky, const double* __restrict__ ca, const double* __restrict__ sa,
+               const double* __restrict__ cd, const double* __restrict__ sd, const double* __restrict__ wr,
+               MaskArgs a, unsigned long long* __restrict__ ss, unsigned long long* __restrict__ sr,
+               unsigned long long* __restrict__ cnt, int* __restrict__ err) {
+  const long long tot = (long long)a.n_alpha * a.n_delta * a.n_r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % a.n_r);
+    const long long pix = e / a.n_r;
+    const int i = (int)(pix % a.n_alpha), j = (int)(pix / a.n_alpha);
+    const double v = sky[pix], wk = wr[k];
+    if (!(v >= 0.0 && v <= 1.0) || !(wk >= 0.0 && wk <= 1.0)) {
+      atomicOr(err, 1);
+      continue;
+    }
+    const double r = __dmul_rn((double)k + 0.5, a.dr);
+    const double ux = __dmul_rn(cd[j], ca[i]), uy = __dmul_rn(cd[j], sa[i]), uz = sd[j];
+    const double fx = floor(__ddiv_rn(__dadd_rn(a.ox, __dmul_rn(r, ux)), a.H));
+    const double fy = floor(__ddiv_rn(__dadd_rn(a.oy, __dmul_rn(r, uy)), a.H));
+    const double fz = floor(__ddiv_rn(__dadd_rn(a.oz, __dmul_rn(r, uz)), a.H));
+    const double nn = (double)a.n;
+    if (!(fx >= 0.0 && fx < nn && fy >= 0.0 && fy < nn && fz >= 0.0 && fz < nn)) continue;
+    const size_t c = ((size_t)fx * a.n + (size_t)fy) * a.n + (size_t)fz;
+    atomicAdd(ss + c, __double2ull_rn(__dmul_rn(v, 4294967296.0)));
+    atomicAdd(sr + c, __double2ull_rn(__dmul_rn(wk, 4294967296.0)));
+    atomicAdd(cnt + c, 1ull);
+  }
+}
+
+// w = (S_sky 2^-32 / count) (S_r 2^-32 / count), 0 where no sample fell
+__global__ void __launch_bounds__(256)
+k_mask_finish(const unsigned long long* __restrict__ ss, const unsigned long long* __restrict__ sr,
+              const unsigned long long* __restrict__ cnt, size_t V, double* __restrict__ w,
+              long long* __restrict__ counts) {
+  const double q32 = 4294967296.0;
+  for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < V; c += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long nc = cnt[c];
+    double v = 0.0;
+    if (nc) {
+      const double cn = __ull2double_rn(nc);
+      v = __dmul_rn(__ddiv_rn(__ddiv_rn(__ull2double_rn(ss[c]), q32), cn),
+                    __ddiv_rn(__ddiv_rn(__ull2double_rn(sr[c]), q32), cn));
+    }
+    w[c] = v;
+    if (counts) counts[c] = (long long)nc;
+  }
+}
+
+wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_alpha, int n_delta, double alpha0,
+                           double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
+                           const double* wr, double* w, int64_t* counts, cudaStream_t st) {
+  if (!sky || !obs || !wr || !w || n_alpha <= 0 || n_delta <= 0 || n_r <= 0 || !(dr > 0.0) || !std::isfinite(dr) ||
+      !std::isfinite(alpha0) || !std::isfinite(dalpha) || !std::isfinite(delta0) || !std::isfinite(ddelta))
+    return WF_ERR_ARG;
+  for (int k = 0; k < n_r; ++k)
+    if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return WF_ERR_ARG;
+  // pixel-centre cosines and sines, as the definition takes them (libm on the host)
+  std::vector<double> h((size_t)2 * n_alpha + 2 * n_delta + n_r);
+  double *ca = h.data(), *sa = ca + n_alpha, *cd = sa + n_alpha, *sd = cd + n_delta, *wrh = sd + n_delta;
+  for (int i = 0; i < n_alpha; ++i) {
+    const double al = alpha0 + ((double)i + 0.5) * dalpha;
+    ca[i] = std::cos(al);
+    sa[i] = std::sin(al);
+  }
+  for (int j = 0; j < n_delta; ++j) {
+    const double de = delta0 + ((double)j + 0.5) * ddelta;
+    cd[j] = std::cos(de);
+    sd[j] = std::sin(de);
+  }
+  for (int k = 0; k < n_r; ++k) wrh[k] = wr[k];
+  const size_t V = (size_t)g.n * g.n * g.n;
+  double* dtab;
+  unsigned long long* acc;
+  int* err;
+  WF_TRY(c.get("mask_tab", h.size() * sizeof(double), (void**)&dtab));
+  WF_TRY(c.get("mask_acc", 3 * V * sizeof(unsigned long long), (void**)&acc));
+  WF_TRY(c.get("mask_err", 64, (void**)&err));
+  WF_CUDA(cudaMemcpyAsync(dtab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  WF_CUDA(cudaMemsetAsync(acc, 0, 3 * V * sizeof(unsigned long long), st));
+  WF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  MaskArgs a{g.n, n_alpha, n_delta, n_r, g.box / (double)g.n, obs[0], obs[1], obs[2], dr};
+  const double* dca = dtab;
+  const double* dsa = dca + n_alpha;
+  const double* dcd = dsa + n_alpha;
+  const double* dsd = dcd + n_delta;
+  const double* dwr = dsd + n_delta;
+  const double samples = (double)n_alpha * n_delta * n_r;
+  c.launch("project_mask", 24.0 * samples, st, [&] {
+    k_project_mask<<<152 * 16, 256, 0, st>>>(sky, dca, dsa, dcd, dsd, dwr, a, acc, acc + V, acc + 2 * V, err);
+  });
+  c.launch("mask_finish", 32.0 * (double)V, st, [&] {
+    k_mask_finish<<<152 * 4, 256, 0, st>>>(acc, acc + V, acc + 2 * V, V, w, reinterpret_cast<long long*>(counts));
+  });
+  WF_CUDA(cudaGetLastError());
+  int* hp = reinterpret_cast<int*>(c.host_pinned);
+  WF_CUDA(cudaMemcpyAsync(hp, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  WF_CUDA(cudaStreamSynchronize(st));  // also keeps h alive until the copy is done
+  return hp[0] ? WF_ERR_ARG : WF_OK;
+}
+
 wf_status selection_at_run(Ctx& c, const wf_selection& sel, const double* pos, int64_t n_pts, bool reciprocal,
                           double* w, cudaStream_t st) {
   if (n_pts < 0 || (n_pts > 0 && (!pos || !w)) || sel.n_holes < 0 || (sel.n_holes > 0 && !sel.holes) ||

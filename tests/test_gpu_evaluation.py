@@ -267,3 +267,34 @@ def test_sd_wiener_filter_flat_prior_end_to_end(ctx):
     tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
     ref = oracle.cg(tab, 1.0, D_o, b_o, tol=1e-12)[0]
     assert rl2(host(s), ref) <= 1e-10
+
+
+# ------------------------------------------------------------------ sky-mask projection (Sec. 2.3)
+def _sky_case(seed, n_alpha, n_delta):
+    rng = np.random.default_rng(seed)
+    sky = np.clip(0.6 + 0.3 * rng.standard_normal((n_delta, n_alpha)), 0.0, 1.0)
+    sky[:, : n_alpha // 5] = 0.0                   # a masked stripe
+    return sky
+
+
+@pytest.mark.parametrize("n,box,n_alpha,n_delta,n_r", [(16, 40.0, 90, 45, 120), (48, 100.0, 180, 90, 300)])
+def test_mask_projection_bit_exact(ctx, n, box, n_alpha, n_delta, n_r):
+    """The same host cosines and sines, explicitly rounded sample positions and Q32 sums on both
+    sides: the mask and the counts bit for bit."""
+    sky = _sky_case(n, n_alpha, n_delta)
+    dr = 0.3 * box / n
+    r = (np.arange(n_r) + 0.5) * dr
+    wr = np.exp(-((r / (0.4 * box)) ** 2))
+    obs = (0.1 * box, 0.5 * box, 0.45 * box)
+    geo = (0.0, 2 * np.pi / n_alpha, -np.pi / 2, np.pi / n_delta)
+    w, cnt = ctx.project_mask(gpu(sky), n, box, *geo, obs, dr, wr, want_counts=True)
+    w_ref, c_ref = oracle.project_mask(sky, n, box, *geo, obs, dr, wr)
+    assert np.array_equal(host(cnt), c_ref)
+    assert np.array_equal(host(w), w_ref)
+
+
+def test_mask_projection_rejects_bad_values(ctx):
+    sky = gpu(np.full((4, 8), 1.5))
+    with pytest.raises(wf.WfError) as e:
+        ctx.project_mask(sky, 16, 16.0, 0.0, 0.5, -1.0, 0.5, (8.0, 8.0, 8.0), 0.5, np.ones(10))
+    assert e.value.status == wf.ERR_ARG

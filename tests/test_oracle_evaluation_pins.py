@@ -239,3 +239,34 @@ def test_jackknife_masses_rule_and_unbiasedness():
     p = alpha / wg
     sigma = math.sqrt(np.sum(p * (1 - p)) / alpha ** 2 / 400)
     assert abs(tot.mean() - np.sum(1.0 / wg)) <= 4 * sigma
+
+
+# ---------------------------------------------------------------- sky-mask projection (Sec. 2.3)
+def test_mask_single_ray():
+    """One pixel on the +x axis, samples every 0.25 cells: 4 samples per crossed cell (2 in the
+    first, which the ray enters half way), the mask is sky value x radial value."""
+    w, c = oracle.project_mask(np.array([[0.75]]), 8, 8.0, -0.01, 0.02, -0.01, 0.02, (0.5, 2.5, 2.5), 0.25,
+                               np.full(40, 0.5))
+    assert c[:, 2, 2].tolist() == [2, 4, 4, 4, 4, 4, 4, 4] and c.sum() == 30
+    assert np.all(w[:, 2, 2] == 0.375) and np.count_nonzero(w) == 8  # values exact in Q32
+
+
+def test_mask_radial_average_and_linearity():
+    """A radial ramp is averaged over each cell's samples; sky values scale the mask linearly."""
+    n_r = 32
+    wr = (np.arange(n_r) + 0.5) / n_r
+    w, c = oracle.project_mask(np.array([[1.0]]), 8, 8.0, -0.01, 0.02, -0.01, 0.02, (0.0, 4.5, 4.5), 0.25, wr)
+    r = (np.arange(n_r) + 0.5) * 0.25
+    for cell in range(8):
+        sel = (r >= cell) & (r < cell + 1)
+        assert abs(w[cell, 4, 4] - wr[sel].mean()) <= 1e-9
+    w2, _ = oracle.project_mask(np.array([[0.5]]), 8, 8.0, -0.01, 0.02, -0.01, 0.02, (0.0, 4.5, 4.5), 0.25, wr)
+    assert np.max(np.abs(w2 - 0.5 * w)) <= 1e-12
+
+
+def test_mask_uniform_sky_is_the_hit_indicator():
+    """Sky and radial completeness 1 everywhere: w = 1 exactly in every reached cell, 0 elsewhere."""
+    sky = np.ones((18, 36))
+    w, c = oracle.project_mask(sky, 12, 24.0, 0.0, 2 * np.pi / 36, -np.pi / 2, np.pi / 18, (12.0, 12.0, 12.0), 0.5,
+                               np.ones(30))
+    assert np.array_equal(w > 0, c > 0) and np.all(w[c > 0] == 1.0)
