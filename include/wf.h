@@ -354,6 +354,29 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
                    double nbar, const double* b, const wf_solve_opts* opts, double* s_out,
                    wf_solve_info* info, void* stream);
 
+/* Linear response of the data to the real-space matter field (Sec. 3): bias B = bias (a constant)
+ * and the mu-averaged redshift operator Z = sqrt(<K D>_mu) of wf_rsd_factor, both diagonal in
+ * Fourier space with the joint factor g(k) = bias sqrt(<K D>_mu(|k|)). */
+typedef struct {
+  double bias;     /* > 0 */
+  double beta;     /* Kaiser beta (finite) */
+  double sigma_v;  /* >= 0, pairwise-velocity dispersion in length units (Lorentzian damping) */
+} wf_response;
+
+/* The variant of Sec. 3 with Z and B inside the response operator, R = W Z B: the Wiener mean of
+ * the real-space matter field s_m solving
+ *     (S^-1 + G diag(nbar w) G) s_m = G b,     G = F^-1 diag(g) F,
+ * with S^-1 from `power` (the real-space matter P(k)) as in wf_solve.  G is invertible and
+ * commutes with S, so this is the same system as (G^-1 S^-1 G^-1 + diag(nbar w)) s_g = b for
+ * s_g = G s_m, a solve with the redshift-space prior g^2 P(k) followed by the deconvolution
+ * s_m = G^-1 s_g (Eq. eq:DEC); that is how it runs.  opts->tol applies to the s_g system, whose
+ * residual is G^-1 times the literal one: info->rel_residual is the s_g system's.
+ *   w, b, s_out  dev double [n^3] as in wf_solve (s_out may not alias w or b)
+ * Errors: as wf_solve, plus WF_ERR_ARG for a bad response. */
+wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const wf_response* response,
+                            const double* w, double nbar, const double* b, const wf_solve_opts* opts,
+                            double* s_out, wf_solve_info* info, void* stream);
+
 /* Solve `count` independent systems (grids may differ in n and box) in one call; the
  * iterations of all unfinished systems are interleaved on the device.  Arrays of length
  * count: grids, powers, w[i], nbar[i], b[i], s_out[i] (dev), infos[i] (host).

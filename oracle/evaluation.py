@@ -1,6 +1,6 @@
 """CPU FP64 oracle of the steps around the solve (Kitaura et al. 2009, arXiv:0906.3978): the
-redshift-distortion factor and the deconvolution B^-1 Z^-1 of Sec. 3 (Eq. eq:DEC), and the
-evaluation of a reconstruction of Sec. 5.1 "Statistical correlation measures" and Sec. 6.2
+redshift-distortion factor, the deconvolution B^-1 Z^-1 (Eq. eq:DEC) and the Wiener filter with
+Z and B inside the response operator, all of Sec. 3, and the evaluation of a reconstruction of Sec. 5.1 "Statistical correlation measures" and Sec. 6.2
 "Statistical analysis": Gaussian smoothing, the correlation coefficient r, the Euclidean distance D_Euc, the
 normalised Kullback-Leibler distance D_KL, and binned density statistics (counts in 1+delta bins
 per radial shell and observed / unobserved region; mean, central moments, skewness, kurtosis,
@@ -150,6 +150,65 @@ def deconvolve(field, box: float, beta: float, sigma_v: float, bias: float) -> n
     mult = 1.0 / (bias * np.sqrt(rsd_factor(2.0 * np.pi * np.sqrt(u) / box, beta, sigma_v)))
     spec = fft3d(f.astype(np.complex128), -1) * mult[inv].reshape(n2.shape)
     return np.real(fft3d(spec, +1)) / float(n) ** 3
+
+
+def n2_grid(n: int) -> np.ndarray:
+    """|m|^2 of the signed DFT index m in (-N/2, N/2] at every node of the [n, n, n] grid."""
+    m = np.fft.fftfreq(n, 1.0 / n).astype(np.int64)
+    m[n // 2] = n // 2
+    return m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2
+
+
+def response_table(n: int, box: float, bias: float, beta: float, sigma_v: float) -> np.ndarray:
+    """g[n2] = b sqrt(<K D>_mu(|k|)), |k| = 2 pi sqrt(n2) / L: the Fourier factor of the response
+    Z B of Sec. 3 (bias and mu-averaged redshift operator), by n2 up to 3 (n/2)^2."""
+    n2 = np.arange(3 * (n // 2) ** 2 + 1)
+    return bias * np.sqrt(rsd_factor(2.0 * np.pi * np.sqrt(n2) / box, beta, sigma_v))
+
+
+def _fourier_apply(x, mult) -> np.ndarray:
+    """F^-1 diag(mult) F x for a real field x (unnormalised forward DFT, 1/V on the inverse)."""
+    return np.real(fft3d(fft3d(np.asarray(x, dtype=np.complex128), -1) * mult, +1)) / float(x.size)
+
+
+def response_matvec(sinv_tab, g_tab, nbar: float, w, s) -> np.ndarray:
+    """(S^-1 + G nbar diag(w) G) s with G = F^-1 diag(g) F: the Wiener operator of Sec. 2.5.1 with
+    the response R = W Z B of Sec. 3 (Z and B inside R)."""
+    n2 = n2_grid(s.shape[0])
+    gs = _fourier_apply(s, g_tab[n2])
+    return _fourier_apply(s, sinv_tab[n2]) + _fourier_apply(nbar * np.asarray(w) * gs, g_tab[n2])
+
+
+def solve_response(sinv_tab, g_tab, nbar: float, w, b, tol: float = 1e-12, max_iter: int = 20000):
+    """The matter field s_m of the literal system (S^-1 + G nbar diag(w) G) s_m = G b by textbook
+    (Hestenes-Stiefel) CG from 0, stopped on the relative residual recomputed from s_m (the same
+    rule as the oracle's plain CG).  Returns (s_m, iterations, relative residual)."""
+    b = np.asarray(b, dtype=np.float64)
+    rhs = _fourier_apply(b, np.asarray(g_tab)[n2_grid(b.shape[0])])
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    p = r.copy()
+    bb = float(np.sum(rhs * rhs))
+    if bb == 0.0:
+        return x, 0, 0.0
+    rr, it = bb, 0
+    while True:
+        if rr <= tol * tol * bb:
+            r = rhs - response_matvec(sinv_tab, g_tab, nbar, w, x)
+            rr = float(np.sum(r * r))
+            if np.sqrt(rr / bb) <= tol:
+                return x, it, float(np.sqrt(rr / bb))
+            p = r.copy()
+        if it >= max_iter:
+            raise RuntimeError("solve_response: not converged")
+        q = response_matvec(sinv_tab, g_tab, nbar, w, p)
+        alpha = rr / float(np.sum(p * q))
+        x += alpha * p
+        r -= alpha * q
+        rr_new = float(np.sum(r * r))
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
 
 
 # ---------------------------------------------------------------- signal-dependent noise (Sec. 2.4.2, App. A)

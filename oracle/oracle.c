@@ -440,6 +440,10 @@ int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n
                         double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
                         const double* wr, double* w, int64_t* counts) {
   if (n <= 0 || !(box > 0) || n_alpha <= 0 || n_delta <= 0 || !(dr > 0) || n_r <= 0) return OR_ERR_ARG;
+  for (int k = 0; k < n_r; ++k)
+    if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return OR_ERR_ARG;
+  for (size_t p = 0; p < (size_t)n_alpha * n_delta; ++p)
+    if (!(sky[p] >= 0.0 && sky[p] <= 1.0)) return OR_ERR_ARG;
   size_t V = (size_t)n * n * n;
   uint64_t* ss = (uint64_t*)calloc(V, sizeof(uint64_t));
   uint64_t* sr = (uint64_t*)calloc(V, sizeof(uint64_t));
@@ -451,14 +455,11 @@ int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n
     return OR_ERR_OOM;
   }
   const double H = box / (double)n, q32 = 4294967296.0;
-  for (int k = 0; k < n_r; ++k)
-    if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return OR_ERR_ARG;
   for (int j = 0; j < n_delta; ++j) {
     const double de = delta0 + ((double)j + 0.5) * ddelta;
     const double cd = cos(de), sd = sin(de);
     for (int i = 0; i < n_alpha; ++i) {
       const double v = sky[(size_t)j * n_alpha + i];
-      if (!(v >= 0.0 && v <= 1.0)) return OR_ERR_ARG;
       const double al = alpha0 + ((double)i + 0.5) * dalpha;
       const double ux = cd * cos(al), uy = cd * sin(al), uz = sd;
       const uint64_t qs = (uint64_t)rint(v * q32);

@@ -10,6 +10,7 @@ Functions mirror the C ABI:
   Context.build_noise   wf_build_noise   window, nbar, data, noise (Sec. 2.3-2.4)
   Context.solve         wf_solve         Wiener filter by CG (Sec. 2.5.1, Eq. eq:WF)
   Context.solve_batch   wf_solve_batch
+  Context.solve_response wf_solve_response  the Sec. 3 variant with Z and B inside R
   Context.submit/poll   wf_submit / wf_poll (serving)
 """
 from __future__ import annotations
@@ -59,6 +60,10 @@ class DensityMoments(ctypes.Structure):
                 ("mu4", c_double), ("skewness", c_double), ("kurtosis", c_double), ("pearson", c_double)]
 
 
+class Response(ctypes.Structure):
+    _fields_ = [("bias", c_double), ("beta", c_double), ("sigma_v", c_double)]
+
+
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("prec", c_int), ("inner_tol", c_double),
                 ("precond", c_int)]
@@ -99,6 +104,8 @@ def lib():
                                      c_void_p, P(c_double), c_void_p]
         L.wf_solve.argtypes = [c_void_p, P(Grid), P(Power), c_void_p, c_double, c_void_p, P(SolveOpts), c_void_p,
                                P(SolveInfo), c_void_p]
+        L.wf_solve_response.argtypes = [c_void_p, P(Grid), P(Power), P(Response), c_void_p, c_double, c_void_p,
+                                        P(SolveOpts), c_void_p, P(SolveInfo), c_void_p]
         L.wf_solve_batch.argtypes = [c_void_p, c_int, P(Grid), P(Power), P(c_void_p), P(c_double), P(c_void_p),
                                      P(SolveOpts), P(c_void_p), P(SolveInfo), c_void_p]
         L.wf_submit.argtypes = [c_void_p, P(Grid), P(Power), c_void_p, c_double, c_void_p, P(SolveOpts), P(c_uint64)]
@@ -127,7 +134,7 @@ def lib():
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
                      "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve",
-                     "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask"):
+                     "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask", "wf_solve_response"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -279,6 +286,8 @@ class Context:
         """The 3D mask [n, n, n] from the sky map sky [n_delta, n_alpha] (device FP64) and the radial
         table wr (host) along rays (wf_project_mask); with want_counts also the samples per cell."""
         import torch
+        if sky.dim() != 2 or sky.dtype != torch.float64 or not sky.is_contiguous() or not sky.is_cuda:
+            raise ValueError("sky must be a contiguous [n_delta, n_alpha] float64 CUDA tensor")
         w = torch.empty((n, n, n), dtype=torch.float64, device=sky.device)
         cnt = torch.empty((n, n, n), dtype=torch.int64, device=sky.device) if want_counts else None
         wr = np.ascontiguousarray(np.asarray(wr, dtype=np.float64).ravel())
@@ -361,6 +370,27 @@ class Context:
                             ctypes.byref(o), _ptr(s_out), ctypes.byref(info), _stream(stream))
         if check and st != OK:
             raise WfError(st, "wf_solve", info)
+        return s_out, info
+
+    def solve_response(self, w, nbar: float, b, box: float, pk_k, pk_p, bias: float, beta: float, sigma_v: float,
+                       tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1, s_out=None, stream=None,
+                       check=True):
+        """(s_m, info): the real-space matter field solving (S^-1 + G nbar diag(w) G) s_m = G b with
+        G the Fourier factor bias sqrt(<K D>_mu) (wf_solve_response)."""
+        import torch
+        n = int(b.shape[0])
+        if s_out is None:
+            s_out = torch.empty_like(b)
+        g = Grid(n, float(box), 1)
+        pw, keep = make_power(pk_k, pk_p)
+        rs = Response(float(bias), float(beta), float(sigma_v))
+        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        info = SolveInfo()
+        st = lib().wf_solve_response(self._h, ctypes.byref(g), ctypes.byref(pw), ctypes.byref(rs), _ptr(w),
+                                     float(nbar), _ptr(b), ctypes.byref(o), _ptr(s_out), ctypes.byref(info),
+                                     _stream(stream))
+        if check and st != OK:
+            raise WfError(st, "wf_solve_response", info)
         return s_out, info
 
     def solve_batch(self, problems, stream=None):

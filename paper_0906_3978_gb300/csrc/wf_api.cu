@@ -406,6 +406,34 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
   return s;
 }
 
+wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const wf_response* response,
+                            const double* w, double nbar, const double* b, const wf_solve_opts* opts,
+                            double* s_out, wf_solve_info* info, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  if (info) std::memset(info, 0, sizeof(*info));
+  SolveArgs a;
+  wf_status s = prepare_solve(grid, power, w, nbar, b, opts, s_out, a);
+  std::vector<double> ginv;
+  if (s == WF_OK) s = response_tables(*grid, response, a.sinv, ginv);
+  if (s != WF_OK) {
+    if (info) info->status = s;
+    return s;
+  }
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  wf_solve_info tmp{};
+  std::vector<SolveArgs*> sys{&a};
+  wf_solve_info* inf = info ? info : &tmp;
+  std::vector<wf_solve_info*> infos{inf};
+  s = solve_many(*c, sys, infos, (cudaStream_t)stream);
+  // s_m = G^-1 s_g; also on a non-converged exit, so that s_out always holds the matter field
+  const wf_status sd = multiply_fourier(*c, grid->n, s_out, s_out, ginv, (cudaStream_t)stream);
+  if (s == WF_OK) s = sd;
+  inf->status = s;
+  return s;
+}
+
 wf_status wf_project_mask(wf_ctx* ctx, const wf_grid* grid, const double* sky, int n_alpha, int n_delta,
                           double alpha0, double dalpha, double delta0, double ddelta, const double* observer,
                           double dr, int n_r, const double* wr, double* w, int64_t* counts, void* stream) {

@@ -204,6 +204,12 @@ struct SolveArgs {
   double sum_w = -1.0;       // filled by the driver
 };
 wf_status build_sinv_table(const wf_grid& g, const wf_power& pw, std::vector<double>& out);
+// S^-1 -> S^-1 / g^2 in place and ginv[n2] = 1 / g(k) for the response g = bias sqrt(<K D>_mu)
+wf_status response_tables(const wf_grid& g, const wf_response* r, std::vector<double>& sinv,
+                          std::vector<double>& ginv);
+// out = F^-1 diag(table[n2]) F in / n^3 (FP64 transforms; out may equal in)
+wf_status multiply_fourier(Ctx& c, int n, const double* in, double* out, const std::vector<double>& table,
+                           cudaStream_t st);
 // Solve every system (grouped by size and precision, groups interleaved on the device).
 // Returns WF_OK if all converged, else the first failing status; infos[i] filled for each.
 wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_info*>& infos, cudaStream_t st);

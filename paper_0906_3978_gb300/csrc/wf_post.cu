@@ -178,8 +178,8 @@ k_density_moments(const unsigned long long* __restrict__ hist, int n_bins, doubl
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
-static wf_status multiply_run(Ctx& c, int n, const double* in, double* out, const std::vector<double>& table,
-                              cudaStream_t st) {
+wf_status multiply_fourier(Ctx& c, int n, const double* in, double* out, const std::vector<double>& table,
+                           cudaStream_t st) {
   switch (n) {
 #define WF_CASE(N) \
   case N:          \
@@ -199,7 +199,7 @@ wf_status smooth_run(Ctx& c, const wf_grid& g, const double* in, double r_s, dou
   std::vector<double> t(n2_entries(g.n));
   const double kf = 2.0 * 3.14159265358979323846 / g.box;
   for (size_t n2 = 0; n2 < t.size(); ++n2) t[n2] = std::exp(-0.5 * kf * kf * (double)n2 * r_s * r_s);
-  return multiply_run(c, g.n, in, out, t, st);
+  return multiply_fourier(c, g.n, in, out, t, st);
 }
 
 // <K D>_mu of Sec. 3 ("Redshift distortion operator"): the mean over mu in [0, 1] of
@@ -236,7 +236,25 @@ wf_status deconvolve_run(Ctx& c, const wf_grid& g, const double* in, double beta
                                         // a non-positive mean only comes from a non-finite input
     t[n2] = 1.0 / (bias * std::sqrt(f));
   }
-  return multiply_run(c, g.n, in, out, t, st);
+  return multiply_fourier(c, g.n, in, out, t, st);
+}
+
+wf_status response_tables(const wf_grid& g, const wf_response* r, std::vector<double>& sinv,
+                          std::vector<double>& ginv) {
+  if (!r || !(r->bias > 0.0) || !std::isfinite(r->bias) || !std::isfinite(r->beta) || !(r->sigma_v >= 0.0) ||
+      !std::isfinite(r->sigma_v))
+    return WF_ERR_ARG;
+  ginv.assign(n2_entries(g.n), 0.0);
+  if (sinv.size() != ginv.size()) return WF_ERR_ARG;
+  const double kf = 2.0 * 3.14159265358979323846 / g.box;
+  for (size_t n2 = 0; n2 < ginv.size(); ++n2) {
+    const double f = rsd_factor(kf * std::sqrt((double)n2), r->beta, r->sigma_v);
+    if (!(f > 0.0)) return WF_ERR_ARG;
+    const double g2 = r->bias * r->bias * f;  // g(k)^2
+    sinv[n2] /= g2;
+    ginv[n2] = 1.0 / (r->bias * std::sqrt(f));
+  }
+  return WF_OK;
 }
 
 wf_status compare_run(Ctx& c, int64_t n_cells, const double* rec, const double* truth, wf_compare_result* out,

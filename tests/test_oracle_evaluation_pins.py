@@ -270,3 +270,73 @@ def test_mask_uniform_sky_is_the_hit_indicator():
     w, c = oracle.project_mask(sky, 12, 24.0, 0.0, 2 * np.pi / 36, -np.pi / 2, np.pi / 18, (12.0, 12.0, 12.0), 0.5,
                                np.ones(30))
     assert np.array_equal(w > 0, c > 0) and np.all(w[c > 0] == 1.0)
+
+
+# ------------------------------------------------------------------ Z and B inside R (Sec. 3)
+def _response_case(n, seed, box=60.0):
+    rng = np.random.default_rng(seed)
+    k, p = synth.lcdm_table()
+    sinv = oracle.sinv_table(n, box, k, p)
+    w = np.clip(rng.uniform(-0.3, 1.0, (n, n, n)), 0.0, 1.0)   # about a quarter of the cells unobserved
+    b = rng.standard_normal((n, n, n)) * w
+    return box, sinv, w, b
+
+
+def test_response_unit_factor_is_the_plain_filter():
+    """g = 1 (bias 1, beta 0, no damping) leaves the plain system, solved by the C textbook CG."""
+    n = 8
+    box, sinv, w, b = _response_case(n, 5)
+    g = ev.response_table(n, box, 1.0, 0.0, 0.0)
+    assert np.allclose(g, 1.0, rtol=0, atol=1e-14)
+    s, _, rel = ev.solve_response(sinv, g, 0.7, w, b, tol=1e-13)
+    ref = oracle.cg(sinv, 0.7, w, b, tol=1e-13)[0]
+    assert rel <= 1e-13
+    assert np.linalg.norm(s - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_response_uniform_selection_closed_form():
+    """w = 1: every Fourier mode decouples, s_m(k) = g(k) b(k) / (S^-1(k) + nbar g(k)^2)."""
+    n, nbar = 8, 0.4
+    box, sinv, _, _ = _response_case(n, 6)
+    b = np.random.default_rng(7).standard_normal((n, n, n))
+    g = ev.response_table(n, box, 1.3, 0.45, 5.0)
+    n2 = ev.n2_grid(n)
+    s, _, _ = ev.solve_response(sinv, g, nbar, np.ones((n, n, n)), b, tol=1e-14)
+    ref = np.real(np.fft.ifftn(np.fft.fftn(b) * g[n2] / (sinv[n2] + nbar * g[n2] ** 2)))
+    assert np.linalg.norm(s - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_response_matches_a_dense_cosine_sum_operator():
+    """4^3 cells: S^-1 and G written as dense cosine sums over the modes (no FFT),
+    A = S^-1 + G diag(nbar w) G and right-hand side G b solved directly."""
+    n, nbar = 4, 0.9
+    box, sinv, w, b = _response_case(n, 8, box=20.0)
+    g = ev.response_table(n, box, 1.1, 0.6, 3.0)
+    f = np.fft.fftfreq(n, 1.0 / n).astype(int)
+    K = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1).reshape(-1, 3)
+    x = np.arange(n)
+    X = np.stack(np.meshgrid(x, x, x, indexing="ij"), -1).reshape(-1, 3)
+    ph = 2 * np.pi * (X @ K.T) / n
+    C, S = np.cos(ph), np.sin(ph)
+    n2 = np.sum(K * K, axis=1)
+
+    def dense(m):
+        return ((C * m) @ C.T + (S * m) @ S.T) / n ** 3
+
+    G = dense(g[n2])
+    A = dense(sinv[n2]) + G @ np.diag(nbar * w.ravel()) @ G
+    ref = np.linalg.solve(A, G @ b.ravel()).reshape(n, n, n)
+    s, _, _ = ev.solve_response(sinv, g, nbar, w, b, tol=1e-14)
+    assert np.linalg.norm(s - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_response_equals_redshift_prior_then_deconvolution():
+    """s_g = G s_m turns the system into the plain one with prior g^2 P (S^-1 / g^2); deconvolving
+    its solution by 1 / g (Eq. eq:DEC) gives the same s_m."""
+    n, nbar, bias, beta, sv = 8, 0.6, 1.2, 0.5, 5.0
+    box, sinv, w, b = _response_case(n, 9)
+    g = ev.response_table(n, box, bias, beta, sv)
+    s_m, _, _ = ev.solve_response(sinv, g, nbar, w, b, tol=1e-14)
+    s_g = oracle.cg(sinv / g ** 2, nbar, w, b, tol=1e-14)[0]
+    via = ev.deconvolve(s_g, box, beta, sv, bias)
+    assert np.linalg.norm(via - s_m) <= 1e-11 * np.linalg.norm(s_m)
