@@ -179,36 +179,89 @@ wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double
 // and one count.  Every operation explicitly rounded in the order of the definition.
 // ------------------------------------------------------------------------------------------
 struct MaskArgs {
-  int n, n_alpha, n_delta, n_r;
-  double H, ox, oy, oz, dr;
+  int n, n_r, kc;  // kc = ceil(n_r / 32): 32-sample chunks per ray
+  long long npix;
+  double H, inv_h, ox, oy, oz;
 };
 
+// Per sky pixel: the unit direction (cos d cos a, cos d sin a, sin d) and the sky value in Q32
+// (rint(v 2^32), in the 4th word); a value outside [0, 1] sets the error flag.
 __global__ void __launch_bounds__(256)
-k_project_mask(const double* __restrict__ sky, const double* __restrict__ ca, const double* __restrict__ sa,
-               const double* __restrict__ cd, const double* __restrict__ sd, const double* __restrict__ wr,
-               MaskArgs a, unsigned long long* __restrict__ ss, unsigned long long* __restrict__ sr,
-               unsigned long long* __restrict__ cnt, int* __restrict__ err) {
-  const long long tot = (long long)a.n_alpha * a.n_delta * a.n_r;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(e % a.n_r);
-    const long long pix = e / a.n_r;
-    const int i = (int)(pix % a.n_alpha), j = (int)(pix / a.n_alpha);
-    const double v = sky[pix], wk = wr[k];
-    if (!(v >= 0.0 && v <= 1.0) || !(wk >= 0.0 && wk <= 1.0)) {
-      atomicOr(err, 1);
-      continue;
+k_mask_pix(const double* __restrict__ sky, const double* __restrict__ ca, const double* __restrict__ sa,
+           const double* __restrict__ cd, const double* __restrict__ sd, int n_alpha, long long npix,
+           double4* __restrict__ pix, int* __restrict__ err) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p % n_alpha), j = (int)(p / n_alpha);
+    const double v = sky[p];
+    unsigned long long q = 0;
+    if (v >= 0.0 && v <= 1.0) q = __double2ull_rn(__dmul_rn(v, 4294967296.0));
+    else atomicOr(err, 1);
+    pix[p] = make_double4(__dmul_rn(cd[j], ca[i]), __dmul_rn(cd[j], sa[i]), sd[j], __longlong_as_double((long long)q));
+  }
+}
+
+// floor(x / H) with the correctly rounded quotient, as the definition takes it.  q = x (1/H)
+// rounded twice is within 2.1 ulp of x / H and the rounded quotient within 0.5 ulp, so when q is
+// further than 8 ulp from every integer both have the same floor; otherwise (and for tiny |q|)
+// the exact division decides.
+WF_D double floor_div(double x, double H, double inv_h) {
+  const double q = __dmul_rn(x, inv_h);
+  const double f = floor(q);
+  const double m = __dmul_rn(fabs(q), 0x1p-50);
+  if (fabs(q) >= 0x1p-900 && __dsub_rn(q, f) > m && __dsub_rn(__dadd_rn(f, 1.0), q) > m) return f;
+  return floor(__ddiv_rn(x, H));
+}
+
+// One warp per (pixel, 32 consecutive radial samples): a ray never re-enters a cell it left, so
+// equal cells form runs of neighbouring lanes; the last lane of a run adds the run's sums (Q32
+// sky value x run length, Q32 radial values, count) with one atomic each.
+__global__ void __launch_bounds__(256)
+k_project_mask(const double4* __restrict__ pix, const double* __restrict__ rk,
+               const unsigned long long* __restrict__ qr, MaskArgs a, unsigned long long* __restrict__ ss,
+               unsigned long long* __restrict__ sr, unsigned long long* __restrict__ cnt) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long ntask = a.npix * a.kc;
+  const double nn = (double)a.n;
+  for (long long t = warp; t < ntask; t += nwarp) {  // warp-uniform loop
+    const long long p = t / a.kc;
+    const int k = (int)(t - p * a.kc) * 32 + lane;
+    const double4 u = pix[p];
+    bool valid = k < a.n_r;
+    unsigned long long key = ~0ull, qv = 0;
+    if (valid) {
+      const double r = rk[k];
+      const double fx = floor_div(__dadd_rn(a.ox, __dmul_rn(r, u.x)), a.H, a.inv_h);
+      const double fy = floor_div(__dadd_rn(a.oy, __dmul_rn(r, u.y)), a.H, a.inv_h);
+      const double fz = floor_div(__dadd_rn(a.oz, __dmul_rn(r, u.z)), a.H, a.inv_h);
+      valid = fx >= 0.0 && fx < nn && fy >= 0.0 && fy < nn && fz >= 0.0 && fz < nn;
+      if (valid) {
+        key = ((unsigned long long)fx * a.n + (unsigned long long)fy) * a.n + (unsigned long long)fz;
+        qv = qr[k];
+      }
     }
-    const double r = __dmul_rn((double)k + 0.5, a.dr);
-    const double ux = __dmul_rn(cd[j], ca[i]), uy = __dmul_rn(cd[j], sa[i]), uz = sd[j];
-    const double fx = floor(__ddiv_rn(__dadd_rn(a.ox, __dmul_rn(r, ux)), a.H));
-    const double fy = floor(__ddiv_rn(__dadd_rn(a.oy, __dmul_rn(r, uy)), a.H));
-    const double fz = floor(__ddiv_rn(__dadd_rn(a.oz, __dmul_rn(r, uz)), a.H));
-    const double nn = (double)a.n;
-    if (!(fx >= 0.0 && fx < nn && fy >= 0.0 && fy < nn && fz >= 0.0 && fz < nn)) continue;
-    const size_t c = ((size_t)fx * a.n + (size_t)fy) * a.n + (size_t)fz;
-    atomicAdd(ss + c, __double2ull_rn(__dmul_rn(v, 4294967296.0)));
-    atomicAdd(sr + c, __double2ull_rn(__dmul_rn(wk, 4294967296.0)));
-    atomicAdd(cnt + c, 1ull);
+    // runs of equal keys: heads, the run start of each lane, and the tails
+    const unsigned long long prev = __shfl_up_sync(FULL, key, 1);
+    const unsigned heads = __ballot_sync(FULL, lane == 0 || prev != key);
+    const int start = 31 - __clz(heads & (FULL >> (31 - lane)));
+    const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    // inclusive prefix sum of the radial values across the warp
+    unsigned long long pre = qv;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long o = __shfl_up_sync(FULL, pre, d);
+      if (lane >= d) pre += o;
+    }
+    const unsigned long long before = __shfl_sync(FULL, pre, start > 0 ? start - 1 : 0);
+    if (valid && tail) {
+      const unsigned long long len = (unsigned long long)(lane - start + 1);
+      const unsigned long long qs = (unsigned long long)__double_as_longlong(u.w);
+      atomicAdd(ss + key, qs * len);
+      atomicAdd(sr + key, start > 0 ? pre - before : pre);
+      atomicAdd(cnt + key, len);
+    }
   }
 }
 
@@ -235,13 +288,17 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
                            double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
                            const double* wr, double* w, int64_t* counts, cudaStream_t st) {
   if (!sky || !obs || !wr || !w || n_alpha <= 0 || n_delta <= 0 || n_r <= 0 || !(dr > 0.0) || !std::isfinite(dr) ||
-      !std::isfinite(alpha0) || !std::isfinite(dalpha) || !std::isfinite(delta0) || !std::isfinite(ddelta))
+      !std::isfinite(alpha0) || !std::isfinite(dalpha) || !std::isfinite(delta0) || !std::isfinite(ddelta) ||
+      !std::isfinite(obs[0]) || !std::isfinite(obs[1]) || !std::isfinite(obs[2]))
     return WF_ERR_ARG;
   for (int k = 0; k < n_r; ++k)
     if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return WF_ERR_ARG;
-  // pixel-centre cosines and sines, as the definition takes them (libm on the host)
-  std::vector<double> h((size_t)2 * n_alpha + 2 * n_delta + n_r);
-  double *ca = h.data(), *sa = ca + n_alpha, *cd = sa + n_alpha, *sd = cd + n_delta, *wrh = sd + n_delta;
+  // pixel-centre cosines and sines (libm on the host, as the definition takes them), the sample
+  // radii (k + 1/2) dr and the radial values in Q32
+  const size_t nd = (size_t)2 * n_alpha + 2 * n_delta + n_r;
+  std::vector<double> h(nd + n_r);
+  double *ca = h.data(), *sa = ca + n_alpha, *cd = sa + n_alpha, *sd = cd + n_delta, *rk = sd + n_delta;
+  unsigned long long* qr = reinterpret_cast<unsigned long long*>(rk + n_r);
   for (int i = 0; i < n_alpha; ++i) {
     const double al = alpha0 + ((double)i + 0.5) * dalpha;
     ca[i] = std::cos(al);
@@ -252,26 +309,36 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
     cd[j] = std::cos(de);
     sd[j] = std::sin(de);
   }
-  for (int k = 0; k < n_r; ++k) wrh[k] = wr[k];
+  for (int k = 0; k < n_r; ++k) {
+    rk[k] = ((double)k + 0.5) * dr;
+    qr[k] = (unsigned long long)std::nearbyint(wr[k] * 4294967296.0);
+  }
   const size_t V = (size_t)g.n * g.n * g.n;
+  const long long npix = (long long)n_alpha * n_delta;
   double* dtab;
+  double4* pix;
   unsigned long long* acc;
   int* err;
   WF_TRY(c.get("mask_tab", h.size() * sizeof(double), (void**)&dtab));
+  WF_TRY(c.get("mask_pix", (size_t)npix * sizeof(double4), (void**)&pix));
   WF_TRY(c.get("mask_acc", 3 * V * sizeof(unsigned long long), (void**)&acc));
   WF_TRY(c.get("mask_err", 64, (void**)&err));
   WF_CUDA(cudaMemcpyAsync(dtab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   WF_CUDA(cudaMemsetAsync(acc, 0, 3 * V * sizeof(unsigned long long), st));
   WF_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
-  MaskArgs a{g.n, n_alpha, n_delta, n_r, g.box / (double)g.n, obs[0], obs[1], obs[2], dr};
   const double* dca = dtab;
   const double* dsa = dca + n_alpha;
   const double* dcd = dsa + n_alpha;
   const double* dsd = dcd + n_delta;
-  const double* dwr = dsd + n_delta;
-  const double samples = (double)n_alpha * n_delta * n_r;
-  c.launch("project_mask", 24.0 * samples, st, [&] {
-    k_project_mask<<<152 * 16, 256, 0, st>>>(sky, dca, dsa, dcd, dsd, dwr, a, acc, acc + V, acc + 2 * V, err);
+  const double* drk = dsd + n_delta;
+  const unsigned long long* dqr = reinterpret_cast<const unsigned long long*>(drk + n_r);
+  const unsigned pgrid = (unsigned)std::min<long long>((npix + 255) / 256, 152 * 8);
+  c.launch("mask_pix", 48.0 * (double)npix, st,
+           [&] { k_mask_pix<<<pgrid, 256, 0, st>>>(sky, dca, dsa, dcd, dsd, n_alpha, npix, pix, err); });
+  MaskArgs a{g.n, n_r, (n_r + 31) / 32, npix, g.box / (double)g.n, (double)g.n / g.box, obs[0], obs[1], obs[2]};
+  const double samples = (double)npix * n_r;
+  c.launch("project_mask", 16.0 * samples, st, [&] {
+    k_project_mask<<<152 * 16, 256, 0, st>>>(pix, drk, dqr, a, acc, acc + V, acc + 2 * V);
   });
   c.launch("mask_finish", 32.0 * (double)V, st, [&] {
     k_mask_finish<<<152 * 4, 256, 0, st>>>(acc, acc + V, acc + 2 * V, V, w, reinterpret_cast<long long*>(counts));

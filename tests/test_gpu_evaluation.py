@@ -277,7 +277,8 @@ def _sky_case(seed, n_alpha, n_delta):
     return sky
 
 
-@pytest.mark.parametrize("n,box,n_alpha,n_delta,n_r", [(16, 40.0, 90, 45, 120), (48, 100.0, 180, 90, 300)])
+@pytest.mark.parametrize("n,box,n_alpha,n_delta,n_r", [(16, 40.0, 90, 45, 120), (48, 100.0, 180, 90, 300),
+                                                       (128, 250.0, 360, 180, 937)])
 def test_mask_projection_bit_exact(ctx, n, box, n_alpha, n_delta, n_r):
     """The same host cosines and sines, explicitly rounded sample positions and Q32 sums on both
     sides: the mask and the counts bit for bit."""
