@@ -429,9 +429,11 @@ int oracle_window(int n, double box, const double* obs, const double* axis, doub
 
 /* Projection of a sky completeness map onto the grid (Sec. 2.3): sky pixel (i, j) of an
  * equidistant alpha x delta map has centre alpha_i = alpha0 + (i + 1/2) dalpha, delta_j =
- * delta0 + (j + 1/2) ddelta; its ray from the observer is sampled at r_k = (k + 1/2) dr,
- * k < n_r, at x = o + r_k (cos delta cos alpha, cos delta sin alpha, sin delta) (Eq. eq:transf);
- * each sample inside the box goes to its nearest-grid-point cell floor(x / H).  Per cell the sky
+ * delta0 + (j + 1/2) ddelta; its ray from the observer is sampled at r_k = (k + 1/2) dr, k < n_r,
+ * at x = o + r_k u with u = (cos delta cos alpha, cos delta sin alpha, sin delta) (Eq. eq:transf);
+ * each sample inside the box goes to its nearest-grid-point cell floor(x / H).  The cell is
+ * decided in FP32 in cell units: O = fl32(o / H), g = fl32(u dr / H) (FP64 products, one
+ * rounding), X = fl32(O + fl32((k + 1/2) g)), cell floor(X) if 0 <= X < n.  Per cell the sky
  * values and the radial completeness values wr[k] of the samples are summed in Q32 fixed point
  * (rint(v 2^32), exact and order-independent) and counted; the mask is
  * (S_sky 2^-32 / count) * (S_r 2^-32 / count), 0 where no sample fell.  sky[j * n_alpha + i],
@@ -454,20 +456,20 @@ int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n
     free(cnt);
     return OR_ERR_OOM;
   }
-  const double H = box / (double)n, q32 = 4294967296.0;
+  const double H = box / (double)n, q32 = 4294967296.0, step = dr / H;
+  const float ox = (float)(obs[0] / H), oy = (float)(obs[1] / H), oz = (float)(obs[2] / H), nf = (float)n;
   for (int j = 0; j < n_delta; ++j) {
     const double de = delta0 + ((double)j + 0.5) * ddelta;
     const double cd = cos(de), sd = sin(de);
     for (int i = 0; i < n_alpha; ++i) {
       const double v = sky[(size_t)j * n_alpha + i];
       const double al = alpha0 + ((double)i + 0.5) * dalpha;
-      const double ux = cd * cos(al), uy = cd * sin(al), uz = sd;
+      const float gx = (float)(cd * cos(al) * step), gy = (float)(cd * sin(al) * step), gz = (float)(sd * step);
       const uint64_t qs = (uint64_t)rint(v * q32);
       for (int k = 0; k < n_r; ++k) {
-        const double r = ((double)k + 0.5) * dr;
-        const double fx = floor((obs[0] + r * ux) / H), fy = floor((obs[1] + r * uy) / H),
-                     fz = floor((obs[2] + r * uz) / H);
-        if (!(fx >= 0.0 && fx < n && fy >= 0.0 && fy < n && fz >= 0.0 && fz < n)) continue;
+        const float t = (float)k + 0.5f;
+        const float fx = floorf(ox + t * gx), fy = floorf(oy + t * gy), fz = floorf(oz + t * gz);
+        if (!(fx >= 0.0f && fx < nf && fy >= 0.0f && fy < nf && fz >= 0.0f && fz < nf)) continue;
         const size_t c = ((size_t)fx * n + (size_t)fy) * n + (size_t)fz;
         ss[c] += qs;
         sr[c] += (uint64_t)rint(wr[k] * q32);

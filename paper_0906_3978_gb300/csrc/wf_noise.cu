@@ -181,42 +181,35 @@ wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double
 struct MaskArgs {
   int n, n_r, kc;  // kc = ceil(n_r / 32): 32-sample chunks per ray
   long long npix;
-  double H, inv_h, ox, oy, oz;
+  double step;     // dr / H
+  float ox, oy, oz;  // observer in cell units, fl32(o / H)
 };
 
-// Per sky pixel: the unit direction (cos d cos a, cos d sin a, sin d) and the sky value in Q32
-// (rint(v 2^32), in the 4th word); a value outside [0, 1] sets the error flag.
+// Per sky pixel: the ray step in cell units g = fl32(u dr / H), u = (cos d cos a, cos d sin a,
+// sin d), and the sky value in Q32 (rint(v 2^32)); a value outside [0, 1] sets the error flag.
 __global__ void __launch_bounds__(256)
 k_mask_pix(const double* __restrict__ sky, const double* __restrict__ ca, const double* __restrict__ sa,
-           const double* __restrict__ cd, const double* __restrict__ sd, int n_alpha, long long npix,
-           double4* __restrict__ pix, int* __restrict__ err) {
+           const double* __restrict__ cd, const double* __restrict__ sd, int n_alpha, long long npix, double step,
+           float4* __restrict__ pix, unsigned long long* __restrict__ qsky, int* __restrict__ err) {
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix; p += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(p % n_alpha), j = (int)(p / n_alpha);
     const double v = sky[p];
     unsigned long long q = 0;
     if (v >= 0.0 && v <= 1.0) q = __double2ull_rn(__dmul_rn(v, 4294967296.0));
     else atomicOr(err, 1);
-    pix[p] = make_double4(__dmul_rn(cd[j], ca[i]), __dmul_rn(cd[j], sa[i]), sd[j], __longlong_as_double((long long)q));
+    qsky[p] = q;
+    pix[p] = make_float4(__double2float_rn(__dmul_rn(__dmul_rn(cd[j], ca[i]), step)),
+                         __double2float_rn(__dmul_rn(__dmul_rn(cd[j], sa[i]), step)),
+                         __double2float_rn(__dmul_rn(sd[j], step)), 0.0f);
   }
 }
 
-// floor(x / H) with the correctly rounded quotient, as the definition takes it.  q = x (1/H)
-// rounded twice is within 2.1 ulp of x / H and the rounded quotient within 0.5 ulp, so when q is
-// further than 8 ulp from every integer both have the same floor; otherwise (and for tiny |q|)
-// the exact division decides.
-WF_D double floor_div(double x, double H, double inv_h) {
-  const double q = __dmul_rn(x, inv_h);
-  const double f = floor(q);
-  const double m = __dmul_rn(fabs(q), 0x1p-50);
-  if (fabs(q) >= 0x1p-900 && __dsub_rn(q, f) > m && __dsub_rn(__dadd_rn(f, 1.0), q) > m) return f;
-  return floor(__ddiv_rn(x, H));
-}
-
-// One warp per (pixel, 32 consecutive radial samples): a ray never re-enters a cell it left, so
-// equal cells form runs of neighbouring lanes; the last lane of a run adds the run's sums (Q32
-// sky value x run length, Q32 radial values, count) with one atomic each.
+// One warp per (pixel, 32 consecutive radial samples).  The cell of sample k is decided in FP32 in
+// cell units, X = O + (k + 1/2) g, each operation rounded once.  A ray never re-enters a cell it
+// left, so equal cells form runs of neighbouring lanes; the last lane of a run adds the run's sums
+// (Q32 sky value x run length, Q32 radial values, count) with one atomic each.
 __global__ void __launch_bounds__(256)
-k_project_mask(const double4* __restrict__ pix, const double* __restrict__ rk,
+k_project_mask(const float4* __restrict__ pix, const unsigned long long* __restrict__ qsky,
                const unsigned long long* __restrict__ qr, MaskArgs a, unsigned long long* __restrict__ ss,
                unsigned long long* __restrict__ sr, unsigned long long* __restrict__ cnt) {
   const unsigned FULL = 0xffffffffu;
@@ -224,21 +217,21 @@ k_project_mask(const double4* __restrict__ pix, const double* __restrict__ rk,
   const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarp = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long ntask = a.npix * a.kc;
-  const double nn = (double)a.n;
+  const float nf = (float)a.n;
   for (long long t = warp; t < ntask; t += nwarp) {  // warp-uniform loop
     const long long p = t / a.kc;
     const int k = (int)(t - p * a.kc) * 32 + lane;
-    const double4 u = pix[p];
+    const float4 g = pix[p];
     bool valid = k < a.n_r;
     unsigned long long key = ~0ull, qv = 0;
     if (valid) {
-      const double r = rk[k];
-      const double fx = floor_div(__dadd_rn(a.ox, __dmul_rn(r, u.x)), a.H, a.inv_h);
-      const double fy = floor_div(__dadd_rn(a.oy, __dmul_rn(r, u.y)), a.H, a.inv_h);
-      const double fz = floor_div(__dadd_rn(a.oz, __dmul_rn(r, u.z)), a.H, a.inv_h);
-      valid = fx >= 0.0 && fx < nn && fy >= 0.0 && fy < nn && fz >= 0.0 && fz < nn;
+      const float tk = __fadd_rn((float)k, 0.5f);
+      const float fx = floorf(__fadd_rn(a.ox, __fmul_rn(tk, g.x)));
+      const float fy = floorf(__fadd_rn(a.oy, __fmul_rn(tk, g.y)));
+      const float fz = floorf(__fadd_rn(a.oz, __fmul_rn(tk, g.z)));
+      valid = fx >= 0.0f && fx < nf && fy >= 0.0f && fy < nf && fz >= 0.0f && fz < nf;
       if (valid) {
-        key = ((unsigned long long)fx * a.n + (unsigned long long)fy) * a.n + (unsigned long long)fz;
+        key = ((unsigned long long)(unsigned)fx * a.n + (unsigned)fy) * a.n + (unsigned)fz;
         qv = qr[k];
       }
     }
@@ -257,8 +250,7 @@ k_project_mask(const double4* __restrict__ pix, const double* __restrict__ rk,
     const unsigned long long before = __shfl_sync(FULL, pre, start > 0 ? start - 1 : 0);
     if (valid && tail) {
       const unsigned long long len = (unsigned long long)(lane - start + 1);
-      const unsigned long long qs = (unsigned long long)__double_as_longlong(u.w);
-      atomicAdd(ss + key, qs * len);
+      atomicAdd(ss + key, qsky[p] * len);
       atomicAdd(sr + key, start > 0 ? pre - before : pre);
       atomicAdd(cnt + key, len);
     }
@@ -293,12 +285,12 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
     return WF_ERR_ARG;
   for (int k = 0; k < n_r; ++k)
     if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return WF_ERR_ARG;
-  // pixel-centre cosines and sines (libm on the host, as the definition takes them), the sample
-  // radii (k + 1/2) dr and the radial values in Q32
-  const size_t nd = (size_t)2 * n_alpha + 2 * n_delta + n_r;
+  // pixel-centre cosines and sines (libm on the host, as the definition takes them) and the radial
+  // values in Q32
+  const size_t nd = (size_t)2 * n_alpha + 2 * n_delta;
   std::vector<double> h(nd + n_r);
-  double *ca = h.data(), *sa = ca + n_alpha, *cd = sa + n_alpha, *sd = cd + n_delta, *rk = sd + n_delta;
-  unsigned long long* qr = reinterpret_cast<unsigned long long*>(rk + n_r);
+  double *ca = h.data(), *sa = ca + n_alpha, *cd = sa + n_alpha, *sd = cd + n_delta;
+  unsigned long long* qr = reinterpret_cast<unsigned long long*>(sd + n_delta);
   for (int i = 0; i < n_alpha; ++i) {
     const double al = alpha0 + ((double)i + 0.5) * dalpha;
     ca[i] = std::cos(al);
@@ -309,18 +301,17 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
     cd[j] = std::cos(de);
     sd[j] = std::sin(de);
   }
-  for (int k = 0; k < n_r; ++k) {
-    rk[k] = ((double)k + 0.5) * dr;
-    qr[k] = (unsigned long long)std::nearbyint(wr[k] * 4294967296.0);
-  }
+  for (int k = 0; k < n_r; ++k) qr[k] = (unsigned long long)std::nearbyint(wr[k] * 4294967296.0);
   const size_t V = (size_t)g.n * g.n * g.n;
   const long long npix = (long long)n_alpha * n_delta;
+  const double H = g.box / (double)g.n;
   double* dtab;
-  double4* pix;
-  unsigned long long* acc;
+  float4* pix;
+  unsigned long long *qsky, *acc;
   int* err;
   WF_TRY(c.get("mask_tab", h.size() * sizeof(double), (void**)&dtab));
-  WF_TRY(c.get("mask_pix", (size_t)npix * sizeof(double4), (void**)&pix));
+  WF_TRY(c.get("mask_pix", (size_t)npix * sizeof(float4), (void**)&pix));
+  WF_TRY(c.get("mask_qsky", (size_t)npix * sizeof(unsigned long long), (void**)&qsky));
   WF_TRY(c.get("mask_acc", 3 * V * sizeof(unsigned long long), (void**)&acc));
   WF_TRY(c.get("mask_err", 64, (void**)&err));
   WF_CUDA(cudaMemcpyAsync(dtab, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -330,15 +321,15 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
   const double* dsa = dca + n_alpha;
   const double* dcd = dsa + n_alpha;
   const double* dsd = dcd + n_delta;
-  const double* drk = dsd + n_delta;
-  const unsigned long long* dqr = reinterpret_cast<const unsigned long long*>(drk + n_r);
+  const unsigned long long* dqr = reinterpret_cast<const unsigned long long*>(dsd + n_delta);
+  const double step = dr / H;
   const unsigned pgrid = (unsigned)std::min<long long>((npix + 255) / 256, 152 * 8);
-  c.launch("mask_pix", 48.0 * (double)npix, st,
-           [&] { k_mask_pix<<<pgrid, 256, 0, st>>>(sky, dca, dsa, dcd, dsd, n_alpha, npix, pix, err); });
-  MaskArgs a{g.n, n_r, (n_r + 31) / 32, npix, g.box / (double)g.n, (double)g.n / g.box, obs[0], obs[1], obs[2]};
+  c.launch("mask_pix", 56.0 * (double)npix, st,
+           [&] { k_mask_pix<<<pgrid, 256, 0, st>>>(sky, dca, dsa, dcd, dsd, n_alpha, npix, step, pix, qsky, err); });
+  MaskArgs a{g.n, n_r, (n_r + 31) / 32, npix, step, (float)(obs[0] / H), (float)(obs[1] / H), (float)(obs[2] / H)};
   const double samples = (double)npix * n_r;
-  c.launch("project_mask", 16.0 * samples, st, [&] {
-    k_project_mask<<<152 * 16, 256, 0, st>>>(pix, drk, dqr, a, acc, acc + V, acc + 2 * V);
+  c.launch("project_mask", 8.0 * samples, st, [&] {
+    k_project_mask<<<152 * 16, 256, 0, st>>>(pix, qsky, dqr, a, acc, acc + V, acc + 2 * V);
   });
   c.launch("mask_finish", 32.0 * (double)V, st, [&] {
     k_mask_finish<<<152 * 4, 256, 0, st>>>(acc, acc + V, acc + 2 * V, V, w, reinterpret_cast<long long*>(counts));
