@@ -436,7 +436,7 @@ int oracle_window(int n, double box, const double* obs, const double* axis, doub
  * rounding), X = fl32(O + fl32((k + 1/2) g)), cell floor(X) if 0 <= X < n.  Per cell the sky
  * values and the radial completeness values wr[k] of the samples are summed in Q32 fixed point
  * (rint(v 2^32), exact and order-independent) and counted; the mask is
- * (S_sky 2^-32 / count) * (S_r 2^-32 / count), 0 where no sample fell.  sky[j * n_alpha + i],
+ * (S_sky 2^-32 rc) * (S_r 2^-32 rc) with rc = fl(1 / count), 0 where no sample fell.  sky[j * n_alpha + i],
  * values in [0, 1]; counts may be NULL. */
 int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n_delta, double alpha0,
                         double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
@@ -478,7 +478,8 @@ int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n
     }
   }
   for (size_t c = 0; c < V; ++c) {
-    w[c] = cnt[c] ? ((double)ss[c] / q32 / (double)cnt[c]) * ((double)sr[c] / q32 / (double)cnt[c]) : 0.0;
+    const double rc = cnt[c] ? 1.0 / (double)cnt[c] : 0.0;
+    w[c] = cnt[c] ? ((double)ss[c] / q32 * rc) * ((double)sr[c] / q32 * rc) : 0.0;
     if (counts) counts[c] = cnt[c];
   }
   free(ss);

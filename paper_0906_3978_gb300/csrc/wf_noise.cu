@@ -47,8 +47,9 @@ WF_D double sel_value(const SelParams& s, const double4* __restrict__ holes, dou
         const double t = __ddiv_rn(r, s.p0);
         val = exp(-__dmul_rn(t, t));
       } else {
+        // t^p1 exp(p1 (1 - t)) as one exponential, exp(p1 (log t + 1 - t))
         const double t = __ddiv_rn(r, s.p0);
-        val = __dmul_rn(pow(t, s.p1), exp(__dmul_rn(s.p1, __dsub_rn(1.0, t))));
+        val = exp(__dmul_rn(s.p1, __dadd_rn(log(t), __dsub_rn(1.0, t))));
       }
     }
   }
@@ -257,19 +258,20 @@ k_project_mask(const float4* __restrict__ pix, const unsigned long long* __restr
   }
 }
 
-// w = (S_sky 2^-32 / count) (S_r 2^-32 / count), 0 where no sample fell
+// w = (S_sky 2^-32 rc) (S_r 2^-32 rc) with rc = fl(1 / count), 0 where no sample fell; rc from
+// the host table rtab for count < kMaskRcp, else the correctly rounded reciprocal
+constexpr int kMaskRcp = 4096;
 __global__ void __launch_bounds__(256)
 k_mask_finish(const unsigned long long* __restrict__ ss, const unsigned long long* __restrict__ sr,
-              const unsigned long long* __restrict__ cnt, size_t V, double* __restrict__ w,
-              long long* __restrict__ counts) {
-  const double q32 = 4294967296.0;
+              const unsigned long long* __restrict__ cnt, const double* __restrict__ rtab, size_t V,
+              double* __restrict__ w, long long* __restrict__ counts) {
   for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < V; c += (size_t)gridDim.x * blockDim.x) {
     const unsigned long long nc = cnt[c];
     double v = 0.0;
     if (nc) {
-      const double cn = __ull2double_rn(nc);
-      v = __dmul_rn(__ddiv_rn(__ddiv_rn(__ull2double_rn(ss[c]), q32), cn),
-                    __ddiv_rn(__ddiv_rn(__ull2double_rn(sr[c]), q32), cn));
+      const double rc = nc < (unsigned long long)kMaskRcp ? rtab[nc] : __drcp_rn(__ull2double_rn(nc));
+      v = __dmul_rn(__dmul_rn(__dmul_rn(__ull2double_rn(ss[c]), 0x1p-32), rc),
+                    __dmul_rn(__dmul_rn(__ull2double_rn(sr[c]), 0x1p-32), rc));
     }
     w[c] = v;
     if (counts) counts[c] = (long long)nc;
@@ -288,7 +290,7 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
   // pixel-centre cosines and sines (libm on the host, as the definition takes them) and the radial
   // values in Q32
   const size_t nd = (size_t)2 * n_alpha + 2 * n_delta;
-  std::vector<double> h(nd + n_r);
+  std::vector<double> h(nd + n_r + kMaskRcp);
   double *ca = h.data(), *sa = ca + n_alpha, *cd = sa + n_alpha, *sd = cd + n_delta;
   unsigned long long* qr = reinterpret_cast<unsigned long long*>(sd + n_delta);
   for (int i = 0; i < n_alpha; ++i) {
@@ -302,6 +304,9 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
     sd[j] = std::sin(de);
   }
   for (int k = 0; k < n_r; ++k) qr[k] = (unsigned long long)std::nearbyint(wr[k] * 4294967296.0);
+  double* rtab = h.data() + nd + n_r;
+  rtab[0] = 0.0;
+  for (int m = 1; m < kMaskRcp; ++m) rtab[m] = 1.0 / (double)m;
   const size_t V = (size_t)g.n * g.n * g.n;
   const long long npix = (long long)n_alpha * n_delta;
   const double H = g.box / (double)g.n;
@@ -322,6 +327,7 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
   const double* dcd = dsa + n_alpha;
   const double* dsd = dcd + n_delta;
   const unsigned long long* dqr = reinterpret_cast<const unsigned long long*>(dsd + n_delta);
+  const double* drtab = dtab + nd + n_r;
   const double step = dr / H;
   const unsigned pgrid = (unsigned)std::min<long long>((npix + 255) / 256, 152 * 8);
   c.launch("mask_pix", 56.0 * (double)npix, st,
@@ -332,7 +338,8 @@ wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_al
     k_project_mask<<<152 * 16, 256, 0, st>>>(pix, qsky, dqr, a, acc, acc + V, acc + 2 * V);
   });
   c.launch("mask_finish", 32.0 * (double)V, st, [&] {
-    k_mask_finish<<<152 * 4, 256, 0, st>>>(acc, acc + V, acc + 2 * V, V, w, reinterpret_cast<long long*>(counts));
+    k_mask_finish<<<152 * 4, 256, 0, st>>>(acc, acc + V, acc + 2 * V, drtab, V, w,
+                                           reinterpret_cast<long long*>(counts));
   });
   WF_CUDA(cudaGetLastError());
   int* hp = reinterpret_cast<int*>(c.host_pinned);
