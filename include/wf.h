@@ -143,10 +143,12 @@ wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
  * map has its centre at alpha_i = alpha0 + (i + 1/2) dalpha, delta_j = delta0 + (j + 1/2) ddelta
  * (radians); its ray is sampled at r_k = (k + 1/2) dr, k < n_r, at the point
  * o + r_k (cos delta cos alpha, cos delta sin alpha, sin delta).  Each sample inside the box
- * [0, box)^3 goes to its nearest-grid-point cell floor(x / H).  Per cell, the sky values and
- * the radial values wr[k] of its samples are averaged; the mask is the product of the two
- * averages (w <= 1), and 0 in cells no sample reached.  The sums are Q32 fixed point with integer
- * atomics, so the result is exact and independent of the order of the samples.
+ * [0, box)^3 goes to its nearest-grid-point cell floor(x / H), decided in FP32 in cell units:
+ * X = fl32(O + fl32((k + 1/2) g)) with O = fl32(o / H) and g = fl32(u dr / H).  Per cell, the sky
+ * values and the radial values wr[k] of its samples are averaged; the mask is the product of the
+ * two averages (w <= 1), and 0 in cells no sample reached.  The sums are Q32 fixed point with
+ * integer atomics, so the result is exact and independent of the order of the samples; each
+ * average is the sum times 2^-32 times fl(1 / count).
  *   sky       dev double [n_delta][n_alpha], values in [0, 1]
  *   observer  host double[3] (box units); wr host double [n_r], values in [0, 1]
  *   w         dev double [n^3];  counts dev int64 [n^3] (samples per cell) or NULL

@@ -332,3 +332,18 @@ def test_solve_response_unit_factor_and_errors(ctx):
         with pytest.raises(wf.WfError) as e:
             ctx.solve_response(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, *bad)
         assert e.value.status == wf.ERR_ARG
+
+
+def test_mask_projection_degenerate_geometry(ctx):
+    """Rays that never enter the box leave an all-zero mask and no counts; a single radial sample
+    and a one-pixel sky still project (bit for bit against the oracle)."""
+    sky = np.full((3, 5), 0.5)
+    geo = (0.0, 2 * np.pi / 5, -np.pi / 2, np.pi / 3)
+    w, cnt = ctx.project_mask(gpu(sky), 16, 16.0, *geo, (-100.0, 8.0, 8.0), 0.5, np.ones(20), want_counts=True)
+    assert not host(w).any() and not host(cnt).any()
+    for sky1, n_r, dr in [(np.array([[0.25]]), 1, 0.37), (np.array([[1.0]]), 64, 0.1)]:
+        args = (16, 16.0, 0.3, 0.1, 0.2, 0.1, (8.1, 7.9, 8.2), dr, np.linspace(0.0, 1.0, n_r))
+        w, cnt = ctx.project_mask(gpu(sky1), *args, want_counts=True)
+        w_ref, c_ref = oracle.project_mask(sky1, *args)
+        assert np.array_equal(host(cnt), c_ref) and np.array_equal(host(w), w_ref)
+        assert c_ref.sum() == n_r
