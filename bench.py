@@ -151,11 +151,27 @@ def oracle_sample(pr, iters, deadline_s=40.0):
     oracle.matvec(tab, 0.05, w, p)
     t_mv = time.perf_counter() - t0
     t_solve = t_assign + t_window + (iters + 5) * t_mv
+    # one thread: a 256^3 matvec, scaled to 512^3 by V log V (x 9)
+    nt = oracle.threads()
+    n1 = pr.n // 2
+    tab1 = oracle.sinv_table(n1, pr.box, pr.pk_k, pr.pk_p)
+    w1 = np.ones((n1, n1, n1))
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.matvec(tab1, 0.05, w1, w1)
+        t_mv1 = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(nt)
+    scale = 8.0 * math.log2(pr.n ** 3) / math.log2(n1 ** 3)
+    single = {"matvec_s_at_half_n": t_mv1, "matvec_s_extrapolated": t_mv1 * scale,
+              "threads_speedup_on_matvec": t_mv1 * scale / t_mv,
+              "note": "1 OpenMP thread, one %d^3 matvec scaled by V log V to %d^3" % (n1, pr.n)}
     sample = ("oracle (plain C, FP64, %d OpenMP threads) at %d^3: assignment of all %d galaxies onto the 2x fine "
               "grid (%.2f s), window (%.2f s), one CG matvec (%.2f s); solve = assignment + window + (%d CG "
               "iterations as the GPU FP64 solve needed + 5 for the low-pass) x matvec"
               % (oracle.threads(), pr.n, pr.n_gal, t_assign, t_window, t_mv, iters))
-    return 1.0 / t_solve, oracle.threads(), sample, t_solve
+    return 1.0 / t_solve, oracle.threads(), sample, t_solve, single
 
 
 def reference_arm(args):
@@ -169,7 +185,7 @@ def reference_arm(args):
     iters = REF_ITERS.get(args.workload, 200)
     vals = []
     for i in range(args.warmup + args.steps):
-        v, cores, sample, t = oracle_sample(pr, iters)
+        v, cores, sample, t, _ = oracle_sample(pr, iters)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
@@ -186,7 +202,24 @@ def reference_arm(args):
 
 # GPU FP64-solve iteration counts on each workload (from the GPU arm), used by the reference
 # arm to scale its per-iteration time to a solve.
-REF_ITERS = {"c3": 200, "c2": 150, "c1": 60}
+REF_ITERS = {"c3": 294, "c2": 150, "c1": 60}
+
+
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo, else lscpu), or the machine type."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
 
 
 # ------------------------------------------------------------------------------------------
@@ -286,7 +319,7 @@ def gpu_arm(args):
     tr = NCU_TRAFFIC.get((dom["name"], n))
     traffic = tr["bytes"] if tr and tr.get("src") == kernel_src_hash() else None
     it_fp64 = infos_fp64[-1]["iters"]
-    cpu_v, cores, sample, _ = oracle_sample(pr, it_fp64)
+    cpu_v, cores, sample, _, single = oracle_sample(pr, it_fp64)
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": k, "warmup": args.warmup,
         "ms_per_step": ms_mixed / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -307,7 +340,8 @@ def gpu_arm(args):
                      "avg_launch_ms": dom["ms"] / dom["launches"]},
         "kernels": [{k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in c.items()}
                     for c in sorted(prof["classes"], key=lambda c: -c["ms"])[:10]],
-        "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu": cpu_model(), "single_thread": single},
         "e2e": {"value": ws * k / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(pr.pos.nbytes),
                 "d2h_bytes_per_step": int(n ** 3 * 8)},
         "gpu_launches": prof["launches"],

@@ -73,6 +73,7 @@ def lib():
         L.oracle_matvec.argtypes = [i, dp, d, dp, dp, dp]
         L.oracle_cg.argtypes = [i, dp, d, dp, dp, d, i, dp, ip, dp]
         L.oracle_threads.restype = i
+        L.oracle_set_threads.restype = None
         _lib = L
     return _lib
 
@@ -98,6 +99,11 @@ def _check(st, what):
 
 def threads() -> int:
     return int(lib().oracle_threads())
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for the following oracle calls."""
+    lib().oracle_set_threads(int(n))
 
 
 def assign(pos, n: int, box: float, scheme: int, ss: int = 2) -> np.ndarray:

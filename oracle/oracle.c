@@ -641,6 +641,16 @@ done:
   return st;
 }
 
+/* Sets the number of OpenMP threads for the following calls (no effect without OpenMP). */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 int oracle_threads(void) {
 #ifdef _OPENMP

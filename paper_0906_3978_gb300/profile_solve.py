@@ -1,7 +1,9 @@
-"""Run one reconstruction (gridding, window/noise, a fixed number of CG iterations) and print
-the per-kernel-class profile.  Small and bounded, for use under a kernel profiler:
+"""Run one reconstruction (gridding, window/noise, a fixed number of CG iterations), or one
+projection of a sky map into the 3D mask, and print the per-kernel-class profile.  Small and
+bounded, for use under a kernel profiler:
 
     python -m paper_0906_3978_gb300.profile_solve --n 256 --prec mixed --iters 4
+    python -m paper_0906_3978_gb300.profile_solve --n 256 --what mask
 """
 import argparse
 import os
@@ -21,9 +23,12 @@ def main():
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--precond", type=int, default=1)
+    ap.add_argument("--what", choices=["solve", "mask"], default="solve")
     a = ap.parse_args()
     wf.build()
     pr = synth.problem("c2", n_override=None if a.n == 256 else a.n, cache=False)
+    if a.what == "mask":
+        return mask(wf, pr)
     with wf.Context(0) as ctx:
         ctx.profile(True)
         nobs = ctx.grid_assign(torch.from_numpy(pr.pos).cuda(), pr.n, pr.box, pr.scheme, 2)
@@ -36,6 +41,33 @@ def main():
     for c in sorted(p["classes"], key=lambda c: -c["ms"]):
         print("  %-12s launches %5d  ms %9.3f  GB/s %s" % (c["name"], c["launches"], c["ms"],
                                                            "%.0f" % c["gbs"] if c["gbs"] else "-"))
+    return 0
+
+
+def mask(wf, pr):
+    """The sky map of 2N x N pixels (completeness 0.9 in the survey cone, 0 elsewhere) and the radial
+    law every 0.25 H out to N H, projected once: 8 N^3 ray samples."""
+    import math
+    import numpy as np
+    import torch
+    n, box = pr.n, pr.box
+    na, nd, nr = 2 * n, n, 4 * n
+    dr = 0.25 * box / n
+    al = (np.arange(na) + 0.5) * 2 * math.pi / na
+    de = -math.pi / 2 + (np.arange(nd) + 0.5) * math.pi / nd
+    ax = np.asarray(pr.sel.axis, dtype=np.float64)
+    dot = (np.cos(de)[:, None] * np.cos(al)[None, :] * ax[0] + np.cos(de)[:, None] * np.sin(al)[None, :] * ax[1]
+           + np.sin(de)[:, None] * ax[2])
+    sky = torch.from_numpy(np.where(dot >= math.cos(pr.sel.half_angle), 0.9, 0.0)).cuda()
+    wr = np.ones(nr)
+    with wf.Context(0) as ctx:
+        ctx.profile(True)
+        ctx.project_mask(sky, n, box, 0.0, 2 * math.pi / na, -math.pi / 2, math.pi / nd, pr.sel.observer, dr, wr)
+        torch.cuda.synchronize()
+        p = ctx.profile_read()
+    print("n=%d mask samples=%d launches=%d" % (n, na * nd * nr, p["launches"]))
+    for c in sorted(p["classes"], key=lambda c: -c["ms"]):
+        print("  %-12s launches %5d  ms %9.3f" % (c["name"], c["launches"], c["ms"]))
     return 0
 
 
