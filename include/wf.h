@@ -374,7 +374,7 @@ typedef struct {
  * s_m = G^-1 s_g (Eq. eq:DEC); that is how it runs.  opts->tol applies to the s_g system, whose
  * residual is G^-1 times the literal one: info->rel_residual is the s_g system's.
  *   w, b, s_out  dev double [n^3] as in wf_solve (s_out may not alias w or b)
- * Errors: as wf_solve, plus WF_ERR_ARG for a bad response. */
+ * Errors: as wf_solve, plus WF_ERR_ARG for a bad response or an aliased s_out. */
 wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const wf_response* response,
                             const double* w, double nbar, const double* b, const wf_solve_opts* opts,
                             double* s_out, wf_solve_info* info, void* stream);

@@ -413,6 +413,7 @@ wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* po
   if (info) std::memset(info, 0, sizeof(*info));
   SolveArgs a;
   wf_status s = prepare_solve(grid, power, w, nbar, b, opts, s_out, a);
+  if (s == WF_OK && (s_out == w || s_out == b)) s = WF_ERR_ARG;  // s_out is deconvolved in place
   std::vector<double> ginv;
   if (s == WF_OK) s = response_tables(*grid, response, a.sinv, ginv);
   if (s != WF_OK) {

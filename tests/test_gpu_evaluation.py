@@ -332,6 +332,10 @@ def test_solve_response_unit_factor_and_errors(ctx):
         with pytest.raises(wf.WfError) as e:
             ctx.solve_response(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, *bad)
         assert e.value.status == wf.ERR_ARG
+    bd = gpu(b)
+    with pytest.raises(wf.WfError) as e:
+        ctx.solve_response(gpu(w), nbar, bd, pr.box, pr.pk_k, pr.pk_p, 1.0, 0.4, 5.0, s_out=bd)
+    assert e.value.status == wf.ERR_ARG
 
 
 def test_mask_projection_degenerate_geometry(ctx):
