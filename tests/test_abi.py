@@ -67,3 +67,22 @@ def test_rsd_factor_matches_oracle():
         a.update(bad)
         with pytest.raises(wf.WfError):
             wf.rsd_factor(a["k"], a["beta"], a["sigma_v"])
+
+
+def test_product_path_never_loads_the_oracle():
+    """The library and its binding stand alone: importing and building them loads no part of the
+    oracle, and no source of the package or the header refers to it."""
+    import subprocess
+    import sys
+    code = ("import sys; import paper_0906_3978_gb300 as wf; wf.build(); wf.lib(); "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad")
+    subprocess.run([sys.executable, "-c", code], cwd=ROOT, check=True, timeout=600)
+    pkg = os.path.join(ROOT, "paper_0906_3978_gb300")
+    for d, _, files in os.walk(pkg):
+        if "_build" in d or "__pycache__" in d:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(d, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b|liboracle|oracle\.c", src, re.M), f
