@@ -132,7 +132,7 @@ def barrier(ws):
 # ------------------------------------------------------------------------------------------
 # CPU oracle baseline: bounded sample of the same workload on the host cores
 # ------------------------------------------------------------------------------------------
-def oracle_sample(pr, iters, deadline_s=40.0):
+def oracle_sample(pr, iters, deadline_s=40.0, single_thread=True):
     """Time the oracle on a bounded sample of the workload and scale it to solves/s:
     full-size assignment and window, one textbook-CG matvec at full size, the ideal low-pass
     counted as 5 matvecs (a 1024^3 and a 512^3 complex transform), and `iters` iterations."""
@@ -151,6 +151,12 @@ def oracle_sample(pr, iters, deadline_s=40.0):
     oracle.matvec(tab, 0.05, w, p)
     t_mv = time.perf_counter() - t0
     t_solve = t_assign + t_window + (iters + 5) * t_mv
+    sample = ("oracle (plain C, FP64, %d OpenMP threads) at %d^3: assignment of all %d galaxies onto the 2x fine "
+              "grid (%.2f s), window (%.2f s), one CG matvec (%.2f s); solve = assignment + window + (%d CG "
+              "iterations as the GPU FP64 solve needed + 5 for the low-pass) x matvec"
+              % (oracle.threads(), pr.n, pr.n_gal, t_assign, t_window, t_mv, iters))
+    if not single_thread:
+        return 1.0 / t_solve, oracle.threads(), sample, t_solve, None
     # one thread: a 256^3 matvec, scaled to 512^3 by V log V (x 9)
     nt = oracle.threads()
     n1 = pr.n // 2
@@ -167,10 +173,6 @@ def oracle_sample(pr, iters, deadline_s=40.0):
     single = {"matvec_s_at_half_n": t_mv1, "matvec_s_extrapolated": t_mv1 * scale,
               "threads_speedup_on_matvec": t_mv1 * scale / t_mv,
               "note": "1 OpenMP thread, one %d^3 matvec scaled by V log V to %d^3" % (n1, pr.n)}
-    sample = ("oracle (plain C, FP64, %d OpenMP threads) at %d^3: assignment of all %d galaxies onto the 2x fine "
-              "grid (%.2f s), window (%.2f s), one CG matvec (%.2f s); solve = assignment + window + (%d CG "
-              "iterations as the GPU FP64 solve needed + 5 for the low-pass) x matvec"
-              % (oracle.threads(), pr.n, pr.n_gal, t_assign, t_window, t_mv, iters))
     return 1.0 / t_solve, oracle.threads(), sample, t_solve, single
 
 
@@ -185,7 +187,7 @@ def reference_arm(args):
     iters = REF_ITERS.get(args.workload, 200)
     vals = []
     for i in range(args.warmup + args.steps):
-        v, cores, sample, t, _ = oracle_sample(pr, iters)
+        v, cores, sample, t, _ = oracle_sample(pr, iters, single_thread=False)
         if i >= args.warmup:
             vals.append(v)
     value = statistics.mean(vals)
