@@ -182,6 +182,26 @@ wf_status wf_sd_noise(wf_ctx* ctx, int64_t n_cells, const double* n_obs, const d
 wf_status wf_jackknife_masses(wf_ctx* ctx, int64_t n_gal, const double* w_gal, const double* u, double alpha,
                               double* out, void* stream);
 
+/* The Jackknife-like signal-dependent-noise filter (Sec. "Statistically unbiased Jackknife-like
+ * scheme" and the mock tests of Sec. 5, which show the mean of 200 reconstructions).  For each
+ * subsample j < n_sub: galaxy masses from u[j] (wf_jackknife_masses), their supersampled gridding
+ * and low-pass N''_j (wf_grid_assign_weighted), the noise of Eq. eq:noisecov with lambda = N''_j
+ * (wf_sd_noise: D_j = nbar^2 w / N''_j, b_j = nbar^2 d / N''_j, no data term where N''_j <= 0),
+ * and the solve (S^-1 + diag(D_j)) s_j = b_j; s_mean = sum_j s_j / n_sub, added in subsample order
+ * (deterministic).  Up to 8 subsamples are solved together.
+ *   grid       the grid and supersampling of the gridding (the solve runs on the same n, box)
+ *   pos        dev double [n_gal][3]; w_gal dev double [n_gal] (the completeness at each galaxy)
+ *   u          dev double [n_sub][n_gal], uniform in [0, 1) (the caller's random numbers)
+ *   n_obs, w   dev double [n^3] (the observed low-passed counts and the window); nbar > 0
+ *   s_mean     dev double [n^3]; infos host [n_sub] or NULL (each subsample's solve)
+ * Returns WF_OK if every solve converged, else the first failing status (s_mean still holds the
+ * mean of what the solves returned).  Errors: WF_ERR_ARG, WF_ERR_UNSUPPORTED, WF_ERR_OOM,
+ * WF_ERR_CUDA, WF_ERR_NOT_CONVERGED, WF_ERR_BREAKDOWN.  Waits for completion. */
+wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const wf_power* power,
+                             const double* pos, int64_t n_gal, const double* w_gal, const double* u, int n_sub,
+                             double alpha, const double* n_obs, const double* w, double nbar,
+                             const wf_solve_opts* opts, double* s_mean, wf_solve_info* infos, void* stream);
+
 /* ---- inverse-weighting estimator (Sec. 5, Eq. def:ngrid with galaxy mass 1/w) ------------- */
 
 /* The selection w (Sec. 2.3: cone x holes x radial law, the same formula and operation order as

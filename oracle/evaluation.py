@@ -1,6 +1,7 @@
 """CPU FP64 oracle of the steps around the solve (Kitaura et al. 2009, arXiv:0906.3978): the
 redshift-distortion factor, the deconvolution B^-1 Z^-1 (Eq. eq:DEC) and the Wiener filter with
-Z and B inside the response operator, all of Sec. 3, and the evaluation of a reconstruction of Sec. 5.1 "Statistical correlation measures" and Sec. 6.2
+Z and B inside the response operator, all of Sec. 3, the mean of the Jackknife-like signal-dependent-noise
+reconstructions (Sec. 2.4 and App. A), and the evaluation of a reconstruction of Sec. 5.1 "Statistical correlation measures" and Sec. 6.2
 "Statistical analysis": Gaussian smoothing, the correlation coefficient r, the Euclidean distance D_Euc, the
 normalised Kullback-Leibler distance D_KL, and binned density statistics (counts in 1+delta bins
 per radial shell and observed / unobserved region; mean, central moments, skewness, kurtosis,
@@ -26,7 +27,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import fft3d
+from . import assign_weighted, cg, fft3d, lowpass_scaled
 
 
 def gaussian_multiplier(n: int, box: float, r_s: float) -> np.ndarray:
@@ -247,3 +248,19 @@ def sd_noise(n_obs, w, lam, nbar: float):
     D = np.where(ok, nb2 * w / np.where(ok, lam, 1.0), 0.0)
     b = np.where(ok, nb2 * d / np.where(ok, lam, 1.0), 0.0)
     return D, b
+
+
+def jackknife_solve(pos, w_gal, u, alpha: float, n_obs, w, nbar: float, n: int, box: float, scheme: int,
+                    ss: int, sinv_tab, tol: float = 1e-12):
+    """The mean over the subsamples j of the signal-dependent-noise reconstructions with
+    lambda = N''_j (Sec. "Statistically unbiased Jackknife-like scheme"; Sec. 5 shows the mean of 200
+    such reconstructions): masses of Eq. eq:selfunc from u[j], their supersampled gridding and ideal
+    low-pass N''_j, the noise of Eq. eq:noisecov, and textbook CG on (S^-1 + diag(D_j)) s_j = b_j.
+    Returns (mean, [s_j])."""
+    sols = []
+    for uj in np.asarray(u, dtype=np.float64):
+        fine = assign_weighted(pos, jackknife_masses(w_gal, uj, alpha), n, box, scheme, ss)
+        lam = lowpass_scaled(fine, n, ss, 2.0 ** -32)
+        D, b = sd_noise(n_obs, w, lam, nbar)
+        sols.append(cg(sinv_tab, 1.0, D, b, tol=tol)[0])
+    return np.mean(sols, axis=0), sols

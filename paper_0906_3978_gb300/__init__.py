@@ -11,6 +11,7 @@ Functions mirror the C ABI:
   Context.solve         wf_solve         Wiener filter by CG (Sec. 2.5.1, Eq. eq:WF)
   Context.solve_batch   wf_solve_batch
   Context.solve_response wf_solve_response  the Sec. 3 variant with Z and B inside R
+  Context.jackknife_solve wf_jackknife_solve  mean of the Jackknife-like SD reconstructions
   Context.submit/poll   wf_submit / wf_poll (serving)
 """
 from __future__ import annotations
@@ -106,6 +107,9 @@ def lib():
                                P(SolveInfo), c_void_p]
         L.wf_solve_response.argtypes = [c_void_p, P(Grid), P(Power), P(Response), c_void_p, c_double, c_void_p,
                                         P(SolveOpts), c_void_p, P(SolveInfo), c_void_p]
+        L.wf_jackknife_solve.argtypes = [c_void_p, P(Grid), c_int, P(Power), c_void_p, c_int64, c_void_p, c_void_p,
+                                         c_int, c_double, c_void_p, c_void_p, c_double, P(SolveOpts), c_void_p,
+                                         c_void_p, c_void_p]
         L.wf_solve_batch.argtypes = [c_void_p, c_int, P(Grid), P(Power), P(c_void_p), P(c_double), P(c_void_p),
                                      P(SolveOpts), P(c_void_p), P(SolveInfo), c_void_p]
         L.wf_submit.argtypes = [c_void_p, P(Grid), P(Power), c_void_p, c_double, c_void_p, P(SolveOpts), P(c_uint64)]
@@ -134,7 +138,8 @@ def lib():
                      "wf_submit", "wf_poll", "wf_profile", "wf_profile_read", "wf_profile_class",
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
                      "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve",
-                     "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask", "wf_solve_response"):
+                     "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask", "wf_solve_response",
+                     "wf_jackknife_solve"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -392,6 +397,27 @@ class Context:
         if check and st != OK:
             raise WfError(st, "wf_solve_response", info)
         return s_out, info
+
+    def jackknife_solve(self, pos, w_gal, u, alpha: float, n_obs, w, nbar: float, n: int, box: float, pk_k, pk_p,
+                        scheme=TSC, supersample=2, tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1,
+                        stream=None, check=True):
+        """(s_mean, [info]): the mean of the signal-dependent-noise reconstructions of the n_sub
+        Jackknife-like subsamples drawn with u [n_sub, n_gal] (wf_jackknife_solve)."""
+        import torch
+        n_sub, n_gal = int(u.shape[0]), int(u.shape[1])
+        if not (u.is_contiguous() and pos.is_contiguous() and w_gal.is_contiguous()):
+            raise ValueError("pos, w_gal and u must be contiguous")
+        s_mean = torch.empty((n, n, n), dtype=torch.float64, device=n_obs.device)
+        g = Grid(int(n), float(box), int(supersample))
+        pw, keep = make_power(pk_k, pk_p)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        infos = (SolveInfo * n_sub)()
+        st = lib().wf_jackknife_solve(self._h, ctypes.byref(g), int(scheme), ctypes.byref(pw), _ptr(pos), n_gal,
+                                      _ptr(w_gal), _ptr(u), n_sub, float(alpha), _ptr(n_obs), _ptr(w), float(nbar),
+                                      ctypes.byref(o), _ptr(s_mean), ctypes.cast(infos, c_void_p), _stream(stream))
+        if check and st != OK:
+            raise WfError(st, "wf_jackknife_solve")
+        return s_mean, list(infos)
 
     def solve_batch(self, problems, stream=None):
         """problems: list of dicts with w, nbar, b, box, pk_k, pk_p, tol, max_iter, prec, inner_tol,

@@ -435,6 +435,66 @@ wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* po
   return s;
 }
 
+wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const wf_power* power,
+                             const double* pos, int64_t n_gal, const double* w_gal, const double* u, int n_sub,
+                             double alpha, const double* n_obs, const double* w, double nbar,
+                             const wf_solve_opts* opts, double* s_mean, wf_solve_info* infos, void* stream) {
+  if (!ctx) return WF_ERR_ARG;
+  WF_TRY(check_grid(grid));
+  if (!power || !pos || !w_gal || !u || !n_obs || !w || !s_mean || !opts || n_gal <= 0 || n_sub <= 0 ||
+      !(alpha > 0.0) || !(alpha <= 1.0) || !(nbar > 0.0) || !std::isfinite(nbar))
+    return WF_ERR_ARG;
+  if (!(opts->tol > 0.0) || opts->max_iter <= 0 || (opts->prec != WF_FP64 && opts->prec != WF_MIXED))
+    return WF_ERR_ARG;
+  if (infos) std::memset(infos, 0, (size_t)n_sub * sizeof(*infos));
+  std::vector<double> sinv;
+  WF_TRY(build_sinv_table(*grid, *power, sinv));
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard dg(c->device);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const int64_t V = (int64_t)grid->n * grid->n * grid->n;
+  const int chunk = n_sub < 8 ? n_sub : 8;  // subsample systems solved together
+  double *masses, *lam, *db, *sj;
+  WF_TRY(c->get("jk_masses", (size_t)n_gal * sizeof(double), (void**)&masses));
+  WF_TRY(c->get("jk_lambda", (size_t)V * sizeof(double), (void**)&lam));
+  WF_TRY(c->get("jk_db", (size_t)chunk * 2 * V * sizeof(double), (void**)&db));
+  WF_TRY(c->get("jk_s", (size_t)chunk * V * sizeof(double), (void**)&sj));
+  WF_CUDA(cudaMemsetAsync(s_mean, 0, (size_t)V * sizeof(double), st));
+  wf_status first_bad = WF_OK;
+  for (int j0 = 0; j0 < n_sub; j0 += chunk) {
+    const int m = std::min(chunk, n_sub - j0);
+    std::vector<SolveArgs> args((size_t)m);
+    std::vector<wf_solve_info> tmp((size_t)m);
+    std::vector<SolveArgs*> sys;
+    std::vector<wf_solve_info*> inf;
+    for (int q = 0; q < m; ++q) {
+      const int j = j0 + q;
+      double* D = db + (size_t)(2 * q) * V;
+      double* b = D + V;
+      // subsample j (Eq. eq:selfunc), its low-passed grid N'' as lambda, the noise of Eq. eq:noisecov
+      WF_TRY(jackknife_run(*c, n_gal, w_gal, u + (size_t)j * n_gal, alpha, masses, st));
+      WF_TRY(assign_weighted_run(*c, *grid, (int)scheme, pos, masses, n_gal, nullptr, lam, st));
+      WF_TRY(sd_noise_run(*c, V, n_obs, w, lam, nbar, D, b, st));
+      SolveArgs& a = args[(size_t)q];
+      a.grid = *grid;
+      a.grid.supersample = 1;
+      a.w = D;
+      a.b = b;
+      a.nbar = 1.0;
+      a.opts = *opts;
+      a.s_out = sj + (size_t)q * V;
+      a.sinv = sinv;
+      sys.push_back(&a);
+      inf.push_back(infos ? infos + j : &tmp[(size_t)q]);
+    }
+    const wf_status s = solve_many(*c, sys, inf, st);
+    if (s != WF_OK && first_bad == WF_OK) first_bad = s;
+    for (int q = 0; q < m; ++q) WF_TRY(add_scaled_run(*c, V, sj + (size_t)q * V, 1.0 / n_sub, s_mean, st));
+  }
+  return first_bad;
+}
+
 wf_status wf_project_mask(wf_ctx* ctx, const wf_grid* grid, const double* sky, int n_alpha, int n_delta,
                           double alpha0, double dalpha, double delta0, double ddelta, const double* observer,
                           double dr, int n_r, const double* wr, double* w, int64_t* counts, void* stream) {

@@ -176,6 +176,7 @@ wf_status sd_noise_run(Ctx& c, int64_t n_cells, const double* n_obs, const doubl
                        double nbar, double* D, double* b, cudaStream_t st);
 wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double* u, double alpha, double* out,
                         cudaStream_t st);
+wf_status add_scaled_run(Ctx& c, int64_t n, const double* s, double f, double* acc, cudaStream_t st);
 wf_status project_mask_run(Ctx& c, const wf_grid& g, const double* sky, int n_alpha, int n_delta, double alpha0,
                            double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
                            const double* wr, double* w, int64_t* counts, cudaStream_t st);

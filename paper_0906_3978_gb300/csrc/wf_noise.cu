@@ -172,6 +172,21 @@ wf_status jackknife_run(Ctx& c, int64_t n_gal, const double* w_gal, const double
   return WF_OK;
 }
 
+// acc += f s, element by element (the mean of the Jackknife reconstructions, added in subsample order)
+__global__ void __launch_bounds__(256)
+k_add_scaled(double* __restrict__ acc, const double* __restrict__ s, double f, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    acc[i] = __dadd_rn(acc[i], __dmul_rn(f, s[i]));
+}
+
+wf_status add_scaled_run(Ctx& c, int64_t n, const double* s, double f, double* acc, cudaStream_t st) {
+  if (n <= 0 || !s || !acc) return WF_ERR_ARG;
+  c.launch("add_scaled", 24.0 * (double)n, st,
+           [&] { k_add_scaled<<<152 * 4, 256, 0, st>>>(acc, s, f, (size_t)n); });
+  WF_CUDA(cudaGetLastError());
+  return WF_OK;
+}
+
 // ------------------------------------------------------------------------------------------
 // Projection of a sky completeness map along rays (Sec. 2.3, Eq. eq:transf): sample (j, i, k) is
 // the point o + r_k u_ij, r_k = (k + 1/2) dr, u = (cos d cos a, cos d sin a, sin d) with the

@@ -29,7 +29,7 @@ def test_header_declares_boundary():
                      "wf_solve_batch", "wf_submit", "wf_poll", "wf_status_string", "wf_set_fused_planes",
                      "wf_smooth", "wf_compare", "wf_density_stats", "wf_selection_eval",
                      "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve", "wf_sd_noise",
-                     "wf_jackknife_masses", "wf_project_mask", "wf_solve_response"]:
+                     "wf_jackknife_masses", "wf_project_mask", "wf_solve_response", "wf_jackknife_solve"]:
         assert required in names
 
 

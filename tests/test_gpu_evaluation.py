@@ -351,3 +351,27 @@ def test_mask_projection_degenerate_geometry(ctx):
         w_ref, c_ref = oracle.project_mask(sky1, *args)
         assert np.array_equal(host(cnt), c_ref) and np.array_equal(host(w), w_ref)
         assert c_ref.sum() == n_r
+
+
+# ------------------------------------------------------------------ Jackknife ensemble (App. A)
+def test_jackknife_ensemble_matches_oracle(ctx):
+    """Three subsamples at 32^3, each solved to residual 1e-12 on both sides: the mean within
+    1e-7 relative L2 (kappa x tol, kappa up to ~1e5 here: D reaches ~110 where N'' is small)."""
+    n = 32
+    pr = synth.problem("c2", n_override=n, cache=False)
+    nobs = oracle.lowpass(oracle.assign(pr.pos, n, pr.box, pr.scheme, 2), n, 2)
+    w = oracle.window(pr.sel, n, pr.box)
+    _, _, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+    wg = oracle.window_at(pr.sel, pr.pos)
+    alpha = 0.9 * wg[wg > 0].min()
+    u = np.random.default_rng(61).uniform(size=(3, pr.n_gal))
+    s, infos = ctx.jackknife_solve(gpu(pr.pos), gpu(wg), gpu(u), alpha, gpu(nobs), gpu(w), nbar, n, pr.box,
+                                   pr.pk_k, pr.pk_p, scheme=pr.scheme, supersample=2, tol=1e-12, max_iter=20000)
+    assert all(i.status == wf.OK and i.rel_residual <= 1e-12 for i in infos)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    ref, _ = ev.jackknife_solve(pr.pos, wg, u, alpha, nobs, w, nbar, n, pr.box, pr.scheme, 2, tab)
+    assert rl2(host(s), ref) <= 1e-7
+    with pytest.raises(wf.WfError) as e:
+        ctx.jackknife_solve(gpu(pr.pos), gpu(wg), gpu(u), 0.0, gpu(nobs), gpu(w), nbar, n, pr.box, pr.pk_k,
+                            pr.pk_p)
+    assert e.value.status == wf.ERR_ARG

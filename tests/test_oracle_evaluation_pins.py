@@ -366,3 +366,44 @@ def test_mask_counts_match_exact_geometry_away_from_cell_faces():
     assert np.abs(c - exact).sum() <= 2 * np.count_nonzero(near)
     assert exact.sum() > 10000  # most rays cross the box
     assert abs(int(c.sum()) - int(exact.sum())) <= np.count_nonzero(near)
+
+
+# ------------------------------------------------------------------ Jackknife ensemble (App. A)
+def _jk_case(n=16):
+    pr = synth.problem("c1", n_override=n, cache=False)
+    nobs = oracle.lowpass(oracle.assign(pr.pos, n, pr.box, pr.scheme, 2), n, 2)
+    w = oracle.window(pr.sel, n, pr.box)
+    _, _, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    return pr, nobs, w, nbar, tab
+
+
+def test_jackknife_ensemble_keeping_every_galaxy_is_the_sd_filter_on_the_counts():
+    """alpha = 1 and u = 0 keep every galaxy with mass 1, so N'' is the unit-mass low-passed grid
+    (up to the Q32 rounding of the masses' weights) and every reconstruction is the SD filter with
+    lambda = n_obs."""
+    pr, nobs, w, nbar, tab = _jk_case()
+    n = pr.n
+    mean, sols = ev.jackknife_solve(pr.pos, np.ones(pr.n_gal), np.zeros((2, pr.n_gal)), 1.0, nobs, w, nbar, n,
+                                    pr.box, pr.scheme, 2, tab)
+    D, b = ev.sd_noise(nobs, w, nobs, nbar)
+    ref = oracle.cg(tab, 1.0, D, b, tol=1e-12)[0]
+    # Q32 mass weights move N'' by ~1e-10 relative; the solves' residual is 1e-12
+    assert np.linalg.norm(mean - ref) <= 1e-9 * np.linalg.norm(ref)
+    assert np.array_equal(sols[0], sols[1])
+
+
+def test_jackknife_ensemble_is_the_mean_of_the_subsample_solves():
+    """Three subsamples: the ensemble is their plain average, and repeating one subsample's numbers
+    three times gives that subsample's reconstruction."""
+    pr, nobs, w, nbar, tab = _jk_case()
+    n = pr.n
+    wg = oracle.window_at(pr.sel, pr.pos)
+    alpha = 0.9 * wg[wg > 0].min()
+    u = np.random.default_rng(8).uniform(size=(3, pr.n_gal))
+    mean, sols = ev.jackknife_solve(pr.pos, wg, u, alpha, nobs, w, nbar, n, pr.box, pr.scheme, 2, tab)
+    assert np.allclose(mean, (sols[0] + sols[1] + sols[2]) / 3.0, rtol=0, atol=1e-14 * np.abs(mean).max())
+    assert not np.array_equal(sols[0], sols[1])
+    rep, _ = ev.jackknife_solve(pr.pos, wg, np.repeat(u[:1], 3, axis=0), alpha, nobs, w, nbar, n, pr.box,
+                                pr.scheme, 2, tab)
+    assert np.linalg.norm(rep - sols[0]) <= 1e-14 * np.linalg.norm(sols[0])
