@@ -400,7 +400,7 @@ def batch_mocks(count=96, seed=2000):
 
 
 def bench_postproc(ctx, pr, s_rec, s_ref, w, b, nbar):
-    """Sec. 5.1 / 6.2 evaluation of the 512^3 reconstruction: Gaussian smoothing at r_S = 10, 20,
+    """Sec. 4.1 / 5.5 evaluation of the 512^3 reconstruction: Gaussian smoothing at r_S = 10, 20,
     30 Mpc/h (FP64 transforms, FP64-ALU-bound), the quality measures of the mixed solution
     against the FP64 one, and the density statistics of the r_S = 10 field in the paper's radial
     shells and observed / unobserved regions (1 + delta bins of 0.03 from -1); also the solve with
@@ -435,7 +435,7 @@ def bench_postproc(ctx, pr, s_rec, s_ref, w, b, nbar):
     ms, _ = timed(lambda: ctx.grid_assign_weighted(pos, ctx.selection_eval(pr.sel, pos, reciprocal=True), n, box,
                                                    pr.scheme, 2))
     out["inverse_weighting_ms"] = ms  # masses 1 / w at the galaxies, 1024^3 fine grid, low-pass
-    # the variant with Z and B inside R (Sec. 3): bias 1, Kaiser beta = 0.24^0.6, sigma_v = 5 Mpc/h
+    # the variant with Z and B inside R (Sec. 3.3.2): bias 1, Kaiser beta = 0.24^0.6, sigma_v = 5 Mpc/h
     # (500 km/s), mixed precision to 1e-6; one solve, as the headline's solve is timed
     beta = 0.24 ** 0.6
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

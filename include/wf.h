@@ -4,9 +4,9 @@
  * The library computes the hot path of the ARGO Wiener reconstruction of Kitaura et al.
  * 2009 ("Cosmic cartography of the large-scale structure with SDSS DR6",
  * arXiv:0906.3978):
- *   galaxies --(Sec. 2.2 supersampling: CIC/TSC on a finer grid, ideal low-pass)--> n_obs
- *   n_obs, w --(Sec. 2.4 data/noise model: eq:datamodel, eq:nmean, eq:noiseav)--> d, b
- *   b, w, P(k) --(Sec. 2.5.1, Eq. eq:WF, Krylov inversion)--> s = <delta_g>_WF
+ *   galaxies --(Sec. 3.1.2 supersampling: CIC/TSC on a finer grid, ideal low-pass)--> n_obs
+ *   n_obs, w --(Sec. 3.2 data/noise model: eq:datamodel, eq:nmean, eq:noiseav)--> d, b
+ *   b, w, P(k) --(Sec. 3.3.1, Eq. eq:WF, Krylov inversion)--> s = <delta_g>_WF
  *
  * General conventions
  *   - Grids are cubic and periodic: N cells per axis, row-major [x][y][z] (z fastest), node
@@ -49,7 +49,7 @@ typedef enum {
 typedef struct wf_ctx wf_ctx;
 
 /* Cubic periodic grid: n cells per axis, box side (length units of the positions),
- * supersample = 1 (plain gridding) or 2 (fine grid 2n, Sec. 2.2). */
+ * supersample = 1 (plain gridding) or 2 (fine grid 2n, Sec. 3.1.2). */
 typedef struct {
   int n;
   double box;
@@ -58,7 +58,7 @@ typedef struct {
 
 typedef enum { WF_CIC = 1, WF_TSC = 2 } wf_scheme;
 
-/* Analytic survey window (the 3D mask of Sec. 2.3, w <= 1), evaluated at the nodes:
+/* Analytic survey window (the 3D mask of Sec. 3.1.3, w <= 1), evaluated at the nodes:
  *   w(x) = [angle(x-o, axis) <= half_angle] * prod_h [angle(x-o, h) >= rho_h] * f(r),
  *   r = |x - o|, w = 0 at r = 0; membership decided by dot products against cos(angle)*r.
  * axis and hole directions are unit vectors; holes points to n_holes rows of
@@ -76,7 +76,7 @@ typedef struct {
 
 /* Prior power spectrum P(k) as a host table (k strictly increasing, all > 0), interpolated
  * log-log linearly (end segments extrapolated).  S^-1(k) = dV / P(k) on the grid, the
- * discrete form of S-hat = (2 pi)^3 P(k) delta_D of Sec. 2.5.1; S^-1(0) = 0. */
+ * discrete form of S-hat = (2 pi)^3 P(k) delta_D of Sec. 3.3.1; S^-1(0) = 0. */
 typedef struct {
   const double* k;
   const double* p;
@@ -126,7 +126,7 @@ const char* wf_status_string(wf_status s);
 const char* wf_last_error(void);
 
 /* Choose how the FP32 transforms of a CG iteration (the mixed-precision inner solves) run
- * between the two x passes (Sec. 2.5.1: the data term applied between the inverse and forward
+ * between the two x passes (Sec. 3.3.1: the data term applied between the inverse and forward
  * transforms of the signal).  on = 0 (the default): three passes (inverse y, the real z
  * transforms with the multiplication by nbar w in between, forward y).  on = 1: where the grid
  * size allows (n = 128, 192, 256, 384, 512), one kernel per x-plane on a thread-block cluster
@@ -136,10 +136,10 @@ const char* wf_last_error(void);
  * differ, the FP32 rounding.  Applies to solves started after the call. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
-/* ---- the 3D mask from a sky completeness map (Sec. 2.3) ------------------------------------ */
+/* ---- the 3D mask from a sky completeness map (Sec. 3.1.3) ------------------------------------ */
 
 /* Projects a sky completeness map and a radial completeness table onto the grid along rays from
- * the observer (Sec. 2.3 with Eq. eq:transf).  Sky pixel (i, j) of an equidistant alpha x delta
+ * the observer (Sec. 3.1.3 with Eq. eq:transf).  Sky pixel (i, j) of an equidistant alpha x delta
  * map has its centre at alpha_i = alpha0 + (i + 1/2) dalpha, delta_j = delta0 + (j + 1/2) ddelta
  * (radians); its ray is sampled at r_k = (k + 1/2) dr, k < n_r, at the point
  * o + r_k (cos delta cos alpha, cos delta sin alpha, sin delta).  Each sample inside the box
@@ -183,7 +183,7 @@ wf_status wf_jackknife_masses(wf_ctx* ctx, int64_t n_gal, const double* w_gal, c
                               double* out, void* stream);
 
 /* The Jackknife-like signal-dependent-noise filter (Sec. "Statistically unbiased Jackknife-like
- * scheme" and the mock tests of Sec. 5, which show the mean of 200 reconstructions).  For each
+ * scheme" and the mock tests of Sec. 4.2, which show the mean of 200 reconstructions).  For each
  * subsample j < n_sub: galaxy masses from u[j] (wf_jackknife_masses), their supersampled gridding
  * and low-pass N''_j (wf_grid_assign_weighted), the noise of Eq. eq:noisecov with lambda = N''_j
  * (wf_sd_noise: D_j = nbar^2 w / N''_j, b_j = nbar^2 d / N''_j, no data term where N''_j <= 0),
@@ -202,9 +202,9 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
                              double alpha, const double* n_obs, const double* w, double nbar,
                              const wf_solve_opts* opts, double* s_mean, wf_solve_info* infos, void* stream);
 
-/* ---- inverse-weighting estimator (Sec. 5, Eq. def:ngrid with galaxy mass 1/w) ------------- */
+/* ---- inverse-weighting estimator (Sec. 4, Eq. def:ngrid with galaxy mass 1/w) ------------- */
 
-/* The selection w (Sec. 2.3: cone x holes x radial law, the same formula and operation order as
+/* The selection w (Sec. 3.1.3: cone x holes x radial law, the same formula and operation order as
  * the window of wf_build_noise) at arbitrary positions, e.g. the completeness at each galaxy.
  * reciprocal = 1 returns 1 / w instead (0 where w = 0): the galaxy masses of the
  * inverse-weighting estimator.
@@ -213,7 +213,7 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
 wf_status wf_selection_eval(wf_ctx* ctx, const wf_selection* sel, const double* pos, int64_t n_pts,
                             int reciprocal, double* out, void* stream);
 
-/* Supersampled assignment with per-galaxy masses (the inverse-weighting estimator of Sec. 5
+/* Supersampled assignment with per-galaxy masses (the inverse-weighting estimator of Sec. 4
  * takes mass 1 / w(x_g)), then the same ideal low-pass as wf_grid_assign.  Each node's
  * contribution is its Q48 fixed-point weight times wgt[g], rounded once to the nearest Q32 unit,
  * so the fine grid is exact and independent of the order of the atomics.
@@ -226,10 +226,10 @@ wf_status wf_grid_assign_weighted(wf_ctx* ctx, const wf_grid* grid, wf_scheme sc
                                   const double* wgt, int64_t n_gal, uint64_t* fine_out, double* n_obs,
                                   void* stream);
 
-/* ---- redshift distortions and the deconvolution (Sec. 3, Eq. eq:DEC) --------------------- */
+/* ---- redshift distortions and the deconvolution (Sec. 3.3.2-3.3.3, Eq. eq:DEC) --------------------- */
 
 /* <K D>_mu(k): the mean over mu in [0, 1] of the Kaiser factor (1 + beta mu^2)^2 times the
- * Lorentzian damping 1 / (1 + k^2 sigma_v^2 mu^2 / 2) (Sec. 3, "Redshift distortion operator").
+ * Lorentzian damping 1 / (1 + k^2 sigma_v^2 mu^2 / 2) (Sec. 3.3.3, "Redshift distortion operator").
  * The redshift-space power spectrum is P^r(k) times this factor (build wf_power tables from it);
  * its square root is the operator Z.  Closed form (power series for k^2 sigma_v^2 < 1).  Host
  * arrays, no context, no device work.
@@ -246,9 +246,9 @@ wf_status wf_rsd_factor(int64_t n_k, const double* k, double beta, double sigma_
 wf_status wf_deconvolve(wf_ctx* ctx, const wf_grid* grid, const double* in, double beta, double sigma_v,
                         double bias, double* out, void* stream);
 
-/* ---- evaluation of a reconstruction (Sec. 5.1 and Sec. 6.2) ------------------------------ */
+/* ---- evaluation of a reconstruction (Sec. 4.1 and Sec. 5.5) ------------------------------ */
 
-/* Gaussian smoothing (Sec. 6.2, eq:GAUSS): out = the field convolved on the periodic grid with
+/* Gaussian smoothing (Sec. 4.1, eq:GAUSS): out = the field convolved on the periodic grid with
  * the normalised Gaussian of radius r_s, i.e. its DFT multiplied by exp(-|k|^2 r_s^2 / 2) with
  * k = 2 pi m / box and m the signed index in (-n/2, n/2].  The paper prints the kernel as
  * exp(+|r|^2 / 2 r_S^2); the decaying Gaussian is the reading taken.  FP64 transforms.
@@ -267,7 +267,7 @@ typedef struct {
   int64_t kl_excluded;  /* cells left out of d_kl */
 } wf_compare_result;
 
-/* Sec. 5.1 quality measures between a reconstructed overdensity `rec` and a reference `truth`
+/* Sec. 4.1 quality measures between a reconstructed overdensity `rec` and a reference `truth`
  * (dev double [n_cells] each, any layout): correlation coefficient, Euclidean distance and
  * normalised Kullback-Leibler distance.  Sums are FP64 and deterministic.  Result on the host;
  * waits for completion.  Errors: WF_ERR_ARG, WF_ERR_OOM, WF_ERR_CUDA. */
@@ -278,7 +278,7 @@ typedef struct {
   double n_cells, mean, mu2, mu3, mu4, skewness, kurtosis, pearson;
 } wf_density_moments;
 
-/* Sec. 6.2 density statistics.  Counts of 1 + delta in n_bins bins [lo + i width, lo + (i + 1)
+/* Sec. 5.5 density statistics.  Counts of 1 + delta in n_bins bins [lo + i width, lo + (i + 1)
  * width) per radial shell (shells[2 s] <= r < shells[2 s + 1], r = |i H - observer| at node i H,
  * no periodic wrap) and region (0: w > 0, 1: w = 0); the bin index is floor(((1 + delta) - lo) /
  * width) in FP64.  For each (shell, region), from the bin centres delta_i = lo + (i + 1/2) width
@@ -316,7 +316,7 @@ wf_status wf_profile_read(wf_ctx* ctx, int64_t* launches, int* n_classes);
 wf_status wf_profile_class(wf_ctx* ctx, int i, char* name, int name_len, int64_t* launches,
                            double* total_ms, double* bytes);
 
-/* ---- Sec. 2.2: supersampled mass assignment ----------------------------------------- */
+/* ---- Sec. 3.1.2: supersampled mass assignment ----------------------------------------- */
 
 /* Grid the galaxies and low-pass them to the target grid.
  *   pos      dev  double [n_gal][3]   positions in [box units]; periodic wrap applied
@@ -334,7 +334,7 @@ wf_status wf_profile_class(wf_ctx* ctx, int i, char* name, int name_len, int64_t
 wf_status wf_grid_assign(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme, const double* pos,
                          int64_t n_gal, uint64_t* fine_out, double* n_obs, void* stream);
 
-/* ---- Sec. 2.3-2.4: window, data and noise ------------------------------------------- */
+/* ---- Sec. 3.1.3-3.2: window, data and noise ------------------------------------------- */
 
 /* w = window at the nodes (wf_selection); nbar = n_gal / sum(w) (eq:nmean, observed volume
  * in cells); d = n_obs / nbar - w (eq:datamodel); b = R^T N^-1 d = nbar d where w > 0 and 0
@@ -364,7 +364,7 @@ wf_status wf_build_noise_noalloc(const wf_grid* grid, const wf_selection* sel, c
                                  int64_t n_gal, double* w, double* d, double* b, double* nbar,
                                  void* stream);
 
-/* ---- Sec. 2.5.1: the Wiener filter, Eq. eq:WF ----------------------------------------- */
+/* ---- Sec. 3.3.1: the Wiener filter, Eq. eq:WF ----------------------------------------- */
 
 /* Solve (S^-1 + nbar diag(w)) s = b for s = <delta_g>_WF by conjugate gradients from s = 0.
  *   w     dev double [n^3]  window (R = diag(w)); nbar > 0 as from wf_build_noise
@@ -376,7 +376,7 @@ wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, cons
                    double nbar, const double* b, const wf_solve_opts* opts, double* s_out,
                    wf_solve_info* info, void* stream);
 
-/* Linear response of the data to the real-space matter field (Sec. 3): bias B = bias (a constant)
+/* Linear response of the data to the real-space matter field (Sec. 3.2.1 and 3.3.3): bias B = bias (a constant)
  * and the mu-averaged redshift operator Z = sqrt(<K D>_mu) of wf_rsd_factor, both diagonal in
  * Fourier space with the joint factor g(k) = bias sqrt(<K D>_mu(|k|)). */
 typedef struct {
@@ -385,7 +385,7 @@ typedef struct {
   double sigma_v;  /* >= 0, pairwise-velocity dispersion in length units (Lorentzian damping) */
 } wf_response;
 
-/* The variant of Sec. 3 with Z and B inside the response operator, R = W Z B: the Wiener mean of
+/* The variant of Sec. 3.3.2 with Z and B inside the response operator, R = W Z B: the Wiener mean of
  * the real-space matter field s_m solving
  *     (S^-1 + G diag(nbar w) G) s_m = G b,     G = F^-1 diag(g) F,
  * with S^-1 from `power` (the real-space matter P(k)) as in wf_solve.  G is invertible and

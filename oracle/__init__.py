@@ -4,17 +4,17 @@ Test infrastructure only: the tests, ``__graft_entry__.smoke()`` and the benchma
 CPU-baseline leg use it; the library under ``paper_0906_3978_gb300`` never imports it.
 
 Each function follows the paper (Kitaura et al. 2009, arXiv:0906.3978):
-  assign      Sec. 2.2 "Supersampling step", Eq. def:ngrid (fixed-point CIC/TSC)
-  lowpass     Sec. 2.2, supersampling step 2 (ideal low-pass, sampling at target grid)
-  window      Sec. 2.3 (3D mask w <= 1; analytic cone x holes x radial law)
+  assign      Sec. 3.1.2 "Supersampling step", Eq. def:ngrid (fixed-point CIC/TSC)
+  lowpass     Sec. 3.1.2, supersampling step 2 (ideal low-pass, sampling at target grid)
+  window      Sec. 3.1.3 (3D mask w <= 1; analytic cone x holes x radial law)
   project_mask
-              Sec. 2.3, projection of a sky completeness map and a radial completeness table
+              Sec. 3.1.3, projection of a sky completeness map and a radial completeness table
               along rays (Eq. eq:transf), NGP-assigned and averaged per cell
   window_at, assign_weighted
-              Sec. 5, Eq. def:ngrid with galaxy mass 1/w (the inverse-weighting estimator)
-  build_noise Sec. 2.4, Eqs. eq:datamodel, eq:nmean, eq:noiseav
-  sinv_table  Sec. 2.5.1, Fourier-diagonal prior S
-  matvec/cg   Sec. 2.5.1, Eq. eq:WF, by a Krylov (CG) inversion
+              Sec. 4, Eq. def:ngrid with galaxy mass 1/w (the inverse-weighting estimator)
+  build_noise Sec. 3.2, Eqs. eq:datamodel, eq:nmean, eq:noiseav
+  sinv_table  Sec. 3.3.1, Fourier-diagonal prior S
+  matvec/cg   Sec. 3.3.1, Eq. eq:WF, by a Krylov (CG) inversion
 
 Parity is pinned by the ``-m "not gpu"`` tests (closed forms, dense direct solve, brute
 force, invariants); see tests/test_oracle_pins.py.
@@ -107,7 +107,7 @@ def set_threads(n: int) -> None:
 
 
 def assign(pos, n: int, box: float, scheme: int, ss: int = 2) -> np.ndarray:
-    """Fine Q48 grid [(ss*n)^3] uint64 (scheme 1 = CIC, 2 = TSC); Sec. 2.2."""
+    """Fine Q48 grid [(ss*n)^3] uint64 (scheme 1 = CIC, 2 = TSC); Sec. 3.1.2."""
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
     nf = ss * n
     fine = np.empty(nf ** 3, dtype=np.uint64)
@@ -116,7 +116,7 @@ def assign(pos, n: int, box: float, scheme: int, ss: int = 2) -> np.ndarray:
 
 
 def lowpass(fine, n: int, ss: int = 2) -> np.ndarray:
-    """n_obs [n^3] FP64 from the fine grid: ideal low-pass then sampling; Sec. 2.2 step 2."""
+    """n_obs [n^3] FP64 from the fine grid: ideal low-pass then sampling; Sec. 3.1.2 step 2."""
     fine = np.ascontiguousarray(fine, dtype=np.uint64)
     out = np.empty(n ** 3, dtype=np.float64)
     _check(lib().oracle_lowpass(n, ss, _u64p(fine), _dp(out)), "lowpass")
@@ -140,7 +140,7 @@ def lowpass_scaled(fine, n: int, ss: int, unit: float) -> np.ndarray:
 
 def assign_weighted(pos, wgt, n: int, box: float, scheme: int, ss: int = 2) -> np.ndarray:
     """Fine grid [(ss n)^3] uint64 in Q32 units of weighted galaxies: each node contribution is
-    rint(Q48 weight * wgt * 2^-16) (Sec. 5, Eq. def:ngrid with galaxy mass wgt)."""
+    rint(Q48 weight * wgt * 2^-16) (Sec. 4, Eq. def:ngrid with galaxy mass wgt)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
     wgt = np.ascontiguousarray(wgt, dtype=np.float64).ravel()
     nf = ss * n
@@ -151,7 +151,7 @@ def assign_weighted(pos, wgt, n: int, box: float, scheme: int, ss: int = 2) -> n
 
 
 def window_at(sel, pts) -> np.ndarray:
-    """The selection w at arbitrary positions pts [m, 3] (Sec. 2.3, the completeness at a galaxy)."""
+    """The selection w at arbitrary positions pts [m, 3] (Sec. 3.1.3, the completeness at a galaxy)."""
     pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
     obs = np.ascontiguousarray(sel.observer, dtype=np.float64)
     ax = np.ascontiguousarray(sel.axis, dtype=np.float64)
@@ -167,7 +167,7 @@ def window_at(sel, pts) -> np.ndarray:
 def project_mask(sky, n: int, box: float, alpha0: float, dalpha: float, delta0: float, ddelta: float,
                  observer, dr: float, wr):
     """(w [n, n, n], counts [n, n, n]): the 3D mask from the sky map sky [n_delta, n_alpha] and the
-    radial completeness wr [n_r] at r_k = (k + 1/2) dr, projected along rays (Sec. 2.3)."""
+    radial completeness wr [n_r] at r_k = (k + 1/2) dr, projected along rays (Sec. 3.1.3)."""
     sky = np.ascontiguousarray(sky, dtype=np.float64)
     wr = np.ascontiguousarray(wr, dtype=np.float64).ravel()
     obs = np.ascontiguousarray(observer, dtype=np.float64)
@@ -180,7 +180,7 @@ def project_mask(sky, n: int, box: float, alpha0: float, dalpha: float, delta0: 
 
 
 def window(sel, n: int, box: float) -> np.ndarray:
-    """w [n^3] at the nodes; Sec. 2.3.  ``sel`` has observer, axis, half_angle, holes [h,4],
+    """w [n^3] at the nodes; Sec. 3.1.3.  ``sel`` has observer, axis, half_angle, holes [h,4],
     radial_kind and radial_params (e.g. ``synth.Selection``)."""
     obs = np.ascontiguousarray(sel.observer, dtype=np.float64)
     ax = np.ascontiguousarray(sel.axis, dtype=np.float64)
@@ -193,7 +193,7 @@ def window(sel, n: int, box: float) -> np.ndarray:
 
 
 def build_noise(n_obs, w, n_gal: int):
-    """(d, b, nbar): Sec. 2.4, eq:datamodel, eq:nmean, eq:noiseav."""
+    """(d, b, nbar): Sec. 3.2, eq:datamodel, eq:nmean, eq:noiseav."""
     n = n_obs.shape[0]
     n_obs = np.ascontiguousarray(n_obs, dtype=np.float64)
     w = np.ascontiguousarray(w, dtype=np.float64)

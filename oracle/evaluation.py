@@ -1,9 +1,9 @@
 """CPU FP64 oracle of the steps around the solve (Kitaura et al. 2009, arXiv:0906.3978): the
 redshift-distortion factor, the deconvolution B^-1 Z^-1 (Eq. eq:DEC) and the Wiener filter with
-Z and B inside the response operator, all of Sec. 3, the mean of the Jackknife-like signal-dependent-noise
-reconstructions (Sec. 2.4 and App. A), and the evaluation of a reconstruction of Sec. 5.1 "Statistical correlation measures" and Sec. 6.2
-"Statistical analysis": Gaussian smoothing, the correlation coefficient r, the Euclidean distance D_Euc, the
-normalised Kullback-Leibler distance D_KL, and binned density statistics (counts in 1+delta bins
+Z and B inside the response operator, all of Sec. 3.3, the mean of the Jackknife-like signal-dependent-noise
+reconstructions (Sec. 3.4), and the evaluation of a reconstruction of Sec. 4.1 "Statistical correlation
+measures" and Sec. 5.5 "Statistics of the density field": Gaussian smoothing, the correlation coefficient
+r, the Euclidean distance D_Euc, the normalised Kullback-Leibler distance D_KL, and binned density statistics (counts in 1+delta bins
 per radial shell and observed / unobserved region; mean, central moments, skewness, kurtosis,
 Pearson's skewness).
 
@@ -31,7 +31,7 @@ from . import assign_weighted, cg, fft3d, lowpass_scaled
 
 
 def gaussian_multiplier(n: int, box: float, r_s: float) -> np.ndarray:
-    """exp(-|k|^2 r_S^2 / 2) on the full [n, n, n] DFT grid (Sec. 6.2, eq:GAUSS as read above)."""
+    """exp(-|k|^2 r_S^2 / 2) on the full [n, n, n] DFT grid (Sec. 4.1, eq:GAUSS as read above)."""
     m = np.fft.fftfreq(n, 1.0 / n)
     m[n // 2] = n // 2  # the Nyquist index as +N/2 (its square is the same)
     k2 = (2.0 * np.pi / box) ** 2 * (m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2)
@@ -48,7 +48,7 @@ def smooth(field, box: float, r_s: float) -> np.ndarray:
 
 
 def compare(rec, true) -> dict:
-    """Sec. 5.1: r = sum(t r) / sqrt(sum t^2 sum r^2); D_Euc = sqrt(mean (r - t)^2);
+    """Sec. 4.1: r = sum(t r) / sqrt(sum t^2 sum r^2); D_Euc = sqrt(mean (r - t)^2);
     D_KL = (1 / N_cells) sum (1 + r) log((1 + r) / (1 + t)) over the cells where both 1 + delta > 0."""
     r = np.asarray(rec, dtype=np.float64).ravel()
     t = np.asarray(true, dtype=np.float64).ravel()
@@ -100,7 +100,7 @@ MOMENT_FIELDS = ("n_cells", "mean", "mu2", "mu3", "mu4", "skewness", "kurtosis",
 
 
 def density_moments(hist, lo: float, width: float) -> np.ndarray:
-    """Sec. 6.2 from the bin counts f_i at the bin centres delta_i = lo + (i + 1/2) width - 1:
+    """Sec. 5.5 from the bin counts f_i at the bin centres delta_i = lo + (i + 1/2) width - 1:
     N = sum f, mean, mu_n = sum f (delta - mean)^n / N, s = mu3 / sigma^3, k = mu4 / sigma^4 - 3,
     s_P = (mean - delta_mode) / sigma.  Returns [..., 8] in MOMENT_FIELDS order (NaN if N = 0)."""
     h = np.asarray(hist, dtype=np.int64)
@@ -123,10 +123,10 @@ def density_moments(hist, lo: float, width: float) -> np.ndarray:
     return out.reshape(h.shape[:-1] + (8,))
 
 
-# ---------------------------------------------------------------- redshift distortions (Sec. 3)
+# ---------------------------------------------------------------- redshift distortions (Sec. 3.3.2-3.3.3)
 def rsd_factor(k, beta: float, sigma_v: float) -> np.ndarray:
     """<K D>_mu: the mean over mu in [0, 1] of the Kaiser factor (1 + beta mu^2)^2 times the
-    Lorentzian damping 1 / (1 + k^2 sigma_v^2 mu^2 / 2) (Sec. 3, "Redshift distortion operator"),
+    Lorentzian damping 1 / (1 + k^2 sigma_v^2 mu^2 / 2) (Sec. 3.3.3, "Redshift distortion operator"),
     by adaptive quadrature of the definition.  The real-space power spectrum times this factor is
     the redshift-space one; its square root is the operator Z."""
     from scipy.integrate import quad
@@ -162,7 +162,7 @@ def n2_grid(n: int) -> np.ndarray:
 
 def response_table(n: int, box: float, bias: float, beta: float, sigma_v: float) -> np.ndarray:
     """g[n2] = b sqrt(<K D>_mu(|k|)), |k| = 2 pi sqrt(n2) / L: the Fourier factor of the response
-    Z B of Sec. 3 (bias and mu-averaged redshift operator), by n2 up to 3 (n/2)^2."""
+    Z B of Sec. 3.2.1 and 3.3.3 (bias and mu-averaged redshift operator), by n2 up to 3 (n/2)^2."""
     n2 = np.arange(3 * (n // 2) ** 2 + 1)
     return bias * np.sqrt(rsd_factor(2.0 * np.pi * np.sqrt(n2) / box, beta, sigma_v))
 
@@ -173,8 +173,8 @@ def _fourier_apply(x, mult) -> np.ndarray:
 
 
 def response_matvec(sinv_tab, g_tab, nbar: float, w, s) -> np.ndarray:
-    """(S^-1 + G nbar diag(w) G) s with G = F^-1 diag(g) F: the Wiener operator of Sec. 2.5.1 with
-    the response R = W Z B of Sec. 3 (Z and B inside R)."""
+    """(S^-1 + G nbar diag(w) G) s with G = F^-1 diag(g) F: the Wiener operator of Sec. 3.3.1 with
+    the response R = W Z B of Sec. 3.3.2 (Z and B inside R)."""
     n2 = n2_grid(s.shape[0])
     gs = _fourier_apply(s, g_tab[n2])
     return _fourier_apply(s, sinv_tab[n2]) + _fourier_apply(nbar * np.asarray(w) * gs, g_tab[n2])
@@ -212,7 +212,7 @@ def solve_response(sinv_tab, g_tab, nbar: float, w, b, tol: float = 1e-12, max_i
         it += 1
 
 
-# ---------------------------------------------------------------- signal-dependent noise (Sec. 2.4.2, App. A)
+# ---------------------------------------------------------------- signal-dependent noise (Sec. 3.4)
 def lambda_mean(n_obs, w) -> np.ndarray:
     """Flat-prior mean estimator of the underlying counts, lambda_mean = (N^o + 1) / w, on w > 0
     (0 elsewhere) (Sec. "flat prior": the posterior mean of a Poisson intensity)."""
@@ -253,7 +253,7 @@ def sd_noise(n_obs, w, lam, nbar: float):
 def jackknife_solve(pos, w_gal, u, alpha: float, n_obs, w, nbar: float, n: int, box: float, scheme: int,
                     ss: int, sinv_tab, tol: float = 1e-12):
     """The mean over the subsamples j of the signal-dependent-noise reconstructions with
-    lambda = N''_j (Sec. "Statistically unbiased Jackknife-like scheme"; Sec. 5 shows the mean of 200
+    lambda = N''_j (Sec. "Statistically unbiased Jackknife-like scheme"; Sec. 4.2 shows the mean of 200
     such reconstructions): masses of Eq. eq:selfunc from u[j], their supersampled gridding and ideal
     low-pass N''_j, the noise of Eq. eq:noisecov, and textbook CG on (S^-1 + diag(D_j)) s_j = b_j.
     Returns (mean, [s_j])."""

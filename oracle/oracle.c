@@ -7,16 +7,16 @@
  *
  * What it computes (Kitaura et al. 2009, "Cosmic cartography of the large-scale
  * structure with SDSS DR6", arXiv:0906.3978):
- *   - supersampled gridding, step 1 (Sec. 2.2 "Supersampling step", Eq. def:ngrid):
+ *   - supersampled gridding, step 1 (Sec. 3.1.2 "Supersampling step", Eq. def:ngrid):
  *     CIC / TSC assignment of point galaxies onto a grid s times finer than the target,
  *     in a fixed-point rule (Q16 per axis, Q48 per galaxy) so the fine grid is exact;
- *   - supersampled gridding, step 2 (Sec. 2.2): the ideal discrete low-pass filter on the
+ *   - supersampled gridding, step 2 (Sec. 3.1.2): the ideal discrete low-pass filter on the
  *     fine grid, then sampling at the target grid;
- *   - the 3D window w (Sec. 2.3 "Calculation of the three-dimensional mask"), here
+ *   - the 3D window w (Sec. 3.1.3 "Calculation of the three-dimensional mask"), here
  *     an analytic cone x holes x radial law evaluated at the nodes;
- *   - the data and noise model (Sec. 2.4, Eqs. eq:datamodel, eq:nmean, eq:noiseav):
+ *   - the data and noise model (Sec. 3.2, Eqs. eq:datamodel, eq:nmean, eq:noiseav):
  *     nbar = N_gal / sum(w), d = n_obs/nbar - w, N = w/nbar, R = diag(w);
- *   - the signal-space Wiener filter (Sec. 2.5.1, Eq. eq:WF), i.e. the linear system
+ *   - the signal-space Wiener filter (Sec. 3.3.1, Eq. eq:WF), i.e. the linear system
  *     (S^-1 + R^T N^-1 R) s = R^T N^-1 d with S diagonal in Fourier space, solved by
  *     textbook conjugate gradients (the paper names a Krylov-space inversion, Sec. 1).
  *
@@ -52,7 +52,7 @@ enum {
 #define OR_PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------------------ */
-/* 1. Fixed-point mass assignment (Sec. 2.2, Eq. def:ngrid; CIC/TSC kernels named there) */
+/* 1. Fixed-point mass assignment (Sec. 3.1.2, Eq. def:ngrid; CIC/TSC kernels named there) */
 /* ------------------------------------------------------------------------------------ */
 
 /* Per-axis nodes and Q16 weights of one galaxy coordinate.
@@ -127,7 +127,7 @@ int oracle_assign(int n, double box, int ss, int scheme, const double* pos, int6
   return overflow ? OR_ERR_OVERFLOW : OR_OK;
 }
 
-/* Weighted assignment for the inverse-weighting estimator (Sec. 5, Eq. def:ngrid with the
+/* Weighted assignment for the inverse-weighting estimator (Sec. 4, Eq. def:ngrid with the
  * galaxy mass 1/w): galaxy g carries weight wgt[g] >= 0.  Each node's contribution is its Q48
  * fixed-point weight (as in oracle_assign) times wgt[g], rounded once to the nearest Q32 unit:
  * rint(double(q48) * wgt[g] * 2^-16).  The grid is then exact and independent of the order of
@@ -261,7 +261,7 @@ int oracle_fft3d(cplx* a, int n, int sign) {
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* 3. Ideal low-pass + downsample (Sec. 2.2, supersampling step 2)                       */
+/* 3. Ideal low-pass + downsample (Sec. 3.1.2, supersampling step 2)                       */
 /* ------------------------------------------------------------------------------------ */
 
 /* signed frequency of index j on an axis of length n; the Nyquist index n/2 maps to n/2 */
@@ -352,7 +352,7 @@ double oracle_lowpass_point(int n, int ss, const uint64_t* fine, int jx, int jy,
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* 4. Window w at the nodes (Sec. 2.3; w <= 1)                                            */
+/* 4. Window w at the nodes (Sec. 3.1.3; w <= 1)                                            */
 /* ------------------------------------------------------------------------------------ */
 
 /* w(x) = [angle(x - o, axis) <= half_angle] * prod_h [angle(x - o, h) >= rho_h] * f(r),
@@ -388,7 +388,7 @@ static double window_value(double dx, double dy, double dz, const double* axis, 
 }
 
 /* The same selection at arbitrary positions pts[3 i] (the completeness at a galaxy, for the
- * inverse-weighting estimator of Sec. 5). */
+ * inverse-weighting estimator of Sec. 4). */
 int oracle_window_at(int64_t n_pts, const double* pts, const double* obs, const double* axis,
                      double half_angle, int n_holes, const double* holes, int radial_kind,
                      const double* rp, double* w) {
@@ -427,7 +427,7 @@ int oracle_window(int n, double box, const double* obs, const double* axis, doub
   return OR_OK;
 }
 
-/* Projection of a sky completeness map onto the grid (Sec. 2.3): sky pixel (i, j) of an
+/* Projection of a sky completeness map onto the grid (Sec. 3.1.3): sky pixel (i, j) of an
  * equidistant alpha x delta map has centre alpha_i = alpha0 + (i + 1/2) dalpha, delta_j =
  * delta0 + (j + 1/2) ddelta; its ray from the observer is sampled at r_k = (k + 1/2) dr, k < n_r,
  * at x = o + r_k u with u = (cos delta cos alpha, cos delta sin alpha, sin delta) (Eq. eq:transf);
@@ -489,12 +489,12 @@ int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* 5. Data and noise (Sec. 2.4: eq:datamodel, eq:nmean, eq:noiseav)                     */
+/* 5. Data and noise (Sec. 3.2: eq:datamodel, eq:nmean, eq:noiseav)                     */
 /* ------------------------------------------------------------------------------------ */
 
 /* nbar = N_gal / sum_i w_i (galaxies per cell; the fair-sample mean of eq:nmean with the
  * observed volume counted in cells); d = n_obs/nbar - w; b = R^T N^-1 d = nbar*d where
- * w > 0 and 0 where w = 0 (no data term in unobserved cells, Sec. 4 "Cluster prediction").
+ * w > 0 and 0 where w = 0 (no data term in unobserved cells, Sec. 5.4 "Cluster prediction").
  * diag(R^T N^-1 R) = nbar*w is not stored: the solver forms it from w and nbar. */
 int oracle_build_noise(int n, const double* n_obs, const double* w, int64_t n_gal, double* d,
                        double* b, double* nbar_out) {
@@ -512,7 +512,7 @@ int oracle_build_noise(int n, const double* n_obs, const double* w, int64_t n_ga
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* 6. Prior S^-1 in Fourier space (Sec. 2.5.1: S-hat = (2 pi)^3 P(k) delta_D)            */
+/* 6. Prior S^-1 in Fourier space (Sec. 3.3.1: S-hat = (2 pi)^3 P(k) delta_D)            */
 /* ------------------------------------------------------------------------------------ */
 
 /* Power spectrum at k by log-log linear interpolation in the table (extrapolated with the
@@ -544,7 +544,7 @@ int oracle_sinv_table(int n, double box, const double* pk_k, const double* pk_p,
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* 7. The Wiener operator and textbook CG (Sec. 2.5.1, Eq. eq:WF; Krylov inversion)       */
+/* 7. The Wiener operator and textbook CG (Sec. 3.3.1, Eq. eq:WF; Krylov inversion)       */
 /* ------------------------------------------------------------------------------------ */
 
 /* q = A p = F^-1[ S^-1(k) F p ] / V_c + nbar * w * p. */

@@ -6,11 +6,11 @@ streams.  There is no fallback: if libwf.so is missing, importing the binding's 
 raises.
 
 Functions mirror the C ABI:
-  Context.grid_assign   wf_grid_assign   supersampled CIC/TSC gridding (paper Sec. 2.2)
-  Context.build_noise   wf_build_noise   window, nbar, data, noise (Sec. 2.3-2.4)
-  Context.solve         wf_solve         Wiener filter by CG (Sec. 2.5.1, Eq. eq:WF)
+  Context.grid_assign   wf_grid_assign   supersampled CIC/TSC gridding (paper Sec. 3.1.2)
+  Context.build_noise   wf_build_noise   window, nbar, data, noise (Sec. 3.1.3-3.2)
+  Context.solve         wf_solve         Wiener filter by CG (Sec. 3.3.1, Eq. eq:WF)
   Context.solve_batch   wf_solve_batch
-  Context.solve_response wf_solve_response  the Sec. 3 variant with Z and B inside R
+  Context.solve_response wf_solve_response  the Sec. 3.3.2 variant with Z and B inside R
   Context.jackknife_solve wf_jackknife_solve  mean of the Jackknife-like SD reconstructions
   Context.submit/poll   wf_submit / wf_poll (serving)
 """
@@ -252,7 +252,7 @@ class Context:
         except Exception:
             pass
 
-    # ---- Sec. 2.2 -----------------------------------------------------------------------
+    # ---- Sec. 3.1.2 -----------------------------------------------------------------------
     def grid_assign(self, pos, n: int, box: float, scheme: int = TSC, supersample: int = 2, fine_out=None,
                     n_obs=None, stream=None, check=True):
         """n_obs [n,n,n] float64 (torch, on the device) from positions pos [N_gal,3] float64."""
@@ -268,7 +268,7 @@ class Context:
             raise WfError(st, "wf_grid_assign")
         return n_obs if check else (st, n_obs)
 
-    # ---- Sec. 2.3-2.4 -------------------------------------------------------------------
+    # ---- Sec. 3.1.3-3.2 -------------------------------------------------------------------
     def build_noise(self, sel, n_obs, n_gal: int, box: float, stream=None, want_d=True, check=True):
         """(w, d, b, nbar): window, data and R^T N^-1 d on the device; nbar on the host."""
         import torch
@@ -285,7 +285,7 @@ class Context:
             raise WfError(st, "wf_build_noise")
         return (w, d, b, nb.value) if check else (st, w, d, b, nb.value)
 
-    # ---- Sec. 2.3: the 3D mask from a sky map ---------------------------------------------
+    # ---- Sec. 3.1.3: the 3D mask from a sky map ---------------------------------------------
     def project_mask(self, sky, n: int, box: float, alpha0: float, dalpha: float, delta0: float, ddelta: float,
                      observer, dr: float, wr, want_counts=False, stream=None):
         """The 3D mask [n, n, n] from the sky map sky [n_delta, n_alpha] (device FP64) and the radial
@@ -329,7 +329,7 @@ class Context:
             raise WfError(st, "wf_jackknife_masses")
         return out
 
-    # ---- Sec. 5: the inverse-weighting estimator -----------------------------------------
+    # ---- Sec. 4: the inverse-weighting estimator -----------------------------------------
     def selection_eval(self, sel, pos, reciprocal=False, stream=None):
         """w (or 1 / w, 0 where w = 0) at positions pos [m, 3] (device FP64) with the window's
         formula (wf_selection_eval)."""
@@ -359,7 +359,7 @@ class Context:
             raise WfError(st, "wf_grid_assign_weighted")
         return n_obs if check else (st, n_obs)
 
-    # ---- Sec. 2.5.1 ---------------------------------------------------------------------
+    # ---- Sec. 3.3.1 ---------------------------------------------------------------------
     def solve(self, w, nbar: float, b, box: float, pk_k, pk_p, tol=1e-6, max_iter=5000, prec=FP64,
               inner_tol=0.0, precond=1, s_out=None, stream=None, check=True):
         """(s, info): Wiener mean s solving (S^-1 + nbar diag(w)) s = b."""
@@ -451,7 +451,7 @@ class Context:
         return st, outs, list(infos)
 
     # ---- tracing ------------------------------------------------------------------------
-    # ---- Sec. 5.1 and 6.2: evaluation of a reconstruction ---------------------------------
+    # ---- Sec. 4.1 and 5.5: evaluation of a reconstruction ---------------------------------
     def smooth(self, field, box: float, r_s: float, out=None, stream=None):
         """Field convolved with the normalised Gaussian of radius r_s (box units) on the periodic
         grid (wf_smooth); FP64 [n,n,n] device tensors, out may be field."""

@@ -1,4 +1,4 @@
-// wf_assign.cu -- supersampled mass assignment (Sec. 2.2 of Kitaura et al. 2009, Eq. def:ngrid).
+// wf_assign.cu -- supersampled mass assignment (Sec. 3.1.2 of Kitaura et al. 2009, Eq. def:ngrid).
 //
 // Step 1: each galaxy is placed on the fine grid (s n)^3 with CIC or TSC weights in fixed
 //         point (Q16 per axis, product Q48) by 64-bit integer atomics, so the fine grid is
@@ -76,7 +76,7 @@ k_assign(const double* __restrict__ pos, long long n_gal, long long nf, double s
     }
 }
 
-// Weighted assignment for the inverse-weighting estimator (Sec. 5, Eq. def:ngrid with galaxy
+// Weighted assignment for the inverse-weighting estimator (Sec. 4, Eq. def:ngrid with galaxy
 // mass wgt[g], e.g. 1 / w): each node contribution is the Q48 weight times wgt[g], rounded once
 // to the nearest Q32 unit, so the grid is exact and independent of the order of the atomics.
 __global__ void __launch_bounds__(256)

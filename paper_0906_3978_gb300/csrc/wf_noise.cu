@@ -1,5 +1,5 @@
 // wf_noise.cu -- 3D window, mean density, data and noise diagonals
-// (Kitaura et al. 2009, Sec. 2.3 and Sec. 2.4: Eqs. eq:datamodel, eq:nmean, eq:noiseav).
+// (Kitaura et al. 2009, Sec. 3.1.3 and Sec. 3.2: Eqs. eq:datamodel, eq:nmean, eq:noiseav).
 //
 //   w    = [in cone] * [outside every hole] * f(r) at node x = i H (no periodic wrap)
 //   nbar = N_gal / sum(w)               (galaxies per cell; the observed volume in cells)
@@ -188,7 +188,7 @@ wf_status add_scaled_run(Ctx& c, int64_t n, const double* s, double f, double* a
 }
 
 // ------------------------------------------------------------------------------------------
-// Projection of a sky completeness map along rays (Sec. 2.3, Eq. eq:transf): sample (j, i, k) is
+// Projection of a sky completeness map along rays (Sec. 3.1.3, Eq. eq:transf): sample (j, i, k) is
 // the point o + r_k u_ij, r_k = (k + 1/2) dr, u = (cos d cos a, cos d sin a, sin d) with the
 // pixel-centre cosines and sines from the host; its nearest-grid-point cell receives the pixel's
 // sky value and the radial table's value in Q32 fixed point (integer atomics: exact, any order)

@@ -1,4 +1,4 @@
-// wf_plane.cuh -- the middle of the Wiener matvec (Sec. 2.5.1: the data term R^T N^-1 R applied
+// wf_plane.cuh -- the middle of the Wiener matvec (Sec. 3.3.1: the data term R^T N^-1 R applied
 // between the inverse and forward transforms of the signal) on one x-plane at a time, held in
 // the distributed shared memory of a thread-block cluster:
 //

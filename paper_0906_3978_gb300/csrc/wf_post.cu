@@ -1,6 +1,6 @@
 // wf_post.cu -- the steps around the solve (Kitaura et al. 2009): the redshift-distortion factor
-// and the deconvolution B^-1 Z^-1 of Sec. 3 (Eq. eq:DEC), and the evaluation of a reconstruction of
-// Sec. 5.1 "Statistical correlation measures" and Sec. 6.2 "Statistical analysis": Gaussian
+// and the deconvolution B^-1 Z^-1 of Sec. 3.3.2 (Eq. eq:DEC), and the evaluation of a reconstruction of
+// Sec. 4.1 "Statistical correlation measures" and Sec. 5.5 "Statistics of the density field": Gaussian
 // smoothing (both Fourier multipliers dispatch to the per-size FP64 transform passes), the
 // correlation coefficient, Euclidean and normalised
 // Kullback-Leibler distances, and binned density statistics per radial shell and observed /
@@ -22,7 +22,7 @@ namespace wf {
 constexpr int kPostBlocks = 152 * 4;  // grid of the sweeps (per-block partials)
 
 // ------------------------------------------------------------------------------------------
-// Sec. 5.1: sums of t r, t^2, r^2, (r - t)^2, (1 + r) log((1 + r) / (1 + t)) (where both
+// Sec. 4.1: sums of t r, t^2, r^2, (r - t)^2, (1 + r) log((1 + r) / (1 + t)) (where both
 // 1 + delta > 0) and the count of the cells left out of the last one.  6 partials per block.
 // ------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
@@ -63,7 +63,7 @@ __global__ void k_compare_fin(const double* __restrict__ partials, int nblk, dou
 }
 
 // ------------------------------------------------------------------------------------------
-// Sec. 6.2: counts of 1 + delta per (shell, region, bin); slot n_bins holds the values below the
+// Sec. 5.5: counts of 1 + delta per (shell, region, bin); slot n_bins holds the values below the
 // bins, slot n_bins + 1 those above.  Shared-memory counters per block, flushed with 64-bit
 // atomics.  grid-stride over the n^3 nodes (n^3 < 2^31).
 // ------------------------------------------------------------------------------------------
@@ -202,7 +202,7 @@ wf_status smooth_run(Ctx& c, const wf_grid& g, const double* in, double r_s, dou
   return multiply_fourier(c, g.n, in, out, t, st);
 }
 
-// <K D>_mu of Sec. 3 ("Redshift distortion operator"): the mean over mu in [0, 1] of
+// <K D>_mu of Sec. 3.3.3 ("Redshift distortion operator"): the mean over mu in [0, 1] of
 // (1 + beta mu^2)^2 / (1 + a mu^2), a = k^2 sigma_v^2 / 2.  Dividing the numerator by 1 + a mu^2
 // gives beta^2 / (3a) + 2 beta / a - beta^2 / a^2 + (1 - beta / a)^2 atan(sqrt a) / sqrt a; for
 // a < 1/2, where those terms cancel, the power series sum_j (-a)^j (1/(2j+1) + 2 beta/(2j+3) +

@@ -1,4 +1,4 @@
-// wf_solver_impl.cuh -- drivers of the Wiener solve (Kitaura et al. 2009, Sec. 2.5.1, Eq. eq:WF).
+// wf_solver_impl.cuh -- drivers of the Wiener solve (Kitaura et al. 2009, Sec. 3.3.1, Eq. eq:WF).
 //
 // System: A s = b with A = S^-1 + diag(nbar w), S^-1 = F^-1 diag(dV/P(k)) F, b = R^T N^-1 d.
 //
@@ -672,7 +672,7 @@ struct GroupMixed : GroupCommon<N> {
 };
 
 // out = F^-1 [g(|m|^2) F in] for one FP64 field, with the multiplier given as a table over
-// n2 = |m|^2 (3 (N/2)^2 + 1 entries): the Gaussian smoothing of Sec. 6.2 and the deconvolution
+// n2 = |m|^2 (3 (N/2)^2 + 1 entries): the Gaussian smoothing of Sec. 4.1 and the deconvolution
 // B^-1 Z^-1 of Eq. eq:DEC.  The x pass applies the table as it applies the prior; the transforms
 // are the solver's FP64 passes.  in may equal out.
 template <int N>

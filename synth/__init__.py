@@ -6,7 +6,7 @@ low-pass, no window at the nodes, no noise model, no solve); the thinning of the
 galaxies by the survey selection is the simulated survey itself, done here at each
 galaxy's continuous position with its own code.
 
-Recipe (stand-in for the paper's SDSS DR6 and Millennium-mock workloads, Sec. 3 and 4,
+Recipe (stand-in for the paper's SDSS DR6 and Millennium-mock workloads, Sec. 2 and 4,
 which are not available):
   * Gaussian field G on the N^3 grid: unit white noise filtered in Fourier space by
     sqrt(P(k)/dV) (so <|G_k|^2> = V_c P(k)/dV), mean mode removed, optional spherical cut

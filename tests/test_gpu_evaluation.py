@@ -1,4 +1,4 @@
-"""GPU evaluation steps (Sec. 5.1 quality measures, Sec. 6.2 smoothing and density statistics)
+"""GPU evaluation steps (Sec. 4.1 quality measures and smoothing, Sec. 5.5 density statistics)
 against the evaluation oracle, through the C ABI, on seeded synthetic fields.
 
 Tolerances: smoothing relative L2 1e-13 (FP64 transforms on both sides, different orders); the
@@ -133,7 +133,7 @@ def test_evaluation_argument_errors(ctx):
     assert e.value.status == wf.ERR_UNSUPPORTED
 
 
-# ------------------------------------------------------------------ inverse weighting (Sec. 5)
+# ------------------------------------------------------------------ inverse weighting (Sec. 4)
 import oracle  # noqa: E402
 import synth  # noqa: E402
 
@@ -187,7 +187,7 @@ def test_weighted_grid_rejects_bad_weights(ctx):
         assert st == wf.ERR_ARG
 
 
-# ------------------------------------------------------------------ deconvolution (Sec. 3, eq:DEC)
+# ------------------------------------------------------------------ deconvolution (Sec. 3.3.2, eq:DEC)
 @pytest.mark.parametrize("n,box,beta,sv,b", [(16, 64.0, 0.42, 5.0, 1.0), (24, 47.0, 0.6, 3.0, 1.3),
                                             (48, 94.0, 0.42, 5.0, 0.8)])
 def test_deconvolution_matches_oracle(ctx, n, box, beta, sv, b):
@@ -269,7 +269,7 @@ def test_sd_wiener_filter_flat_prior_end_to_end(ctx):
     assert rl2(host(s), ref) <= 1e-10
 
 
-# ------------------------------------------------------------------ sky-mask projection (Sec. 2.3)
+# ------------------------------------------------------------------ sky-mask projection (Sec. 3.1.3)
 def _sky_case(seed, n_alpha, n_delta):
     rng = np.random.default_rng(seed)
     sky = np.clip(0.6 + 0.3 * rng.standard_normal((n_delta, n_alpha)), 0.0, 1.0)
@@ -301,7 +301,7 @@ def test_mask_projection_rejects_bad_values(ctx):
     assert e.value.status == wf.ERR_ARG
 
 
-# ------------------------------------------------------------------ Z and B inside R (Sec. 3)
+# ------------------------------------------------------------------ Z and B inside R (Sec. 3.3.2)
 @pytest.mark.parametrize("n,prec", [(16, wf.FP64), (32, wf.FP64), (32, wf.MIXED)])
 def test_solve_response_matches_the_literal_system(ctx, n, prec):
     """The library solves the redshift-prior system and deconvolves; the oracle runs textbook CG on
@@ -353,7 +353,7 @@ def test_mask_projection_degenerate_geometry(ctx):
         assert c_ref.sum() == n_r
 
 
-# ------------------------------------------------------------------ Jackknife ensemble (App. A)
+# ------------------------------------------------------------------ Jackknife ensemble (Sec. 3.4)
 def test_jackknife_ensemble_matches_oracle(ctx):
     """Three subsamples at 32^3, each solved to residual 1e-12 on both sides: the mean within
     1e-7 relative L2 (kappa x tol, kappa up to ~1e5 here: D reaches ~110 where N'' is small)."""

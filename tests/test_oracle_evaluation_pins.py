@@ -1,4 +1,4 @@
-"""Pins of the evaluation oracle (Sec. 5.1 and Sec. 6.2: Gaussian smoothing, correlation and
+"""Pins of the evaluation oracle (Sec. 4.1 and Sec. 5.5: Gaussian smoothing, correlation and
 distance measures, binned density statistics) against closed forms and hand-worked cases."""
 import math
 
@@ -114,7 +114,7 @@ def test_moments_empty_region_is_nan():
     assert mom[0] == 0 and np.all(np.isnan(mom[1:]))
 
 
-# ---------------------------------------------------------------- inverse weighting (Sec. 5)
+# ---------------------------------------------------------------- inverse weighting (Sec. 4)
 import oracle  # noqa: E402
 import synth  # noqa: E402
 
@@ -172,7 +172,7 @@ def test_inverse_weighting_uniform_selection():
     assert np.max(np.abs(fw - f / c)) <= 1e-8
 
 
-# ---------------------------------------------------------------- redshift distortions (Sec. 3)
+# ---------------------------------------------------------------- redshift distortions (Sec. 3.3.2-3.3.3)
 @pytest.mark.parametrize("beta", [0.0, 0.42, 1.0])
 def test_rsd_factor_limits(beta):
     """k = 0 or sigma_v = 0: the angle-averaged Kaiser factor 1 + 2 beta / 3 + beta^2 / 5;
@@ -205,7 +205,7 @@ def test_deconvolution_plane_wave_and_bias():
 # ---------------------------------------------------------------- signal-dependent noise
 def test_sd_noise_reduces_to_the_lsq_noise():
     """lambda = nbar everywhere: the diagonal is nbar w and the right-hand side nbar d, the LSQ
-    Wiener filter's (Sec. 2.4, eq:noiseav)."""
+    Wiener filter's (Sec. 3.2, eq:noiseav)."""
     pr = synth.problem("c1", n_override=16, cache=False)
     nobs = oracle.lowpass(oracle.assign(pr.pos, 16, pr.box, pr.scheme, 2), 16, 2)
     w = oracle.window(pr.sel, 16, pr.box)
@@ -241,7 +241,7 @@ def test_jackknife_masses_rule_and_unbiasedness():
     assert abs(tot.mean() - np.sum(1.0 / wg)) <= 4 * sigma
 
 
-# ---------------------------------------------------------------- sky-mask projection (Sec. 2.3)
+# ---------------------------------------------------------------- sky-mask projection (Sec. 3.1.3)
 def test_mask_single_ray():
     """One pixel on the +x axis, samples every 0.25 cells: 4 samples per crossed cell (2 in the
     first, which the ray enters half way), the mask is sky value x radial value."""
@@ -272,7 +272,7 @@ def test_mask_uniform_sky_is_the_hit_indicator():
     assert np.array_equal(w > 0, c > 0) and np.all(w[c > 0] == 1.0)
 
 
-# ------------------------------------------------------------------ Z and B inside R (Sec. 3)
+# ------------------------------------------------------------------ Z and B inside R (Sec. 3.3.2)
 def _response_case(n, seed, box=60.0):
     rng = np.random.default_rng(seed)
     k, p = synth.lcdm_table()
@@ -368,7 +368,7 @@ def test_mask_counts_match_exact_geometry_away_from_cell_faces():
     assert abs(int(c.sum()) - int(exact.sum())) <= np.count_nonzero(near)
 
 
-# ------------------------------------------------------------------ Jackknife ensemble (App. A)
+# ------------------------------------------------------------------ Jackknife ensemble (Sec. 3.4)
 def _jk_case(n=16):
     pr = synth.problem("c1", n_override=n, cache=False)
     nobs = oracle.lowpass(oracle.assign(pr.pos, n, pr.box, pr.scheme, 2), n, 2)

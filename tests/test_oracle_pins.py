@@ -326,7 +326,7 @@ def test_cg_noiseless_limit():
 
 
 def test_unobserved_cells_carry_no_data():
-    """Sec. 4 'Cluster prediction': data in w = 0 cells never reaches the solution."""
+    """Sec. 5.4 'Cluster prediction': data in w = 0 cells never reaches the solution."""
     pr = synth.problem("c1", n_override=16, n_gal_override=3000, cache=False)
     fine = oracle.assign(pr.pos, 16, pr.box, pr.scheme, 2)
     nobs = oracle.lowpass(fine, 16, 2)
