@@ -86,3 +86,28 @@ def test_product_path_never_loads_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(d, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b|liboracle|oracle\.c", src, re.M), f
+
+
+def test_header_is_plain_c_and_links(lib):
+    """include/wf.h compiles as strict C11 without warnings, and a C program links against the
+    library and calls a host-only entry point (no GPU needed)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    d = os.path.join(ROOT, "paper_0906_3978_gb300", "_build", "ctest")
+    os.makedirs(d, exist_ok=True)
+    src = os.path.join(d, "use.c")
+    with open(src, "w") as f:
+        f.write('#include "wf.h"\n#include <stdio.h>\n'
+                'int main(void) { printf("%s %d\\n", wf_status_string(WF_ERR_ARG), wf_supported_size(384)); '
+                'return 0; }\n')
+    libdir = os.path.join(ROOT, "paper_0906_3978_gb300")
+    exe = os.path.join(d, "use")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        src, "-L", libdir, "-lwf", "-Wl,-rpath," + libdir, "-o", exe],
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0 and out.stdout.split() == ["invalid", "argument", "1"]
