@@ -111,15 +111,20 @@ typedef struct {
 /* ---- context ------------------------------------------------------------------------ */
 
 /* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device memory the
- * context may hold for workspaces (0 = no cap).  *ctx receives the handle. */
+ * context may hold for workspaces (0 = no cap).  *ctx receives the handle (NULL on failure); the
+ * caller owns it and frees it with wf_destroy.
+ * Errors: WF_ERR_ARG (ctx NULL, no such device), WF_ERR_CUDA (no CUDA device, or the pinned
+ * host buffer could not be allocated). */
 wf_status wf_create(wf_ctx** ctx, int device, size_t hbm_budget_bytes);
 
-/* Free every workspace, plan and the serving thread of ctx.  Waits for its device work. */
+/* Free every workspace, plan and the serving thread of ctx.  Waits for its device work; serving
+ * requests not yet finished are dropped with the scheduler.  Errors: WF_ERR_ARG (ctx NULL). */
 wf_status wf_destroy(wf_ctx* ctx);
 
-/* 1 if grid size n is compiled into this library, else 0. */
+/* 1 if grid size n is compiled into this library, else 0.  Host only, never fails. */
 int wf_supported_size(int n);
 
+/* A static description of status s ("unknown status" for values outside wf_status). */
 const char* wf_status_string(wf_status s);
 
 /* Text of the last CUDA error seen by this thread (empty string if none). */
@@ -133,7 +138,7 @@ const char* wf_last_error(void);
  * does all three, holding the plane in the cluster's distributed shared memory (fewer HBM
  * bytes, but on GB300 it measures slower than the three passes).  Both compute the same
  * operator with the same arithmetic; the choice affects speed and, where the radix plans
- * differ, the FP32 rounding.  Applies to solves started after the call. */
+ * differ, the FP32 rounding.  Applies to solves started after the call.  Errors: WF_ERR_ARG. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
 /* ---- the 3D mask from a sky completeness map (Sec. 3.1.3) ------------------------------------ */
@@ -304,15 +309,17 @@ wf_status wf_density_stats(wf_ctx* ctx, const wf_grid* grid, const double* delta
 /* Reset the context's launch counters and enable (1) or disable (0) per-kernel timing.
  * Every kernel launch is counted; while enabled, each launch is bracketed by CUDA events on
  * its stream and attributed to a kernel class (e.g. "cg_xinv", "ypass", "zturn") together
- * with its algorithmic bytes (the DRAM traffic the pass cannot avoid). */
+ * with its algorithmic bytes (the DRAM traffic the pass cannot avoid).  While enabled, CG blocks
+ * run as direct launches instead of CUDA graphs.  Errors: WF_ERR_ARG. */
 wf_status wf_profile(wf_ctx* ctx, int enable);
 
 /* Launches since the last wf_profile call and the number of kernel classes recorded.
- * Waits for the recorded events. */
+ * Waits for the recorded events.  Errors: WF_ERR_ARG (NULL arguments). */
 wf_status wf_profile_read(wf_ctx* ctx, int64_t* launches, int* n_classes);
 
 /* Class i (0 <= i < n_classes): name (NUL-terminated, truncated to name_len), timed launches,
- * summed device milliseconds and summed algorithmic bytes. */
+ * summed device milliseconds and summed algorithmic bytes.  Errors: WF_ERR_ARG (i out of range,
+ * NULL arguments). */
 wf_status wf_profile_class(wf_ctx* ctx, int i, char* name, int name_len, int64_t* launches,
                            double* total_ms, double* bytes);
 
@@ -371,7 +378,10 @@ wf_status wf_build_noise_noalloc(const wf_grid* grid, const wf_selection* sel, c
  *   b     dev double [n^3]  right-hand side R^T N^-1 d
  *   s_out dev double [n^3]  solution
  *   info  host out (filled on success and on NOT_CONVERGED/BREAKDOWN)
- * The stop test recomputes ||b - A s|| in FP64 from the returned s.  Waits for completion. */
+ * The stop test recomputes ||b - A s|| in FP64 from the returned s.  Waits for completion.
+ * Errors: WF_ERR_ARG (bad grid, power table, tolerances; an empty window; non-finite w or b),
+ * WF_ERR_UNSUPPORTED, WF_ERR_OOM, WF_ERR_CUDA, WF_ERR_NOT_CONVERGED (max_iter reached; s_out holds
+ * the last iterate), WF_ERR_BREAKDOWN. */
 wf_status wf_solve(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const double* w,
                    double nbar, const double* b, const wf_solve_opts* opts, double* s_out,
                    wf_solve_info* info, void* stream);
