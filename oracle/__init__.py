@@ -15,6 +15,7 @@ Each function follows the paper (Kitaura et al. 2009, arXiv:0906.3978):
   build_noise Sec. 3.2, Eqs. eq:datamodel, eq:nmean, eq:noiseav
   sinv_table  Sec. 3.3.1, Fourier-diagonal prior S
   matvec/cg   Sec. 3.3.1, Eq. eq:WF, by a Krylov (CG) inversion
+  pcg         the same Krylov inversion with a Fourier-diagonal preconditioner
 
 Parity is pinned by the ``-m "not gpu"`` tests (closed forms, dense direct solve, brute
 force, invariants); see tests/test_oracle_pins.py.
@@ -72,6 +73,7 @@ def lib():
         L.oracle_fft3d.argtypes = [ctypes.c_void_p, i, i]
         L.oracle_matvec.argtypes = [i, dp, d, dp, dp, dp]
         L.oracle_cg.argtypes = [i, dp, d, dp, dp, d, i, dp, ip, dp]
+        L.oracle_pcg.argtypes = [i, dp, dp, d, dp, dp, d, i, dp, ip, dp]
         L.oracle_threads.restype = i
         L.oracle_set_threads.restype = None
         _lib = L
@@ -249,4 +251,21 @@ def cg(table, nbar: float, w, b, tol: float = 1e-12, max_iter: int = 100000, all
                          _dp(x), ctypes.byref(it), ctypes.byref(rel))
     if not (allow_unconverged and st == ERR_NOT_CONVERGED):
         _check(st, "cg")
+    return x, it.value, rel.value
+
+
+def pcg(table, ptable, nbar: float, w, b, tol: float = 1e-12, max_iter: int = 100000, allow_unconverged=False):
+    """(x, iters, rel_residual) of preconditioned CG with M^-1 = F^-1 diag(ptable[|k|^2]) F;
+    ptable = 1 everywhere is textbook CG.  Raises like ``cg``."""
+    n = b.shape[0]
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    ptable = np.ascontiguousarray(ptable, dtype=np.float64)
+    x = np.empty_like(b)
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    st = lib().oracle_pcg(n, _dp(np.ascontiguousarray(table)), _dp(ptable), nbar, _dp(w), _dp(b), tol, max_iter,
+                          _dp(x), ctypes.byref(it), ctypes.byref(rel))
+    if not (allow_unconverged and st == ERR_NOT_CONVERGED):
+        _check(st, "pcg")
     return x, it.value, rel.value

@@ -641,6 +641,108 @@ done:
   return st;
 }
 
+/* z = M^-1 r with M^-1 = F^-1 diag(ptable(|k|^2)) F / V_c: a real, even Fourier multiplier,
+ * applied with the same FFT as the matvec. */
+static int fourier_apply(int n, const double* ptable, const double* r, double* z) {
+  size_t N = (size_t)n, V = N * N * N;
+  cplx* a = (cplx*)malloc(V * sizeof(cplx));
+  if (!a) return OR_ERR_OOM;
+  for (size_t i = 0; i < V; ++i) a[i] = r[i];
+  int st = oracle_fft3d(a, n, -1);
+  if (st == OR_OK) {
+    for (size_t ix = 0; ix < N; ++ix)
+      for (size_t iy = 0; iy < N; ++iy)
+        for (size_t iz = 0; iz < N; ++iz) {
+          long kx = sfreq((long)ix, (long)N), ky = sfreq((long)iy, (long)N), kz = sfreq((long)iz, (long)N);
+          a[(ix * N + iy) * N + iz] *= ptable[kx * kx + ky * ky + kz * kz];
+        }
+    st = oracle_fft3d(a, n, +1);
+  }
+  if (st == OR_OK)
+    for (size_t i = 0; i < V; ++i) z[i] = creal(a[i]) / (double)V;
+  free(a);
+  return st;
+}
+
+/* Preconditioned CG (Hestenes-Stiefel with a preconditioner M) on A x = b from x0 = 0, where
+ * M^-1 = F^-1 diag(ptable) F is Fourier-diagonal (ptable indexed by n2 = |k|^2 like the prior
+ * table, entries > 0).  The paper names only a Krylov-space inversion (Sec. 1, 3.3.1); a
+ * Fourier-diagonal preconditioner keeps the same Krylov method on the same canonical system, and
+ * with ptable = 1 every step is that of oracle_cg.  Each iteration:
+ *   q = A p;  alpha = <r, z> / <p, q>;  x += alpha p;  r -= alpha q;  z = M^-1 r;
+ *   beta = <r', z'> / <r, z>;  p = z + beta p      (p0 = z0 = M^-1 b).
+ * Stop test as oracle_cg: the true relative residual ||b - A x|| / ||b|| <= tol, recomputed when
+ * the recurrence residual ||r|| reaches tol, with r replaced and p restarted if it has not. */
+int oracle_pcg(int n, const double* table, const double* ptable, double nbar, const double* w, const double* b,
+               double tol, int max_iter, double* x, int* iters_out, double* rel_res_out) {
+  size_t V = (size_t)n * n * n;
+  double *r = (double*)malloc(V * sizeof(double)), *p = (double*)malloc(V * sizeof(double)),
+         *q = (double*)malloc(V * sizeof(double)), *z = (double*)malloc(V * sizeof(double));
+  int st = OR_OK, it = 0;
+  double rel = 0.0;
+  if (!r || !p || !q || !z) {
+    st = OR_ERR_OOM;
+    goto done;
+  }
+  double bb = dot(b, b, V);
+  for (size_t i = 0; i < V; ++i) {
+    x[i] = 0.0;
+    r[i] = b[i];
+  }
+  if (bb == 0.0) goto done;
+  st = fourier_apply(n, ptable, r, z);
+  if (st) goto done;
+  for (size_t i = 0; i < V; ++i) p[i] = z[i];
+  double rz = dot(r, z, V), rr = bb;
+  for (;;) {
+    if (rr <= tol * tol * bb) { /* recompute the true residual */
+      st = oracle_matvec(n, table, nbar, w, x, q);
+      if (st) goto done;
+      for (size_t i = 0; i < V; ++i) r[i] = b[i] - q[i];
+      rr = dot(r, r, V);
+      rel = sqrt(rr / bb);
+      if (rel <= tol) break;
+      st = fourier_apply(n, ptable, r, z);
+      if (st) goto done;
+      for (size_t i = 0; i < V; ++i) p[i] = z[i];
+      rz = dot(r, z, V);
+    }
+    if (it >= max_iter) {
+      rel = sqrt(rr / bb);
+      st = OR_ERR_NOT_CONVERGED;
+      break;
+    }
+    st = oracle_matvec(n, table, nbar, w, p, q);
+    if (st) goto done;
+    double pq = dot(p, q, V);
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st = OR_ERR_BREAKDOWN;
+      break;
+    }
+    double alpha = rz / pq;
+    for (size_t i = 0; i < V; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * q[i];
+    }
+    st = fourier_apply(n, ptable, r, z);
+    if (st) goto done;
+    double rz_new = dot(r, z, V);
+    double beta = rz_new / rz;
+    rz = rz_new;
+    rr = dot(r, r, V);
+    for (size_t i = 0; i < V; ++i) p[i] = z[i] + beta * p[i];
+    ++it;
+  }
+done:
+  if (iters_out) *iters_out = it;
+  if (rel_res_out) *rel_res_out = rel;
+  free(r);
+  free(p);
+  free(q);
+  free(z);
+  return st;
+}
+
 /* Sets the number of OpenMP threads for the following calls (no effect without OpenMP). */
 void oracle_set_threads(int n) {
 #ifdef _OPENMP

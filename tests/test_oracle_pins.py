@@ -243,6 +243,38 @@ def test_sinv_table_power_law_closed_form():
     assert np.allclose(t[1:], (box / n) ** 3 / (3.0 * kk ** -1.5), rtol=1e-12)
 
 
+def test_sinv_table_broken_power_law_by_hand():
+    """A three-segment broken power law with slopes +1, -2, -3 and breakpoints at k = 0.1, 0.4,
+    1.6, 3.2 h/Mpc: log-log interpolation is exact inside each segment, so every entry equals the
+    piecewise law written out by hand, including n2 exactly at each breakpoint (the grid's k is
+    built with the same operations as the table's), below the first point (extrapolated with the
+    first segment) and above the last (extrapolated with the last).  An off-by-one in the segment
+    search or a clamped end would put the wrong slope on some n2 and fail."""
+    n = 128
+    box = 40.0 * np.pi                            # 2 pi / L = 0.05 h/Mpc; kmax = 0.05 sqrt(3 * 64^2) = 5.5
+    kf = 2.0 * np.pi / box
+    n2_break = np.array([4, 64, 1024, 4096])      # k = 0.1, 0.4, 1.6, 3.2 (up to one rounding of kf)
+    pk_k = kf * np.sqrt(n2_break.astype(np.float64))
+    pk_p = np.array([100.0, 400.0, 25.0, 3.125])  # slopes +1, -2, -3 between the points
+    t = oracle.sinv_table(n, box, pk_k, pk_p)
+    n2 = np.arange(t.size)
+    k = kf * np.sqrt(n2.astype(np.float64))
+    seg = np.searchsorted(n2_break, n2, side="left") - 1   # n2 == break: the segment ending there
+    seg = np.clip(seg, 0, 2)
+    slope = np.array([1.0, -2.0, -3.0])[seg]
+    P = pk_p[seg] * (k / pk_k[seg]) ** slope
+    dV = (box / n) ** 3
+    assert t[0] == 0.0
+    assert np.allclose(t[1:], dV / P[1:], rtol=1e-12, atol=0)
+    # the cases the docstring names are all present
+    assert n2[1] < 4 and t.size - 1 > 4096
+    for j, p in zip(n2_break, pk_p):
+        assert abs(t[j] - dV / p) <= 1e-13 * (dV / p)
+    # hand values: k = 0.05 (below the table), 0.2, 0.8, 2.4 (inside segments 1-3), 4.0 (above it)
+    for j, p in [(1, 50.0), (16, 200.0), (256, 100.0), (2304, 25.0 / 3.375), (6400, 1.6)]:
+        assert abs(t[j] - dV / p) <= 1e-12 * (dV / p), (j, dV / t[j], p)
+
+
 # ----------------------------------------------------------------------------- operator/CG
 def _small_problem(n=8, seed=0, uniform=False, nbar=0.7):
     rng = np.random.default_rng(seed)
@@ -341,6 +373,78 @@ def test_unobserved_cells_carry_no_data():
     x2 = oracle.cg(t, nbar2, w, b2, tol=1e-12)[0]
     assert np.array_equal(x1, x2)
     assert np.abs(x1[w == 0]).max() > 0            # the prior extrapolates into the gaps
+
+
+def _dense_fourier_multiplier(n, table):
+    """M_ij = (1/V_c) sum_k table(|k|^2) cos(k.(x_i - x_j)): the dense form of a Fourier-diagonal
+    operator, built by cosine sums (no FFT)."""
+    return _dense_operator(n, table, 0.0, np.zeros((n, n, n)))
+
+
+def _prior_preconditioner(table, nbar, w):
+    """The Fourier-diagonal preconditioner of the GPU's split-preconditioned CG, c^2 with
+    c = S^(1/2) off k = 0 and c_0^2 = V_c / (nbar sum w) at k = 0."""
+    p = np.empty_like(table)
+    p[1:] = 1.0 / table[1:]
+    p[0] = w.size / (nbar * w.sum())
+    return p
+
+
+def test_pcg_unit_preconditioner_is_textbook_cg():
+    """ptable = 1 makes z = r (up to one FFT round trip), so every iterate is textbook CG's."""
+    t, nbar, w, b, _ = _small_problem(n=12, seed=11)
+    for k in (1, 4, 15):
+        x1 = oracle.cg(t, nbar, w, b, tol=1e-15, max_iter=k, allow_unconverged=True)[0]
+        x2 = oracle.pcg(t, np.ones_like(t), nbar, w, b, tol=1e-15, max_iter=k, allow_unconverged=True)[0]
+        assert np.linalg.norm(x2 - x1) <= 1e-12 * np.linalg.norm(x1)
+
+
+def test_pcg_exact_preconditioner_solves_in_one_step():
+    """w = 1 makes A Fourier-diagonal, A = F^-1 diag(S^-1 + nbar) F; with M^-1 = A^-1 the first PCG
+    step lands on the solution, the closed form s_k = b_k / (S^-1(k) + nbar)."""
+    n = 16
+    t, nbar, w, b, _ = _small_problem(n=n, seed=12, uniform=True, nbar=0.35)
+    x, it, rel = oracle.pcg(t, 1.0 / (t + nbar), nbar, w, b, tol=1e-12)
+    assert it == 1 and rel <= 1e-12
+    f = np.fft.fftfreq(n, 1.0 / n).astype(int)
+    n2 = f[:, None, None] ** 2 + f[None, :, None] ** 2 + f[None, None, :] ** 2
+    ref = np.real(np.fft.ifftn(np.fft.fftn(b) / (t[n2] + nbar)))
+    assert np.linalg.norm(x - ref) <= 1e-13 * np.linalg.norm(ref)
+
+
+def test_pcg_iterates_minimise_the_energy_error_over_the_krylov_space():
+    """Brute force at 4^3: the k-th PCG iterate is the A-norm-closest point to the solution in
+    K_k(M^-1 A, M^-1 b), i.e. x_k = Q (Q^T A Q)^-1 Q^T b with Q an orthonormal basis of that space
+    (dense A and M^-1 from cosine sums).  A transposed operand, a wrong beta (e.g. <r,r> in place
+    of <r,z>) or an unpreconditioned residual changes x_k."""
+    n = 4
+    t, nbar, w, b, _ = _small_problem(n=n, seed=13)
+    pt = _prior_preconditioner(t, nbar, w)
+    A = _dense_operator(n, t, nbar, w)
+    Mi = _dense_fourier_multiplier(n, pt)
+    bv = b.ravel()
+    v = Mi @ bv
+    K = []
+    for k in range(1, 6):
+        K.append(v)
+        v = Mi @ (A @ v)
+        Q, _ = np.linalg.qr(np.stack(K, 1))
+        ref = Q @ np.linalg.solve(Q.T @ A @ Q, Q.T @ bv)
+        x = oracle.pcg(t, pt, nbar, w, b, tol=1e-15, max_iter=k, allow_unconverged=True)[0]
+        assert np.linalg.norm(x.ravel() - ref) <= 1e-10 * np.linalg.norm(ref), k
+
+
+def test_pcg_matches_dense_cholesky():
+    """The prior preconditioner leaves the solution unchanged: 8^3 against the dense solve."""
+    t, nbar, w, b, _ = _small_problem()
+    A = _dense_operator(8, t, nbar, w)
+    L = np.linalg.cholesky(A)
+    ref = np.linalg.solve(L.T, np.linalg.solve(L, b.ravel()))
+    x, it, rel = oracle.pcg(t, _prior_preconditioner(t, nbar, w), nbar, w, b, tol=1e-13)
+    assert rel <= 1e-13
+    assert np.linalg.norm(x.ravel() - ref) <= 1e-10 * np.linalg.norm(ref)
+    true = np.linalg.norm(b - oracle.matvec(t, nbar, w, x)) / np.linalg.norm(b)
+    assert true <= 1e-13
 
 
 def test_cg_zero_rhs_and_residual_contract():
