@@ -63,7 +63,7 @@ def lib():
         L.oracle_assign_weighted.argtypes = [i, d, i, i, dp, dp, i64, u64p]
         L.oracle_window_at.argtypes = [i64, dp, dp, dp, d, i, dp, i, dp, dp]
         L.oracle_project_mask.argtypes = [i, d, dp, i, i, d, d, d, d, dp, d, i, dp, dp,
-                                          ctypes.POINTER(ctypes.c_int64)]
+                                          ctypes.POINTER(ctypes.c_int64), d, ctypes.POINTER(ctypes.c_int64)]
         L.oracle_lowpass_point.argtypes = [i, i, u64p, i, i, i]
         L.oracle_lowpass_point.restype = d
         L.oracle_window.argtypes = [i, d, dp, dp, d, i, dp, i, dp, dp]
@@ -167,17 +167,26 @@ def window_at(sel, pts) -> np.ndarray:
 
 
 def project_mask(sky, n: int, box: float, alpha0: float, dalpha: float, delta0: float, ddelta: float,
-                 observer, dr: float, wr):
+                 observer, dr: float, wr, face_margin: float = 0.0):
     """(w [n, n, n], counts [n, n, n]): the 3D mask from the sky map sky [n_delta, n_alpha] and the
-    radial completeness wr [n_r] at r_k = (k + 1/2) dr, projected along rays (Sec. 3.1.3)."""
+    radial completeness wr [n_r] at r_k = (k + 1/2) dr, projected along rays (Sec. 3.1.3), each
+    sample's cell decided in exact FP64 geometry.  With face_margin > 0 a third array is returned:
+    per cell, the samples within face_margin cells of a face of this cell or a neighbour's (the
+    samples that a position error below face_margin could move, and the cells they could move
+    between)."""
     sky = np.ascontiguousarray(sky, dtype=np.float64)
     wr = np.ascontiguousarray(wr, dtype=np.float64).ravel()
     obs = np.ascontiguousarray(observer, dtype=np.float64)
     w = np.empty(n ** 3, dtype=np.float64)
     cnt = np.empty(n ** 3, dtype=np.int64)
+    near = np.empty(n ** 3, dtype=np.int64) if face_margin > 0 else None
+    i64p = ctypes.POINTER(ctypes.c_int64)
     _check(lib().oracle_project_mask(n, box, _dp(sky), sky.shape[1], sky.shape[0], alpha0, dalpha, delta0, ddelta,
-                                     _dp(obs), dr, wr.size, _dp(wr), _dp(w),
-                                     cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))), "project_mask")
+                                     _dp(obs), dr, wr.size, _dp(wr), _dp(w), cnt.ctypes.data_as(i64p),
+                                     float(face_margin), near.ctypes.data_as(i64p) if near is not None else None),
+           "project_mask")
+    if near is not None:
+        return w.reshape(n, n, n), cnt.reshape(n, n, n), near.reshape(n, n, n)
     return w.reshape(n, n, n), cnt.reshape(n, n, n)
 
 

@@ -431,16 +431,20 @@ int oracle_window(int n, double box, const double* obs, const double* axis, doub
  * equidistant alpha x delta map has centre alpha_i = alpha0 + (i + 1/2) dalpha, delta_j =
  * delta0 + (j + 1/2) ddelta; its ray from the observer is sampled at r_k = (k + 1/2) dr, k < n_r,
  * at x = o + r_k u with u = (cos delta cos alpha, cos delta sin alpha, sin delta) (Eq. eq:transf);
- * each sample inside the box goes to its nearest-grid-point cell floor(x / H).  The cell is
- * decided in FP32 in cell units: O = fl32(o / H), g = fl32(u dr / H) (FP64 products, one
- * rounding), X = fl32(O + fl32((k + 1/2) g)), cell floor(X) if 0 <= X < n.  Per cell the sky
- * values and the radial completeness values wr[k] of the samples are summed in Q32 fixed point
- * (rint(v 2^32), exact and order-independent) and counted; the mask is
- * (S_sky 2^-32 rc) * (S_r 2^-32 rc) with rc = fl(1 / count), 0 where no sample fell.  sky[j * n_alpha + i],
- * values in [0, 1]; counts may be NULL. */
+ * each sample inside the box goes to its nearest-grid-point cell floor(x / H) (exact geometry in
+ * FP64).  Per cell the sky values and the radial completeness values wr[k] of the samples are
+ * summed in Q32 fixed point (rint(v 2^32), exact and order-independent) and counted; each
+ * projection is normalised by the number of samples ("mask counts") and the two are multiplied:
+ * w = (S_sky 2^-32 / count) * (S_r 2^-32 / count), 0 where no sample fell.  sky[j * n_alpha + i],
+ * values in [0, 1]; counts may be NULL.
+ * near (may be NULL) reports how close the decisions came to a cell face: with face_margin > 0, a
+ * sample whose position x / H lies within face_margin (cell units) of a cell face on some axis adds
+ * 1 to near[] at its own cell and at the cell across each such face (those inside the box).  A
+ * computation of x / H with an error below face_margin can move only those samples, and only
+ * between those cells. */
 int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n_delta, double alpha0,
                         double dalpha, double delta0, double ddelta, const double* obs, double dr, int n_r,
-                        const double* wr, double* w, int64_t* counts) {
+                        const double* wr, double* w, int64_t* counts, double face_margin, int64_t* near) {
   if (n <= 0 || !(box > 0) || n_alpha <= 0 || n_delta <= 0 || !(dr > 0) || n_r <= 0) return OR_ERR_ARG;
   for (int k = 0; k < n_r; ++k)
     if (!(wr[k] >= 0.0 && wr[k] <= 1.0)) return OR_ERR_ARG;
@@ -456,30 +460,57 @@ int oracle_project_mask(int n, double box, const double* sky, int n_alpha, int n
     free(cnt);
     return OR_ERR_OOM;
   }
-  const double H = box / (double)n, q32 = 4294967296.0, step = dr / H;
-  const float ox = (float)(obs[0] / H), oy = (float)(obs[1] / H), oz = (float)(obs[2] / H), nf = (float)n;
+  if (near)
+    for (size_t c = 0; c < V; ++c) near[c] = 0;
+  const double H = box / (double)n, q32 = 4294967296.0;
   for (int j = 0; j < n_delta; ++j) {
     const double de = delta0 + ((double)j + 0.5) * ddelta;
-    const double cd = cos(de), sd = sin(de);
     for (int i = 0; i < n_alpha; ++i) {
       const double v = sky[(size_t)j * n_alpha + i];
       const double al = alpha0 + ((double)i + 0.5) * dalpha;
-      const float gx = (float)(cd * cos(al) * step), gy = (float)(cd * sin(al) * step), gz = (float)(sd * step);
+      const double u[3] = {cos(de) * cos(al), cos(de) * sin(al), sin(de)};
       const uint64_t qs = (uint64_t)rint(v * q32);
       for (int k = 0; k < n_r; ++k) {
-        const float t = (float)k + 0.5f;
-        const float fx = floorf(ox + t * gx), fy = floorf(oy + t * gy), fz = floorf(oz + t * gz);
-        if (!(fx >= 0.0f && fx < nf && fy >= 0.0f && fy < nf && fz >= 0.0f && fz < nf)) continue;
-        const size_t c = ((size_t)fx * n + (size_t)fy) * n + (size_t)fz;
-        ss[c] += qs;
-        sr[c] += (uint64_t)rint(wr[k] * q32);
-        cnt[c] += 1;
+        const double r = ((double)k + 0.5) * dr;
+        double X[3];
+        long f[3];
+        int inside = 1;
+        for (int a = 0; a < 3; ++a) {
+          X[a] = (obs[a] + r * u[a]) / H;
+          const double fa = floor(X[a]);
+          f[a] = (fa >= 0.0 && fa < (double)n) ? (long)fa : -1;
+          if (f[a] < 0) inside = 0;
+        }
+        if (inside) {
+          const size_t c = ((size_t)f[0] * n + (size_t)f[1]) * n + (size_t)f[2];
+          ss[c] += qs;
+          sr[c] += (uint64_t)rint(wr[k] * q32);
+          cnt[c] += 1;
+        }
+        if (near && face_margin > 0.0) {
+          /* the cell and its neighbours across every face within the margin */
+          long lo[3], hi[3];
+          int any = 0;
+          for (int a = 0; a < 3; ++a) {
+            const double fa = floor(X[a]);
+            lo[a] = (long)fa;
+            hi[a] = (long)fa;
+            if (X[a] - fa < face_margin) { lo[a] -= 1; any = 1; }
+            if (fa + 1.0 - X[a] < face_margin) { hi[a] += 1; any = 1; }
+          }
+          if (any)
+            for (long ax = lo[0]; ax <= hi[0]; ++ax)
+              for (long ay = lo[1]; ay <= hi[1]; ++ay)
+                for (long az = lo[2]; az <= hi[2]; ++az)
+                  if (ax >= 0 && ax < n && ay >= 0 && ay < n && az >= 0 && az < n)
+                    near[((size_t)ax * n + (size_t)ay) * n + (size_t)az] += 1;
+        }
       }
     }
   }
   for (size_t c = 0; c < V; ++c) {
-    const double rc = cnt[c] ? 1.0 / (double)cnt[c] : 0.0;
-    w[c] = cnt[c] ? ((double)ss[c] / q32 * rc) * ((double)sr[c] / q32 * rc) : 0.0;
+    const double cn = (double)cnt[c];
+    w[c] = cnt[c] ? ((double)ss[c] / q32 / cn) * ((double)sr[c] / q32 / cn) : 0.0;
     if (counts) counts[c] = cnt[c];
   }
   free(ss);
