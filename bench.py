@@ -63,12 +63,16 @@ class Clocks:
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
+        # nvidia-smi numbers physical GPUs and ignores CUDA_VISIBLE_DEVICES: select the GPU this
+        # process runs on by its UUID instead of the CUDA ordinal
         self.index = index
+        self.uuid = gpu_uuid(index)
         self.p = None
 
     def __enter__(self):
         try:
-            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+            sel = self.uuid if self.uuid else str(self.index)
+            self.p = subprocess.Popen(["nvidia-smi", "-i", sel, "--query-gpu=" + self.Q,
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
@@ -98,7 +102,17 @@ class Clocks:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(self.rows), "gpu_uuid": self.uuid}
+
+
+def gpu_uuid(index):
+    """'GPU-xxxxxxxx-...' of CUDA device `index` (nvidia-smi's form), or None without torch/CUDA."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(index).uuid)
+    except Exception:
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 def dist_init():

@@ -358,10 +358,12 @@ wf_status wf_build_noise(wf_ctx* ctx, const wf_grid* grid, const wf_selection* s
  * capacity limit, or a latency-critical pipeline where cudaMalloc's implicit device-wide
  * synchronisation is unacceptable.  No counterpart in the paper: this is a deployment variant.
  * It takes no context and allocates nothing: its scratch (reduction partials, the nbar
- * scalars, the hole table) is one fixed 14,000-byte array compiled into the library's device
- * image, which every GPU that loads libwf.so holds until the process exits.
+ * scalars, the hole table) is one fixed 17,952-byte array (2244 doubles) compiled into the
+ * library's device image, which every GPU that loads libwf.so holds until the process exits.
  *   - Runs on the current CUDA device.  The first call on each device looks up the scratch
  *     address (cudaGetSymbolAddress); make that first call before any stream capture starts.
+ *     The address is kept per (device, CUDA context id): after cudaDeviceReset the next call
+ *     makes a new lookup in the new context, which again should come before any capture.
  *   - Limit: sel->n_holes <= 256; larger tables return WF_ERR_ARG (see wf_last_error()).
  *   - All calls share the one scratch array: calls that may overlap on the GPU (other streams,
  *     other host threads) race and must be serialised by the caller.  Every scratch word a
@@ -403,8 +405,10 @@ typedef struct {
  * s_g = G s_m, a solve with the redshift-space prior g^2 P(k) followed by the deconvolution
  * s_m = G^-1 s_g (Eq. eq:DEC); that is how it runs.  opts->tol applies to the s_g system, whose
  * residual is G^-1 times the literal one: info->rel_residual is the s_g system's.
- *   w, b, s_out  dev double [n^3] as in wf_solve (s_out may not alias w or b)
- * Errors: as wf_solve, plus WF_ERR_ARG for a bad response or an aliased s_out. */
+ *   w, b, s_out  dev double [n^3] as in wf_solve (s_out may not overlap w or b: it is
+ *                deconvolved in place after the solve)
+ * Errors: as wf_solve, plus WF_ERR_ARG for a bad response or an s_out that shares any byte with
+ * w or b. */
 wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, const wf_response* response,
                             const double* w, double nbar, const double* b, const wf_solve_opts* opts,
                             double* s_out, wf_solve_info* info, void* stream);

@@ -413,7 +413,18 @@ wf_status wf_solve_response(wf_ctx* ctx, const wf_grid* grid, const wf_power* po
   if (info) std::memset(info, 0, sizeof(*info));
   SolveArgs a;
   wf_status s = prepare_solve(grid, power, w, nbar, b, opts, s_out, a);
-  if (s == WF_OK && (s_out == w || s_out == b)) s = WF_ERR_ARG;  // s_out is deconvolved in place
+  // s_out is deconvolved in place after the solve: it must not share a byte with w or b
+  if (s == WF_OK) {
+    const size_t bytes = sizeof(double) * (size_t)grid->n * grid->n * grid->n;
+    const auto overlaps = [bytes](const void* p, const void* q) {
+      const uintptr_t a = reinterpret_cast<uintptr_t>(p), c = reinterpret_cast<uintptr_t>(q);
+      return a < c + bytes && c < a + bytes;
+    };
+    if (overlaps(s_out, w) || overlaps(s_out, b)) {
+      set_last_error("wf_solve_response: s_out overlaps w or b", cudaSuccess);
+      s = WF_ERR_ARG;
+    }
+  }
   std::vector<double> ginv;
   if (s == WF_OK) s = response_tables(*grid, response, a.sinv, ginv);
   if (s != WF_OK) {

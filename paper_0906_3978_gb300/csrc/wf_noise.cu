@@ -8,9 +8,13 @@
 // The cone and hole tests are decisions taken in floating point; they are evaluated with
 // explicitly rounded IEEE operations in a fixed order (no contraction), so the decision is the
 // one the plain definition gives.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "wf_ctx.h"
 #include "wf_spectral.cuh"
@@ -459,18 +463,49 @@ namespace wf {
 constexpr int kNoallocParts = 152 * 8;   // blocks of the window kernel = partial sums
 constexpr int kNoallocMaxHoles = 256;    // largest hole table the scratch can hold
 // layout (doubles): [0, kNoallocParts) partials | 4 scalars | 4 * kNoallocMaxHoles hole rows
-constexpr int kNoallocDoubles = kNoallocParts + 4 + 4 * kNoallocMaxHoles;  // 14,000 B
+constexpr int kNoallocDoubles = kNoallocParts + 4 + 4 * kNoallocMaxHoles;  // 2244 doubles
+constexpr size_t kNoallocBytes = sizeof(double) * kNoallocDoubles;           // 17,952 bytes
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
+static_assert(sizeof(g_noalloc_scratch) == 17952, "the header states the scratch size");
+static_assert(kNoallocBytes == 17952, "the header states the scratch size");
 
-// Device addresses of g_noalloc_scratch, looked up once per device (host code must not use
-// the symbol itself: on the host it is only a stand-in, not a device address).
+// Device addresses of g_noalloc_scratch, looked up once per (device, context) -- host code must
+// not use the symbol itself: on the host it is only a stand-in, not a device address.  The key
+// includes the driver's unique context id, so a context created after cudaDeviceReset (whose
+// copy of the array may sit elsewhere) gets its own lookup instead of a stale address.
 static std::mutex g_noalloc_mu;
-static std::map<int, double*> g_noalloc_addr;
+static std::map<std::pair<int, unsigned long long>, double*> g_noalloc_addr;
+
+// The current context's unique id (0 if the driver cannot tell), through the runtime's driver
+// entry points, so the library does not link libcuda itself.
+static unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (PFN_cuCtxGetCurrent_v4000)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (PFN_cuCtxGetId_v12000)f;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx) get_id(ctx, &id);
+  return id;
+}
 
 static wf_status noalloc_scratch(int device, double** out) {
+  // (before the runtime's first call on this device there is no context yet: id 0, and the
+  // next call, with the context made, looks the address up once more)
+  const std::pair<int, unsigned long long> key(device, current_context_id());
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  auto it = g_noalloc_addr.find(device);
+  auto it = g_noalloc_addr.find(key);
   if (it != g_noalloc_addr.end()) {
     *out = it->second;
     return WF_OK;
@@ -481,7 +516,7 @@ static wf_status noalloc_scratch(int device, double** out) {
     set_last_error("cudaGetSymbolAddress(g_noalloc_scratch)", e);
     return WF_ERR_CUDA;
   }
-  g_noalloc_addr[device] = p;
+  g_noalloc_addr[key] = p;
   *out = p;
   return WF_OK;
 }

@@ -363,6 +363,16 @@ def test_solve_response_unit_factor_and_errors(ctx):
     with pytest.raises(wf.WfError) as e:
         ctx.solve_response(gpu(w), nbar, bd, pr.box, pr.pk_k, pr.pk_p, 1.0, 0.4, 5.0, s_out=bd)
     assert e.value.status == wf.ERR_ARG
+    # an s_out that only partly overlaps b (an offset view of one buffer) is rejected too
+    n = b.shape[0]
+    buf = torch.zeros(2 * n ** 3, dtype=torch.float64, device=DEV)
+    bview = buf[: n ** 3].view(n, n, n)
+    bview.copy_(bd)
+    sview = buf[n ** 3 // 2: n ** 3 // 2 + n ** 3].view(n, n, n)
+    with pytest.raises(wf.WfError) as e:
+        ctx.solve_response(gpu(w), nbar, bview, pr.box, pr.pk_k, pr.pk_p, 1.0, 0.4, 5.0, s_out=sview)
+    assert e.value.status == wf.ERR_ARG
+    assert np.array_equal(host(bview), b)          # the inputs were left alone
 
 
 def test_mask_projection_degenerate_geometry(ctx):

@@ -274,6 +274,80 @@ def test_fixed_iterations_large_grid(ctx, n):
     assert rl2(host(s), ref) <= 1e-11
 
 
+def _prior_preconditioner(tab, nbar, w):
+    """m = c^2 of the GPU's split preconditioning (precond = 1): c = S^(1/2) off k = 0 (m = P/dV =
+    1/S^-1) and c_0^2 = V_c / (nbar sum w).  CG on (C A C) y = C b with s = C y takes the same
+    iterates as preconditioned CG on A s = b with M^-1 = C^2, which the oracle runs."""
+    m = np.empty_like(tab)
+    m[1:] = 1.0 / tab[1:]
+    m[0] = w.size / (nbar * w.sum())
+    return m
+
+
+def fp32_iterate_tol(n):
+    """Bound for a few FP32 CG iterates against the FP64 ones.  One FP32 operator application
+    (a forward and an inverse 3D transform of log2(V) radix stages each, storage in FP32) has a
+    relative error of about 2 log2(V) u, u = 2^-24; the tolerance allows twice that,
+    4 log2(V) u (5e-6 at 128^3, 6.4e-6 at 512^3).  For the iterates checked here (k <= 3 with
+    the prior preconditioner, k <= 20 textbook) the Krylov recurrences do not amplify that error:
+    a CPU emulation of the FP32 arithmetic (FP32 vectors and transforms, FP64 dots) stays at
+    2e-7 to 4e-7 of the FP64 iterates at 128^3 and 256^3.  (With the prior preconditioner at
+    k = 20 the FP32 and FP64 iterates part by a few percent: the recurrences have lost
+    orthogonality at different rates, so that case is not an iterate comparison.)"""
+    return 4.0 * 3 * math.log2(n) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("n", [48, 128, 256])
+def test_fixed_iterations_preconditioned_match_oracle_pcg(ctx, n):
+    """precond = 1 (the production solver): after k iterations from 0, the FP64 path holds the
+    oracle's preconditioned-CG iterate to 1e-11, and the FP32 inner solve of the mixed path (one
+    refinement step, k inner iterations, s = C e_k) holds it within the FP32 bound."""
+    pr = synth.problem("c2", n_override=n, cache=False)
+    nobs = ctx.grid_assign(gpu(pr.pos), pr.n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+    wh, bh = host(w), host(b)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    pt = _prior_preconditioner(tab, nbar, wh)
+    for k in ((1, 3, 7) if n <= 48 else (3,)):
+        ref = oracle.pcg(tab, pt, nbar, wh, bh, tol=1e-14, max_iter=k, allow_unconverged=True)[0]
+        s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, precond=1, prec=wf.FP64,
+                            check=False)
+        assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k
+        assert rl2(host(s), ref) <= 1e-11, k
+        if k > 3:
+            continue
+        s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, precond=1, prec=wf.MIXED,
+                            check=False)
+        assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k and info.outer_iters == 1
+        assert rl2(host(s), ref) <= fp32_iterate_tol(n), k
+
+
+def test_fixed_iterations_full_size_workload(ctx):
+    """The 512^3 workload the benchmark times, where a converged oracle solve does not fit in test
+    time: both sides run k = 20 textbook-CG iterations from 0 (precond = 0).  The FP64 path holds
+    the oracle's x_20 to 1e-10; the FP32 inner solve of the mixed path (its 512^3 geometry: 32
+    elements per thread, radix-16/32 z passes, 16-line tiles) within the FP32 bound."""
+    pr = synth.problem("c3")
+    n, k = pr.n, 20
+    nobs = ctx.grid_assign(gpu(pr.pos), n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box, want_d=False)
+    del nobs, d
+    wh, bh = host(w), host(b)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, precond=0, prec=wf.FP64,
+                        check=False)
+    assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k
+    s64 = host(s).copy()
+    s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, precond=0, prec=wf.MIXED,
+                        check=False)
+    assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k and info.outer_iters == 1
+    s32 = host(s).copy()
+    del s, w, b
+    ref = oracle.cg(tab, nbar, wh, bh, tol=1e-14, max_iter=k, allow_unconverged=True)[0]
+    assert rl2(s64, ref) <= 1e-10
+    assert rl2(s32, ref) <= fp32_iterate_tol(n)
+
+
 @pytest.mark.parametrize("n", [128, 192, 256, 384])
 def test_fused_planes_match_separate_passes(n):
     """The cluster kernel for the y / z / y transforms (clusters of 2, 3, 4, 6 CTAs at these
