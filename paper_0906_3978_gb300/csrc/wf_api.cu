@@ -211,8 +211,8 @@ Group* make_group_n(int n, int prec) {
 // Device bytes of a group (the buffers GroupFP64 / GroupMixed allocate, tables excluded).
 size_t Group::footprint(int n, int prec, int count) {
   const double V = (double)n * n * n, spec = V / 2;
-  const double per = prec == WF_MIXED ? 6 * spec * 8 + 2 * spec * 16 + 4 * V + 4 * 8 * V
-                                      : 7 * spec * 16 + 5 * 8 * V;
+  const double per = prec == WF_MIXED ? 5 * spec * 8 + 2 * spec * 16 + 4 * V + 4 * 8 * V
+                                      : 6 * spec * 16 + 5 * 8 * V;
   return (size_t)(per * count) + (size_t)count * (3 * (n / 2) * (n / 2) + 1) * 24 + (64u << 10);
 }
 

@@ -12,15 +12,16 @@
 // its norm is estimated every iteration from the preconditioned residual (||C^-1 r~||) and,
 // once the estimate is below tol, recomputed in FP64 from s.
 //
-// One CG iteration = 5 FFT passes + 1 update sweep:
+// One CG iteration = 5 FFT passes (17 spectra of traffic):
 //   x pass 1: p = r + beta p, x += alpha_prev p_old, T = IFFT_x(c p)
 //   y pass  : IFFT_y
 //   z turn  : IFFT_z, times D / V_c, FFT_z
 //   y pass  : FFT_y
-//   x pass 2: FFT_x, q = m p + c T, <p, q>
+//   finisher: alpha = rr / <p, A p> (<p, m p> from x pass 1, <c p, D c p> from the z turn)
+//   x pass 2: FFT_x, q = m p + c T, r -= alpha q, <r, r>, ||C^-1 r||^2 (q is never stored)
 // (for FP32 at the sizes plane_cs() lists, the three middle passes run as one thread-block
 // cluster kernel per x-plane, k_plane_turn)
-//   finisher: alpha;  update: r -= alpha q, <r, r>, ||C^-1 r||^2;  finisher: beta, stop test
+//   finisher: beta, stop test
 #pragma once
 #include <algorithm>
 #include <cmath>
@@ -60,13 +61,13 @@ struct Spec {
   static constexpr size_t SMz = ZG<R, N>::SMEM;
   static constexpr int GXY = (NH / NLxy) * N;   // blocks of an x or y pass (per system)
   static constexpr int GZ = N * N / NLz;        // blocks of a z pass (per system)
-  static constexpr int GU = 152 * 4;            // blocks of the update sweep (per system)
   static constexpr size_t SPEC = (size_t)N * N * NH;  // complex elements of a spectrum
   static constexpr size_t V = (size_t)N * N * N;
   static constexpr int TAB = 3 * (N / 2) * (N / 2) + 1;
-  // partial sums per system: the largest of GXY + (z-turn or plane-kernel blocks), GZ, 2 GU
+  // partial sums per system: the largest of GXY + (z-turn or plane-kernel blocks), GZ, 2 GXY (the
+  // fused update's two sums per block)
   static constexpr int NMID = GZ > N * 8 ? GZ : N * 8;
-  static constexpr int NPART = GXY + NMID > 2 * GU ? GXY + NMID : 2 * GU;
+  static constexpr int NPART = GXY + NMID > 2 * GXY ? GXY + NMID : 2 * GXY;
   static dim3 gxy(int nb) { return dim3(NH / NLxy, N, nb); }
   static dim3 gz(int nb) { return dim3(GZ, 1, nb); }
   static Bat bat() { return Bat{SPEC, V, TAB, NPART}; }
@@ -86,7 +87,8 @@ struct Spec {
     WF_A((k_ypass<R, N, +1>), SMxy);
     WF_A((k_cg_xinv<R, N, true>), SMxy);
     WF_A((k_cg_xinv<R, N, false>), SMxy);
-    WF_A((k_cg_xfwd<R, N>), SMxy);
+    WF_A((k_cg_xupd<R, N, true>), SMxy);
+    WF_A((k_cg_xupd<R, N, false>), SMxy);
     WF_A((k_xmul<R, N, true, false, true>), SMxy);
     WF_A((k_xmul<R, N, false, true, false>), SMxy);
     WF_A((k_xmul<R, N, true, true, false>), SMxy);
@@ -131,7 +133,7 @@ struct Spec {
   }
 
   // One CG iteration of every unfinished system (no host synchronisation).
-  static void iteration(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, ST* q, const SS* D, const SS* ctab,
+  static void iteration(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* D, const SS* ctab,
                         const SS* mtab, bool unit_m, const ST* tw, double* part, CgScal* sc, double inv_vc,
                         cudaStream_t st) {
     const Bat b = bat();
@@ -155,13 +157,12 @@ struct Spec {
                [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, part + GXY, sc, b); });
       c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
     }
-    c.launch("cg_xfwd", 2 * BS * nb, st, [&] { k_cg_xfwd<R, N><<<gxy(nb), NTx, SMxy, st>>>(T, q, ctab, tw, sc, b); });
     c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, GXY, nmid, sc, b); });
-    c.launch("cg_update", 4 * BS * nb, st, [&] {
-      if (unit_m) k_update<R, N, true><<<dim3(GU, nb), 256, 0, st>>>(r, P0, P1, q, ctab, mtab, part, sc, b);
-      else k_update<R, N, false><<<dim3(GU, nb), 256, 0, st>>>(r, P0, P1, q, ctab, mtab, part, sc, b);
+    c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+      if (unit_m) k_cg_xupd<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, b);
+      else k_cg_xupd<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, b);
     });
-    c.launch("fin", 0, st, [&] { k_fin_beta<<<nb, 1024, 0, st>>>(part, GU, inv_vc, sc, b); });
+    c.launch("fin", 0, st, [&] { k_fin_beta<<<nb, 1024, 0, st>>>(part, GXY, inv_vc, sc, b); });
   }
 };
 
@@ -345,7 +346,7 @@ struct GroupFP64 : GroupCommon<N> {
   using Base::nb; using Base::sys; using Base::info; using Base::key; using Base::W; using Base::B;
   using Base::S; using Base::RES; using Base::part; using Base::sc; using Base::tw; using Base::h;
   using Base::phase; using Base::inv_vc; using Base::bb0; using Base::rel; using Base::state;
-  ST *xh, *rh, *P0, *P1, *qh, *T, *T2;
+  ST *xh, *rh, *P0, *P1, *T, *T2;
   double *D, *ct, *mt, *stab;
   std::vector<int> restarts;
   bool unit_m = true;
@@ -356,9 +357,9 @@ struct GroupFP64 : GroupCommon<N> {
     WF_CUDA(SP::attrs());
     const size_t SPEC = SP::SPEC, V = SP::V;
     WF_TRY(c.tw(N, &tw));
-    const char* nm[7] = {"x", "r", "p0", "p1", "q", "T", "T2"};
-    ST** ptr[7] = {&xh, &rh, &P0, &P1, &qh, &T, &T2};
-    for (int i = 0; i < 7; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(ST), (void**)ptr[i]));
+    const char* nm[6] = {"x", "r", "p0", "p1", "T", "T2"};
+    ST** ptr[6] = {&xh, &rh, &P0, &P1, &T, &T2};
+    for (int i = 0; i < 6; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(ST), (void**)ptr[i]));
     WF_TRY(c.get(key + "D", nb * V * sizeof(double), (void**)&D));
     WF_TRY(c.get(key + "W", nb * V * sizeof(double), (void**)&W));
     WF_TRY(c.get(key + "B", nb * V * sizeof(double), (void**)&B));
@@ -421,7 +422,7 @@ struct GroupFP64 : GroupCommon<N> {
   wf_status block(Ctx& c, cudaStream_t st) {
     return this->run_block(c, st, [&](cudaStream_t s2) {
       for (int i = 0; i < check_every<N>(); ++i)
-        SP::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw, part, sc, inv_vc, s2);
+        SP::iteration(c, nb, rh, P0, P1, xh, T, D, ct, mt, unit_m, tw, part, sc, inv_vc, s2);
     });
   }
   wf_status enqueue(Ctx& c, cudaStream_t st) override {
@@ -504,7 +505,7 @@ struct GroupMixed : GroupCommon<N> {
   using Base::nb; using Base::sys; using Base::info; using Base::key; using Base::W; using Base::B;
   using Base::S; using Base::RES; using Base::part; using Base::sc; using Base::tw; using Base::h;
   using Base::phase; using Base::inv_vc; using Base::bb0; using Base::rel; using Base::state;
-  float2 *xh, *rh, *P0, *P1, *qh, *T;
+  float2 *xh, *rh, *P0, *P1, *T;
   float* D;
   double2 *T64, *T64b;
   const float2* tw32 = nullptr;  // FP32 copy of the twiddle table for the FP32 passes
@@ -522,9 +523,9 @@ struct GroupMixed : GroupCommon<N> {
     const size_t SPEC = SF::SPEC, V = SF::V;
     WF_TRY(c.tw(N, &tw));
     WF_TRY(c.tw32(N, &tw32));
-    const char* nm[6] = {"x", "r", "p0", "p1", "q", "T"};
-    float2** ptr[6] = {&xh, &rh, &P0, &P1, &qh, &T};
-    for (int i = 0; i < 6; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(float2), (void**)ptr[i]));
+    const char* nm[5] = {"x", "r", "p0", "p1", "T"};
+    float2** ptr[5] = {&xh, &rh, &P0, &P1, &T};
+    for (int i = 0; i < 5; ++i) WF_TRY(c.get(key + nm[i], nb * SPEC * sizeof(float2), (void**)ptr[i]));
     WF_TRY(c.get(key + "D", nb * V * sizeof(float), (void**)&D));
     WF_TRY(c.get(key + "T64", nb * SPEC * sizeof(double2), (void**)&T64));
     WF_TRY(c.get(key + "T64b", nb * SPEC * sizeof(double2), (void**)&T64b));
@@ -611,7 +612,7 @@ struct GroupMixed : GroupCommon<N> {
     if (phase == 1) {
       WF_TRY(this->run_block(c, st, [&](cudaStream_t s2) {
         for (int i = 0; i < check_every<N>(); ++i)
-          SF::iteration(c, nb, rh, P0, P1, xh, T, qh, D, ct, mt, unit_m, tw32, part, sc, inv_vc, s2);
+          SF::iteration(c, nb, rh, P0, P1, xh, T, D, ct, mt, unit_m, tw32, part, sc, inv_vc, s2);
       }));
     } else if (phase == 2) {
       c.launch("axpy", 3 * SF::BS * nb, st,

@@ -368,30 +368,47 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
 }
 
 // ------------------------------------------------------------------------------------------
-// CG x pass 2 (end of A p):  out = FFT_x(T), with c applied to the packed column only (it needs
-// the partner line); the update applies c to the other columns, where it reads c(k) anyway,
-// and forms q = m p + c T^.  grid (N/2 / NL, N).  out != T: the partner line is read from T.
+// CG x pass 2 (end of A p) fused with the CG update:
+//   T^ = FFT_x(T);  q = m p + c T^;  r -= alpha q;  partials of <r, r> and ||C^-1 r||^2.
+// alpha = rr / <p, A p> is already known: both terms of <p, A p> were summed by the first x pass
+// and the z turn, and the finisher ran before this pass.  So q never goes to memory: the pass
+// reads T, p and r and writes r (4 spectra), where a separate transform and update sweep moved 6.
+// On the packed column c is applied to T^ as a pair (it needs the partner line -ky), and the m term
+// combines p with its partner element p(-kx, -ky, 0).  partials [2 per block]: <r, r> (packed
+// weights, without 1/V_c) and an upper estimate of V_c ||C^-1 r||^2 (the canonical residual): on
+// column 0 the larger of the two planes' 1/c^2 is used.  grid (N/2 / NL, N).
 // ------------------------------------------------------------------------------------------
-template <class R, int N>
+template <class R, int N, bool UNIT_M>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
-k_cg_xfwd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ out,
-          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::T* __restrict__ twtab,
+k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ r,
+          const typename Store<R>::T* P0, const typename Store<R>::T* P1,
+          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
+          const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials,
           const CgScal* __restrict__ sc, Bat bt) {
   using G = XYG<R, N>;
+  using ST = typename Store<R>::T;
+  using SS = typename Store<R>::S;
+  using VT = typename G::VT;
   constexpr int NH = G::NH;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
+  __shared__ double red[32];
   const int z = blockIdx.z;
   sc += z;
   if (sc->done) return;
+  const ST* __restrict__ p = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;  // this iteration's p_new
   T += z * bt.spec;
-  out += z * bt.spec;
+  r += z * bt.spec;
   ctab += z * bt.tab;
+  mtab += z * bt.tab;
+  partials += z * bt.part;
   const int tid = threadIdx.x;
   const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
   const int ky_s = sfreq(ky, N);
   const int pky = (N - ky) % N;
+  const SS alpha = (SS)sc->alpha;
   load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
   const size_t rowstride = (size_t)N * NH;
   const size_t base = (size_t)ky * NH + kz0;
@@ -404,7 +421,80 @@ k_cg_xfwd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __re
     fft_line<R, G::M, G::TPL, G::LD, -1>(tile + G::NL, tid / G::NL, tw, tid % G::NL == 0);
     combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
   }
-  tile_store<G>(tile, out + base, rowstride, tid);
+  // epilogue: r -= alpha (m p + c T^), vector by vector in the tile's row layout
+  typename AccFor<SS>::T a_rr, a_rc;
+  constexpr int CH = 4;  // vectors per thread whose two loads are in flight together
+  constexpr int SPV = sizeof(VT) / sizeof(SS);
+#pragma unroll
+  for (int k0 = 0; k0 < G::PER; k0 += CH) {
+    VT rv[CH], pv[CH];
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (G::EVEN || idx < G::NVEC) {
+        const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+        const size_t e = base + (size_t)i * rowstride + c0;
+        rv[k] = *reinterpret_cast<const VT*>(r + e);
+        pv[k] = *reinterpret_cast<const VT*>(p + e);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (G::EVEN || idx < G::NVEC) {
+        const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+        const size_t e = base + (size_t)i * rowstride + c0;
+        SS* rs = reinterpret_cast<SS*>(&rv[k]);
+        const SS* ps = reinterpret_cast<const SS*>(&pv[k]);
+        const int kxs = sfreq(i, N);
+        SS s_rr = 0, s_rc = 0;
+#pragma unroll
+        for (int u = 0; u < G::VW; ++u) {
+          const int kz = kz0 + c0 + u;
+          const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
+          const cx<R> t = tile[i * G::LD + c0 + u];
+          const SS c = ctab[n2];
+          SS ic2 = (SS)1 / (c * c);
+          SS q0, q1;
+          if (kz == 0) {
+            // packed column: T^ already carries c; the m term combines p with p(-kx, -ky, 0) (in the
+            // storage type: FP64 here would run on GB300's 1/64-rate unit)
+            const SS cN = ctab[n2 + NH * NH];
+            const SS i2 = (SS)1 / (cN * cN);
+            ic2 = ic2 > i2 ? ic2 : i2;
+            const SS m0 = mtab[n2], mN = mtab[n2 + NH * NH];
+            const SS a = (SS)0.5 * (m0 + mN), b = (SS)0.5 * (m0 - mN);
+            ST pp = ST{};
+            if (b != (SS)0) pp = p[(size_t)((N - i) % N) * rowstride + (size_t)pky * NH];
+            q0 = a * ps[2 * u] + b * pp.x + (SS)t.x;
+            q1 = a * ps[2 * u + 1] - b * pp.y + (SS)t.y;
+          } else {
+            const SS m = UNIT_M ? (SS)1 : mtab[n2];
+            q0 = m * ps[2 * u] + c * (SS)t.x;
+            q1 = m * ps[2 * u + 1] + c * (SS)t.y;
+          }
+          rs[2 * u] -= alpha * q0;
+          rs[2 * u + 1] -= alpha * q1;
+          const SS wgt = kz == 0 ? (SS)1 : (SS)2;
+          const SS m2 = wgt * (rs[2 * u] * rs[2 * u] + rs[2 * u + 1] * rs[2 * u + 1]);
+          s_rr += m2;
+          s_rc += ic2 * m2;
+        }
+        (void)SPV;
+        *reinterpret_cast<VT*>(r + e) = rv[k];
+        // the terms are >= 0: a vector's terms are summed in the storage type first
+        a_rr.add(s_rr);
+        a_rc.add(s_rc);
+      }
+    }
+  }
+  const double s1 = block_sum(a_rr.get(), red);
+  const double s2 = block_sum(a_rc.get(), red);
+  if (tid == 0) {
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    partials[2 * bid] = s1;
+    partials[2 * bid + 1] = s2;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -779,98 +869,6 @@ k_zinv(const typename Store<R>::T* __restrict__ in, double* __restrict__ out,
   if constexpr (MODE == ZI_RESID) {
     const double sum = block_sum(acc.get(), red);
     if (tid == 0) partials[blockIdx.x] = sum;
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// CG update: q = m p + c T^ (column 0: T^ already carries c, and the m term is combined with the
-// partner element p(-kx, -ky, 0)); r -= alpha q; partials [2 per block]: <r, r> (packed
-// weights, without 1/V_c) and an upper estimate of V_c ||C^-1 r||^2 (the canonical residual):
-// on column 0 the larger of the two planes' 1/c^2 is used.  Grid-stride; fixed grid size.
-// ------------------------------------------------------------------------------------------
-template <class R, int N, bool UNIT_M>
-__global__ void __launch_bounds__(256)
-k_update(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* P0, const typename Store<R>::T* P1,
-         const typename Store<R>::T* __restrict__ tq, const typename Store<R>::S* __restrict__ ctab,
-         const typename Store<R>::S* __restrict__ mtab, double* __restrict__ partials,
-         const CgScal* __restrict__ sc, Bat bt) {
-  using ST = typename Store<R>::T;
-  using SS = typename Store<R>::S;
-  constexpr int NH = N / 2;
-  constexpr int VW = sizeof(ST) == 8 ? 2 : 1;  // complex elements per 16-byte vector
-  using VT = typename std::conditional<VW == 2, float4, ST>::type;
-  __shared__ double red[32];
-  const int z = blockIdx.y;
-  sc += z;
-  if (sc->done) return;
-  const ST* __restrict__ p = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;  // this iteration's p_new
-  r += z * bt.spec;
-  tq += z * bt.spec;
-  ctab += z * bt.tab;
-  mtab += z * bt.tab;
-  partials += z * bt.part;
-  const SS alpha = (SS)sc->alpha;
-  // 32-bit indices: N^3 / 2 elements fit for every supported N (<= 512)
-  constexpr unsigned NVR = NH / VW;  // vectors per (kx, ky) row
-  constexpr unsigned nvec = (unsigned)N * N * NVR;
-  static_assert((unsigned long long)N * N * NH < (1ull << 31), "32-bit spectrum indices");
-  VT* r4 = reinterpret_cast<VT*>(r);
-  const VT* q4 = reinterpret_cast<const VT*>(tq);
-  const VT* p4 = reinterpret_cast<const VT*>(p);
-  typename AccFor<SS>::T a_rr, a_rc;
-#pragma unroll 4
-  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += gridDim.x * blockDim.x) {
-    VT rv = r4[v];
-    const VT qv = q4[v], pv = p4[v];
-    SS* rs = reinterpret_cast<SS*>(&rv);
-    const SS* qs = reinterpret_cast<const SS*>(&qv);
-    const SS* ps = reinterpret_cast<const SS*>(&pv);
-    const unsigned row = v / NVR, kz0 = (v % NVR) * VW;
-    const int ky = (int)(row % N), kx = (int)(row / N);
-    const int kxs = sfreq(kx, N), kys = sfreq(ky, N);
-    SS s_rr = 0, s_rc = 0;
-#pragma unroll
-    for (int u = 0; u < VW; ++u) {
-      const int kz = (int)kz0 + u;
-      const int n2 = kxs * kxs + kys * kys + kz * kz;
-      const SS c = ctab[n2];
-      SS ic2 = (SS)1 / (c * c);
-      SS q0, q1;  // q = m p + c T^ (tq holds T^, with c already applied on column 0)
-      if (kz == 0) {
-        // packed column: m-term combined with the partner element p(-kx, -ky, 0)
-        const SS cN = ctab[n2 + NH * NH];
-        const SS i2 = (SS)1 / (cN * cN);
-        ic2 = ic2 > i2 ? ic2 : i2;
-        // (in the storage type: FP64 here would run on GB300's 1/64-rate unit for every warp
-        // that holds a column-0 lane)
-        const SS m0 = mtab[n2], mN = mtab[n2 + NH * NH];
-        const SS a = (SS)0.5 * (m0 + mN), b = (SS)0.5 * (m0 - mN);
-        ST pp = ST{};
-        if (b != (SS)0) pp = p[((size_t)((N - kx) % N) * N + (size_t)((N - ky) % N)) * NH];
-        q0 = a * ps[2 * u] + b * pp.x + qs[2 * u];
-        q1 = a * ps[2 * u + 1] - b * pp.y + qs[2 * u + 1];
-      } else {
-        const SS m = UNIT_M ? (SS)1 : mtab[n2];
-        q0 = m * ps[2 * u] + c * qs[2 * u];
-        q1 = m * ps[2 * u + 1] + c * qs[2 * u + 1];
-      }
-      rs[2 * u] -= alpha * q0;
-      rs[2 * u + 1] -= alpha * q1;
-      const SS wgt = kz == 0 ? (SS)1 : (SS)2;
-      const SS m2 = wgt * (rs[2 * u] * rs[2 * u] + rs[2 * u + 1] * rs[2 * u + 1]);
-      s_rr += m2;
-      s_rc += ic2 * m2;
-    }
-    r4[v] = rv;
-    // the terms are >= 0: a vector's terms are summed in the storage type first
-    a_rr.add(s_rr);
-    a_rc.add(s_rc);
-  }
-  const double s1 = block_sum(a_rr.get(), red);
-  const double s2 = block_sum(a_rc.get(), red);
-  if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = s1;
-    partials[2 * blockIdx.x + 1] = s2;
   }
 }
 
