@@ -256,6 +256,8 @@ def gpu_arm(args):
     pos = torch.from_numpy(pr.pos).to(dev)
     n, box = pr.n, pr.box
     tol = pr.tol
+    # launch variants of the spectral passes timed once for this size (outside any timed region)
+    tuning = {"mixed": ctx.autotune(n, wf.MIXED), "fp64": ctx.autotune(n, wf.FP64)}
 
     def step(prec, s_out=None, pos_d=pos):
         with torch.cuda.stream(st):
@@ -377,6 +379,9 @@ def gpu_arm(args):
                      "avg_launch_ms": dom["ms"] / dom["launches"]},
         "kernels": [{k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in c.items()}
                     for c in sorted(prof["classes"], key=lambda c: -c["ms"])[:10]],
+        "tuning": {prec: {p["pass"]: {"chosen": p["chosen"],
+                                      "ms": {v["name"]: round(v["ms"], 4) for v in p["variants"]}}
+                          for p in rep} for prec, rep in tuning.items()},
         "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
                          "cpu": cpu_model(), "single_thread": single},
         "e2e": {"value": ws * k / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(pr.pos.nbytes),

@@ -141,6 +141,27 @@ const char* wf_last_error(void);
  * differ, the FP32 rounding.  Applies to solves started after the call.  Errors: WF_ERR_ARG. */
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on);
 
+/* ---- launch autotuning (no counterpart in the paper: how the transforms of Sec. 3.3.1 map to
+ * this GPU) ---------------------------------------------------------------------------------
+ * The spectral passes come in launch variants (lines per tile, tiles in flight per CTA, largest
+ * radix of the transform stages).  wf_autotune times every variant of every pass for grid size n
+ * and precision prec (WF_MIXED tunes the FP32 inner passes, WF_FP64 the FP64 ones) on this
+ * context's device, on a working set of at least 256 MB, and keeps the fastest per pass in the
+ * context's tuning table; later solves of that size and precision launch it.  Results do not
+ * depend on the variant beyond rounding (the transforms' stage order changes).
+ *   report  host char [report_len] out: JSON array, one object per pass with each variant's
+ *           milliseconds per launch and the one chosen; may be NULL
+ * Allocates and frees a scratch buffer; waits for completion.
+ * Errors: WF_ERR_ARG (bad precision, report too small), WF_ERR_UNSUPPORTED (size), WF_ERR_OOM,
+ * WF_ERR_CUDA, WF_ERR_TIMEOUT (a kernel's bounded wait for a bulk copy ran out). */
+wf_status wf_autotune(wf_ctx* ctx, int n, wf_precision prec, char* report, int report_len);
+/* The context's tuning table as JSON text {"ypass/f32/512": 1, ...} (NUL-terminated) in json
+ * [len]; WF_ERR_ARG if it does not fit. */
+wf_status wf_tune_get(wf_ctx* ctx, char* json, int len);
+/* Merge a table written by wf_tune_get into the context's (a saved tuning, reused without timing).
+ * A variant index beyond a pass's variants launches variant 0.  WF_ERR_ARG on malformed text. */
+wf_status wf_tune_set(wf_ctx* ctx, const char* json);
+
 /* ---- the 3D mask from a sky completeness map (Sec. 3.1.3) ------------------------------------ */
 
 /* Projects a sky completeness map and a radial completeness table onto the grid along rays from

@@ -116,6 +116,9 @@ def lib():
         L.wf_poll.argtypes = [c_void_p, c_uint64, c_int, c_void_p, P(SolveInfo)]
         L.wf_profile.argtypes = [c_void_p, c_int]
         L.wf_set_fused_planes.argtypes = [c_void_p, c_int]
+        L.wf_autotune.argtypes = [c_void_p, c_int, c_int, ctypes.c_char_p, c_int]
+        L.wf_tune_get.argtypes = [c_void_p, ctypes.c_char_p, c_int]
+        L.wf_tune_set.argtypes = [c_void_p, ctypes.c_char_p]
         L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
         L.wf_project_mask.argtypes = [c_void_p, P(Grid), c_void_p, c_int, c_int, c_double, c_double, c_double,
                                       c_double, P(c_double), c_double, c_int, P(c_double), c_void_p, c_void_p,
@@ -139,7 +142,7 @@ def lib():
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
                      "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve",
                      "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask", "wf_solve_response",
-                     "wf_jackknife_solve"):
+                     "wf_jackknife_solve", "wf_autotune", "wf_tune_get", "wf_tune_set"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -509,6 +512,33 @@ class Context:
         st = lib().wf_set_fused_planes(self._h, 1 if on else 0)
         if st != OK:
             raise WfError(st, "wf_set_fused_planes")
+
+    def autotune(self, n: int, prec=MIXED, report_len: int = 1 << 16):
+        """Time the launch variants of the spectral passes for grid size n and precision prec and
+        keep the fastest per pass for later solves (wf_autotune); returns the report (a list of
+        per-pass dicts: variants with ms per launch, the one chosen)."""
+        import json
+        buf = ctypes.create_string_buffer(report_len)
+        st = lib().wf_autotune(self._h, int(n), int(prec), buf, report_len)
+        if st != OK:
+            raise WfError(st, "wf_autotune")
+        return json.loads(buf.value.decode())
+
+    def tune_get(self) -> dict:
+        """The context's tuning table {"pass/prec/n": variant} (wf_tune_get)."""
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        st = lib().wf_tune_get(self._h, buf, 1 << 16)
+        if st != OK:
+            raise WfError(st, "wf_tune_get")
+        return json.loads(buf.value.decode())
+
+    def tune_set(self, table: dict):
+        """Merge a saved tuning table into the context's (wf_tune_set)."""
+        import json
+        st = lib().wf_tune_set(self._h, json.dumps(table).encode())
+        if st != OK:
+            raise WfError(st, "wf_tune_set")
 
     def profile(self, enable: bool = True):
         """Reset launch counters; enable/disable per-kernel CUDA-event timing (wf_profile)."""

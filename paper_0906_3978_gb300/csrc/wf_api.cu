@@ -1,6 +1,7 @@
 // wf_api.cu -- the C ABI (include/wf.h): context, argument checks, dispatch to the kernels.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <iterator>
 #include <string>
@@ -48,6 +49,35 @@ wf_status Ctx::get(const std::string& name, size_t bytes, void** out) {
   b.bytes = bytes;
   held += bytes;
   *out = p;
+  return WF_OK;
+}
+
+wf_status Ctx::err_word(int** out) {
+  if (!dev_err) {
+    void* p = nullptr;
+    WF_TRY(get("dev_err", 64, &p));
+    WF_CUDA(cudaMemset(p, 0, 64));
+    dev_err = reinterpret_cast<int*>(p);
+  }
+  if (!sm_count) WF_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, device));
+  *out = dev_err;
+  return WF_OK;
+}
+
+wf_status Ctx::check_device_errors() {
+  if (map_failed) {
+    map_failed = false;
+    set_last_error("cuTensorMapEncodeTiled refused a spectrum map", cudaSuccess);
+    return WF_ERR_CUDA;
+  }
+  if (!dev_err) return WF_OK;
+  int h = 0;
+  WF_CUDA(cudaMemcpy(&h, dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    WF_CUDA(cudaMemset(dev_err, 0, sizeof(int)));
+    set_last_error("a kernel's wait for a bulk copy timed out", cudaSuccess);
+    return WF_ERR_TIMEOUT;
+  }
   return WF_OK;
 }
 
@@ -149,6 +179,7 @@ void Ctx::release_all() {
   for (auto& kv : bufs)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
   bufs.clear();
+  dev_err = nullptr;
   held = 0;
   for (auto& kv : twiddles) cudaFree(kv.second);
   twiddles.clear();
@@ -208,6 +239,18 @@ Group* make_group_n(int n, int prec) {
   }
 }
 
+wf_status autotune(Ctx& c, int n, int prec, std::string& report) {
+  switch (n) {
+#define WF_CASE(N) \
+  case N:          \
+    return autotune_n<N>(c, prec, report);
+    WF_SIZES(WF_CASE)
+#undef WF_CASE
+    default:
+      return WF_ERR_UNSUPPORTED;
+  }
+}
+
 // Device bytes of a group (the buffers GroupFP64 / GroupMixed allocate, tables excluded).
 size_t Group::footprint(int n, int prec, int count) {
   const double V = (double)n * n * n, spec = V / 2;
@@ -245,6 +288,8 @@ wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_
     gs.push_back(s);
     ++k;
   }
+  int* err = nullptr;
+  WF_TRY(c.err_word(&err));
   wf_status status = WF_OK;
   for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) status = gl[i]->prepare(c, gs[i]);
   for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) WF_CUDA(cudaStreamSynchronize(gs[i]));
@@ -270,6 +315,7 @@ wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_
   WF_CUDA(cudaStreamSynchronize(st));
   cudaEventDestroy(ev);
   if (status != WF_OK) return status;
+  WF_TRY(c.check_device_errors());
   for (auto* inf : infos)
     if (inf && inf->status != WF_OK) return inf->status;
   return WF_OK;
@@ -604,6 +650,66 @@ wf_status wf_density_stats(wf_ctx* ctx, const wf_grid* grid, const double* delta
   DeviceGuard g(c->device);
   return density_run(*c, *grid, delta, w, observer, n_shells, shells, lo, width, n_bins, hist, moments,
                      (cudaStream_t)stream);
+}
+
+static wf_status copy_text(const std::string& t, char* out, int len) {
+  if (!out || len <= 0) return WF_ERR_ARG;
+  if ((int)t.size() + 1 > len) {
+    set_last_error("output buffer too small for the JSON text", cudaSuccess);
+    return WF_ERR_ARG;
+  }
+  std::memcpy(out, t.c_str(), t.size() + 1);
+  return WF_OK;
+}
+
+wf_status wf_autotune(wf_ctx* ctx, int n, wf_precision prec, char* report, int report_len) {
+  if (!ctx || (prec != WF_FP64 && prec != WF_MIXED)) return WF_ERR_ARG;
+  if (!supported_size(n)) return WF_ERR_UNSUPPORTED;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  std::string rep = "[";
+  WF_TRY(autotune(*c, n, (int)prec, rep));
+  rep += "]";
+  return report ? copy_text(rep, report, report_len) : WF_OK;
+}
+
+wf_status wf_tune_get(wf_ctx* ctx, char* json, int len) {
+  if (!ctx) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  std::string t = "{";
+  bool first = true;
+  for (const auto& kv : c->tuned) {
+    t += (first ? "\"" : ", \"") + kv.first + "\": " + std::to_string(kv.second);
+    first = false;
+  }
+  t += "}";
+  return copy_text(t, json, len);
+}
+
+// Reads {"pass/prec/n": variant, ...}: every quoted key followed by ':' and an integer.
+wf_status wf_tune_set(wf_ctx* ctx, const char* json) {
+  if (!ctx || !json) return WF_ERR_ARG;
+  std::map<std::string, int> parsed;
+  const char* p = json;
+  while ((p = std::strchr(p, '"'))) {
+    const char* q = std::strchr(p + 1, '"');
+    if (!q) return WF_ERR_ARG;
+    std::string key(p + 1, q);
+    const char* r = q + 1;
+    while (*r == ' ' || *r == '\t' || *r == '\n') ++r;
+    if (*r != ':') return WF_ERR_ARG;
+    char* end = nullptr;
+    const long v = std::strtol(r + 1, &end, 10);
+    if (end == r + 1 || v < 0 || v > 1000) return WF_ERR_ARG;
+    parsed[key] = (int)v;
+    p = end;
+  }
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  for (const auto& kv : parsed) c->tuned[kv.first] = kv.second;
+  return WF_OK;
 }
 
 wf_status wf_set_fused_planes(wf_ctx* ctx, int on) {

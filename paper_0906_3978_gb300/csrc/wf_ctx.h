@@ -107,6 +107,11 @@ struct Ctx {
   void* host_pinned = nullptr;       // small pinned staging area for scalars
   struct Server* server = nullptr;   // serving loop, created on first wf_submit
   bool fused_planes = false;         // FP32 y / z / y passes as one cluster kernel where possible
+  int* dev_err = nullptr;            // device word: nonzero after a kernel's bounded wait timed out
+  bool map_failed = false;           // the driver refused a tensor map for a launch
+  int sm_count = 0;
+  // launch variant per "pass/precision/size" chosen by wf_autotune (variant 0 when absent)
+  std::map<std::string, int> tuned;
   Prof prof;
 
   // Launch `f` (which enqueues one kernel on st), counting it and, when profiling, timing it.
@@ -135,6 +140,11 @@ struct Ctx {
   // i-th library-owned non-blocking stream.
   wf_status stream(int i, cudaStream_t* out);
   wf_status capture_stream(cudaStream_t* out);
+  // The device error word (zeroed on first use) and the SM count; call before any capture.
+  wf_status err_word(int** out);
+  // WF_ERR_TIMEOUT (and the word cleared) if a kernel reported a timed-out wait, WF_ERR_CUDA if a
+  // tensor map was refused since the last check.  Synchronises with the device.
+  wf_status check_device_errors();
   // Free every device and pinned buffer whose name starts with `prefix`.
   void release_prefix(const std::string& prefix);
   void release_all();

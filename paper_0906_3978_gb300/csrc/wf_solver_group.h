@@ -31,4 +31,11 @@ template <int N>
 wf_status fourier_multiply_n(Ctx& c, const double* in, double* out, const std::vector<double>& table,
                              cudaStream_t st);
 
+// Time every launch variant of the spectral passes of grid size N in precision prec (the FP32
+// inner passes for WF_MIXED, the FP64 ones for WF_FP64), keep the fastest per pass in c.tuned and
+// append a JSON object per pass to `report`.
+template <int N>
+wf_status autotune_n(Ctx& c, int prec, std::string& report);
+wf_status autotune(Ctx& c, int n, int prec, std::string& report);
+
 }  // namespace wf

@@ -24,6 +24,7 @@
 //   finisher: beta, stop test
 #pragma once
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <vector>
 
@@ -77,14 +78,14 @@ struct Spec {
   static constexpr double BV = (double)V;
   // cluster size of the fused y / z / y plane kernel (0: not available at this size)
   static constexpr int PCS = plane_cs<R, N>(), PE = plane_e<R, N>();
+  // the persistent passes with tensor copies: tile lines and buffers in flight
+  static constexpr int NLT = tma_lines<R, N>();
 
   static cudaError_t attrs() {
     static bool done = false;
     if (done) return cudaSuccess;
     cudaError_t e = cudaSuccess;
 #define WF_A(k, b) if (e == cudaSuccess) e = set_smem(k, b)
-    WF_A((k_ypass<R, N, -1>), SMxy);
-    WF_A((k_ypass<R, N, +1>), SMxy);
     WF_A((k_cg_xinv<R, N, true>), SMxy);
     WF_A((k_cg_xinv<R, N, false>), SMxy);
     WF_A((k_cg_xupd<R, N, true>), SMxy);
@@ -100,15 +101,77 @@ struct Spec {
     WF_A((k_zinv<R, N, ZI_RESID>), SMz);
     WF_A((k_zinv<R, N, ZI_ACCUM>), SMz);
 #undef WF_A
+    for (const PassVariant& v : yvariants())
+      if (e == cudaSuccess) e = v.setup();
     if (e == cudaSuccess) done = true;
     return e;
   }
 
+  // persistent grid: every SM holds its resident CTAs, capped by the number of tiles
+  static unsigned persistent_grid(const Ctx& c, int occ, long long tiles) {
+    const long long g = (long long)occ * (c.sm_count > 0 ? c.sm_count : 152);
+    return (unsigned)(tiles < g ? tiles : g);
+  }
+  // ---- launch variants of a pass (tile lines, buffers in flight, radix cap); the context's
+  // tuning table picks one per (pass, precision, size), variant 0 by default ------------------
+  using PassRun = void (*)(Ctx&, int, ST*, const ST*, const CgScal*, int, cudaStream_t);
+  struct PassVariant {
+    const char* name;
+    cudaError_t (*setup)();
+    PassRun run;
+  };
+  // y pass variant <NL, STG, RMAX>: complex FFT along y of every (x, kz) line, in place
+  template <int NL, int STG, int RMAX>
+  struct YV {
+    using G = TG<R, N, NL, STG>;
+    static inline int occ = 1;  // resident CTAs per SM
+    static cudaError_t setup() {
+      cudaError_t e = set_smem(k_ypass_tma<R, N, -1, NL, STG, RMAX>, G::SMEM);
+      if (e == cudaSuccess) e = set_smem(k_ypass_tma<R, N, +1, NL, STG, RMAX>, G::SMEM);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_ypass_tma<R, N, -1, NL, STG, RMAX>, G::NT, G::SMEM);
+      if (occ < 1) occ = 1;
+      return e;
+    }
+    static void run(Ctx& c, int nb, ST* t, const ST* tw, const CgScal* sc, int dir, cudaStream_t st) {
+      CUtensorMap m;
+      if (!make_spectrum_map(&m, t, N, nb, sizeof(SS) == 8, NL, G::BR, 1)) {
+        c.map_failed = true;
+        return;
+      }
+      const unsigned grid = persistent_grid(c, occ, (long long)nb * G::TPS);
+      c.launch("ypass", 2 * BS * nb, st, [&] {
+        if (dir < 0) k_ypass_tma<R, N, -1, NL, STG, RMAX><<<grid, G::NT, G::SMEM, st>>>(m, tw, sc, nb, c.dev_err);
+        else k_ypass_tma<R, N, +1, NL, STG, RMAX><<<grid, G::NT, G::SMEM, st>>>(m, tw, sc, nb, c.dev_err);
+      });
+    }
+  };
+  // candidates: FP32 grids of 128 and up (the inner solves) get a few; everything else the default
+  static const std::vector<PassVariant>& yvariants() {
+    static const std::vector<PassVariant> v = [] {
+      std::vector<PassVariant> out{{"nl_s2_r8", YV<NLT, 2, 8>::setup, YV<NLT, 2, 8>::run}};
+      if constexpr (std::is_same<R, float>::value && N >= 128) {
+        constexpr int H = NLT / 2;
+        out.push_back({"nl_s2_r32", YV<NLT, 2, 32>::setup, YV<NLT, 2, 32>::run});
+        out.push_back({"nl_s3_r32", YV<NLT, 3, 32>::setup, YV<NLT, 3, 32>::run});
+        out.push_back({"nl/2_s2_r32", YV<H, 2, 32>::setup, YV<H, 2, 32>::run});
+        out.push_back({"nl/2_s3_r16", YV<H, 3, 16>::setup, YV<H, 3, 16>::run});
+      }
+      return out;
+    }();
+    return v;
+  }
+  static std::string tune_key(const char* pass) {
+    return std::string(pass) + (sizeof(SS) == 8 ? "/f64/" : "/f32/") + std::to_string(N);
+  }
+  static const PassVariant& pick(const Ctx& c, const char* pass, const std::vector<PassVariant>& vs) {
+    auto it = c.tuned.find(tune_key(pass));
+    const int i = it == c.tuned.end() ? 0 : it->second;
+    return vs[i >= 0 && i < (int)vs.size() ? i : 0];
+  }
+  // complex FFT along y of every (x, kz) line of nb spectra, in place
   static void ypass(Ctx& c, int nb, ST* t, const ST* tw, const CgScal* sc, int dir, cudaStream_t st) {
-    c.launch("ypass", 2 * BS * nb, st, [&] {
-      if (dir < 0) k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(t, tw, sc, bat());
-      else k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(t, tw, sc, bat());
-    });
+    pick(c, "ypass", yvariants()).run(c, nb, t, tw, sc, dir, st);
   }
   // out = [IFFT_x] tab (.) [FFT_x] in
   template <bool FWD, bool INV, bool DOT>
@@ -152,10 +215,10 @@ struct Spec {
       }
     }
     if (!fused) {
-      c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, +1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
+      ypass(c, nb, T, tw, sc, +1, st);
       c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st,
                [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, part + GXY, sc, b); });
-      c.launch("ypass", 2 * BS * nb, st, [&] { k_ypass<R, N, -1><<<gxy(nb), NTy, SMxy, st>>>(T, tw, sc, b); });
+      ypass(c, nb, T, tw, sc, -1, st);
     }
     c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, GXY, nmid, sc, b); });
     c.launch("cg_xupd", 4 * BS * nb, st, [&] {
@@ -354,6 +417,8 @@ struct GroupFP64 : GroupCommon<N> {
   wf_status prepare(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
     key = this->tag + "f64_" + std::to_string(N) + "_";
+    int* err;
+    WF_TRY(c.err_word(&err));
     WF_CUDA(SP::attrs());
     const size_t SPEC = SP::SPEC, V = SP::V;
     WF_TRY(c.tw(N, &tw));
@@ -518,6 +583,8 @@ struct GroupMixed : GroupCommon<N> {
   wf_status prepare(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
     key = this->tag + "mix_" + std::to_string(N) + "_";
+    int* err;
+    WF_TRY(c.err_word(&err));
     WF_CUDA(SF::attrs());
     WF_CUDA(SD::attrs());
     const size_t SPEC = SF::SPEC, V = SF::V;
@@ -680,6 +747,8 @@ template <int N>
 wf_status fourier_multiply_n(Ctx& c, const double* in, double* out, const std::vector<double>& table, cudaStream_t st) {
   using SD = Spec<FP64Arith, N>;
   if ((int)table.size() != SD::TAB) return WF_ERR_ARG;
+  int* err;
+  WF_TRY(c.err_word(&err));
   WF_CUDA(SD::attrs());
   const double2* tw;
   WF_TRY(c.tw(N, &tw));
@@ -697,7 +766,93 @@ wf_status fourier_multiply_n(Ctx& c, const double* in, double* out, const std::v
   SD::template zinv<ZI_STORE>(c, 1, T2, out, nullptr, nullptr, nullptr, 1.0 / (double)SD::V, tw, part, nullptr,
                               st);
   WF_CUDA(cudaGetLastError());
+  WF_CUDA(cudaStreamSynchronize(st));
+  return c.check_device_errors();
+}
+
+// ---- autotuner: time each launch variant of a pass on a working set larger than L2 ----------
+template <class SP, class V>
+wf_status tune_pass(Ctx& c, const char* pass, const std::vector<V>& vs, typename SP::ST* buf, int nb,
+                    const typename SP::ST* tw, cudaStream_t st, std::string& report) {
+  const std::string key = SP::tune_key(pass);
+  char head[160];
+  std::snprintf(head, sizeof head, "{\"pass\": \"%s\", \"systems\": %d, \"variants\": [", key.c_str(), nb);
+  report += head;
+  cudaEvent_t a, b;
+  WF_CUDA(cudaEventCreate(&a));
+  WF_CUDA(cudaEventCreate(&b));
+  int best = 0;
+  float best_ms = 1e30f;
+  const bool prof = c.prof.on;
+  c.prof.on = false;  // the tuner's launches are not part of a profile
+  wf_status status = WF_OK;
+  for (size_t i = 0; i < vs.size() && status == WF_OK; ++i) {
+    constexpr int kWarm = 2, kRuns = 6;
+    for (int r = 0; r < kWarm; ++r) vs[i].run(c, nb, buf, tw, nullptr, -1, st);
+    cudaEventRecord(a, st);
+    for (int r = 0; r < kRuns; ++r) vs[i].run(c, nb, buf, tw, nullptr, r & 1 ? +1 : -1, st);
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) {
+      set_last_error("autotune timing", e);
+      status = WF_ERR_CUDA;
+      break;
+    }
+    ms /= kRuns;
+    char item[128];
+    std::snprintf(item, sizeof item, "%s{\"name\": \"%s\", \"ms\": %.5f}", i ? ", " : "", vs[i].name, ms);
+    report += item;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = (int)i;
+    }
+  }
+  c.prof.on = prof;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  WF_TRY(status);
+  WF_TRY(c.check_device_errors());
+  c.tuned[key] = best;
+  char tail[96];
+  std::snprintf(tail, sizeof tail, "], \"chosen\": \"%s\"}", vs[best].name);
+  report += tail;
   return WF_OK;
+}
+
+template <class SP>
+wf_status tune_spec(Ctx& c, std::string& report) {
+  using ST = typename SP::ST;
+  int* err;
+  WF_TRY(c.err_word(&err));
+  WF_CUDA(SP::attrs());
+  const ST* tw;
+  if constexpr (sizeof(typename SP::SS) == 8) {
+    WF_TRY(c.tw(SP::NH * 2, &tw));
+  } else {
+    WF_TRY(c.tw32(SP::NH * 2, &tw));
+  }
+  // enough systems that the working set (read and written once per pass) is at least 256 MB,
+  // so that the passes stream from HBM as they do in a large solve or a batch
+  const double spec_bytes = (double)SP::SPEC * sizeof(ST);
+  int nb = (int)std::ceil((256.0 * (1 << 20)) / spec_bytes);
+  nb = std::max(1, std::min(nb, 64));
+  ST* buf;
+  WF_TRY(c.get("tune_spec", (size_t)nb * SP::SPEC * sizeof(ST), (void**)&buf));
+  cudaStream_t st;
+  WF_TRY(c.stream(0, &st));
+  WF_CUDA(cudaMemsetAsync(buf, 0, (size_t)nb * SP::SPEC * sizeof(ST), st));
+  WF_TRY(tune_pass<SP>(c, "ypass", SP::yvariants(), buf, nb, tw, st, report));
+  WF_CUDA(cudaStreamSynchronize(st));
+  c.release_prefix("tune_spec");
+  return WF_OK;
+}
+
+template <int N>
+wf_status autotune_n(Ctx& c, int prec, std::string& report) {
+  if (prec == WF_MIXED) return tune_spec<Spec<float, N>>(c, report);
+  return tune_spec<Spec<FP64Arith, N>>(c, report);
 }
 
 template <int N>

@@ -10,4 +10,5 @@ namespace wf {
 template Group* make_group<WF_N>(int prec);
 template wf_status fourier_multiply_n<WF_N>(Ctx& c, const double* in, double* out, const std::vector<double>& table,
                                             cudaStream_t st);
+template wf_status autotune_n<WF_N>(Ctx& c, int prec, std::string& report);
 }

@@ -14,8 +14,8 @@
 // The inner product of two real fields u, v is (1/V_c) sum over the packed spectrum of
 // wgt * Re(conj(u) v) with wgt = 1 on column 0 and 2 elsewhere.
 //
-// Passes (all one CTA per tile of NL lines):
-//   y pass      complex FFT along y, in place
+// Passes (one CTA per tile of NL lines, or persistent CTAs walking the tiles):
+//   y pass      complex FFT along y, in place (tiles moved by tensor copies)
 //   x passes    multiplier(s) + complex FFT along x, fused with CG vector updates
 //   z turn      packed -> C2R -> multiply by a real diagonal -> R2C -> packed (one z line)
 //   z fwd/inv   real rows <-> packed spectrum rows, with epilogues
@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include "wf_fft.cuh"
+#include "wf_tma.cuh"
 
 namespace wf {
 
@@ -175,26 +176,145 @@ WF_D void tile_store(const cx<R>* tile, typename G::ST* g, size_t rowstride, int
   }
 }
 
-// y pass: complex FFT along y of every (x, kz) line; in place.  grid (N/2 / NL, N).
-template <class R, int N, int DIR, int EX = elems_for<R>(N, xy_lines<R, N>())>
-__global__ void __launch_bounds__(XYG<R, N, EX>::NT)
-k_ypass(typename Store<R>::T* __restrict__ spec, const typename Store<R>::T* __restrict__ twtab,
-        const CgScal* __restrict__ sc, Bat bt) {
-  using G = XYG<R, N, EX>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
-  cx<R>* tw = tile + G::M * G::LD;
-  const int z = blockIdx.z;
-  if (sc && sc[z].done) return;
-  spec += z * bt.spec;
+// ------------------------------------------------------------------------------------------
+// Persistent passes with tensor copies.  Geometry: a tile is M = N rows (the transform axis) by
+// NL consecutive kz columns, stored densely in shared memory (row i, column l at i NL + l: a row
+// is NL x 8 bytes for FP32, so two rows fill the 32 banks and a warp's row accesses need the two
+// wavefronts 256 bytes take anyway).  The tensor copy moves the tile as NBOX boxes of BR rows
+// (a box side is at most 256).  A CTA keeps STG tiles in flight and walks the tiles t =
+// blockIdx.x, blockIdx.x + gridDim.x, ... of all systems, skipping finished ones.
+// ------------------------------------------------------------------------------------------
+// lines per tile of the tensor-copy passes: the largest divisor of N/2 up to the 128-byte row
+// whose row and column offsets keep the copies 16-byte aligned (2 NL reals a multiple of 16 bytes)
+template <class R, int N> constexpr int tma_lines() {
+  int d = cmin(N / 2, tile_lines<R>());
+  while (d > 1 && ((N / 2) % d != 0 || (2 * d * (int)sizeof(typename Store<R>::S)) % 16 != 0)) --d;
+  return d;
+}
+
+template <class R, int N, int NL_, int STG_>
+struct TG {
+  using ST = typename Store<R>::T;
+  static constexpr int M = N, NH = N / 2, NL = NL_, STG = STG_;
+  static constexpr int E = elems_for<R>(N, NL);
+  static constexpr int TPL = M / E >= 1 ? M / E : 1;
+  static constexpr int NT = NL * TPL;
+  static constexpr int BR = N <= 256 ? N : N / 2;  // rows per tensor box
+  static constexpr int NBOX = N / BR;
+  static constexpr unsigned TILE_BYTES = (unsigned)(M * NL * sizeof(ST));
+  // buffers start on 128-byte boundaries (tensor copies into shared memory need that)
+  static constexpr int SSTR = (int)(((TILE_BYTES + 127) / 128) * 128 / sizeof(ST));  // elements
+  static constexpr int KB = NH / NL;  // kz blocks per plane
+  static constexpr int TPS = KB * N;  // tiles per system
+  static constexpr size_t SMEM = 128 + (size_t)STG * SSTR * sizeof(cx<R>) + (size_t)M * sizeof(cx<R>) + 16 * STG;
+  static_assert(NH % NL == 0 && BR <= 256 && N % BR == 0, "tile geometry");
+  static_assert((2 * NL * sizeof(typename Store<R>::S)) % 16 == 0, "16-byte aligned tensor copies");
+  static_assert(NBOX == 1 || (BR * NL * sizeof(ST)) % 128 == 0, "boxes of a tile on 128-byte boundaries");
+  static_assert(sizeof(cx<R>) == sizeof(ST), "tiles hold storage elements");
+};
+
+// Tile order of the persistent passes: id -> (system z, plane index a, kz block kb).
+template <class G> struct TileSeq {
+  const CgScal* sc;
+  int total;
+  WF_D bool live(int id) const { return !(sc && sc[id / G::TPS].done); }
+  // the first live tile at or after id in steps of `step` (total if none)
+  WF_D int next(int id, int step) const {
+    while (id < total && !live(id)) id += step;
+    return id < total ? id : total;
+  }
+};
+
+// Wait (bounded) for the tile in buffer s; returns false for every thread if any thread timed
+// out, after reporting it in *err.  Must be called by all threads.
+// (A thread whose own wait completed has consumed that phase: its parity bit flips and the buffer
+// leaves its `pending` set.)
+template <int STG>
+WF_D bool tile_arrived(uint64_t* bar, int s, unsigned& phase, unsigned& pending, int* err) {
+  const bool mine = mbar_wait(&bar[s], (phase >> s) & 1u);
+  if (mine) {
+    phase ^= 1u << s;
+    pending &= ~(1u << s);
+  }
+  const bool bad = __syncthreads_or(!mine);
+  if (bad && threadIdx.x == 0 && err) atomicExch(err, 1);
+  return !bad;
+}
+
+// Before the CTA exits: wait for its stores, and after a timeout also (bounded) for the loads
+// still in flight into its buffers.  Thread 0 only.
+template <int STG>
+WF_D void tiles_drain(uint64_t* bar, unsigned phase, unsigned pending, bool ok) {
+  if (!ok)
+    for (int j = 0; j < STG; ++j)
+      if ((pending >> j) & 1u) (void)mbar_wait(&bar[j], (phase >> j) & 1u);
+  bulk_wait<0>();
+}
+
+// y pass with tensor copies: complex FFT along y of every (x, kz) line, in place.  The map covers
+// the spectra with box {2 NL, BR, 1, 1} (rows = y).  grid: persistent.
+// RMAX caps the radix of the transform's stages (8, 16 or 32: larger radices take fewer
+// shared-memory round trips and more registers).
+template <class R, int N, int DIR, int NL, int STG, int RMAX>
+__global__ void __launch_bounds__(TG<R, N, NL, STG>::NT)
+k_ypass_tma(const __grid_constant__ CUtensorMap tm, const typename Store<R>::T* __restrict__ twtab,
+            const CgScal* __restrict__ sc, int nb, int* __restrict__ err) {
+  using G = TG<R, N, NL, STG>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+  cx<R>* tw = buf + STG * G::SSTR;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tw + G::M);
   const int tid = threadIdx.x;
-  const int kz0 = blockIdx.x * G::NL, x = blockIdx.y;
-  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
-  typename G::ST* base = spec + (size_t)x * N * G::NH + kz0;
-  tile_load<G>(tile, base, G::NH, tid);
+  const TileSeq<G> seq{sc, nb * G::TPS};
+  if (tid == 0) {
+    prefetch_tensormap(&tm);
+    for (int s = 0; s < STG; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
   __syncthreads();
-  fft_line<R, G::M, G::TPL, G::LD, DIR>(tile + tid % G::NL, tid / G::NL, tw);
-  tile_store<G>(tile, base, G::NH, tid);
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
+  auto issue = [&](int id, int s) {
+    const int z = id / G::TPS, rem = id % G::TPS, x = rem / G::KB, kz0 = (rem % G::KB) * NL;
+    mbar_expect_tx(&bar[s], G::TILE_BYTES);
+    for (int q = 0; q < G::NBOX; ++q) tma_load_4d(buf + s * G::SSTR + q * G::BR * NL, &tm, 2 * kz0, q * G::BR, x, z, &bar[s]);
+  };
+  // the tiles of this CTA, STG - 1 of them loading ahead of the one being transformed
+  int ids[STG];
+  ids[0] = seq.next(blockIdx.x, gridDim.x);
+  for (int j = 1; j < STG; ++j) ids[j] = seq.next(ids[j - 1] < seq.total ? ids[j - 1] + gridDim.x : seq.total, gridDim.x);
+  unsigned pending = 0;  // buffers with a load in flight (thread 0's view)
+  if (tid == 0)
+    for (int j = 0; j < STG - 1; ++j)
+      if (ids[j] < seq.total) {
+        issue(ids[j], j);
+        pending |= 1u << j;
+      }
+  unsigned phase = 0;
+  bool ok = true;
+  for (int k = 0; ids[0] < seq.total; ++k) {
+    const int s = k % STG;
+    // refill the buffer the previous tile used (its store must have finished reading it)
+    if (tid == 0 && ids[STG - 1] < seq.total) {
+      bulk_wait_read<0>();
+      issue(ids[STG - 1], (k + STG - 1) % STG);
+      pending |= 1u << ((k + STG - 1) % STG);
+    }
+    ok = tile_arrived<STG>(bar, s, phase, pending, err);
+    if (!ok) break;
+    cx<R>* tile = buf + s * G::SSTR;
+    fft_line<R, G::M, G::TPL, NL, DIR, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + tid % NL, tid / NL, tw);
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      const int id = ids[0];
+      const int z = id / G::TPS, rem = id % G::TPS, x = rem / G::KB, kz0 = (rem % G::KB) * NL;
+      for (int q = 0; q < G::NBOX; ++q) tma_store_4d(&tm, 2 * kz0, q * G::BR, x, z, tile + q * G::BR * NL);
+      bulk_commit();
+    }
+    for (int j = 0; j < STG - 1; ++j) ids[j] = ids[j + 1];
+    ids[STG - 1] = seq.next(ids[STG - 2] < seq.total ? ids[STG - 2] + gridDim.x : seq.total, gridDim.x);
+  }
+  if (tid == 0) tiles_drain<STG>(bar, phase, pending, ok);
 }
 
 // Apply the packed-column multiplier pair to column 0 of a tile (slot 0) using the partner

@@ -322,6 +322,40 @@ def test_fixed_iterations_preconditioned_match_oracle_pcg(ctx, n):
         assert rl2(host(s), ref) <= fp32_iterate_tol(n), k
 
 
+def test_autotune_every_variant_matches_oracle(ctx):
+    """wf_autotune times each launch variant of the FP32 passes at 128^3 and keeps the fastest;
+    every variant (forced through the tuning table) gives the oracle's preconditioned-CG iterate
+    within the FP32 bound, and the table round-trips through its JSON form."""
+    n = 128
+    pr = synth.problem("c2", n_override=n, cache=False)
+    nobs = ctx.grid_assign(gpu(pr.pos), pr.n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
+    wh, bh = host(w), host(b)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    ref = oracle.pcg(tab, _prior_preconditioner(tab, nbar, wh), nbar, wh, bh, tol=1e-14, max_iter=3,
+                     allow_unconverged=True)[0]
+    before = ctx.tune_get()
+    report = ctx.autotune(n, wf.MIXED)
+    passes = {p["pass"]: p for p in report}
+    table = ctx.tune_get()
+    assert set(passes) <= set(table)
+    for key, p in passes.items():
+        names = [v["name"] for v in p["variants"]]
+        assert len(names) >= 2 and all(v["ms"] > 0 for v in p["variants"])
+        assert names[table[key]] == p["chosen"]
+        assert p["variants"][table[key]]["ms"] == min(v["ms"] for v in p["variants"])
+        for i in range(len(names)):
+            ctx.tune_set({key: i})
+            s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=3, precond=1,
+                                prec=wf.MIXED, check=False)
+            assert info.iters == 3
+            assert rl2(host(s), ref) <= fp32_iterate_tol(n), (key, names[i])
+    ctx.tune_set(table)
+    assert ctx.tune_get() == table
+    ctx.tune_set({k: 0 for k in table if k not in before})   # leave the shared context as it was
+    ctx.tune_set(before)
+
+
 def test_fixed_iterations_full_size_workload(ctx):
     """The 512^3 workload the benchmark times, where a converged oracle solve does not fit in test
     time: both sides run k = 20 textbook-CG iterations from 0 (precond = 0).  The FP64 path holds
