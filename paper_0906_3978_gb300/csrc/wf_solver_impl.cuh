@@ -25,6 +25,7 @@
 #pragma once
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <cmath>
 #include <vector>
 
@@ -65,10 +66,12 @@ struct Spec {
   static constexpr size_t SPEC = (size_t)N * N * NH;  // complex elements of a spectrum
   static constexpr size_t V = (size_t)N * N * N;
   static constexpr int TAB = 3 * (N / 2) * (N / 2) + 1;
-  // partial sums per system: the largest of GXY + (z-turn or plane-kernel blocks), GZ, 2 GXY (the
-  // fused update's two sums per block)
+  // partial sums per system.  An x pass writes one (the first) or two (the second) per tile, at
+  // most NX tiles whatever its variant; the middle passes (z turn or plane kernel) write theirs
+  // from offset NX.
+  static constexpr int NX = N * NH;
   static constexpr int NMID = GZ > N * 8 ? GZ : N * 8;
-  static constexpr int NPART = GXY + NMID > 2 * GXY ? GXY + NMID : 2 * GXY;
+  static constexpr int NPART = NX + NMID > 2 * NX ? NX + NMID : 2 * NX;
   static dim3 gxy(int nb) { return dim3(NH / NLxy, N, nb); }
   static dim3 gz(int nb) { return dim3(GZ, 1, nb); }
   static Bat bat() { return Bat{SPEC, V, TAB, NPART}; }
@@ -102,6 +105,8 @@ struct Spec {
     WF_A((k_zinv<R, N, ZI_ACCUM>), SMz);
 #undef WF_A
     for (const PassVariant& v : yvariants())
+      if (e == cudaSuccess) e = v.setup();
+    for (const XVariant& v : xvariants())
       if (e == cudaSuccess) e = v.setup();
     if (e == cudaSuccess) done = true;
     return e;
@@ -161,10 +166,120 @@ struct Spec {
     }();
     return v;
   }
+  // ---- x-pass variants: the two CG x passes, staged by tensor copies (<NL, STG, RMAX>) or the
+  // register-staged kernels; each launcher returns the number of partial sums it wrote -------
+  using XinvRun = int (*)(Ctx&, int, ST*, ST*, ST*, ST*, ST*, const SS*, const SS*, bool, const ST*, double*,
+                          CgScal*, cudaStream_t);
+  using XupdRun = int (*)(Ctx&, int, const ST*, ST*, ST*, ST*, const SS*, const SS*, bool, const ST*, double*,
+                          CgScal*, cudaStream_t);
+  struct XVariant {
+    const char* name;
+    cudaError_t (*setup)();
+    XinvRun xinv;
+    XupdRun xupd;
+  };
+  template <int NL, int STG, int RMAX, int EX = elems_for<R>(N, NL), int COPY = 0>
+  struct XV {
+    using G = TG<R, N, NL, STG, EX>;
+    static constexpr size_t SM = TXG<R, N, NL, STG, 3>::SMEM;
+    static inline int occ = 1;
+    static cudaError_t setup() {
+      cudaError_t e = set_smem(k_cg_xinv_tma<R, N, true, NL, STG, RMAX, EX, COPY>, SM);
+      if (e == cudaSuccess) e = set_smem(k_cg_xinv_tma<R, N, false, NL, STG, RMAX, EX, COPY>, SM);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd_tma<R, N, true, NL, STG, RMAX, EX, COPY>, SM);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd_tma<R, N, false, NL, STG, RMAX, EX, COPY>, SM);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cg_xinv_tma<R, N, true, NL, STG, RMAX, EX, COPY>,
+                                                          G::NT, SM);
+      if (occ < 1) occ = 1;
+      return e;
+    }
+    // tensor maps for the tensor-copy form; the row-copy form passes zeroed (unused) maps
+    static bool map(Ctx& c, CUtensorMap* m, const void* p, int nb) {
+      if (COPY == 1) {
+        std::memset(m, 0, sizeof(*m));
+        return true;
+      }
+      if (make_spectrum_map(m, const_cast<void*>(p), N, nb, sizeof(SS) == 8, NL, 1, G::BR)) return true;
+      c.map_failed = true;
+      return false;
+    }
+    static int xinv(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* ctab, const SS* mtab, bool unit_m,
+                    const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
+      CUtensorMap mr, m0, m1, mx, mt;
+      if (!map(c, &mr, r, nb) || !map(c, &m0, P0, nb) || !map(c, &m1, P1, nb) || !map(c, &mx, x, nb) ||
+          !map(c, &mt, T, nb))
+        return G::TPS;
+      const unsigned grid = persistent_grid(c, occ, (long long)nb * G::TPS);
+      c.launch("cg_xinv", 6 * BS * nb, st, [&] {
+        if (unit_m)
+          k_cg_xinv_tma<R, N, true, NL, STG, RMAX, EX, COPY><<<grid, G::NT, SM, st>>>(
+              mr, m0, m1, mx, mt, r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat(), nb, c.dev_err);
+        else
+          k_cg_xinv_tma<R, N, false, NL, STG, RMAX, EX, COPY><<<grid, G::NT, SM, st>>>(
+              mr, m0, m1, mx, mt, r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat(), nb, c.dev_err);
+      });
+      return G::TPS;
+    }
+    static int xupd(Ctx& c, int nb, const ST* T, ST* r, ST* P0, ST* P1, const SS* ctab, const SS* mtab, bool unit_m,
+                    const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
+      CUtensorMap mt, mr, m0, m1;
+      if (!map(c, &mt, T, nb) || !map(c, &mr, r, nb) || !map(c, &m0, P0, nb) || !map(c, &m1, P1, nb)) return G::TPS;
+      const unsigned grid = persistent_grid(c, occ, (long long)nb * G::TPS);
+      c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+        if (unit_m)
+          k_cg_xupd_tma<R, N, true, NL, STG, RMAX, EX, COPY><<<grid, G::NT, SM, st>>>(
+              mt, mr, m0, m1, T, P0, P1, r, ctab, mtab, tw, part, sc, bat(), nb, c.dev_err);
+        else
+          k_cg_xupd_tma<R, N, false, NL, STG, RMAX, EX, COPY><<<grid, G::NT, SM, st>>>(
+              mt, mr, m0, m1, T, P0, P1, r, ctab, mtab, tw, part, sc, bat(), nb, c.dev_err);
+      });
+      return G::TPS;
+    }
+  };
+  // the register-staged kernels (one CTA per tile, loads through registers)
+  struct XReg {
+    static cudaError_t setup() { return cudaSuccess; }  // attrs() sets their shared memory
+    static int xinv(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* ctab, const SS* mtab, bool unit_m,
+                    const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
+      c.launch("cg_xinv", 6 * BS * nb, st, [&] {
+        if (unit_m) k_cg_xinv<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
+        else k_cg_xinv<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
+      });
+      return GXY;
+    }
+    static int xupd(Ctx& c, int nb, const ST* T, ST* r, ST* P0, ST* P1, const SS* ctab, const SS* mtab, bool unit_m,
+                    const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
+      c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+        if (unit_m) k_cg_xupd<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
+        else k_cg_xupd<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
+      });
+      return GXY;
+    }
+  };
+  static constexpr int NLX = xtma_lines<R, N, 3, 2>();
+  static const std::vector<XVariant>& xvariants() {
+    static const std::vector<XVariant> v = [] {
+      // variant 0: the register-staged kernels, measured fastest at every size (512^3 FP32: 0.72 and
+      // 0.58 ms against 1.23-1.83 ms for the staged forms, whose single resident CTA per SM
+      // serialises each tile's table gathers, transform and epilogue); the staged forms stay
+      // candidates for the tuner on the FP32 grids of 128 and up
+      std::vector<XVariant> out{{"registers", XReg::setup, XReg::xinv, XReg::xupd}};
+      if constexpr (std::is_same<R, float>::value && N >= 128 && N % 8 == 0 && NLX * (N / 8) <= 512) {
+        using E8 = XV<NLX, 2, 8, 8, 1>;  // per-thread row copies, 8 elements per thread
+        using T8 = XV<NLX, 2, 8, 8, 0>;  // tensor copies, 8 elements per thread
+        out.push_back({"rows_s2_e8", E8::setup, E8::xinv, E8::xupd});
+        out.push_back({"tensor_s2_e8", T8::setup, T8::xinv, T8::xupd});
+      }
+      return out;
+    }();
+    return v;
+  }
   static std::string tune_key(const char* pass) {
     return std::string(pass) + (sizeof(SS) == 8 ? "/f64/" : "/f32/") + std::to_string(N);
   }
-  static const PassVariant& pick(const Ctx& c, const char* pass, const std::vector<PassVariant>& vs) {
+  template <class V>
+  static const V& pick(const Ctx& c, const char* pass, const std::vector<V>& vs) {
     auto it = c.tuned.find(tune_key(pass));
     const int i = it == c.tuned.end() ? 0 : it->second;
     return vs[i >= 0 && i < (int)vs.size() ? i : 0];
@@ -200,16 +315,13 @@ struct Spec {
                         const SS* mtab, bool unit_m, const ST* tw, double* part, CgScal* sc, double inv_vc,
                         cudaStream_t st) {
     const Bat b = bat();
-    c.launch("cg_xinv", 6 * BS * nb, st, [&] {
-      if (unit_m) k_cg_xinv<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, b);
-      else k_cg_xinv<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, b);
-    });
-    int nmid = GZ;  // blocks that sum the data term of <p, A p> into part[GXY ...]
+    const int n1 = pick(c, "xinv", xvariants()).xinv(c, nb, r, P0, P1, x, T, ctab, mtab, unit_m, tw, part, sc, st);
+    int nmid = GZ;  // blocks that sum the data term of <p, A p> into part[NX ...]
     bool fused = false;
     if constexpr (PCS > 0) {
       if (c.fused_planes) {
         c.launch("plane_turn", (2 * BS + sizeof(SS) * BV) * nb, st,
-                 [&] { plane_turn_launch<R, N, PCS, PE>(T, D, tw, part + GXY, sc, b, nb, st); });
+                 [&] { plane_turn_launch<R, N, PCS, PE>(T, D, tw, part + NX, sc, b, nb, st); });
         nmid = N * PCS;
         fused = true;
       }
@@ -217,15 +329,12 @@ struct Spec {
     if (!fused) {
       ypass(c, nb, T, tw, sc, +1, st);
       c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st,
-               [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, part + GXY, sc, b); });
+               [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, part + NX, sc, b); });
       ypass(c, nb, T, tw, sc, -1, st);
     }
-    c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, GXY, nmid, sc, b); });
-    c.launch("cg_xupd", 4 * BS * nb, st, [&] {
-      if (unit_m) k_cg_xupd<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, b);
-      else k_cg_xupd<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, b);
-    });
-    c.launch("fin", 0, st, [&] { k_fin_beta<<<nb, 1024, 0, st>>>(part, GXY, inv_vc, sc, b); });
+    c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, n1, NX, nmid, sc, b); });
+    const int n3 = pick(c, "xupd", xvariants()).xupd(c, nb, T, r, P0, P1, ctab, mtab, unit_m, tw, part, sc, st);
+    c.launch("fin", 0, st, [&] { k_fin_beta<<<nb, 1024, 0, st>>>(part, n3, inv_vc, sc, b); });
   }
 };
 
@@ -846,6 +955,56 @@ wf_status tune_spec(Ctx& c, std::string& report) {
   WF_TRY(tune_pass<SP>(c, "ypass", SP::yvariants(), buf, nb, tw, st, report));
   WF_CUDA(cudaStreamSynchronize(st));
   c.release_prefix("tune_spec");
+  // the CG x passes: five spectra per system, scalars of running systems, unit tables
+  using SS = typename SP::SS;
+  const size_t SPEC = SP::SPEC;
+  ST* xb;
+  SS* tab;
+  double* part;
+  CgScal* sc;
+  WF_TRY(c.get("tune_x", (size_t)5 * nb * SPEC * sizeof(ST), (void**)&xb));
+  WF_TRY(c.get("tune_xtab", (size_t)nb * SP::TAB * sizeof(SS), (void**)&tab));
+  WF_TRY(c.get("tune_xpart", (size_t)nb * SP::NPART * sizeof(double), (void**)&part));
+  WF_TRY(c.get("tune_xsc", (size_t)nb * sizeof(CgScal), (void**)&sc));
+  WF_CUDA(cudaMemsetAsync(xb, 0, (size_t)5 * nb * SPEC * sizeof(ST), st));
+  WF_CUDA(cudaMemsetAsync(sc, 0, (size_t)nb * sizeof(CgScal), st));
+  {
+    std::vector<SS> ones((size_t)nb * SP::TAB, (SS)1);
+    WF_CUDA(cudaMemcpyAsync(tab, ones.data(), ones.size() * sizeof(SS), cudaMemcpyHostToDevice, st));
+    WF_CUDA(cudaStreamSynchronize(st));
+  }
+  ST *r = xb, *P0 = xb + nb * SPEC, *P1 = xb + 2 * nb * SPEC, *x = xb + 3 * nb * SPEC, *T = xb + 4 * nb * SPEC;
+  struct XRun {
+    const typename SP::XVariant* v;
+    bool inv;
+    const char* name;
+    void run(Ctx& c, int nb, cudaStream_t st, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* tab, const ST* tw,
+             double* part, CgScal* sc, int, int) const {
+      if (inv) v->xinv(c, nb, r, P0, P1, x, T, tab, tab, true, tw, part, sc, st);
+      else v->xupd(c, nb, T, r, P0, P1, tab, tab, true, tw, part, sc, st);
+    }
+  };
+  for (int inv = 1; inv >= 0; --inv) {
+    std::vector<XRun> runs;
+    for (const auto& v : SP::xvariants()) runs.push_back(XRun{&v, inv == 1, v.name});
+    struct Adapter {
+      const XRun* x;
+      ST *r, *P0, *P1, *xx, *T;
+      const SS* tab;
+      double* part;
+      CgScal* sc;
+      const char* name;
+      void run(Ctx& c, int nb, ST*, const ST* tw, const CgScal*, int, cudaStream_t st) const {
+        x->run(c, nb, st, r, P0, P1, xx, T, tab, tw, part, sc, 0, 0);
+      }
+    };
+    std::vector<Adapter> ad;
+    for (const auto& rr : runs) ad.push_back(Adapter{&rr, r, P0, P1, x, T, tab, part, sc, rr.name});
+    report += ", ";
+    WF_TRY(tune_pass<SP>(c, inv ? "xinv" : "xupd", ad, r, nb, tw, st, report));
+  }
+  WF_CUDA(cudaStreamSynchronize(st));
+  c.release_prefix("tune_x");
   return WF_OK;
 }
 

@@ -192,11 +192,11 @@ template <class R, int N> constexpr int tma_lines() {
   return d;
 }
 
-template <class R, int N, int NL_, int STG_>
+template <class R, int N, int NL_, int STG_, int EX = elems_for<R>(N, NL_)>
 struct TG {
   using ST = typename Store<R>::T;
   static constexpr int M = N, NH = N / 2, NL = NL_, STG = STG_;
-  static constexpr int E = elems_for<R>(N, NL);
+  static constexpr int E = EX;  // elements per thread (a divisor of N)
   static constexpr int TPL = M / E >= 1 ? M / E : 1;
   static constexpr int NT = NL * TPL;
   static constexpr int BR = N <= 256 ? N : N / 2;  // rows per tensor box
@@ -207,7 +207,7 @@ struct TG {
   static constexpr int KB = NH / NL;  // kz blocks per plane
   static constexpr int TPS = KB * N;  // tiles per system
   static constexpr size_t SMEM = 128 + (size_t)STG * SSTR * sizeof(cx<R>) + (size_t)M * sizeof(cx<R>) + 16 * STG;
-  static_assert(NH % NL == 0 && BR <= 256 && N % BR == 0, "tile geometry");
+  static_assert(NH % NL == 0 && BR <= 256 && N % BR == 0 && N % E == 0, "tile geometry");
   static_assert((2 * NL * sizeof(typename Store<R>::S)) % 16 == 0, "16-byte aligned tensor copies");
   static_assert(NBOX == 1 || (BR * NL * sizeof(ST)) % 128 == 0, "boxes of a tile on 128-byte boundaries");
   static_assert(sizeof(cx<R>) == sizeof(ST), "tiles hold storage elements");
@@ -615,6 +615,467 @@ k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __re
     partials[2 * bid] = s1;
     partials[2 * bid + 1] = s2;
   }
+}
+
+// ------------------------------------------------------------------------------------------
+// Persistent CG x passes with tensor copies.  A stage holds NS tiles (one per staged stream), all
+// loaded by tensor copies along x (box {2 NL, 1, BR, 1}) and completed on the stage's barrier.
+// The packed column's partner line (-ky) is read with plain loads into its own buffer, only by
+// the tiles that hold column kz = 0.  Partial sums are written per tile, at index
+// ky * (N/2 / NL) + kz0 / NL of the system, so the finishers sum them in a fixed order.
+// ------------------------------------------------------------------------------------------
+// lines per tile of the staged x passes: the largest divisor of N/2 up to the 128-byte row that
+// keeps the copies 16-byte aligned and lets STG stages of NS tiles fit in shared memory
+template <class R, int N, int NS, int STG> constexpr int xtma_lines() {
+  int d = cmin(N / 2, tile_lines<R>());
+  while (d > 1 && ((N / 2) % d != 0 || (2 * d * (int)sizeof(typename Store<R>::S)) % 16 != 0 ||
+                   (long)STG * NS * N * d * (long)sizeof(cx<R>) + 2L * N * (long)sizeof(cx<R>) > 200L * 1024))
+    --d;
+  return d;
+}
+
+// shared memory of a staged x pass: STG stages of NS tiles, the twiddles, the partner line, one
+// tile of Fourier-table entries and the barriers
+template <class R, int N, int NL, int STG, int NS>
+struct TXG {
+  using G = TG<R, N, NL, STG>;
+  static constexpr size_t SMEM = 128 + (size_t)STG * NS * G::SSTR * sizeof(cx<R>) + 2 * (size_t)N * sizeof(cx<R>) +
+                                 (size_t)N * NL * sizeof(typename Store<R>::S) + 16 * STG;
+};
+
+// Row copies of a dense x-pass tile (M rows of NL elements, row i at g + i rowstride) as 16-byte
+// pieces, each thread a fixed share: per-thread asynchronous copies in, plain vector stores out.
+template <class G, class R, class ST>
+WF_D void tile_rows_async(cx<R>* tile, const ST* g, size_t rowstride, int tid) {
+  constexpr int VW = 16 / (int)sizeof(ST), NV = G::NL / VW, NVEC = G::M * NV;
+  static_assert(G::NL % VW == 0, "whole 16-byte pieces per row");
+#pragma unroll 4
+  for (int idx = tid; idx < NVEC; idx += G::NT) {
+    const int i = idx / NV, v = (idx % NV) * VW;
+    cp_async16(tile + i * G::NL + v, g + (size_t)i * rowstride + v);
+  }
+}
+template <class G, class R, class ST>
+WF_D void tile_rows_store(const cx<R>* tile, ST* g, size_t rowstride, int tid) {
+  constexpr int VW = 16 / (int)sizeof(ST), NV = G::NL / VW, NVEC = G::M * NV;
+#pragma unroll 4
+  for (int idx = tid; idx < NVEC; idx += G::NT) {
+    const int i = idx / NV, v = (idx % NV) * VW;
+    *reinterpret_cast<float4*>(g + (size_t)i * rowstride + v) = *reinterpret_cast<const float4*>(tile + i * G::NL + v);
+  }
+}
+
+// The multiplier pair of the packed column (slot 0 of each row) with its partner line held in
+// `part` (element kx at part[kx]).  Must be called by all threads; synchronises.
+template <class R, int N, int LD, class TAB>
+WF_D void combine_col0_sep(cx<R>* tile, const cx<R>* part, int ky_s, const TAB* tab, int tid, int nt) {
+  constexpr int NH = N / 2;
+  for (int kx = tid; kx < N; kx += nt) {
+    const int kxs = sfreq(kx, N);
+    const int n2 = kxs * kxs + ky_s * ky_s;
+    const R m0 = tab_to<R>(tab[n2]);
+    const R mN = tab_to<R>(tab[n2 + NH * NH]);
+    const R h = RT<R>::c(0.5);
+    const R a = (m0 + mN) * h, b = (m0 - mN) * h;
+    const cx<R> zc = tile[kx * LD];
+    const cx<R> zp = conj(part[(N - kx) % N]);
+    tile[kx * LD] = scale(zc, a) + scale(zp, b);
+  }
+  __syncthreads();
+}
+
+// x pass 1, staged (the work of k_cg_xinv):  p_new = r + beta p_old;  x += alpha_prev p_old;
+// T = IFFT_x(c (.) p_new);  partial of <p_new, m p_new>.  Stage tiles: r (becomes p_new), p_old
+// (becomes c p_new, then T), x.  COPY 0: tensor copies (maps mR, mP0, mP1, mX, mT) completed on
+// the stage's barrier, tensor stores; COPY 1: per-thread asynchronous row copies completed by
+// copy groups, plain stores (the maps are unused).
+template <class R, int N, bool UNIT_M, int NL, int STG, int RMAX, int EX, int COPY>
+__global__ void __launch_bounds__(TG<R, N, NL, STG, EX>::NT)
+k_cg_xinv_tma(const __grid_constant__ CUtensorMap mR, const __grid_constant__ CUtensorMap mP0,
+              const __grid_constant__ CUtensorMap mP1, const __grid_constant__ CUtensorMap mX,
+              const __grid_constant__ CUtensorMap mT, const typename Store<R>::T* __restrict__ r,
+              typename Store<R>::T* P0, typename Store<R>::T* P1, typename Store<R>::T* __restrict__ xg,
+              typename Store<R>::T* __restrict__ Tg,
+              const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
+              const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials,
+              const CgScal* __restrict__ sc, Bat bt, int nb, int* __restrict__ err) {
+  using G = TG<R, N, NL, STG, EX>;
+  using ST = typename Store<R>::T;
+  using SS = typename Store<R>::S;
+  constexpr int NS = 3, M = N, NH = N / 2;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[32];
+  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+  cx<R>* tw = buf + STG * NS * G::SSTR;
+  cx<R>* pl = tw + M;  // partner line of the packed column
+  uint64_t* bar = reinterpret_cast<uint64_t*>(reinterpret_cast<typename Store<R>::S*>(pl + M) + M * NL);
+  const int tid = threadIdx.x;
+  const TileSeq<G> seq{sc, nb * G::TPS};
+  if (tid == 0) {
+    prefetch_tensormap(&mR);
+    prefetch_tensormap(&mX);
+    prefetch_tensormap(&mT);
+    for (int s = 0; s < STG; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  load_tw<R, M, 2 * N>(tw, twtab, tid, G::NT);
+  const size_t rowstride = (size_t)N * NH;
+  auto issue = [&](int id, int s) {
+    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kz0 = (rem % G::KB) * NL;
+    if constexpr (COPY == 0) {
+      const CUtensorMap* mpo = (sc[z].lit & 1) ? &mP1 : &mP0;  // p_old
+      mbar_expect_tx(&bar[s], NS * G::TILE_BYTES);
+      for (int q = 0; q < G::NBOX; ++q) {
+        const int off = q * G::BR * NL;
+        tma_load_4d(buf + (s * NS + 0) * G::SSTR + off, &mR, 2 * kz0, ky, q * G::BR, z, &bar[s]);
+        tma_load_4d(buf + (s * NS + 1) * G::SSTR + off, mpo, 2 * kz0, ky, q * G::BR, z, &bar[s]);
+        tma_load_4d(buf + (s * NS + 2) * G::SSTR + off, &mX, 2 * kz0, ky, q * G::BR, z, &bar[s]);
+      }
+    } else {
+      const size_t o = z * bt.spec + (size_t)ky * NH + kz0;
+      const ST* po = ((sc[z].lit & 1) ? P1 : P0) + o;
+      tile_rows_async<G>(buf + (s * NS + 0) * G::SSTR, r + o, rowstride, tid);
+      tile_rows_async<G>(buf + (s * NS + 1) * G::SSTR, po, rowstride, tid);
+      tile_rows_async<G>(buf + (s * NS + 2) * G::SSTR, xg + o, rowstride, tid);
+    }
+  };
+  int ids[STG];
+  ids[0] = seq.next(blockIdx.x, gridDim.x);
+  for (int j = 1; j < STG; ++j) ids[j] = seq.next(ids[j - 1] < seq.total ? ids[j - 1] + gridDim.x : seq.total, gridDim.x);
+  unsigned pending = 0, phase = 0;
+  for (int j = 0; j < STG - 1; ++j) {
+    if (COPY == 0 && tid == 0 && ids[j] < seq.total) {
+      issue(ids[j], j);
+      pending |= 1u << j;
+    }
+    if constexpr (COPY == 1) {
+      if (ids[j] < seq.total) issue(ids[j], j);
+      cp_async_commit();
+    }
+  }
+  // Fourier-table entries of this thread's elements, one tile ahead: the next tile's are gathered
+  // while the current one is processed, so their latency overlaps the work
+  constexpr int PER = G::E;  // elements per thread: M NL / NT
+  SS cv[PER], mv[PER], cn[PER], mn[PER];
+  auto gather = [&](int id, SS* c, SS* m) {
+    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kz0 = (rem % G::KB) * NL;
+    const int ky_s = sfreq(ky, N);
+    const SS* ctz = ctab + z * bt.tab;
+    const SS* mtz = mtab + z * bt.tab;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = tid + k * G::NT, i = e / NL, kz = kz0 + e % NL;
+      const int kxs = sfreq(i, N);
+      const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
+      c[k] = ctz[n2];
+      m[k] = UNIT_M ? (SS)1 : mtz[n2];
+    }
+  };
+  if (ids[0] < seq.total) gather(ids[0], cv, mv);
+  bool ok = true;
+  for (int k = 0; ids[0] < seq.total; ++k) {
+    const int s = k % STG;
+    if constexpr (COPY == 0) {
+      if (tid == 0 && ids[STG - 1] < seq.total) {
+        bulk_wait_read<0>();
+        issue(ids[STG - 1], (k + STG - 1) % STG);
+        pending |= 1u << ((k + STG - 1) % STG);
+      }
+    } else {
+      if (ids[STG - 1] < seq.total) issue(ids[STG - 1], (k + STG - 1) % STG);
+      cp_async_commit();
+    }
+    const int id = ids[0];
+    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kb = rem % G::KB, kz0 = kb * NL;
+    const int ky_s = sfreq(ky, N);
+    const CgScal& S = sc[z];
+    const SS beta = (SS)S.beta, alpha_prev = (SS)S.alpha_prev;
+    const size_t o = z * bt.spec + (size_t)ky * NH + kz0;
+    const SS* ct = ctab + z * bt.tab;
+    const SS* mt = mtab + z * bt.tab;
+    // partner line of column 0: p_new at (kx, -ky, 0), recomputed from the inputs (plain loads,
+    // in flight while the tiles arrive)
+    if (kz0 == 0) {
+      const ST* pold = ((S.lit & 1) ? P1 : P0) + z * bt.spec;
+      const ST* rz = r + z * bt.spec;
+      const size_t pb = (size_t)((N - ky) % N) * NH;
+      for (int i = tid; i < M; i += G::NT) {
+        const size_t e = pb + (size_t)i * N * NH;
+        const ST rv = rz[e], po = pold[e];
+        pl[i] = cx<R>{rv.x + beta * po.x, rv.y + beta * po.y};
+      }
+    }
+    if (STG > 1 && ids[1] < seq.total) gather(ids[1], cn, mn);
+    if constexpr (COPY == 0) {
+      ok = tile_arrived<STG>(bar, s, phase, pending, err);
+      if (!ok) break;
+    } else {
+      cp_async_wait<STG - 1>();
+      __syncthreads();
+    }
+    cx<R>* tr = buf + (s * NS + 0) * G::SSTR;  // r -> p_new
+    cx<R>* tp = buf + (s * NS + 1) * G::SSTR;  // p_old -> c p_new -> T
+    cx<R>* tx = buf + (s * NS + 2) * G::SSTR;  // x
+    typename AccFor<SS>::T acc;  // <p_new, m p_new> over the columns kz != 0 (weight 2)
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = tid + k * G::NT, kz = kz0 + e % NL;
+      const cx<R> rv = tr[e], po = tp[e], xv = tx[e];
+      const cx<R> pn = cx<R>{rv.x + beta * po.x, rv.y + beta * po.y};
+      tx[e] = cx<R>{xv.x + alpha_prev * po.x, xv.y + alpha_prev * po.y};
+      tr[e] = pn;
+      if (kz != 0) {
+        acc.add((SS)2 * mv[k] * (pn.x * pn.x + pn.y * pn.y));
+        tp[e] = cx<R>{pn.x * cv[k], pn.y * cv[k]};
+      } else {
+        tp[e] = pn;  // the packed column stays raw for the pair combine
+      }
+    }
+    if constexpr (COPY == 0) {
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {  // p_new and x are final: store them while T is transformed
+        const CUtensorMap* mpn = (S.lit & 1) ? &mP0 : &mP1;
+        for (int q = 0; q < G::NBOX; ++q) {
+          tma_store_4d(mpn, 2 * kz0, ky, q * G::BR, z, tr + q * G::BR * NL);
+          tma_store_4d(&mX, 2 * kz0, ky, q * G::BR, z, tx + q * G::BR * NL);
+        }
+      }
+    } else {
+      __syncthreads();
+      tile_rows_store<G>(tr, ((S.lit & 1) ? P0 : P1) + o, rowstride, tid);
+      tile_rows_store<G>(tx, xg + o, rowstride, tid);
+    }
+    if (kz0 == 0) {
+      // m term of the packed column (weight 1): m0 |P0|^2 + mN |PN|^2 of its two planes
+      for (int kx = tid; kx < N; kx += G::NT) {
+        const int kxs = sfreq(kx, N);
+        const int n2 = kxs * kxs + ky_s * ky_s;
+        const cx<R> zc = tp[kx * NL];
+        const cx<R> zp = pl[(N - kx) % N];
+        const SS h = (SS)0.5;
+        const SS a0 = h * (zc.x + zp.x), b0 = h * (zc.y - zp.y);
+        const SS aN = h * (zc.y + zp.y), bN = h * (zp.x - zc.x);
+        acc.add(mt[n2] * (a0 * a0 + b0 * b0) + mt[n2 + NH * NH] * (aN * aN + bN * bN));
+      }
+      combine_col0_sep<R, N, NL>(tp, pl, ky_s, ct, tid, G::NT);
+    }
+    fft_line<R, M, G::TPL, NL, +1, 1, cmin(RMAX, rmax_for(M, G::TPL))>(tp + tid % NL, tid / NL, tw);
+    if constexpr (COPY == 0) {
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        for (int q = 0; q < G::NBOX; ++q) tma_store_4d(&mT, 2 * kz0, ky, q * G::BR, z, tp + q * G::BR * NL);
+        bulk_commit();
+      }
+    } else {
+      tile_rows_store<G>(tp, Tg + o, rowstride, tid);
+    }
+    const double sum = block_sum(acc.get(), red);
+    if (tid == 0) partials[z * bt.part + ky * G::KB + kb] = sum;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      cv[j] = cn[j];
+      mv[j] = mn[j];
+    }
+    for (int j = 0; j < STG - 1; ++j) ids[j] = ids[j + 1];
+    ids[STG - 1] = seq.next(ids[STG - 2] < seq.total ? ids[STG - 2] + gridDim.x : seq.total, gridDim.x);
+  }
+  if (COPY == 0 && tid == 0) tiles_drain<STG>(bar, phase, pending, ok);
+  if constexpr (COPY == 1) cp_async_wait<0>();
+}
+
+// x pass 2, staged (the work of k_cg_xupd):  T^ = FFT_x(T);  q = m p + c T^;  r -= alpha q;
+// partials of <r, r> and ||C^-1 r||^2 (two per tile).  Stage tiles: T, r, p_new.  COPY as for
+// x pass 1.
+template <class R, int N, bool UNIT_M, int NL, int STG, int RMAX, int EX, int COPY>
+__global__ void __launch_bounds__(TG<R, N, NL, STG, EX>::NT)
+k_cg_xupd_tma(const __grid_constant__ CUtensorMap mT, const __grid_constant__ CUtensorMap mR,
+              const __grid_constant__ CUtensorMap mP0, const __grid_constant__ CUtensorMap mP1,
+              const typename Store<R>::T* __restrict__ T, const typename Store<R>::T* P0,
+              const typename Store<R>::T* P1, typename Store<R>::T* __restrict__ rg,
+              const typename Store<R>::S* __restrict__ ctab,
+              const typename Store<R>::S* __restrict__ mtab, const typename Store<R>::T* __restrict__ twtab,
+              double* __restrict__ partials, const CgScal* __restrict__ sc, Bat bt, int nb, int* __restrict__ err) {
+  using G = TG<R, N, NL, STG, EX>;
+  using ST = typename Store<R>::T;
+  using SS = typename Store<R>::S;
+  constexpr int NS = 3, M = N, NH = N / 2;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ double red[32];
+  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
+  cx<R>* tw = buf + STG * NS * G::SSTR;
+  cx<R>* pl = tw + M;  // partner line of the packed column
+  typename Store<R>::S* ctile = reinterpret_cast<typename Store<R>::S*>(pl + M);  // c(k) of the tile
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ctile + M * NL);
+  const int tid = threadIdx.x;
+  const TileSeq<G> seq{sc, nb * G::TPS};
+  if (tid == 0) {
+    prefetch_tensormap(&mT);
+    prefetch_tensormap(&mR);
+    for (int s = 0; s < STG; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  load_tw<R, M, 2 * N>(tw, twtab, tid, G::NT);
+  const size_t rowstride = (size_t)N * NH;
+  auto issue = [&](int id, int s) {
+    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kz0 = (rem % G::KB) * NL;
+    if constexpr (COPY == 0) {
+      const CUtensorMap* mp = (sc[z].lit & 1) ? &mP0 : &mP1;  // this iteration's p_new
+      mbar_expect_tx(&bar[s], NS * G::TILE_BYTES);
+      for (int q = 0; q < G::NBOX; ++q) {
+        const int off = q * G::BR * NL;
+        tma_load_4d(buf + (s * NS + 0) * G::SSTR + off, &mT, 2 * kz0, ky, q * G::BR, z, &bar[s]);
+        tma_load_4d(buf + (s * NS + 1) * G::SSTR + off, &mR, 2 * kz0, ky, q * G::BR, z, &bar[s]);
+        tma_load_4d(buf + (s * NS + 2) * G::SSTR + off, mp, 2 * kz0, ky, q * G::BR, z, &bar[s]);
+      }
+    } else {
+      const size_t o = z * bt.spec + (size_t)ky * NH + kz0;
+      tile_rows_async<G>(buf + (s * NS + 0) * G::SSTR, T + o, rowstride, tid);
+      tile_rows_async<G>(buf + (s * NS + 1) * G::SSTR, rg + o, rowstride, tid);
+      tile_rows_async<G>(buf + (s * NS + 2) * G::SSTR, ((sc[z].lit & 1) ? P0 : P1) + o, rowstride, tid);
+    }
+  };
+  int ids[STG];
+  ids[0] = seq.next(blockIdx.x, gridDim.x);
+  for (int j = 1; j < STG; ++j) ids[j] = seq.next(ids[j - 1] < seq.total ? ids[j - 1] + gridDim.x : seq.total, gridDim.x);
+  unsigned pending = 0, phase = 0;
+  for (int j = 0; j < STG - 1; ++j) {
+    if (COPY == 0 && tid == 0 && ids[j] < seq.total) {
+      issue(ids[j], j);
+      pending |= 1u << j;
+    }
+    if constexpr (COPY == 1) {
+      if (ids[j] < seq.total) issue(ids[j], j);
+      cp_async_commit();
+    }
+  }
+  // c(k) of this thread's elements, one tile ahead (gathered while the current tile is processed)
+  constexpr int PER = G::E;  // elements per thread: M NL / NT
+  SS cv[PER], cn[PER];
+  auto gather = [&](int id, SS* c) {
+    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kz0 = (rem % G::KB) * NL;
+    const int ky_s = sfreq(ky, N);
+    const SS* ctz = ctab + z * bt.tab;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = tid + k * G::NT, i = e / NL, kz = kz0 + e % NL;
+      const int kxs = sfreq(i, N);
+      c[k] = ctz[kxs * kxs + ky_s * ky_s + kz * kz];
+    }
+  };
+  if (ids[0] < seq.total) gather(ids[0], cv);
+  bool ok = true;
+  for (int k = 0; ids[0] < seq.total; ++k) {
+    const int s = k % STG;
+    if constexpr (COPY == 0) {
+      if (tid == 0 && ids[STG - 1] < seq.total) {
+        bulk_wait_read<0>();
+        issue(ids[STG - 1], (k + STG - 1) % STG);
+        pending |= 1u << ((k + STG - 1) % STG);
+      }
+    } else {
+      if (ids[STG - 1] < seq.total) issue(ids[STG - 1], (k + STG - 1) % STG);
+      cp_async_commit();
+    }
+    const int id = ids[0];
+    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kb = rem % G::KB, kz0 = kb * NL;
+    const int ky_s = sfreq(ky, N), pky = (N - ky) % N;
+    const CgScal& S = sc[z];
+    const SS alpha = (SS)S.alpha;
+    const SS* ct = ctab + z * bt.tab;
+    const SS* mt = mtab + z * bt.tab;
+    const ST* p = ((S.lit & 1) ? P0 : P1) + z * bt.spec;
+    if (kz0 == 0) {  // partner line of T at -ky, column 0 (plain loads)
+      const ST* Tz = T + z * bt.spec;
+      for (int i = tid; i < M; i += G::NT) pl[i] = ld_c<R>(Tz + (size_t)pky * NH + (size_t)i * N * NH);
+    }
+    if (STG > 1 && ids[1] < seq.total) gather(ids[1], cn);
+    if constexpr (COPY == 0) {
+      ok = tile_arrived<STG>(bar, s, phase, pending, err);
+      if (!ok) break;
+    } else {
+      cp_async_wait<STG - 1>();
+      __syncthreads();
+    }
+    cx<R>* tt = buf + (s * NS + 0) * G::SSTR;
+    cx<R>* tr = buf + (s * NS + 1) * G::SSTR;
+    const cx<R>* tp = buf + (s * NS + 2) * G::SSTR;
+    fft_line<R, M, G::TPL, NL, -1, 1, cmin(RMAX, rmax_for(M, G::TPL))>(tt + tid % NL, tid / NL, tw);
+    if (kz0 == 0) {  // transform the partner line too, then apply c to column 0 as a packed pair
+      // (by all threads, a few elements each: a separate, small instance of the transform keeps
+      // the main one's register budget)
+      fft_line_map<R, M, G::NT, -1, 1, 8>(pl, Strided<1>{}, tid, tw);
+      combine_col0_sep<R, N, NL>(tt, pl, ky_s, ct, tid, G::NT);
+    }
+    typename AccFor<SS>::T a_rr, a_rc;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int e = tid + k * G::NT, i = e / NL, kz = kz0 + e % NL;
+      const cx<R> t = tt[e], pv = tp[e];
+      cx<R> rv = tr[e];
+      const SS c = cv[k];
+      SS ic2 = (SS)1 / (c * c);
+      SS q0, q1;
+      if (kz == 0) {
+        const int kxs = sfreq(i, N);
+        const int n2 = kxs * kxs + ky_s * ky_s;
+        // packed column: T^ already carries c; the m term combines p with p(-kx, -ky, 0) (in the
+        // storage type: FP64 here would run on GB300's 1/64-rate unit)
+        const SS cN = ct[n2 + NH * NH];
+        const SS i2 = (SS)1 / (cN * cN);
+        ic2 = ic2 > i2 ? ic2 : i2;
+        const SS m0 = mt[n2], mN = mt[n2 + NH * NH];
+        const SS a = (SS)0.5 * (m0 + mN), b = (SS)0.5 * (m0 - mN);
+        ST pp = ST{};
+        if (b != (SS)0) pp = p[(size_t)((N - i) % N) * N * NH + (size_t)pky * NH];
+        q0 = a * pv.x + b * pp.x + t.x;
+        q1 = a * pv.y - b * pp.y + t.y;
+      } else {
+        SS m = (SS)1;
+        if constexpr (!UNIT_M) {
+          const int kxs = sfreq(i, N);
+          m = mt[kxs * kxs + ky_s * ky_s + kz * kz];
+        }
+        q0 = m * pv.x + c * t.x;
+        q1 = m * pv.y + c * t.y;
+      }
+      rv.x -= alpha * q0;
+      rv.y -= alpha * q1;
+      tr[e] = rv;
+      const SS wgt = kz == 0 ? (SS)1 : (SS)2;
+      const SS m2 = wgt * (rv.x * rv.x + rv.y * rv.y);
+      a_rr.add(m2);
+      a_rc.add(ic2 * m2);
+    }
+    if constexpr (COPY == 0) {
+      fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        for (int q = 0; q < G::NBOX; ++q) tma_store_4d(&mR, 2 * kz0, ky, q * G::BR, z, tr + q * G::BR * NL);
+        bulk_commit();
+      }
+    } else {
+      __syncthreads();
+      tile_rows_store<G>(tr, rg + z * bt.spec + (size_t)ky * NH + kz0, rowstride, tid);
+    }
+    const double s1 = block_sum(a_rr.get(), red);
+    const double s2 = block_sum(a_rc.get(), red);
+    if (tid == 0) {
+      partials[z * bt.part + 2 * (ky * G::KB + kb)] = s1;
+      partials[z * bt.part + 2 * (ky * G::KB + kb) + 1] = s2;
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) cv[j] = cn[j];
+    for (int j = 0; j < STG - 1; ++j) ids[j] = ids[j + 1];
+    ids[STG - 1] = seq.next(ids[STG - 2] < seq.total ? ids[STG - 2] + gridDim.x : seq.total, gridDim.x);
+  }
+  if (COPY == 0 && tid == 0) tiles_drain<STG>(bar, phase, pending, ok);
+  if constexpr (COPY == 1) cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1037,14 +1498,15 @@ static __global__ void k_fin_init(const double* __restrict__ partials, int n, Cg
   }
 }
 
-// <p, A p> = partials [0, n1) (the m term, from the x pass) + [n1, n1 + n2) (the data term,
+// <p, A p> = partials [0, n1) (the m term, from the x pass) + [off2, off2 + n2) (the data term,
 // from the z turn); alpha = rr / <p, A p>.
-static __global__ void k_fin_alpha(const double* __restrict__ partials, int n1, int n2, CgScal* sc, Bat bt) {
+// (the first n1 partials of the system, and n2 from offset off2)
+static __global__ void k_fin_alpha(const double* __restrict__ partials, int n1, int off2, int n2, CgScal* sc, Bat bt) {
   __shared__ double red[32];
   sc += blockIdx.x;
   if (sc->done) return;
   const double pm = sum_partials(partials + blockIdx.x * bt.part, n1, 1, 0, red);
-  const double pd = sum_partials(partials + blockIdx.x * bt.part + n1, n2, 1, 0, red);
+  const double pd = sum_partials(partials + blockIdx.x * bt.part + off2, n2, 1, 0, red);
   const double pq = pm + pd;
   if (threadIdx.x == 0) {
     sc->pq = pq;

@@ -4,6 +4,9 @@ bounded, for use under a kernel profiler:
 
     python -m paper_0906_3978_gb300.profile_solve --n 256 --prec mixed --iters 4
     python -m paper_0906_3978_gb300.profile_solve --n 256 --what mask
+
+--tune times the launch variants first (wf_autotune) and prints the report; --variant
+xinv/f32/256=1 forces a variant of a pass (the context's tuning table).
 """
 import argparse
 import os
@@ -24,12 +27,22 @@ def main():
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--precond", type=int, default=1)
     ap.add_argument("--what", choices=["solve", "mask"], default="solve")
+    ap.add_argument("--tune", action="store_true")
+    ap.add_argument("--variant", action="append", default=[])
     a = ap.parse_args()
     wf.build()
     pr = synth.problem("c2", n_override=None if a.n == 256 else a.n, cache=False)
     if a.what == "mask":
         return mask(wf, pr)
     with wf.Context(0) as ctx:
+        prec = wf.MIXED if a.prec == "mixed" else wf.FP64
+        if a.tune:
+            for p in ctx.autotune(pr.n, prec):
+                print("tune %-14s chosen %-16s %s" % (p["pass"], p["chosen"],
+                                                       " ".join("%s=%.4f" % (v["name"], v["ms"]) for v in p["variants"])))
+        for v in a.variant:
+            key, idx = v.split("=")
+            ctx.tune_set({key: int(idx)})
         ctx.profile(True)
         nobs = ctx.grid_assign(torch.from_numpy(pr.pos).cuda(), pr.n, pr.box, pr.scheme, 2)
         w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
