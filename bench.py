@@ -190,6 +190,36 @@ def oracle_sample(pr, iters, deadline_s=40.0, single_thread=True):
     return 1.0 / t_solve, oracle.threads(), sample, t_solve, single
 
 
+def config_of(args, pr, ws):
+    """The workload description both arms print (identical keys and values)."""
+    return {"workload": WORKLOADS[args.workload], "n": pr.n, "n_gal": pr.n_gal,
+            "l2": "inputs larger than L2 (fine grid 8.6 GB, spectra 0.5-1.1 GB at 512^3)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
+def oracle_full_solve(name, threads):
+    """Seconds of one whole oracle reconstruction of workload `name` (assignment, low-pass, window,
+    noise, textbook CG to the workload's tolerance) on `threads` OpenMP threads, and its CG
+    iterations."""
+    import oracle
+    import synth
+    pr = synth.problem(name)
+    nt = oracle.threads()
+    oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        fine = oracle.assign(pr.pos, pr.n, pr.box, pr.scheme, 2)
+        nobs = oracle.lowpass(fine, pr.n, 2)
+        del fine
+        w = oracle.window(pr.sel, pr.n, pr.box)
+        d, b, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+        tab = oracle.sinv_table(pr.n, pr.box, pr.pk_k, pr.pk_p)
+        x, it, rel = oracle.cg(tab, nbar, w, b, tol=pr.tol, max_iter=100000)
+        return time.perf_counter() - t0, it, rel
+    finally:
+        oracle.set_threads(nt)
+
+
 def reference_arm(args):
     ws, rank, _ = dist_init()
     if rank != 0:
@@ -208,17 +238,20 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "n": pr.n, "n_gal": pr.n_gal},
+            "config": config_of(args, pr, args.gpus),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "extrapolated": True, "iterations_used": iters,
+                             "iterations_source": ITERS_SOURCE},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-# GPU FP64-solve iteration counts on each workload (from the GPU arm), used by the reference
-# arm to scale its per-iteration time to a solve.
-REF_ITERS = {"c3": 294, "c2": 150, "c1": 60}
+# GPU FP64-solve iteration counts on each workload, used by the reference arm (which runs without
+# a GPU) to scale its per-iteration time to a solve; the GPU arm uses the count it measures.
+REF_ITERS = {"c3": 297, "c2": 150, "c1": 60}
+ITERS_SOURCE = ("the GPU FP64 solve's CG iterations on this workload as bench.py's GPU arm measured them "
+                "(512^3: 297); the GPU arm's own cpu_baseline uses the count of its run")
 
 
 def cpu_model():
@@ -358,13 +391,19 @@ def gpu_arm(args):
     traffic = tr["bytes"] if tr and tr.get("src") == kernel_src_hash() else None
     it_fp64 = infos_fp64[-1]["iters"]
     cpu_v, cores, sample, _, single = oracle_sample(pr, it_fp64)
+    # whole oracle reconstructions of the 64^3 workload (seconds each), on all and on one thread
+    import oracle
+    t_all, it_c1, _ = oracle_full_solve("c1", oracle.threads())
+    t_one, _, _ = oracle_full_solve("c1", 1)
+    full = {"c1": {"workload": WORKLOADS["c1"], "cg_iters": it_c1, "threads": oracle.threads(),
+                   "s": round(t_all, 3), "s_1_thread": round(t_one, 3), "solves_per_s": 1.0 / t_all,
+                   "solves_per_s_1_thread": 1.0 / t_one},
+            "c2": "bench.py --cpu-full (minutes of host time)"}
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": k, "warmup": args.warmup,
         "ms_per_step": ms_mixed / k, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 FFT/CG inner, f64 dots+refinement", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "n": n, "n_gal": pr.n_gal,
-                   "l2": "inputs larger than L2 (fine grid 8.6 GB, spectra 0.5-1.1 GB at 512^3)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": config_of(args, pr, ws),
         "mixed": {"iters": infos_mixed[-1]["iters"], "outer": infos_mixed[-1]["outer_iters"],
                   "rel_residual": infos_mixed[-1]["rel_residual"], "rel_l2_vs_fp64_solve": diff,
                   "rel_l2_vs_converged": err_mixed},
@@ -383,7 +422,9 @@ def gpu_arm(args):
                                       "ms": {v["name"]: round(v["ms"], 4) for v in p["variants"]}}
                           for p in rep} for prec, rep in tuning.items()},
         "cpu_baseline": {"value": cpu_v, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
-                         "cpu": cpu_model(), "single_thread": single},
+                         "extrapolated": True, "iterations_used": it_fp64,
+                         "iterations_source": "this run's GPU FP64 solve", "cpu": cpu_model(),
+                         "single_thread": single, "full_solves": full},
         "e2e": {"value": ws * k / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(pr.pos.nbytes),
                 "d2h_bytes_per_step": int(n ** 3 * 8),
                 "note": "pinned host buffers; each solution's copy to the host overlaps the next step"},
@@ -518,18 +559,31 @@ def bench_batch(ctx, dev):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     probs = prepare()
+    torch.cuda.synchronize()
+    t_prep = time.perf_counter() - t0
     st, outs, infos = ctx.solve_batch(probs)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
-    # the same systems, one plain FP64 solve after another, same tolerance
-    t0 = time.perf_counter()
-    iters64 = 0
-    for pr in probs:
-        s, info = ctx.solve(pr["w"], pr["nbar"], pr["b"], pr["box"], pr["pk_k"], pr["pk_p"], tol=1e-6,
-                            max_iter=20000, prec=wf.FP64)
-        iters64 += info.iters
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
+    t_batch_solve = t_batch - t_prep
+
+    # the same work (gridding + window/noise + solve, same tolerance), one system after another:
+    # plain FP64, and mixed precision without batching
+    def sequential(prec):
+        for (n, box, sel, pos, k, p), pd in zip(mocks[:2], pos_d[:2]):   # warm each path once
+            nobs = ctx.grid_assign(pd, n, box, wf.TSC, 2)
+            w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
+            ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for (n, box, sel, pos, k, p), pd in zip(mocks, pos_d):
+            nobs = ctx.grid_assign(pd, n, box, wf.TSC, 2)
+            w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
+            ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    t_seq64 = sequential(wf.FP64)
+    t_seqmix = sequential(wf.MIXED)
     sizes = {}
     for m in mocks:
         sizes[m[0]] = sizes.get(m[0], 0) + 1
@@ -537,9 +591,13 @@ def bench_batch(ctx, dev):
                         "gridding + window/noise + one wf_solve_batch (mixed, FP32 inner / FP64 refinement) "
                         "to 1e-6" % sizes,
             "value": len(mocks) / t_batch, "unit": "solves/s", "status": st,
+            "solve_only": {"value": len(mocks) / t_batch_solve, "unit": "solves/s"},
             "max_rel_residual": max(i.rel_residual for i in infos),
-            "fp64_sequential": {"value": len(mocks) / t_seq, "unit": "solves/s",
-                                "note": "plain FP64 wf_solve one system at a time, same tolerance, solve only"}}
+            "fp64_sequential": {"value": len(mocks) / t_seq64, "unit": "solves/s",
+                                "note": "the same work (gridding + window/noise + plain FP64 wf_solve), one "
+                                        "system at a time, same tolerance"},
+            "mixed_sequential": {"value": len(mocks) / t_seqmix, "unit": "solves/s",
+                                 "note": "the same work with mixed-precision wf_solve, one system at a time"}}
 
 
 # ------------------------------------------------------------------------------------------
@@ -600,17 +658,74 @@ def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
     t_total = time.perf_counter() - t_start
     lat = np.array(lat)
     mean64 = float(np.mean([t64[int(n)] for n in sizes]))
+    # capacity: the first n_sat requests of the same size mix, all submitted at t = 0
+    n_sat = n_req // 2
+    t0 = time.perf_counter()
+    ids = []
+    for i in range(n_sat):
+        w, b, nbar, box = pool[int(sizes[i])]
+        ids.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED))
+    sat_lat, sat_ok = [], 0
+    for rid in ids:
+        st, info = ctx.poll(rid, timeout_ms=-1)
+        sat_ok += st == 0
+        sat_lat.append(info.latency_s)
+    t_sat = time.perf_counter() - t0
     return {"workload": "%d requests, Poisson arrivals at %.0f/s, N uniform over %s, L = 1.953 N Mpc/h, "
                         "0.009 N^3 x U(0.5,1.5) galaxies, random cone 20-45 deg and radial peak; mixed "
                         "precision to 1e-6 through wf_submit/wf_poll" % (n_req, rate, SERVE_SIZES),
             "value": n_req / t_total, "unit": "solves/s", "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "ok": int(sum(1 for s in stats if s == 0)),
+            "capacity": {"value": n_sat / t_sat, "unit": "solves/s", "requests": n_sat, "ok": int(sat_ok),
+                         "p50_s": float(np.percentile(sat_lat, 50)), "p99_s": float(np.percentile(sat_lat, 99)),
+                         "note": "all requests submitted at once: the served throughput at saturation"},
             "fp64_sequential": {"value": 1.0 / mean64, "unit": "solves/s",
                                 "note": "1 / mean service time of one plain FP64 wf_solve over the same size mix"}}
 
 
 def read_profile(ctx):
     return ctx.profile_read()
+
+
+def cpu_full():
+    """Whole oracle reconstructions of the 64^3 (tol 1e-8) and 256^3 (tol 1e-6) workloads on all host
+    threads and on one.  The one-thread 256^3 figure is a whole solve only if it finishes within an
+    hour's budget; otherwise it is scaled from the all-thread solve by the one-thread / all-thread
+    time of one 256^3 matvec, and says so."""
+    import numpy as np
+    import oracle
+    import synth
+    oracle.build()
+    nt = oracle.threads()
+    out = {"kind": "oracle", "cpu": cpu_model(), "threads": nt}
+    for name in ("c1", "c2"):
+        t_all, it, rel = oracle_full_solve(name, nt)
+        rec = {"workload": WORKLOADS[name], "cg_iters": it, "rel_residual": rel, "s": t_all,
+               "solves_per_s": 1.0 / t_all}
+        if name == "c1":
+            t_one, _, _ = oracle_full_solve(name, 1)
+            rec.update({"s_1_thread": t_one, "solves_per_s_1_thread": 1.0 / t_one})
+        else:
+            pr = synth.problem(name)
+            tab = oracle.sinv_table(pr.n, pr.box, pr.pk_k, pr.pk_p)
+            w = np.ones((pr.n,) * 3)
+            t0 = time.perf_counter()
+            oracle.matvec(tab, 0.05, w, w)
+            mv_all = time.perf_counter() - t0
+            oracle.set_threads(1)
+            try:
+                t0 = time.perf_counter()
+                oracle.matvec(tab, 0.05, w, w)
+                mv_one = time.perf_counter() - t0
+            finally:
+                oracle.set_threads(nt)
+            rec.update({"s_1_thread": t_all * mv_one / mv_all, "extrapolated_1_thread": True,
+                        "note_1_thread": "the all-thread solve x (one-thread / all-thread time of one matvec: "
+                                         "%.2f / %.2f s)" % (mv_one, mv_all)})
+            rec["solves_per_s_1_thread"] = 1.0 / rec["s_1_thread"]
+        out[name] = rec
+    print(json.dumps(out))
+    return 0
 
 
 def main():
@@ -622,7 +737,12 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-forms", dest="no_forms", action="store_true",
                     help="leave out the batched and served forms (reported after the timed 512^3 steps)")
+    ap.add_argument("--cpu-full", dest="cpu_full", action="store_true",
+                    help="only time whole oracle reconstructions of the 64^3 and 256^3 workloads on the host "
+                         "(all threads and one thread) and print them as one JSON line")
     args = ap.parse_args()
+    if args.cpu_full:
+        return cpu_full()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

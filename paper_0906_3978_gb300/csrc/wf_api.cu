@@ -5,6 +5,7 @@
 #include <cstring>
 #include <iterator>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <map>
@@ -291,20 +292,55 @@ wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_
   int* err = nullptr;
   WF_TRY(c.err_word(&err));
   wf_status status = WF_OK;
-  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) status = gl[i]->prepare(c, gs[i]);
-  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) WF_CUDA(cudaStreamSynchronize(gs[i]));
-  bool busy = status == WF_OK;
-  while (busy && status == WF_OK) {
-    busy = false;
-    for (size_t i = 0; i < gl.size() && status == WF_OK; ++i)
-      if (!gl[i]->done()) status = gl[i]->enqueue(c, gs[i]);
+  // start every group's preparation, then finish each one as its stream gets there
+  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) status = gl[i]->prepare_begin(c, gs[i]);
+  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) {
+    WF_CUDA(cudaStreamSynchronize(gs[i]));
+    status = gl[i]->prepare_end(c, gs[i]);
+  }
+  // Each group alternates a block of device work (ending with an event) and the host step that
+  // reads its scalars.  A group whose block has finished takes its host step and starts its next
+  // block at once, without waiting for the slower groups.
+  std::vector<cudaEvent_t> evs(gl.size(), nullptr);
+  std::vector<char> inflight(gl.size(), 0);
+  for (size_t i = 0; i < gl.size() && status == WF_OK; ++i)
+    if (cudaEventCreateWithFlags(&evs[i], cudaEventDisableTiming) != cudaSuccess) status = WF_ERR_CUDA;
+  while (status == WF_OK) {
+    bool any = false, progressed = false;
+    int running = -1, n_running = 0;
     for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) {
       if (gl[i]->done()) continue;
-      WF_CUDA(cudaStreamSynchronize(gs[i]));
-      status = gl[i]->advance(c);
-      busy = busy || !gl[i]->done();
+      any = true;
+      if (inflight[i]) {
+        const cudaError_t q = cudaEventQuery(evs[i]);
+        if (q == cudaErrorNotReady) {
+          running = (int)i;
+          ++n_running;
+          continue;
+        }
+        if (q != cudaSuccess) {
+          set_last_error("CG block", q);
+          status = WF_ERR_CUDA;
+          break;
+        }
+        inflight[i] = 0;
+        status = gl[i]->advance(c);
+        progressed = true;
+        if (status != WF_OK || gl[i]->done()) continue;
+      }
+      status = gl[i]->enqueue(c, gs[i]);
+      if (status == WF_OK && cudaEventRecord(evs[i], gs[i]) != cudaSuccess) status = WF_ERR_CUDA;
+      inflight[i] = 1;
+      progressed = true;
+    }
+    if (!any || status != WF_OK) break;
+    if (!progressed) {
+      if (n_running == 1) cudaEventSynchronize(evs[running]);  // a single group: just wait for it
+      else std::this_thread::yield();
     }
   }
+  for (auto e : evs)
+    if (e) cudaEventDestroy(e);
   for (size_t i = 0; i < gl.size() && status == WF_OK; ++i) {
     status = gl[i]->finish(c, gs[i]);
     if (status == WF_OK && gs[i] != st) {

@@ -10,7 +10,15 @@ namespace wf {
 
 struct Group {
   virtual ~Group() {}
-  virtual wf_status prepare(Ctx& c, cudaStream_t st) = 0;  // allocate, copy inputs, start CG
+  // allocate, copy inputs and start the sums of w and b^2 (no host synchronisation) ...
+  virtual wf_status prepare_begin(Ctx& c, cudaStream_t st) = 0;
+  // ... and, once the stream has passed prepare_begin's work: tables, scalars, start CG
+  virtual wf_status prepare_end(Ctx& c, cudaStream_t st) = 0;
+  wf_status prepare(Ctx& c, cudaStream_t st) {  // both, waiting in between
+    WF_TRY(prepare_begin(c, st));
+    WF_CUDA(cudaStreamSynchronize(st));
+    return prepare_end(c, st);
+  }
   virtual wf_status enqueue(Ctx& c, cudaStream_t st) = 0;  // next block of device work
   virtual wf_status advance(Ctx& c) = 0;                   // after a sync: consume scalars
   virtual bool done() const = 0;

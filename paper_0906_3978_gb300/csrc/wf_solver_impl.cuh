@@ -382,14 +382,17 @@ static void make_tables(const std::vector<double>& sinv, bool precond, double c0
   }
 }
 
+// Device table `name` from v, converted to T, through a page-locked staging buffer of the same
+// name (an asynchronous copy: the staging buffer is rewritten only by a later solve of the same
+// workspace, after this one's stream has finished).
 template <class T>
 static inline wf_status upload_tables(Ctx& c, const std::string& name, const std::vector<double>& v, T** out,
                                       cudaStream_t st) {
-  std::vector<T> tmp(v.begin(), v.end());
-  T* d;
-  WF_TRY(c.get(name, tmp.size() * sizeof(T), (void**)&d));
-  WF_CUDA(cudaMemcpyAsync(d, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, st));
-  WF_CUDA(cudaStreamSynchronize(st));  // tmp goes out of scope
+  T *h, *d;
+  WF_TRY(c.get_pinned(name + "_stage", v.size() * sizeof(T), (void**)&h));
+  for (size_t i = 0; i < v.size(); ++i) h[i] = (T)v[i];
+  WF_TRY(c.get(name, v.size() * sizeof(T), (void**)&d));
+  WF_CUDA(cudaMemcpyAsync(d, h, v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
   *out = d;
   return WF_OK;
 }
@@ -471,9 +474,10 @@ struct GroupCommon : Group {
   }
 };
 
-// Per-system sums of w and b^2: two reductions into the partial slots [0,152) and [152,304).
+// Per-system sums of w and b^2: two reductions into the partial slots [0,152) and [152,304),
+// enqueued with the copy of the scalars back to the host (no synchronisation) ...
 template <int N>
-static wf_status group_sums(Ctx& c, GroupCommon<N>& g, int npart, cudaStream_t st) {
+static wf_status group_sums_begin(Ctx& c, GroupCommon<N>& g, int npart, cudaStream_t st) {
   const size_t V = GroupCommon<N>::V;
   g.h.assign(g.nb, CgScal{});
   WF_TRY(g.push_scalars(st));
@@ -483,8 +487,11 @@ static wf_status group_sums(Ctx& c, GroupCommon<N>& g, int npart, cudaStream_t s
   c.launch("reduce", 8.0 * V * g.nb, st, [&] { k_sum<true><<<dim3(152, g.nb), 256, 0, st>>>(g.B, V, g.part, npart); });
   c.launch("fin", 0, st, [&] { k_fin_sum<<<g.nb, 1024, 0, st>>>(g.part, 152, 1, g.sc, b); });
   WF_CUDA(cudaGetLastError());
-  WF_TRY(g.pull_scalars(st));
-  WF_CUDA(cudaStreamSynchronize(st));
+  return g.pull_scalars(st);
+}
+// ... and read once the stream has passed them.
+template <int N>
+static void group_sums_end(GroupCommon<N>& g) {
   g.read_scalars();
   g.sumw.resize(g.nb);
   g.bb0.resize(g.nb);
@@ -500,7 +507,6 @@ static wf_status group_sums(Ctx& c, GroupCommon<N>& g, int npart, cudaStream_t s
       if (g.info[m]) *g.info[m] = wf_solve_info{0, 0, 0.0, g.sys[m]->nbar, WF_ERR_ARG};
     }
   }
-  return WF_OK;
 }
 
 // Check interval: grids of 256^3 and up check the device flags every 4 iterations.
@@ -523,7 +529,7 @@ struct GroupFP64 : GroupCommon<N> {
   std::vector<int> restarts;
   bool unit_m = true;
 
-  wf_status prepare(Ctx& c, cudaStream_t st) override {
+  wf_status prepare_begin(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
     key = this->tag + "f64_" + std::to_string(N) + "_";
     int* err;
@@ -546,7 +552,11 @@ struct GroupFP64 : GroupCommon<N> {
       WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDefault, st));
       WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDefault, st));
     }
-    WF_TRY(group_sums<N>(c, *this, SP::NPART, st));
+    return group_sums_begin<N>(c, *this, SP::NPART, st);
+  }
+  wf_status prepare_end(Ctx& c, cudaStream_t st) override {
+    const size_t SPEC = SP::SPEC, V = SP::V;
+    group_sums_end<N>(*this);
     // tables
     const int TAB = SP::TAB;
     std::vector<double> vc((size_t)nb * TAB), vm((size_t)nb * TAB), vs((size_t)nb * TAB);
@@ -689,7 +699,7 @@ struct GroupMixed : GroupCommon<N> {
   bool unit_m = true;
   static constexpr int NPART = SF::NPART > SD::NPART ? SF::NPART : SD::NPART;
 
-  wf_status prepare(Ctx& c, cudaStream_t st) override {
+  wf_status prepare_begin(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
     key = this->tag + "mix_" + std::to_string(N) + "_";
     int* err;
@@ -716,7 +726,11 @@ struct GroupMixed : GroupCommon<N> {
       WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDefault, st));
       WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDefault, st));
     }
-    WF_TRY(group_sums<N>(c, *this, NPART, st));
+    return group_sums_begin<N>(c, *this, NPART, st);
+  }
+  wf_status prepare_end(Ctx& c, cudaStream_t st) override {
+    const size_t V = SF::V;
+    group_sums_end<N>(*this);
     const int TAB = SF::TAB;
     std::vector<double> vc((size_t)nb * TAB), vm((size_t)nb * TAB), vs((size_t)nb * TAB);
     unit_m = true;

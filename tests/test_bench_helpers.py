@@ -37,3 +37,10 @@ def test_reference_arm_prints_one_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "solves/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["cpu_baseline"]["extrapolated"] is True and d["cpu_baseline"]["iterations_used"] > 0
+    # the same config keys and values as the GPU arm prints
+    import synth
+
+    class A:
+        workload = "c1"
+    assert d["config"] == bench.config_of(A, synth.problem("c1"), 1)
