@@ -108,6 +108,8 @@ struct Spec {
       if (e == cudaSuccess) e = v.setup();
     for (const XVariant& v : xvariants())
       if (e == cudaSuccess) e = v.setup();
+    for (const ZVariant& v : zvariants())
+      if (e == cudaSuccess) e = v.setup();
     if (e == cudaSuccess) done = true;
     return e;
   }
@@ -237,22 +239,33 @@ struct Spec {
       return G::TPS;
     }
   };
-  // the register-staged kernels (one CTA per tile, loads through registers)
+  // the register-staged kernels (one CTA per tile, loads through registers), radix cap RMAX
+  template <int RMAX>
   struct XReg {
-    static cudaError_t setup() { return cudaSuccess; }  // attrs() sets their shared memory
+    static cudaError_t setup() {
+      cudaError_t e = set_smem(k_cg_xinv<R, N, true, RMAX>, SMxy);
+      if (e == cudaSuccess) e = set_smem(k_cg_xinv<R, N, false, RMAX>, SMxy);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd<R, N, true, RMAX>, SMxy);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd<R, N, false, RMAX>, SMxy);
+      return e;
+    }
     static int xinv(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* ctab, const SS* mtab, bool unit_m,
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
       c.launch("cg_xinv", 6 * BS * nb, st, [&] {
-        if (unit_m) k_cg_xinv<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
-        else k_cg_xinv<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
+        if (unit_m)
+          k_cg_xinv<R, N, true, RMAX><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
+        else
+          k_cg_xinv<R, N, false, RMAX><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
       });
       return GXY;
     }
     static int xupd(Ctx& c, int nb, const ST* T, ST* r, ST* P0, ST* P1, const SS* ctab, const SS* mtab, bool unit_m,
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
       c.launch("cg_xupd", 4 * BS * nb, st, [&] {
-        if (unit_m) k_cg_xupd<R, N, true><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
-        else k_cg_xupd<R, N, false><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
+        if (unit_m)
+          k_cg_xupd<R, N, true, RMAX><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
+        else
+          k_cg_xupd<R, N, false, RMAX><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
       });
       return GXY;
     }
@@ -264,12 +277,45 @@ struct Spec {
       // 0.58 ms against 1.23-1.83 ms for the staged forms, whose single resident CTA per SM
       // serialises each tile's table gathers, transform and epilogue); the staged forms stay
       // candidates for the tuner on the FP32 grids of 128 and up
-      std::vector<XVariant> out{{"registers", XReg::setup, XReg::xinv, XReg::xupd}};
+      std::vector<XVariant> out{{"registers", XReg<8>::setup, XReg<8>::xinv, XReg<8>::xupd}};
+      if constexpr (std::is_same<R, float>::value && N >= 128) {
+        out.push_back({"registers_r16", XReg<16>::setup, XReg<16>::xinv, XReg<16>::xupd});
+        out.push_back({"registers_r32", XReg<32>::setup, XReg<32>::xinv, XReg<32>::xupd});
+      }
       if constexpr (std::is_same<R, float>::value && N >= 128 && N % 8 == 0 && NLX * (N / 8) <= 512) {
         using E8 = XV<NLX, 2, 8, 8, 1>;  // per-thread row copies, 8 elements per thread
         using T8 = XV<NLX, 2, 8, 8, 0>;  // tensor copies, 8 elements per thread
         out.push_back({"rows_s2_e8", E8::setup, E8::xinv, E8::xupd});
         out.push_back({"tensor_s2_e8", T8::setup, T8::xinv, T8::xupd});
+      }
+      return out;
+    }();
+    return v;
+  }
+  // ---- z-turn variants: elements per thread (threads per CTA) ------------------------------
+  using ZRun = void (*)(Ctx&, int, ST*, const SS*, const ST*, double*, const CgScal*, cudaStream_t);
+  struct ZVariant {
+    const char* name;
+    cudaError_t (*setup)();
+    ZRun run;
+  };
+  template <int EZ>
+  struct ZV {
+    static cudaError_t setup() { return set_smem(k_zturn<R, N, EZ>, ZG<R, N, EZ>::SMEM); }
+    static void run(Ctx& c, int nb, ST* T, const SS* D, const ST* tw, double* part, const CgScal* sc,
+                    cudaStream_t st) {
+      c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st, [&] {
+        k_zturn<R, N, EZ><<<gz(nb), ZG<R, N, EZ>::NT, ZG<R, N, EZ>::SMEM, st>>>(T, D, tw, part, sc, bat());
+      });
+    }
+  };
+  static const std::vector<ZVariant>& zvariants() {
+    static const std::vector<ZVariant> v = [] {
+      constexpr int E0 = z_elems<R, N>();
+      std::vector<ZVariant> out{{"e_default", ZV<E0>::setup, ZV<E0>::run}};
+      if constexpr (std::is_same<R, float>::value && N >= 128) {
+        if constexpr (E0 / 2 >= 4 && (N / 2) % (E0 / 2) == 0) out.push_back({"e/2", ZV<E0 / 2>::setup, ZV<E0 / 2>::run});
+        if constexpr (E0 / 4 >= 4 && (N / 2) % (E0 / 4) == 0) out.push_back({"e/4", ZV<E0 / 4>::setup, ZV<E0 / 4>::run});
       }
       return out;
     }();
@@ -328,8 +374,7 @@ struct Spec {
     }
     if (!fused) {
       ypass(c, nb, T, tw, sc, +1, st);
-      c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st,
-               [&] { k_zturn<R, N><<<gz(nb), NTz, SMz, st>>>(T, D, tw, part + NX, sc, b); });
+      pick(c, "zturn", zvariants()).run(c, nb, T, D, tw, part + NX, sc, st);
       ypass(c, nb, T, tw, sc, -1, st);
     }
     c.launch("fin", 0, st, [&] { k_fin_alpha<<<nb, 1024, 0, st>>>(part, n1, NX, nmid, sc, b); });
@@ -1016,6 +1061,23 @@ wf_status tune_spec(Ctx& c, std::string& report) {
     for (const auto& rr : runs) ad.push_back(Adapter{&rr, r, P0, P1, x, T, tab, part, sc, rr.name});
     report += ", ";
     WF_TRY(tune_pass<SP>(c, inv ? "xinv" : "xupd", ad, r, nb, tw, st, report));
+  }
+  {  // the z turn: T and D (FP32/FP64 real field, one spectrum's bytes or half) from the scratch
+    struct ZAdapter {
+      const typename SP::ZVariant* v;
+      SS* D;
+      double* part;
+      CgScal* sc;
+      const char* name;
+      void run(Ctx& c, int nb, ST* buf, const ST* tw, const CgScal*, int, cudaStream_t st) const {
+        v->run(c, nb, buf, D, tw, part, sc, st);
+      }
+    };
+    std::vector<ZAdapter> za;
+    SS* D = reinterpret_cast<SS*>(x);  // the x buffer holds nb fields of V reals (zeroed)
+    for (const auto& v : SP::zvariants()) za.push_back(ZAdapter{&v, D, part, sc, v.name});
+    report += ", ";
+    WF_TRY(tune_pass<SP>(c, "zturn", za, T, nb, tw, st, report));
   }
   WF_CUDA(cudaStreamSynchronize(st));
   c.release_prefix("tune_x");

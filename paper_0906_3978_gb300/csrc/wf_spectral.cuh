@@ -357,7 +357,7 @@ WF_D void tile_mul(cx<R>* tile, int kz0, int ky_s, const TAB* tab, int tid) {
 // P0 = (Z + conj Z(-k)) / 2 and PN = (Z - conj Z(-k)) / 2i (Z(-k) from the partner line).
 // UNIT_M: m = 1 at every k != 0 (the preconditioned system), so m is read only on column 0.
 // ------------------------------------------------------------------------------------------
-template <class R, int N, bool UNIT_M>
+template <class R, int N, bool UNIT_M, int RMAX = 8>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
 k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, typename Store<R>::T* P1,
           typename Store<R>::T* __restrict__ x, typename Store<R>::T* __restrict__ T,
@@ -481,7 +481,7 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
     }
     combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
   }
-  fft_line<R, G::M, G::TPL, G::LD, +1>(tile + tid % G::NL, tid / G::NL, tw);
+  fft_line<R, G::M, G::TPL, G::LD, +1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + tid % G::NL, tid / G::NL, tw);
   tile_store<G>(tile, T + base, rowstride, tid);
   const double sum = block_sum(acc.get(), red);
   if (tid == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = sum;
@@ -498,7 +498,7 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
 // weights, without 1/V_c) and an upper estimate of V_c ||C^-1 r||^2 (the canonical residual): on
 // column 0 the larger of the two planes' 1/c^2 is used.  grid (N/2 / NL, N).
 // ------------------------------------------------------------------------------------------
-template <class R, int N, bool UNIT_M>
+template <class R, int N, bool UNIT_M, int RMAX = 8>
 __global__ void __launch_bounds__(XYG<R, N>::NT)
 k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ r,
           const typename Store<R>::T* P0, const typename Store<R>::T* P1,
@@ -536,9 +536,10 @@ k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __re
   if (kz0 == 0)
     for (int i = tid; i < G::M; i += G::NT) tile[i * G::LD + G::NL] = ld_c<R>(T + (size_t)pky * NH + (size_t)i * rowstride);
   __syncthreads();
-  fft_line<R, G::M, G::TPL, G::LD, -1>(tile + tid % G::NL, tid / G::NL, tw);
+  fft_line<R, G::M, G::TPL, G::LD, -1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + tid % G::NL, tid / G::NL, tw);
   if (kz0 == 0) {  // transform the partner line too, then apply c to column 0 as a packed pair
-    fft_line<R, G::M, G::TPL, G::LD, -1>(tile + G::NL, tid / G::NL, tw, tid % G::NL == 0);
+    fft_line<R, G::M, G::TPL, G::LD, -1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + G::NL, tid / G::NL, tw,
+                                                                                 tid % G::NL == 0);
     combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
   }
   // epilogue: r -= alpha (m p + c T^), vector by vector in the tile's row layout
