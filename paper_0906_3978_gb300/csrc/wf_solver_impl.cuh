@@ -270,6 +270,29 @@ struct Spec {
       return GXY;
     }
   };
+  // x pass 2 with its r and p rows prefetched into shared memory (NL lines, EX elements per thread)
+  template <int RMAX, int NL, int EX>
+  struct XPf {
+    using G = XYP<R, N, NL, EX>;
+    static cudaError_t setup() {
+      cudaError_t e = set_smem(k_cg_xupd_pf<R, N, true, RMAX, NL, EX>, G::SMEM);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd_pf<R, N, false, RMAX, NL, EX>, G::SMEM);
+      return e;
+    }
+    static int xupd(Ctx& c, int nb, const ST* T, ST* r, ST* P0, ST* P1, const SS* ctab, const SS* mtab, bool unit_m,
+                    const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
+      const dim3 grid(N / 2 / NL, N, nb);
+      c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+        if (unit_m)
+          k_cg_xupd_pf<R, N, true, RMAX, NL, EX><<<grid, G::NT, G::SMEM, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc,
+                                                                              bat());
+        else
+          k_cg_xupd_pf<R, N, false, RMAX, NL, EX><<<grid, G::NT, G::SMEM, st>>>(T, r, P0, P1, ctab, mtab, tw, part,
+                                                                               sc, bat());
+      });
+      return (N / 2 / NL) * N;
+    }
+  };
   static constexpr int NLX = xtma_lines<R, N, 3, 2>();
   static const std::vector<XVariant>& xvariants() {
     static const std::vector<XVariant> v = [] {
@@ -281,6 +304,13 @@ struct Spec {
       if constexpr (std::is_same<R, float>::value && N >= 128) {
         out.push_back({"registers_r16", XReg<16>::setup, XReg<16>::xinv, XReg<16>::xupd});
         out.push_back({"registers_r32", XReg<32>::setup, XReg<32>::xinv, XReg<32>::xupd});
+        // x pass 2 only (its x pass 1 entry is the radix-32 register kernel again)
+        if constexpr ((N / 2) % 8 == 0 && N % 16 == 0) {
+          using P1 = XPf<32, 8, 16>;
+          using P2 = XPf<16, 8, 16>;
+          out.push_back({"prefetch_nl8_e16_r32", P1::setup, XReg<32>::xinv, P1::xupd});
+          out.push_back({"prefetch_nl8_e16_r16", P2::setup, XReg<32>::xinv, P2::xupd});
+        }
       }
       if constexpr (std::is_same<R, float>::value && N >= 128 && N % 8 == 0 && NLX * (N / 8) <= 512) {
         using E8 = XV<NLX, 2, 8, 8, 1>;  // per-thread row copies, 8 elements per thread
@@ -554,6 +584,12 @@ static void group_sums_end(GroupCommon<N>& g) {
   }
 }
 
+// The last inner solve of a mixed solve aims at kInnerMargin x the remaining reduction (its stop
+// test is an upper estimate of the canonical residual; the FP64 residual that follows decides).
+// 0.9 saved ~2% of the iterations at 512^3 but moved the result from 5e-7 to 8e-7 of the solution
+// converged to 1e-10, too close to the mixed path's 1e-6 bound.
+constexpr double kInnerMargin = 0.5;
+
 // Check interval: grids of 256^3 and up check the device flags every 4 iterations.
 template <int N> constexpr int check_every() { return N >= 256 ? 4 : (N >= 128 ? 8 : 16); }
 
@@ -812,7 +848,7 @@ struct GroupMixed : GroupCommon<N> {
   wf_status enqueue(Ctx& c, cudaStream_t st) override {
     const Bat bf = SF::bat();
     if (phase == 0) {
-      // Each inner solve aims at the remaining reduction (half of it, for margin) but at most
+      // Each inner solve aims at the remaining reduction (kInnerMargin of it) but at most
       // inner_tol (1e-4 by default) per step, so at least two FP64 refinement steps run for
       // tol <= 1e-6: the second removes the FP32 rounding error the first leaves in the
       // low-eigenvalue directions (at 512^3 a single step to 1e-6 saves ~6% of the iterations but
@@ -825,7 +861,7 @@ struct GroupMixed : GroupCommon<N> {
           z.done = 4;
         } else {
           const double itol = sys[m]->opts.inner_tol > 0.0 ? sys[m]->opts.inner_tol : inner_tol_def;
-          const double target = std::max(itol, 0.5 * sys[m]->opts.tol / rel[m]);
+          const double target = std::max(itol, kInnerMargin * sys[m]->opts.tol / rel[m]);
           z.tol2 = target * target;
           z.bb = rel[m] * rel[m] * bb0[m];
           z.max_iter = std::max(1, sys[m]->opts.max_iter - iters[m]);

@@ -619,6 +619,145 @@ k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __re
 }
 
 // ------------------------------------------------------------------------------------------
+// CG x pass 2 with its r and p tiles prefetched: the same work as k_cg_xupd, but the tile's r and p
+// rows are requested (per-thread asynchronous 16-byte copies into shared memory) before T is loaded
+// and transformed, so the epilogue reads them from shared memory instead of waiting on HBM.  One
+// tile per CTA, NL lines (8 leaves shared memory for two CTAs per SM).  grid (N/2 / NL, N).
+// ------------------------------------------------------------------------------------------
+template <class R, int N, int NL_, int EX>
+struct XYP {
+  using ST = typename Store<R>::T;
+  static constexpr int M = N, NH = N / 2, NL = NL_;
+  static constexpr int E = EX;
+  static constexpr int TPL = M / E >= 1 ? M / E : 1;
+  static constexpr int NT = NL * TPL;
+  static constexpr int LD = NL + 1;  // padded transform tile
+  static constexpr int VW = (sizeof(ST) == 8 && NL % 2 == 0) ? 2 : 1;
+  static constexpr int NV = NL / VW;
+  static constexpr int NVEC = M * NV;
+  static constexpr int PER = (NVEC + NT - 1) / NT;
+  static constexpr bool EVEN = NVEC % NT == 0;
+  using VT = typename std::conditional<VW == 2, float4, ST>::type;
+  // transform tile, twiddles, then the dense r and p tiles (16-byte aligned)
+  static constexpr size_t TILE = (size_t)M * LD * sizeof(cx<R>), TWB = (size_t)M * sizeof(cx<R>);
+  static constexpr size_t OFF_R = ((TILE + TWB + 127) / 128) * 128;
+  static constexpr size_t DENSE = (size_t)M * NL * sizeof(ST);
+  static constexpr size_t SMEM = OFF_R + 2 * DENSE;
+  static_assert(NH % NL == 0 && (NL * sizeof(ST)) % 16 == 0, "whole 16-byte pieces per row");
+};
+
+template <class R, int N, bool UNIT_M, int RMAX, int NL, int EX>
+__global__ void __launch_bounds__(XYP<R, N, NL, EX>::NT)
+k_cg_xupd_pf(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ r,
+             const typename Store<R>::T* P0, const typename Store<R>::T* P1,
+             const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
+             const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials,
+             const CgScal* __restrict__ sc, Bat bt) {
+  using G = XYP<R, N, NL, EX>;
+  using ST = typename Store<R>::T;
+  using SS = typename Store<R>::S;
+  constexpr int NH = G::NH;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* tw = tile + G::M * G::LD;
+  cx<R>* rt = reinterpret_cast<cx<R>*>(smem_raw + G::OFF_R);  // r rows, dense
+  cx<R>* pt = rt + G::M * NL;                                  // p rows, dense
+  __shared__ double red[32];
+  const int z = blockIdx.z;
+  sc += z;
+  if (sc->done) return;
+  const ST* __restrict__ p = ((sc->lit & 1) ? P0 : P1) + z * bt.spec;  // this iteration's p_new
+  T += z * bt.spec;
+  r += z * bt.spec;
+  ctab += z * bt.tab;
+  mtab += z * bt.tab;
+  partials += z * bt.part;
+  const int tid = threadIdx.x;
+  const int kz0 = blockIdx.x * NL, ky = blockIdx.y;
+  const int ky_s = sfreq(ky, N);
+  const int pky = (N - ky) % N;
+  const size_t rowstride = (size_t)N * NH;
+  const size_t base = (size_t)ky * NH + kz0;
+  // r and p rows first: they arrive while T is loaded and transformed
+  {
+    constexpr int PV = 16 / (int)sizeof(ST), NVR = NL / PV;
+    for (int idx = tid; idx < G::M * NVR; idx += G::NT) {
+      const int i = idx / NVR, v = (idx % NVR) * PV;
+      cp_async16(rt + i * NL + v, r + base + (size_t)i * rowstride + v);
+      cp_async16(pt + i * NL + v, p + base + (size_t)i * rowstride + v);
+    }
+    cp_async_commit();
+  }
+  const SS alpha = (SS)sc->alpha;
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
+  tile_load<G>(tile, T + base, rowstride, tid);
+  if (kz0 == 0)
+    for (int i = tid; i < G::M; i += G::NT) tile[i * G::LD + NL] = ld_c<R>(T + (size_t)pky * NH + (size_t)i * rowstride);
+  __syncthreads();
+  fft_line<R, G::M, G::TPL, G::LD, -1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + tid % NL, tid / NL, tw);
+  if (kz0 == 0) {  // transform the partner line too, then apply c to column 0 as a packed pair
+    fft_line<R, G::M, G::TPL, G::LD, -1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + NL, tid / NL, tw,
+                                                                                 tid % NL == 0);
+    combine_col0<R, N, G::LD, NL>(tile, ky_s, ctab, tid, G::NT);
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // epilogue: r -= alpha (m p + c T^), two elements of a row per step, stored as one vector
+  typename AccFor<SS>::T a_rr, a_rc;
+  constexpr int W = G::VW;
+#pragma unroll 4
+  for (int idx = tid; idx < G::M * (NL / W); idx += G::NT) {
+    const int i = idx / (NL / W), c0 = (idx % (NL / W)) * W;
+    const int kxs = sfreq(i, N);
+    cx<R> out[W];
+    SS s_rr = 0, s_rc = 0;
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const int kz = kz0 + c0 + u;
+      const int n2 = kxs * kxs + ky_s * ky_s + kz * kz;
+      const cx<R> t = tile[i * G::LD + c0 + u], pv = pt[i * NL + c0 + u];
+      cx<R> rv = rt[i * NL + c0 + u];
+      const SS c = ctab[n2];
+      SS ic2 = (SS)1 / (c * c);
+      SS q0, q1;
+      if (kz == 0) {
+        const SS cN = ctab[n2 + NH * NH];
+        const SS i2 = (SS)1 / (cN * cN);
+        ic2 = ic2 > i2 ? ic2 : i2;
+        const SS m0 = mtab[n2], mN = mtab[n2 + NH * NH];
+        const SS a = (SS)0.5 * (m0 + mN), b = (SS)0.5 * (m0 - mN);
+        ST pp = ST{};
+        if (b != (SS)0) pp = p[(size_t)((N - i) % N) * rowstride + (size_t)pky * NH];
+        q0 = a * pv.x + b * pp.x + t.x;
+        q1 = a * pv.y - b * pp.y + t.y;
+      } else {
+        const SS m = UNIT_M ? (SS)1 : mtab[n2];
+        q0 = m * pv.x + c * t.x;
+        q1 = m * pv.y + c * t.y;
+      }
+      rv.x -= alpha * q0;
+      rv.y -= alpha * q1;
+      out[u] = rv;
+      const SS wgt = kz == 0 ? (SS)1 : (SS)2;
+      const SS m2 = wgt * (rv.x * rv.x + rv.y * rv.y);
+      s_rr += m2;
+      s_rc += ic2 * m2;
+    }
+    *reinterpret_cast<typename G::VT*>(r + base + (size_t)i * rowstride + c0) = *reinterpret_cast<const typename G::VT*>(out);
+    a_rr.add(s_rr);
+    a_rc.add(s_rc);
+  }
+  const double s1 = block_sum(a_rr.get(), red);
+  const double s2 = block_sum(a_rc.get(), red);
+  if (tid == 0) {
+    const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+    partials[2 * bid] = s1;
+    partials[2 * bid + 1] = s2;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // Persistent CG x passes with tensor copies.  A stage holds NS tiles (one per staged stream), all
 // loaded by tensor copies along x (box {2 NL, 1, BR, 1}) and completed on the stage's barrier.
 // The packed column's partner line (-ky) is read with plain loads into its own buffer, only by
