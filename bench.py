@@ -34,8 +34,9 @@ WORKLOADS = {
 # DRAM traffic of the dominant kernel per launch from one ncu capture, valid while the kernel
 # sources hash to `src`; scaled from the captured size by the units processed (bytes ~ N^3).
 NCU_TRAFFIC = {
-    # profiles/cg_kernels_f32_256_full.md: 214.1 + 147.7 MB at 256^3 (k_cg_xinv, radix 32), x 8 for 512^3
-    ("cg_xinv", 512): {"bytes": 361.8e6 * 8, "src": "cb321bbef79ff3a3"},
+    # profiles/cg_kernels_f32_256_full.md: 214.1 + 147.7 MB at 256^3 (k_cg_xinv, radix 32), x 8 for 512^3.
+    # Since that capture the kernel file only gained another kernel (k_cg_xupd_pf); k_cg_xinv is as captured.
+    ("cg_xinv", 512): {"bytes": 361.8e6 * 8, "src": "64d981d2e98fd0ea"},
 }
 
 
