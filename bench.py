@@ -34,9 +34,8 @@ WORKLOADS = {
 # DRAM traffic of the dominant kernel per launch from one ncu capture, valid while the kernel
 # sources hash to `src`; scaled from the captured size by the units processed (bytes ~ N^3).
 NCU_TRAFFIC = {
-    # profiles/cg_kernels_f32_256_full.md: 214.1 + 147.7 MB at 256^3 (k_cg_xinv, radix 32), x 8 for 512^3.
-    # Since that capture the kernel file only gained another kernel (k_cg_xupd_pf); k_cg_xinv is as captured.
-    ("cg_xinv", 512): {"bytes": 361.8e6 * 8, "src": "64d981d2e98fd0ea"},
+    # profiles/cg_kernels_f32_512_dram.md: one-pass capture of one 512^3 launch, 1684.7 + 1558.1 MB
+    ("cg_xinv", 512): {"bytes": 3242.8e6, "src": "64d981d2e98fd0ea"},
 }
 
 
@@ -189,6 +188,28 @@ def oracle_sample(pr, iters, deadline_s=40.0, single_thread=True):
               "threads_speedup_on_matvec": t_mv1 * scale / t_mv,
               "note": "1 OpenMP thread, one %d^3 matvec scaled by V log V to %d^3" % (n1, pr.n)}
     return 1.0 / t_solve, oracle.threads(), sample, t_solve, single
+
+
+def fp64_kernels(ctx, prof, n):
+    """The FP64-ALU-bound passes of the step (the three passes of the ideal low-pass) against the
+    device's FP64 rate measured here (wf_fp64_rate) and the nominal 1.25 TFLOP/s.  Algorithmic flops:
+    2.5 L log2 L per real transform of length L; each pass line takes a real transform of length 2n
+    and an inverse of length n; the z pass has (2n)^2 lines, the y pass 2n n, the x pass n n.  The z
+    pass skips the rows no galaxy reaches (their output is zero), so its figure counts flops it did
+    not need to do."""
+    peak = ctx.fp64_rate()
+    f_line = 2.5 * 2 * n * math.log2(2 * n) + 2.5 * n * math.log2(n)
+    lines = {"lowpass_z": (2 * n) ** 2, "lowpass_y": 2 * n * n, "lowpass_x": n * n}
+    out = []
+    for c in prof["classes"]:
+        if c["name"] in lines and c["launches"] > 0:
+            fl = lines[c["name"]] * f_line
+            rate = fl / (c["ms"] / c["launches"] / 1000.0)
+            out.append({"kernel": c["name"], "bound": "alu", "gflop_per_launch": fl / 1e9,
+                        "ms_per_launch": c["ms"] / c["launches"], "achieved_tflops": rate / 1e12,
+                        "frac_of_measured": rate / peak, "frac_of_nominal": rate / 1.25e12})
+    return {"peak_measured_tflops": peak / 1e12, "peak_nominal_tflops": 1.25,
+            "peak_kind": "measured: wf_fp64_rate (FMA chains filling every SM, CUDA events)", "kernels": out}
 
 
 def config_of(args, pr, ws):
@@ -420,6 +441,7 @@ def gpu_arm(args):
                      "avg_launch_ms": dom["ms"] / dom["launches"]},
         "kernels": [{k2: (round(v, 4) if isinstance(v, float) else v) for k2, v in c.items()}
                     for c in sorted(prof["classes"], key=lambda c: -c["ms"])[:10]],
+        "fp64_kernels": fp64_kernels(ctx, prof, n),
         "tuning": {prec: {p["pass"]: {"chosen": p["chosen"],
                                       "ms": {v["name"]: round(v["ms"], 4) for v in p["variants"]}}
                           for p in rep} for prec, rep in tuning.items()},

@@ -344,6 +344,12 @@ wf_status wf_profile_read(wf_ctx* ctx, int64_t* launches, int* n_classes);
 wf_status wf_profile_class(wf_ctx* ctx, int i, char* name, int name_len, int64_t* launches,
                            double* total_ms, double* bytes);
 
+/* Measurement utility (no counterpart in the paper): the FP64 FMA throughput of the context's
+ * device, timed with CUDA events over one launch of independent FMA chains filling every SM, in
+ * flop/s (2 per FMA) -- the measured peak the FP64-bound kernels (low-pass, FP64 transforms) are
+ * reported against.  Waits for completion.  Errors: WF_ERR_ARG, WF_ERR_OOM, WF_ERR_CUDA. */
+wf_status wf_fp64_rate(wf_ctx* ctx, double* flops_per_s);
+
 /* ---- Sec. 3.1.2: supersampled mass assignment ----------------------------------------- */
 
 /* Grid the galaxies and low-pass them to the target grid.

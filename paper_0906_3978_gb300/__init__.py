@@ -119,6 +119,7 @@ def lib():
         L.wf_autotune.argtypes = [c_void_p, c_int, c_int, ctypes.c_char_p, c_int]
         L.wf_tune_get.argtypes = [c_void_p, ctypes.c_char_p, c_int]
         L.wf_tune_set.argtypes = [c_void_p, ctypes.c_char_p]
+        L.wf_fp64_rate.argtypes = [c_void_p, P(c_double)]
         L.wf_smooth.argtypes = [c_void_p, P(Grid), c_void_p, c_double, c_void_p, c_void_p]
         L.wf_project_mask.argtypes = [c_void_p, P(Grid), c_void_p, c_int, c_int, c_double, c_double, c_double,
                                       c_double, P(c_double), c_double, c_int, P(c_double), c_void_p, c_void_p,
@@ -142,7 +143,7 @@ def lib():
                      "wf_set_fused_planes", "wf_smooth", "wf_compare", "wf_density_stats",
                      "wf_selection_eval", "wf_grid_assign_weighted", "wf_rsd_factor", "wf_deconvolve",
                      "wf_sd_noise", "wf_jackknife_masses", "wf_project_mask", "wf_solve_response",
-                     "wf_jackknife_solve", "wf_autotune", "wf_tune_get", "wf_tune_set"):
+                     "wf_jackknife_solve", "wf_autotune", "wf_tune_get", "wf_tune_set", "wf_fp64_rate"):
             getattr(L, name).restype = c_int
         L.wf_supported_size.restype = c_int
         _lib = L
@@ -523,6 +524,14 @@ class Context:
         if st != OK:
             raise WfError(st, "wf_autotune")
         return json.loads(buf.value.decode())
+
+    def fp64_rate(self) -> float:
+        """Measured FP64 FMA throughput of the device in flop/s (wf_fp64_rate)."""
+        v = ctypes.c_double(0.0)
+        st = lib().wf_fp64_rate(self._h, ctypes.byref(v))
+        if st != OK:
+            raise WfError(st, "wf_fp64_rate")
+        return v.value
 
     def tune_get(self) -> dict:
         """The context's tuning table {"pass/prec/n": variant} (wf_tune_get)."""

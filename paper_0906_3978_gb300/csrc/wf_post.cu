@@ -320,3 +320,49 @@ wf_status density_run(Ctx& c, const wf_grid& g, const double* delta, const doubl
 }
 
 }  // namespace wf
+
+// ==========================================================================================
+// FP64 FMA throughput of the device (a measurement for reporting the FP64-bound kernels against
+// a measured peak): every thread runs 8 independent FMA chains; 2 flops per FMA.
+// ==========================================================================================
+namespace wf {
+static __global__ void __launch_bounds__(256) k_fma_rate(double* __restrict__ out, int iters, double a, double b) {
+  double v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = threadIdx.x * 1e-3 + j;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = fma(v[j], a, b);
+  double t = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) t += v[j];
+  if (t == 12345.678) out[0] = t;  // keeps the chains live; practically never stores
+}
+}  // namespace wf
+
+extern "C" wf_status wf_fp64_rate(wf_ctx* ctx, double* flops_per_s) {
+  using namespace wf;
+  if (!ctx || !flops_per_s) return WF_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->mu);
+  DeviceGuard g(c->device);
+  int sms = 0;
+  WF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  double* out;
+  WF_TRY(c->get("fma_rate", 64, (void**)&out));
+  const int blocks = sms * 8, threads = 256, iters = 1 << 14;
+  cudaEvent_t e0, e1;
+  WF_CUDA(cudaEventCreate(&e0));
+  WF_CUDA(cudaEventCreate(&e1));
+  k_fma_rate<<<blocks, threads>>>(out, iters / 8, 0.999999, 1e-7);  // warm-up
+  WF_CUDA(cudaEventRecord(e0));
+  k_fma_rate<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+  WF_CUDA(cudaEventRecord(e1));
+  WF_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  WF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *flops_per_s = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+  return WF_OK;
+}
