@@ -30,7 +30,7 @@ wf_status prepare_solve(const wf_grid* grid, const wf_power* power, const double
                         const double* b, const wf_solve_opts* opts, double* s_out, SolveArgs& a);
 
 namespace {
-constexpr int kMaxResident = 64;
+constexpr int kMaxResident = 160;
 constexpr size_t kMaxQueued = 4096;
 constexpr int kFirstStream = 8;  // library streams 0..7 belong to wf_solve_batch
 constexpr size_t kPinnedCap = (size_t)16 << 30;  // page-locked request buffers, all requests together
