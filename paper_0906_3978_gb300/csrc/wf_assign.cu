@@ -142,7 +142,7 @@ k_lowpass(const IN* __restrict__ in, double* __restrict__ out, double in_scale,
   constexpr int M = N, NL = lp_lines<R, N>(), LD = NL + 1;
   constexpr int TPL = tpl<R, M>(), NT = NL * TPL;
   static_assert(N % NL == 0, "tile width must divide N");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + M * LD;  // exp(-2 pi i e/(2N)), e < 2N
   const int tid = threadIdx.x;

@@ -210,7 +210,7 @@ k_plane_turn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S
              Bat bt) {
   using G = PlaneG<R, N, CS, E>;
   namespace cg = cooperative_groups;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::TILE;
   __shared__ double red[32];

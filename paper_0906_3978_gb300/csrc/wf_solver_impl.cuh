@@ -239,23 +239,24 @@ struct Spec {
       return G::TPS;
     }
   };
-  // the register-staged kernels (one CTA per tile, loads through registers), radix cap RMAX
-  template <int RMAX>
+  // the register-staged kernels (one CTA per tile, loads through registers), radix cap RMAX, at
+  // least MINB resident CTAs per SM (the register cap that allows them: 128 for 2, 85 for 3)
+  template <int RMAX, int MINB = 0>
   struct XReg {
     static cudaError_t setup() {
-      cudaError_t e = set_smem(k_cg_xinv<R, N, true, RMAX>, SMxy);
-      if (e == cudaSuccess) e = set_smem(k_cg_xinv<R, N, false, RMAX>, SMxy);
-      if (e == cudaSuccess) e = set_smem(k_cg_xupd<R, N, true, RMAX>, SMxy);
-      if (e == cudaSuccess) e = set_smem(k_cg_xupd<R, N, false, RMAX>, SMxy);
+      cudaError_t e = set_smem(k_cg_xinv<R, N, true, RMAX, MINB>, SMxy);
+      if (e == cudaSuccess) e = set_smem(k_cg_xinv<R, N, false, RMAX, MINB>, SMxy);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd<R, N, true, RMAX, MINB>, SMxy);
+      if (e == cudaSuccess) e = set_smem(k_cg_xupd<R, N, false, RMAX, MINB>, SMxy);
       return e;
     }
     static int xinv(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* ctab, const SS* mtab, bool unit_m,
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
       c.launch("cg_xinv", 6 * BS * nb, st, [&] {
         if (unit_m)
-          k_cg_xinv<R, N, true, RMAX><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
+          k_cg_xinv<R, N, true, RMAX, MINB><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
         else
-          k_cg_xinv<R, N, false, RMAX><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
+          k_cg_xinv<R, N, false, RMAX, MINB><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
       });
       return GXY;
     }
@@ -263,9 +264,9 @@ struct Spec {
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
       c.launch("cg_xupd", 4 * BS * nb, st, [&] {
         if (unit_m)
-          k_cg_xupd<R, N, true, RMAX><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
+          k_cg_xupd<R, N, true, RMAX, MINB><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
         else
-          k_cg_xupd<R, N, false, RMAX><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
+          k_cg_xupd<R, N, false, RMAX, MINB><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
       });
       return GXY;
     }

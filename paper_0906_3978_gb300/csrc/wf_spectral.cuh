@@ -357,8 +357,8 @@ WF_D void tile_mul(cx<R>* tile, int kz0, int ky_s, const TAB* tab, int tid) {
 // P0 = (Z + conj Z(-k)) / 2 and PN = (Z - conj Z(-k)) / 2i (Z(-k) from the partner line).
 // UNIT_M: m = 1 at every k != 0 (the preconditioned system), so m is read only on column 0.
 // ------------------------------------------------------------------------------------------
-template <class R, int N, bool UNIT_M, int RMAX = 8>
-__global__ void __launch_bounds__(XYG<R, N>::NT)
+template <class R, int N, bool UNIT_M, int RMAX = 8, int MINB = 0>
+__global__ void __launch_bounds__(XYG<R, N>::NT, MINB)
 k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, typename Store<R>::T* P1,
           typename Store<R>::T* __restrict__ x, typename Store<R>::T* __restrict__ T,
           const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
@@ -370,7 +370,7 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
   using VT = typename G::VT;
   constexpr int NH = G::NH;
   static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
@@ -498,8 +498,8 @@ k_cg_xinv(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* P0, 
 // weights, without 1/V_c) and an upper estimate of V_c ||C^-1 r||^2 (the canonical residual): on
 // column 0 the larger of the two planes' 1/c^2 is used.  grid (N/2 / NL, N).
 // ------------------------------------------------------------------------------------------
-template <class R, int N, bool UNIT_M, int RMAX = 8>
-__global__ void __launch_bounds__(XYG<R, N>::NT)
+template <class R, int N, bool UNIT_M, int RMAX = 8, int MINB = 0>
+__global__ void __launch_bounds__(XYG<R, N>::NT, MINB)
 k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __restrict__ r,
           const typename Store<R>::T* P0, const typename Store<R>::T* P1,
           const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
@@ -511,7 +511,7 @@ k_cg_xupd(const typename Store<R>::T* __restrict__ T, typename Store<R>::T* __re
   using VT = typename G::VT;
   constexpr int NH = G::NH;
   static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
@@ -1230,7 +1230,7 @@ k_xmul(const typename Store<R>::T* __restrict__ in, typename Store<R>::T* __rest
   using G = XYG<R, N>;
   using SS = typename Store<R>::S;
   constexpr int NH = G::NH;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
@@ -1412,7 +1412,7 @@ k_zturn(typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __r
   using G = ZG<R, N, EZ>;
   using SS = typename Store<R>::S;
   static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;  // 2N entries
   __shared__ double red[32];
@@ -1483,7 +1483,7 @@ k_zfwd(const double* __restrict__ in, typename Store<R>::T* __restrict__ out,
        const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials, const CgScal* __restrict__ sc,
        Bat bt) {
   using G = ZG<R, N>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
@@ -1540,7 +1540,7 @@ k_zinv(const typename Store<R>::T* __restrict__ in, double* __restrict__ out,
        double scl, const typename Store<R>::T* __restrict__ twtab, double* __restrict__ partials,
        const CgScal* __restrict__ sc, Bat bt) {
   using G = ZG<R, N>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
   cx<R>* tw = tile + G::M * G::LD;
   __shared__ double red[32];
