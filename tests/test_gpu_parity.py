@@ -356,6 +356,13 @@ def test_autotune_every_variant_matches_oracle(ctx):
     ctx.tune_set(before)
 
 
+def test_fp64_rate_is_plausible(ctx):
+    """wf_fp64_rate, the FP64 peak the bench reports the FP64 passes against: positive, repeatable
+    to 10%, and within the range GB300-class parts span (0.3-100 TFLOP/s FP64 FMA)."""
+    a, b = ctx.fp64_rate(), ctx.fp64_rate()
+    assert 0.3e12 < a < 100e12 and abs(a - b) <= 0.1 * max(a, b)
+
+
 def test_fixed_iterations_full_size_workload(ctx):
     """The 512^3 workload the benchmark times, where a converged oracle solve does not fit in test
     time: both sides run k = 20 textbook-CG iterations from 0 (precond = 0).  The FP64 path holds
