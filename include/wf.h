@@ -97,6 +97,12 @@ typedef struct {
                          1e-4; each step asks for half the remaining reduction, at most this) */
   int precond;        /* 1: CG in Fourier variables split-preconditioned by S^(1/2)
                          (same canonical system and residual); 0: plain CG on A */
+  int deflate;        /* WF_MIXED only: 0 off; K in [1, 12] with 4 K < n: each inner CG is
+                         preconditioned on the coarse space of the Fourier modes |k|^2 <= K^2
+                         (grid units), whose Galerkin block Z^T (C A C) Z is formed and inverted
+                         on the device once per solve (two-level "A-DEF2" form, Tang et al. 2009).
+                         Same system, residual and stop rule; fewer iterations where the mask
+                         couples the long-wavelength modes.  Errors: WF_ERR_ARG otherwise. */
 } wf_solve_opts;
 
 typedef struct {

@@ -67,7 +67,7 @@ class Response(ctypes.Structure):
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", c_double), ("max_iter", c_int), ("prec", c_int), ("inner_tol", c_double),
-                ("precond", c_int)]
+                ("precond", c_int), ("deflate", c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -225,8 +225,8 @@ def make_power(pk_k, pk_p):
     return pw, (k, p)
 
 
-def make_opts(tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1):
-    return SolveOpts(float(tol), int(max_iter), int(prec), float(inner_tol), int(precond))
+def make_opts(tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1, deflate=0):
+    return SolveOpts(float(tol), int(max_iter), int(prec), float(inner_tol), int(precond), int(deflate))
 
 
 class Context:
@@ -365,15 +365,16 @@ class Context:
 
     # ---- Sec. 3.3.1 ---------------------------------------------------------------------
     def solve(self, w, nbar: float, b, box: float, pk_k, pk_p, tol=1e-6, max_iter=5000, prec=FP64,
-              inner_tol=0.0, precond=1, s_out=None, stream=None, check=True):
-        """(s, info): Wiener mean s solving (S^-1 + nbar diag(w)) s = b."""
+              inner_tol=0.0, precond=1, s_out=None, stream=None, check=True, deflate=0):
+        """(s, info): Wiener mean s solving (S^-1 + nbar diag(w)) s = b.  deflate = K > 0 (WF_MIXED):
+        inner solves preconditioned on the coarse Fourier modes |k| <= K."""
         import torch
         n = int(b.shape[0])
         if s_out is None:
             s_out = torch.empty_like(b)
         g = Grid(n, float(box), 1)
         pw, keep = make_power(pk_k, pk_p)
-        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond, deflate)
         info = SolveInfo()
         st = lib().wf_solve(self._h, ctypes.byref(g), ctypes.byref(pw), _ptr(w), float(nbar), _ptr(b),
                             ctypes.byref(o), _ptr(s_out), ctypes.byref(info), _stream(stream))
@@ -425,7 +426,7 @@ class Context:
 
     def solve_batch(self, problems, stream=None):
         """problems: list of dicts with w, nbar, b, box, pk_k, pk_p, tol, max_iter, prec, inner_tol,
-        precond (and optional s_out).  Returns (status, [s], [info])."""
+        precond, deflate (and optional s_out).  Returns (status, [s], [info])."""
         import torch
         cnt = len(problems)
         grids = (Grid * cnt)()
@@ -444,7 +445,7 @@ class Context:
             keep.append(kk)
             pows[i] = pw
             opts[i] = make_opts(pr.get("tol", 1e-6), pr.get("max_iter", 5000), pr.get("prec", FP64),
-                                pr.get("inner_tol", 0.0), pr.get("precond", 1))
+                                pr.get("inner_tol", 0.0), pr.get("precond", 1), pr.get("deflate", 0))
             s = pr.get("s_out")
             if s is None:
                 s = torch.empty_like(pr["b"])
@@ -572,14 +573,14 @@ class Context:
 
     # ---- serving ------------------------------------------------------------------------
     def submit(self, w_host, nbar, b_host, box, pk_k, pk_p, tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0,
-               precond=1) -> int:
+               precond=1, deflate=0) -> int:
         """Queue a solve from HOST float64 arrays; returns the request id."""
         w_host = np.ascontiguousarray(w_host, dtype=np.float64)
         b_host = np.ascontiguousarray(b_host, dtype=np.float64)
         n = int(b_host.shape[0])
         g = Grid(n, float(box), 1)
         pw, keep = make_power(pk_k, pk_p)
-        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond, deflate)
         rid = c_uint64(0)
         st = lib().wf_submit(self._h, ctypes.byref(g), ctypes.byref(pw), w_host.ctypes.data, float(nbar),
                              b_host.ctypes.data, ctypes.byref(o), ctypes.byref(rid))

@@ -6,6 +6,7 @@
 #include <iterator>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include <map>
@@ -252,21 +253,44 @@ wf_status autotune(Ctx& c, int n, int prec, std::string& report) {
   }
 }
 
-// Device bytes of a group (the buffers GroupFP64 / GroupMixed allocate, tables excluded).
-size_t Group::footprint(int n, int prec, int count) {
+// Coarse modes of radius K: one of each +-k pair, k != 0 (kz > 0, or kz = 0 with ky > 0, or
+// kz = ky = 0 with kx > 0), as (kx, ky, kz, |k|^2), in the order kz, ky, kx.
+std::vector<int4> deflation_modes(int K) {
+  std::vector<int4> m;
+  for (int kz = 0; kz <= K; ++kz)
+    for (int ky = -K; ky <= K; ++ky)
+      for (int kx = -K; kx <= K; ++kx) {
+        const int n2 = kx * kx + ky * ky + kz * kz;
+        if (n2 > K * K || n2 == 0) continue;
+        if (kz > 0 || ky > 0 || (ky == 0 && kx > 0)) m.push_back(make_int4(kx, ky, kz, n2));
+      }
+  return m;
+}
+int deflation_ncp(int K) {
+  const int nc = 2 * (int)deflation_modes(K).size() + 1;
+  return (nc + 63) / 64 * 64;
+}
+
+// Device bytes of a group (the buffers GroupFP64 / GroupMixed allocate, tables excluded), with the
+// coarse-space buffers of a deflated group (K > 0).
+size_t Group::footprint(int n, int prec, int count, int K) {
   const double V = (double)n * n * n, spec = V / 2;
-  const double per = prec == WF_MIXED ? 5 * spec * 8 + 2 * spec * 16 + 4 * V + 4 * 8 * V
-                                      : 6 * spec * 16 + 5 * 8 * V;
+  double per = prec == WF_MIXED ? 5 * spec * 8 + 2 * spec * 16 + 4 * V + 4 * 8 * V : 6 * spec * 16 + 5 * 8 * V;
+  if (K > 0) {
+    const double ncp = deflation_ncp(K), C = 4.0 * K + 1;
+    per += 4 * ncp * ncp + 2 * 4 * 64 * ncp + 8 * ncp + 8 * (double)n * n * (K + 1) +
+           8 * (2.0 * K + 1) * (K + 1) * n + 8 * C * C * C + 24 * ncp + 4 * 64 * 64 + 4.0 * (3 * (n / 2) * (n / 2) + 1);
+  }
   return (size_t)(per * count) + (size_t)count * (3 * (n / 2) * (n / 2) + 1) * 24 + (64u << 10);
 }
 
 wf_status solve_many(Ctx& c, std::vector<SolveArgs*>& sys, std::vector<wf_solve_info*>& infos, cudaStream_t st) {
-  std::map<std::pair<int, int>, std::unique_ptr<Group>> groups;
+  std::map<std::tuple<int, int, int>, std::unique_ptr<Group>> groups;
   for (size_t i = 0; i < sys.size(); ++i) {
-    const auto key = std::make_pair(sys[i]->grid.n, (int)sys[i]->opts.prec);
+    const auto key = std::make_tuple(sys[i]->grid.n, (int)sys[i]->opts.prec, sys[i]->opts.deflate);
     auto& g = groups[key];
     if (!g) {
-      g.reset(make_group_n(key.first, key.second));
+      g.reset(make_group_n(std::get<0>(key), std::get<1>(key)));
       if (!g) return WF_ERR_UNSUPPORTED;
     }
     g->sys.push_back(sys[i]);
@@ -371,6 +395,11 @@ wf_status prepare_solve(const wf_grid* grid, const wf_power* power, const double
   if (!(nbar > 0.0) || !std::isfinite(nbar)) return WF_ERR_ARG;
   if (!(opts->tol > 0.0) || opts->max_iter <= 0 || (opts->prec != WF_FP64 && opts->prec != WF_MIXED))
     return WF_ERR_ARG;
+  if (opts->deflate != 0 &&
+      (opts->prec != WF_MIXED || opts->deflate < 1 || opts->deflate > kDeflMaxRadius || 4 * opts->deflate >= grid->n)) {
+    set_last_error("deflate: a coarse radius in [1, 12] with 4 K < n, for WF_MIXED solves only", cudaSuccess);
+    return WF_ERR_ARG;
+  }
   a.grid = *grid;
   a.w = w;
   a.b = b;
@@ -539,6 +568,11 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
     return WF_ERR_ARG;
   if (!(opts->tol > 0.0) || opts->max_iter <= 0 || (opts->prec != WF_FP64 && opts->prec != WF_MIXED))
     return WF_ERR_ARG;
+  if (opts->deflate != 0 &&
+      (opts->prec != WF_MIXED || opts->deflate < 1 || opts->deflate > kDeflMaxRadius || 4 * opts->deflate >= grid->n)) {
+    set_last_error("deflate: a coarse radius in [1, 12] with 4 K < n, for WF_MIXED solves only", cudaSuccess);
+    return WF_ERR_ARG;
+  }
   if (infos) std::memset(infos, 0, (size_t)n_sub * sizeof(*infos));
   std::vector<double> sinv;
   WF_TRY(build_sinv_table(*grid, *power, sinv));

@@ -16,6 +16,9 @@
 
 namespace wf {
 
+// largest coarse radius of a deflated solve (wf_solve_opts.deflate)
+constexpr int kDeflMaxRadius = 12;
+
 void set_last_error(const char* what, cudaError_t e);
 
 #define WF_CUDA(...)                                   \

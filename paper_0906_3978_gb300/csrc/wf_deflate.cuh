@@ -1,0 +1,544 @@
+// wf_deflate.cuh -- two-level preconditioning of the inner CG by the lowest Fourier modes.
+//
+// The Wiener system is solved by CG in Fourier variables (Sec. 3.3.1); its slowest directions are
+// the long-wavelength modes, where the prior S is largest and couples them through the survey
+// mask.  The coarse space Z is spanned by the modes with |k|^2 <= K^2 (k in grid units), and
+// E = Z^T A' Z is its Galerkin block of the preconditioned operator A' = C A C:
+//     E(p, q) = m(p) delta_pq + c(p) c(q) Dh(p - q),   Dh = DFT of D = nbar w / V_c,
+// a dense matrix built from the transform of the window at the differences of coarse modes.  Each
+// inner CG runs preconditioned by the "A-DEF2" two-level operator of the deflation literature
+// (Tang, Nabben, Vuik and Erlangga 2009, Sec. 2.3.3 there):
+//     z = r - Z E^-1 Z^T (A' r - r),   started from x0 = Z E^-1 Z^T b (one step with alpha = 1),
+// which, unlike plain deflated CG, keeps converging when E^-1 and A' r are only accurate to
+// FP32.  E^-1 is formed once per solve by block Gauss-Jordan exchange in FP32.
+//
+// Coordinates.  A real field's spectrum is Hermitian, so the coarse space has nc = 2 nh + 1 real
+// coordinates: k = 0 (the value y_0) and, for each of the nh half-space modes h (kz > 0, or
+// kz = 0 with ky > 0, or kz = ky = 0 with kx > 0), a_h = sqrt2 Re y_h and b_h = sqrt2 Im y_h.  This
+// basis is orthonormal for the CG inner product (the full-spectrum sum of Re(conj u v)).
+//
+// Per iteration (FP32 vectors, the packed half spectrum of wf_spectral.cuh):
+//   T  = IFFT_x(c r), IFFT_y          (the solver's own passes)
+//   k_zcoarse   IFFT_z, times D, FFT_z; keep kz <= K (the kz = 0 plane only)   -> Gz [N][N][K+1]
+//   k_ycoarse   DFT along y at |ky| <= K                                      -> Gy [2K+1][K+1][N]
+//   k_xcoarse   DFT along x at the coarse modes; g = coords of (m - 1) r + c Gc, and coords of r
+//   k_defl_mu   mu = E^-1 g (one warp per mode); r -= Z mu kept aside for the x pass, which forms
+//               p = (r - Z mu) + beta p; partials of <r, Z mu>
+//   k_fin_defl  <r, z> = <r, r> - <r, Z mu>; beta = <r, z> / <r, z>_prev; alpha's numerator
+//   (x pass 1)  then k_defl_restore puts the saved coarse entries of r back
+#pragma once
+#include "wf_spectral.cuh"
+
+namespace wf {
+
+constexpr int kDeflTile = 64;   // block of the coarse Gauss-Jordan exchange
+
+// packed-spectrum index of the signed mode (kx, ky, kz), 0 <= kz < N/2
+template <int N> WF_D size_t dslot(int kx, int ky, int kz) {
+  return ((size_t)((kx + N) % N) * N + (size_t)((ky + N) % N)) * (N / 2) + kz;
+}
+
+// ------------------------------------------------------------------------------------------
+// z stage of the coarse projection (the z turn without its full store): each (x, y) line of the
+// y-transformed field is taken to real space, multiplied by D, transformed forward, and its
+// kz = 0..K coefficients are stored; element 0 keeps only the kz = 0 plane (its real part), so the
+// later x / y DFTs give that plane's coefficients directly.  grid (N*N / NL, 1, systems).
+// ------------------------------------------------------------------------------------------
+template <class R, int N>
+__global__ void __launch_bounds__(ZG<R, N>::NT)
+k_zcoarse(const typename Store<R>::T* __restrict__ spec, const typename Store<R>::S* __restrict__ D,
+          const typename Store<R>::T* __restrict__ twtab, typename Store<R>::T* __restrict__ gz, int K,
+          const CgScal* __restrict__ sc, Bat bt, size_t gzs) {
+  using G = ZG<R, N>;
+  using SS = typename Store<R>::S;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* tw = tile + G::M * G::LD;  // 2N entries
+  const int z = blockIdx.z;
+  if (sc[z].done) return;
+  spec += z * bt.spec;
+  D += z * bt.real;
+  gz += z * gzs;
+  const int tid = threadIdx.x;
+  const size_t row0 = (size_t)blockIdx.x * G::NL;
+  if (tid < G::NL) prefetch_l2(D + (row0 + tid) * N, N * sizeof(SS));
+  for (int e = tid; e < 2 * N; e += G::NT) tw[e] = ld_c<R>(twtab + e);
+  zrows_load<G>(tile, spec, row0, tid);
+  __syncthreads();
+  const int l = tid % G::NL, t = tid / G::NL;
+  c2r_prep<R, N, G::LD>(tile + l, t, G::TPL, tw);
+  __syncthreads();
+  fft_line<R, G::M, G::TPL, G::LD, +1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
+  // real samples 2i, 2i+1 of line l sit in element i
+#pragma unroll 4
+  for (int k = 0; k < G::PER; ++k) {
+    const int idx = tid + k * G::NT;
+    if (!(G::EVEN || idx < G::NVEC)) continue;
+    const int ll = idx / G::NV, i = (idx % G::NV) * G::VW;
+    const SS* dp = D + (row0 + ll) * N + 2 * i;
+    if constexpr (G::VW == 2) {
+      const float4 d = *reinterpret_cast<const float4*>(dp);
+      cx<R> a = tile[i * G::LD + ll], b = tile[(i + 1) * G::LD + ll];
+      a.x = a.x * RT<R>::from_f(d.x);
+      a.y = a.y * RT<R>::from_f(d.y);
+      b.x = b.x * RT<R>::from_f(d.z);
+      b.y = b.y * RT<R>::from_f(d.w);
+      tile[i * G::LD + ll] = a;
+      tile[(i + 1) * G::LD + ll] = b;
+    } else {
+      const double2 d = *reinterpret_cast<const double2*>(dp);
+      cx<R> a = tile[i * G::LD + ll];
+      a.x = a.x * RT<R>::c(d.x);
+      a.y = a.y * RT<R>::c(d.y);
+      tile[i * G::LD + ll] = a;
+    }
+  }
+  __syncthreads();
+  fft_line<R, G::M, G::TPL, G::LD, -1, 4, rmax_for(G::M, G::TPL)>(tile + l, t, tw);
+  r2c_post<R, N, G::LD>(tile + l, t, G::TPL, tw);
+  __syncthreads();
+  for (int e = tid; e < G::NL * (K + 1); e += G::NT) {
+    const int ll = e / (K + 1), i = e % (K + 1);
+    cx<R> v = tile[i * G::LD + ll];
+    if (i == 0) v.y = RT<R>::c(0.0);  // drop the kz = N/2 plane packed beside kz = 0
+    st_c(gz + (row0 + ll) * (K + 1) + i, v);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// y stage: Gy[ky + K][kz][x] = sum_y exp(-2 pi i ky y / N) Gz[x][y][kz] for |ky| <= K.
+// grid (N, systems), 256 threads; shared memory N (K + 1) + N complex values.
+// ------------------------------------------------------------------------------------------
+template <class R, int N>
+__global__ void __launch_bounds__(256)
+k_ycoarse(const typename Store<R>::T* __restrict__ gz, const typename Store<R>::T* __restrict__ twtab,
+          typename Store<R>::T* __restrict__ gy, int K, const CgScal* __restrict__ sc, size_t gzs, size_t gys) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int KZ = K + 1;
+  cx<R>* a = reinterpret_cast<cx<R>*>(smem_raw);  // [N][K+1]
+  cx<R>* tw = a + N * KZ;                          // tw[e] = exp(-2 pi i e / N)
+  const int z = blockIdx.y;
+  if (sc[z].done) return;
+  const int x = blockIdx.x;
+  gz += z * gzs + (size_t)x * N * KZ;
+  gy += z * gys;
+  for (int e = threadIdx.x; e < N * KZ; e += blockDim.x) a[e] = ld_c<R>(gz + e);
+  for (int e = threadIdx.x; e < N; e += blockDim.x) tw[e] = ld_c<R>(twtab + 2 * e);
+  __syncthreads();
+  const int nout = (2 * K + 1) * KZ;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    const int ky = o / KZ - K, kz = o % KZ;
+    const int step = (ky + N) % N;
+    R sr = RT<R>::c(0.0), si = RT<R>::c(0.0);
+    int e = 0;
+    for (int y = 0; y < N; ++y) {
+      const cx<R> v = a[y * KZ + kz], w = tw[e];
+      sr += v.x * w.x - v.y * w.y;
+      si += v.x * w.y + v.y * w.x;
+      e += step;
+      if (e >= N) e -= N;
+    }
+    st_c(gy + (size_t)o * N + x, cx<R>{sr, si});
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// x stage and coordinates: one warp per half-space mode (warp nh: k = 0).
+// MODE 0: gco = rco = coordinates of r (the start, x0 = Z E^-1 Z^T r).
+// MODE 1: Gc = sum_x exp(-2 pi i kx x / N) Gy[ky + K][kz][x];  w = (m - 1) r + c Gc;
+//         gco = coordinates of w (= Z^T (A' r - r)), rco = coordinates of r.
+// r on the kz = 0 plane is unpacked from the column pair: r0(h) = (Z(h) + conj Z(-h)) / 2.
+// grid (ceil((nh + 1) / 8), systems), 256 threads.
+// ------------------------------------------------------------------------------------------
+template <class R, int N, int MODE>
+__global__ void __launch_bounds__(256)
+k_xcoarse(const typename Store<R>::T* __restrict__ gy, const typename Store<R>::T* __restrict__ r,
+          const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::S* __restrict__ mtab,
+          const typename Store<R>::T* __restrict__ twtab, const int4* __restrict__ modes, int nh, int K,
+          float* __restrict__ gco, float* __restrict__ rco, const CgScal* __restrict__ sc, Bat bt, size_t gys,
+          int ncp) {
+  const int z = blockIdx.y;
+  if (sc[z].done) return;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (warp > nh) return;
+  r += z * bt.spec;
+  ctab += z * bt.tab;
+  mtab += z * bt.tab;
+  gy += z * gys;
+  gco += (size_t)z * ncp;
+  rco += (size_t)z * ncp;
+  int4 md = make_int4(0, 0, 0, 0);
+  if (warp < nh) md = modes[warp];
+  const cx<R> v1 = ld_c<R>(r + dslot<N>(md.x, md.y, md.z));
+  cx<R> rh = v1;
+  if (md.z == 0) {
+    const cx<R> v2 = ld_c<R>(r + dslot<N>(-md.x, -md.y, 0));
+    const R h = RT<R>::c(0.5);
+    rh = cx<R>{(v1.x + v2.x) * h, (v1.y - v2.y) * h};
+  }
+  R gr = RT<R>::c(0.0), gi = RT<R>::c(0.0);
+  if constexpr (MODE == 1) {
+    const typename Store<R>::T* line = gy + (size_t)((md.y + K) * (K + 1) + md.z) * N;
+    const int step = (md.x + N) % N;
+    const int step32 = (int)(((long long)step * 32) % N);
+    int e = (int)(((long long)step * lane) % N);
+    for (int xx = lane; xx < N; xx += 32) {
+      const cx<R> v = ld_c<R>(line + xx), w = ld_c<R>(twtab + 2 * e);
+      gr += v.x * w.x - v.y * w.y;
+      gi += v.x * w.y + v.y * w.x;
+      e += step32;
+      if (e >= N) e -= N;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      gr += __shfl_xor_sync(0xffffffffu, gr, o);
+      gi += __shfl_xor_sync(0xffffffffu, gi, o);
+    }
+  }
+  if (lane != 0) return;
+  R wr = rh.x, wi = rh.y;
+  if constexpr (MODE == 1) {
+    const R c = tab_to<R>(ctab[md.w]), m1 = tab_to<R>(mtab[md.w]) - RT<R>::c(1.0);
+    wr = m1 * rh.x + c * gr;
+    wi = m1 * rh.y + c * gi;
+  }
+  const float s2 = 1.41421356237309505f;
+  if (warp < nh) {
+    gco[1 + 2 * warp] = s2 * (float)wr;
+    gco[2 + 2 * warp] = s2 * (float)wi;
+    rco[1 + 2 * warp] = s2 * (float)rh.x;
+    rco[2 + 2 * warp] = s2 * (float)rh.y;
+  } else {
+    gco[0] = (float)wr;
+    rco[0] = (float)rh.x;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// mu = E^-1 g, one warp per half-space mode (rows 1 + 2j, 2 + 2j; warp nh: row 0), and its use:
+// MODE 0: vec (zeroed) receives Z mu (the start vector).
+// MODE 1: the coarse entries of vec (= r) are saved to rsave and replaced by r - Z mu; the
+//         partial <r, Z mu> = rco . mu of the warp goes to dpart[warp].
+// Z mu has (a + i b) / sqrt2 at h and its conjugate at -h (stored on the kz = 0 plane only).
+// grid (ceil((nh + 1) / 8), systems), 256 threads, ncp floats of shared memory.
+// ------------------------------------------------------------------------------------------
+template <class R, int N, int MODE>
+__global__ void __launch_bounds__(256)
+k_defl_mu(const float* __restrict__ Einv, const float* __restrict__ gco, const float* __restrict__ rco,
+          const int4* __restrict__ modes, int nh, int ncp, typename Store<R>::T* __restrict__ vec,
+          typename Store<R>::T* __restrict__ rsave, double* __restrict__ dpart, const CgScal* __restrict__ sc,
+          Bat bt) {
+  using ST = typename Store<R>::T;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* gs = reinterpret_cast<float*>(smem_raw);
+  const int z = blockIdx.y;
+  if (sc[z].done) return;
+  Einv += (size_t)z * ncp * ncp;
+  gco += (size_t)z * ncp;
+  rco += (size_t)z * ncp;
+  vec += z * bt.spec;
+  rsave += (size_t)z * (2 * nh + 1);
+  dpart += (size_t)z * (nh + 1);
+  for (int e = threadIdx.x; e < ncp; e += blockDim.x) gs[e] = gco[e];
+  __syncthreads();
+  const int warp = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)), lane = threadIdx.x & 31;
+  if (warp > nh) return;
+  const int ra = warp < nh ? 1 + 2 * warp : 0;
+  const float4* rowa = reinterpret_cast<const float4*>(Einv + (size_t)ra * ncp);
+  const float4* rowb = reinterpret_cast<const float4*>(Einv + (size_t)(ra + 1) * ncp);
+  const float4* g4 = reinterpret_cast<const float4*>(gs);
+  float sa = 0.f, sb = 0.f;
+  for (int q = lane; q < ncp / 4; q += 32) {
+    const float4 g = g4[q];
+    const float4 a = __ldg(rowa + q);
+    sa += a.x * g.x + a.y * g.y + a.z * g.z + a.w * g.w;
+    if (warp < nh) {
+      const float4 b = __ldg(rowb + q);
+      sb += b.x * g.x + b.y * g.y + b.z * g.z + b.w * g.w;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+  }
+  if (lane != 0) return;
+  if (warp < nh) {
+    const int4 md = modes[warp];
+    const float h = 0.70710678118654752f;
+    const cx<R> v{RT<R>::from_f(sa * h), RT<R>::from_f(sb * h)};
+    const size_t s1 = dslot<N>(md.x, md.y, md.z);
+    const size_t s2 = dslot<N>(-md.x, -md.y, 0);
+    if constexpr (MODE == 0) {
+      st_c(vec + s1, v);
+      if (md.z == 0) st_c(vec + s2, conj(v));
+    } else {
+      dpart[warp] = (double)rco[ra] * (double)sa + (double)rco[ra + 1] * (double)sb;
+      const ST o1 = vec[s1];
+      rsave[2 * warp] = o1;
+      st_c(vec + s1, ld_c<R>(&o1) - v);
+      if (md.z == 0) {
+        const ST o2 = vec[s2];
+        rsave[2 * warp + 1] = o2;
+        st_c(vec + s2, ld_c<R>(&o2) - conj(v));
+      }
+    }
+  } else {
+    const cx<R> v{RT<R>::from_f(sa), RT<R>::c(0.0)};
+    if constexpr (MODE == 0) {
+      st_c(vec, v);
+    } else {
+      dpart[nh] = (double)rco[0] * (double)sa;
+      const ST o = vec[0];
+      rsave[2 * nh] = o;
+      st_c(vec, ld_c<R>(&o) - v);
+    }
+  }
+}
+
+// the coarse entries of r as they were before k_defl_mu<MODE 1>; grid (ceil((nh + 1) / 256), systems)
+template <class R, int N>
+__global__ void k_defl_restore(typename Store<R>::T* __restrict__ r, const typename Store<R>::T* __restrict__ rsave,
+                               const int4* __restrict__ modes, int nh, const CgScal* __restrict__ sc, Bat bt) {
+  const int z = blockIdx.y;
+  if (sc[z].done) return;
+  const int u = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (u > nh) return;
+  r += z * bt.spec;
+  rsave += (size_t)z * (2 * nh + 1);
+  if (u == nh) {
+    r[0] = rsave[2 * nh];
+    return;
+  }
+  const int4 md = modes[u];
+  r[dslot<N>(md.x, md.y, md.z)] = rsave[2 * u];
+  if (md.z == 0) r[dslot<N>(-md.x, -md.y, 0)] = rsave[2 * u + 1];
+}
+
+// <r, z> = <r, r> - <r, Z mu> (sc->rr holds <r, r> from the last x pass 2); beta = <r, z> over its
+// previous value (0 on the first iteration after the start step); alpha's numerator becomes
+// <r, z>.  grid = systems.
+static __global__ void k_fin_defl(const double* __restrict__ dpart, int nh, CgScal* sc) {
+  __shared__ double red[32];
+  sc += blockIdx.x;
+  if (sc->done) return;
+  const double s = sum_partials(dpart + (size_t)blockIdx.x * (nh + 1), nh + 1, 1, 0, red);
+  if (threadIdx.x == 0) {
+    const double rz = sc->rr - s;
+    if (!(rz > 0.0) || !isfinite(rz)) {
+      sc->done = 3;
+      return;
+    }
+    sc->beta = sc->defl == 1 ? 0.0 : rz / sc->rzo;
+    if (sc->defl == 1) sc->defl = 0;
+    sc->rzo = rz;
+    sc->rr = rz;
+  }
+}
+
+// arm the start step (alpha = 1) of every running system; grid = systems
+static __global__ void k_defl_arm(CgScal* sc) {
+  sc += blockIdx.x;
+  if (threadIdx.x == 0 && sc->done == 0) sc->defl = 2;
+}
+
+// ------------------------------------------------------------------------------------------
+// Set-up: the transform of D at the differences of coarse modes, the coarse matrix, its inverse.
+// ------------------------------------------------------------------------------------------
+// DH[(dx + 2K) C^2 + (dy + 2K) C + dz + 2K] = scale * What(dx, dy, dz), C = 4K + 1, |d.| <= 2K,
+// from the packed spectrum What of w (negative dz by conjugate symmetry, dz = 0 unpacked from the
+// column pair); scale = nbar / V_c turns it into the transform of D.  grid (ceil(C^3 / 256), systems)
+template <class R, int N>
+__global__ void k_dh_gather(const typename Store<R>::T* __restrict__ what, float2* __restrict__ dh, int K,
+                            double inv_vc, const CgScal* __restrict__ sc, Bat bt) {
+  const int z = blockIdx.y;
+  const int C = 4 * K + 1;
+  const int i = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= C * C * C) return;
+  what += z * bt.spec;
+  dh += (size_t)z * C * C * C;
+  const int dx = i / (C * C) - 2 * K, dy = (i / C) % C - 2 * K, dz = i % C - 2 * K;
+  cx<R> v;
+  if (dz > 0) {
+    v = ld_c<R>(what + dslot<N>(dx, dy, dz));
+  } else if (dz < 0) {
+    v = conj(ld_c<R>(what + dslot<N>(-dx, -dy, -dz)));
+  } else {
+    const cx<R> a = ld_c<R>(what + dslot<N>(dx, dy, 0)), b = ld_c<R>(what + dslot<N>(-dx, -dy, 0));
+    const R h = RT<R>::c(0.5);
+    v = cx<R>{(a.x + b.x) * h, (a.y - b.y) * h};
+  }
+  const double s = sc[z].nbar * inv_vc;
+  dh[i] = make_float2((float)((double)v.x * s), (float)((double)v.y * s));
+}
+
+// E[i][j] over the coarse coordinates (identity on the padding [nc, ncp)):
+//   (0, 0)      m0 + c0^2 Dh(0)
+//   (0, a|b h)  sqrt2 c0 c_h Re|Im Dh(h)
+//   (a h, a h') m_h [h = h'] + c c' (Re Dh(h - h') + Re Dh(h + h'))
+//   (a h, b h') c c' (Im Dh(h + h') - Im Dh(h - h'))
+//   (b h, a h') c c' (Im Dh(h - h') + Im Dh(h + h'))
+//   (b h, b h') m_h [h = h'] + c c' (Re Dh(h - h') - Re Dh(h + h'))
+// grid (ncp / 16, ncp / 16, systems), 16 x 16 threads
+template <class S>
+__global__ void k_ebuild(const float2* __restrict__ dh, const S* __restrict__ ctab, const S* __restrict__ mtab,
+                         const int4* __restrict__ modes, int nh, int ncp, int K, float* __restrict__ E, int tabs) {
+  const int z = blockIdx.z;
+  const int C = 4 * K + 1;
+  const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+  dh += (size_t)z * C * C * C;
+  ctab += (size_t)z * tabs;
+  mtab += (size_t)z * tabs;
+  E += (size_t)z * ncp * ncp;
+  const int nc = 2 * nh + 1;
+  if (i >= ncp || j >= ncp) return;
+  if (i >= nc || j >= nc) {
+    E[(size_t)i * ncp + j] = i == j ? 1.f : 0.f;
+    return;
+  }
+  auto D = [&](int x, int y, int w) { return dh[((x + 2 * K) * C + (y + 2 * K)) * C + (w + 2 * K)]; };
+  const double s2 = 1.41421356237309505;
+  double v;
+  if (i == 0 && j == 0) {
+    v = (double)mtab[0] + (double)ctab[0] * (double)ctab[0] * (double)D(0, 0, 0).x;
+  } else if (i == 0 || j == 0) {
+    const int c = i == 0 ? j : i;
+    const int4 h = modes[(c - 1) / 2];
+    const float2 d = D(h.x, h.y, h.z);
+    v = s2 * (double)ctab[0] * (double)ctab[h.w] * (double)(((c - 1) % 2) == 0 ? d.x : d.y);
+  } else {
+    const int u = (i - 1) / 2, u2 = (j - 1) / 2, pi = (i - 1) % 2, pj = (j - 1) % 2;
+    const int4 h = modes[u], g = modes[u2];
+    const float2 A = D(h.x - g.x, h.y - g.y, h.z - g.z), B = D(h.x + g.x, h.y + g.y, h.z + g.z);
+    const double cc = (double)ctab[h.w] * (double)ctab[g.w];
+    const double dg = u == u2 ? (double)mtab[h.w] : 0.0;
+    if (pi == 0 && pj == 0) v = dg + cc * ((double)A.x + (double)B.x);
+    else if (pi == 0) v = cc * ((double)B.y - (double)A.y);
+    else if (pj == 0) v = cc * ((double)A.y + (double)B.y);
+    else v = dg + cc * ((double)A.x - (double)B.x);
+  }
+  E[(size_t)i * ncp + j] = (float)v;
+}
+
+// Block Gauss-Jordan exchange on block row / column kb of the SPD matrix M (ncp x ncp, row-major;
+// after every block of the diagonal is exchanged, M holds M^-1):
+//   P = M_kk^-1;  M_kj <- -P M_kj;  M_ik <- M_ik P;  M_ij <- M_ij - M_ik P M_kj  (i, j != k).
+// No pivoting: every diagonal block of an SPD matrix's successive Schur complements is SPD.
+// (1) the pivot block, exchanged element by element in shared memory (one CTA, 256 threads)
+static __global__ void __launch_bounds__(256) k_gj_pivot(float* __restrict__ M, float* __restrict__ P, int ncp, int kb) {
+  constexpr int B = kDeflTile;
+  __shared__ float a[B][B + 1];
+  const int z = blockIdx.z;
+  M += (size_t)z * ncp * ncp + (size_t)kb * B * ncp + (size_t)kb * B;
+  P += (size_t)z * B * B;
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) a[e / B][e % B] = M[(size_t)(e / B) * ncp + e % B];
+  __syncthreads();
+  float nv[B * B / 256];
+  for (int k = 0; k < B; ++k) {
+    const float inv = 1.f / a[k][k];
+#pragma unroll
+    for (int q = 0; q < B * B / 256; ++q) {
+      const int e = threadIdx.x + q * 256, i = e / B, j = e % B;
+      if (i == k && j == k) nv[q] = inv;
+      else if (i == k) nv[q] = -a[k][j] * inv;
+      else if (j == k) nv[q] = a[i][k] * inv;
+      else nv[q] = a[i][j] - a[i][k] * (a[k][j] * inv);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < B * B / 256; ++q) {
+      const int e = threadIdx.x + q * 256;
+      a[e / B][e % B] = nv[q];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    const float v = a[e / B][e % B];
+    M[(size_t)(e / B) * ncp + e % B] = v;
+    P[e] = v;
+  }
+}
+
+// 64 x 64 x 64 product on 256 threads (4 x 4 outputs each): acc = As^T-stored A times Bs.
+// As[k][i] = A(i, k) and Bs[k][j] = B(k, j), rows padded to 68 floats.
+WF_D void gj_tile_mma(const float (*As)[68], const float (*Bs)[68], float acc[4][4], int ty, int tx) {
+#pragma unroll 8
+  for (int k = 0; k < kDeflTile; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
+    const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+// (2) the block row: Rp_j = P M_kj (kept for (3)), M_kj <- -Rp_j; and the old block column
+// Cp_j = M_jk copied aside.  grid (ncp / 64, 1, systems), 256 threads.
+static __global__ void __launch_bounds__(256) k_gj_panel(float* __restrict__ M, const float* __restrict__ P,
+                                                  float* __restrict__ Rp, float* __restrict__ Cp, int ncp, int kb) {
+  constexpr int B = kDeflTile;
+  __shared__ __align__(16) float As[B][68];
+  __shared__ __align__(16) float Bs[B][68];
+  const int z = blockIdx.z, jb = blockIdx.x;
+  if (jb == kb) return;
+  M += (size_t)z * ncp * ncp;
+  P += (size_t)z * B * B;
+  Rp += (size_t)z * B * ncp;
+  Cp += (size_t)z * ncp * B;
+  float* Mkj = M + (size_t)kb * B * ncp + (size_t)jb * B;
+  const float* Mjk = M + (size_t)jb * B * ncp + (size_t)kb * B;
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    const int i = e / B, j = e % B;
+    As[j][i] = P[e];                      // As[k][i] = P(i, k)
+    Bs[i][j] = Mkj[(size_t)i * ncp + j];  // Bs[k][j] = M_kj(k, j)
+    Cp[((size_t)jb * B + i) * B + j] = Mjk[(size_t)i * ncp + j];
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  float acc[4][4] = {};
+  gj_tile_mma(As, Bs, acc, ty, tx);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty * 4 + i, c = tx * 4 + j;
+      Rp[(size_t)r * ncp + (size_t)jb * B + c] = acc[i][j];
+      Mkj[(size_t)r * ncp + c] = -acc[i][j];
+    }
+}
+
+// (3) every block (ib, jb), ib != kb: M_ib,jb -= Cp_ib Rp_jb, or M_ib,kb = Cp_ib P.
+// grid (ncp / 64, ncp / 64, systems), 256 threads.
+static __global__ void __launch_bounds__(256) k_gj_update(float* __restrict__ M, const float* __restrict__ P,
+                                                   const float* __restrict__ Rp, const float* __restrict__ Cp,
+                                                   int ncp, int kb) {
+  constexpr int B = kDeflTile;
+  __shared__ __align__(16) float As[B][68];
+  __shared__ __align__(16) float Bs[B][68];
+  const int z = blockIdx.z, jb = blockIdx.x, ib = blockIdx.y;
+  if (ib == kb) return;
+  M += (size_t)z * ncp * ncp;
+  P += (size_t)z * B * B;
+  Rp += (size_t)z * B * ncp;
+  Cp += (size_t)z * ncp * B;
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    const int i = e / B, j = e % B;
+    As[j][i] = Cp[((size_t)ib * B + i) * B + j];  // As[k][i] = Cp_ib(i, k)
+    Bs[i][j] = jb == kb ? P[e] : Rp[(size_t)i * ncp + (size_t)jb * B + j];
+  }
+  __syncthreads();
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  float acc[4][4] = {};
+  gj_tile_mma(As, Bs, acc, ty, tx);
+  float* T = M + (size_t)ib * B * ncp + (size_t)jb * B;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const size_t o = (size_t)(ty * 4 + i) * ncp + tx * 4 + j;
+      T[o] = jb == kb ? acc[i][j] : T[o] - acc[i][j];
+    }
+}
+
+}  // namespace wf

@@ -20,6 +20,7 @@
 #include <map>
 #include <memory>
 #include <thread>
+#include <tuple>
 
 #include "wf_ctx.h"
 #include "wf_solver_group.h"
@@ -149,11 +150,11 @@ void Server::run() {
       std::lock_guard<std::mutex> ck(c.mu);
       DeviceGuard dg(c.device);
       // new groups from the admitted requests, by (size, precision): start their preparation
-      std::map<std::pair<int, int>, std::vector<std::shared_ptr<Request>>> by;
-      for (auto& r : admit) by[{r->args.grid.n, (int)r->args.opts.prec}].push_back(r);
+      std::map<std::tuple<int, int, int>, std::vector<std::shared_ptr<Request>>> by;
+      for (auto& r : admit) by[{r->args.grid.n, (int)r->args.opts.prec, r->args.opts.deflate}].push_back(r);
       for (auto& kv : by) {
         ResidentGroup rg;
-        rg.g.reset(make_group_n(kv.first.first, kv.first.second));
+        rg.g.reset(make_group_n(std::get<0>(kv.first), std::get<1>(kv.first)));
         rg.g->tag = "srv" + std::to_string(next_group++) + "_";
         for (auto& r : kv.second) {
           rg.g->sys.push_back(&r->args);
@@ -302,7 +303,7 @@ wf_status wf_submit(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, con
   wf_power pw{r->k.data(), r->p.data(), power->n};
   wf_status st = prepare_solve(grid, &pw, r->w, nbar, r->b, opts, r->s, r->args);
   if (st != WF_OK) return st;
-  r->footprint = Group::footprint(grid->n, (int)opts->prec, 1);
+  r->footprint = Group::footprint(grid->n, (int)opts->prec, 1, opts->deflate);
   r->t_submit = Clock::now();
   Server* s = server_of(c);
   {

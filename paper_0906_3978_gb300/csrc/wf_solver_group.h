@@ -27,11 +27,15 @@ struct Group {
   std::vector<wf_solve_info*> info;
   int nb = 0;
   std::string tag;  // prefix of this group's workspace names ("" = shared, reused across calls)
-  // Device bytes a group of `count` systems of size n and precision prec holds.
-  static size_t footprint(int n, int prec, int count);
+  // Device bytes a group of `count` systems of size n and precision prec holds (coarse radius K).
+  static size_t footprint(int n, int prec, int count, int K = 0);
 };
 
 Group* make_group_n(int n, int prec);
+// the coarse modes of a deflated solve of radius K, (kx, ky, kz, |k|^2), and the padded number
+// of coarse coordinates 2 nh + 1
+std::vector<int4> deflation_modes(int K);
+int deflation_ncp(int K);
 
 // out = F^-1 [table(|m|^2) F in] for one field of size N (instantiated with the solve drivers of
 // each size); table has 3 (N/2)^2 + 1 entries.

@@ -33,6 +33,7 @@
 #include "wf_solver_group.h"
 #include "wf_plane.cuh"
 #include "wf_spectral.cuh"
+#include "wf_deflate.cuh"
 
 namespace wf {
 
@@ -97,6 +98,10 @@ struct Spec {
     WF_A((k_xmul<R, N, false, true, false>), SMxy);
     WF_A((k_xmul<R, N, true, true, false>), SMxy);
     WF_A((k_zturn<R, N>), SMz);
+    if constexpr (std::is_same<R, float>::value) {
+      WF_A((k_zcoarse<R, N>), SMz);
+      WF_A((k_ycoarse<R, N>), (size_t)N * (kDeflMaxRadius + 2) * sizeof(cx<R>));
+    }
     if constexpr (PCS > 0) WF_A((k_plane_turn<R, N, PCS, PE>), (PlaneG<R, N, PCS, PE>::SMEM));
     WF_A((k_zfwd<R, N, true>), SMz);
     WF_A((k_zfwd<R, N, false>), SMz);
@@ -387,12 +392,19 @@ struct Spec {
              [&] { k_zinv<R, N, MODE><<<gz(nb), NTz, SMz, st>>>(in, out, s, w, b, scl, tw, part, sc, bat()); });
   }
 
-  // One CG iteration of every unfinished system (no host synchronisation).
+  struct NoHook {
+    void operator()(cudaStream_t) const {}
+  };
+  // One CG iteration of every unfinished system (no host synchronisation).  The first x pass forms
+  // p from rin (default r); after_xinv(st) is enqueued right after it.
+  template <class H = NoHook>
   static void iteration(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* D, const SS* ctab,
                         const SS* mtab, bool unit_m, const ST* tw, double* part, CgScal* sc, double inv_vc,
-                        cudaStream_t st) {
+                        cudaStream_t st, ST* rin = nullptr, H after_xinv = H()) {
     const Bat b = bat();
-    const int n1 = pick(c, "xinv", xvariants()).xinv(c, nb, r, P0, P1, x, T, ctab, mtab, unit_m, tw, part, sc, st);
+    const int n1 = pick(c, "xinv", xvariants())
+                       .xinv(c, nb, rin ? rin : r, P0, P1, x, T, ctab, mtab, unit_m, tw, part, sc, st);
+    after_xinv(st);
     int nmid = GZ;  // blocks that sum the data term of <p, A p> into part[NX ...]
     bool fused = false;
     if constexpr (PCS > 0) {
@@ -780,6 +792,13 @@ struct GroupMixed : GroupCommon<N> {
   std::vector<int> outer, iters;
   bool unit_m = true;
   static constexpr int NPART = SF::NPART > SD::NPART ? SF::NPART : SD::NPART;
+  // coarse space of a deflated group (K > 0; every system of the group has the same K)
+  int K = 0, nh = 0, ncp = 0;
+  int4* dmodes = nullptr;
+  float *Einv = nullptr, *gco = nullptr, *rco = nullptr, *Pb = nullptr, *Rp = nullptr, *Cp = nullptr;
+  float2 *Gz = nullptr, *Gy = nullptr, *rsave = nullptr, *DH = nullptr;
+  double* dpart = nullptr;
+  size_t gzs = 0, gys = 0;
 
   wf_status prepare_begin(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
@@ -808,7 +827,104 @@ struct GroupMixed : GroupCommon<N> {
       WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDefault, st));
       WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDefault, st));
     }
+    K = sys[0]->opts.deflate;
+    if (K > 0) WF_TRY(defl_alloc(c, st));
     return group_sums_begin<N>(c, *this, NPART, st);
+  }
+  // the coarse-space buffers and the mode table
+  wf_status defl_alloc(Ctx& c, cudaStream_t st) {
+    const std::vector<int4> modes = deflation_modes(K);
+    nh = (int)modes.size();
+    ncp = deflation_ncp(K);
+    const size_t C = 4 * K + 1;
+    gzs = (size_t)N * N * (K + 1);
+    gys = (size_t)(2 * K + 1) * (K + 1) * N;
+    const std::string dk = key + "d" + std::to_string(K) + "_";
+    WF_TRY(c.get(dk + "E", (size_t)nb * ncp * ncp * sizeof(float), (void**)&Einv));
+    WF_TRY(c.get(dk + "gco", (size_t)nb * ncp * sizeof(float), (void**)&gco));
+    WF_TRY(c.get(dk + "rco", (size_t)nb * ncp * sizeof(float), (void**)&rco));
+    WF_TRY(c.get(dk + "P", (size_t)nb * kDeflTile * kDeflTile * sizeof(float), (void**)&Pb));
+    WF_TRY(c.get(dk + "Rp", (size_t)nb * kDeflTile * ncp * sizeof(float), (void**)&Rp));
+    WF_TRY(c.get(dk + "Cp", (size_t)nb * ncp * kDeflTile * sizeof(float), (void**)&Cp));
+    WF_TRY(c.get(dk + "Gz", (size_t)nb * gzs * sizeof(float2), (void**)&Gz));
+    WF_TRY(c.get(dk + "Gy", (size_t)nb * gys * sizeof(float2), (void**)&Gy));
+    WF_TRY(c.get(dk + "rsave", (size_t)nb * (2 * nh + 1) * sizeof(float2), (void**)&rsave));
+    WF_TRY(c.get(dk + "DH", (size_t)nb * C * C * C * sizeof(float2), (void**)&DH));
+    WF_TRY(c.get(dk + "dpart", (size_t)nb * (nh + 1) * sizeof(double), (void**)&dpart));
+    WF_TRY(c.get(dk + "modes", modes.size() * sizeof(int4), (void**)&dmodes));
+    int4* hm;
+    WF_TRY(c.get_pinned(dk + "hmodes", modes.size() * sizeof(int4), (void**)&hm));
+    std::copy(modes.begin(), modes.end(), hm);
+    WF_CUDA(cudaMemcpyAsync(dmodes, hm, modes.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    WF_CUDA(cudaMemsetAsync(gco, 0, (size_t)nb * ncp * sizeof(float), st));
+    WF_CUDA(cudaMemsetAsync(rco, 0, (size_t)nb * ncp * sizeof(float), st));
+    return WF_OK;
+  }
+  // E^-1 of every system: the transform of w (FP32 passes, P0 as scratch), Dh at the differences
+  // of coarse modes, the Galerkin block, and its block Gauss-Jordan exchange
+  wf_status defl_setup(Ctx& c, cudaStream_t st) {
+    const Bat bf = SF::bat();
+    std::vector<double> ones((size_t)nb * SF::TAB, 1.0);
+    float* tone;
+    WF_TRY(upload_tables<float>(c, key + "t1", ones, &tone, st));
+    SF::zfwd(c, nb, W, T, tw32, part, false, nullptr, st);
+    SF::ypass(c, nb, T, tw32, nullptr, -1, st);
+    SF::template xmul<true, false, true>(c, nb, T, P0, tone, tw32, part, nullptr, st);
+    const int C = 4 * K + 1;
+    c.launch("defl_dh", 0, st, [&] {
+      k_dh_gather<float, N><<<dim3((C * C * C + 255) / 256, nb), 256, 0, st>>>(P0, DH, K, inv_vc, sc, bf);
+    });
+    c.launch("defl_E", 0, st, [&] {
+      k_ebuild<float><<<dim3(ncp / 16, ncp / 16, nb), dim3(16, 16), 0, st>>>(DH, ct, mt, dmodes, nh, ncp, K, Einv,
+                                                                            SF::TAB);
+    });
+    const int nbk = ncp / kDeflTile;
+    for (int kb = 0; kb < nbk; ++kb) {
+      c.launch("gj", 0, st, [&] { k_gj_pivot<<<dim3(1, 1, nb), 256, 0, st>>>(Einv, Pb, ncp, kb); });
+      c.launch("gj", 0, st, [&] { k_gj_panel<<<dim3(nbk, 1, nb), 256, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
+      c.launch("gj", 0, st, [&] { k_gj_update<<<dim3(nbk, nbk, nb), 256, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
+    }
+    WF_CUDA(cudaGetLastError());
+    return WF_OK;
+  }
+  // coordinates of A' r - r and of r, and r -= Z E^-1 g kept aside (MODE 1); or the start vector
+  // Z E^-1 Z^T r into `out` (MODE 0)
+  template <int MODE>
+  void defl_project(Ctx& c, float2* out, cudaStream_t st) {
+    const Bat bf = SF::bat();
+    const int gw = (nh + 1 + 7) / 8;
+    if constexpr (MODE == 1) {
+      SF::template xmul<false, true, false>(c, nb, rh, T, ct, tw32, part, sc, st);
+      SF::ypass(c, nb, T, tw32, sc, +1, st);
+      c.launch("defl_z", (SF::BS + 4 * SF::BV) * nb, st, [&] {
+        k_zcoarse<float, N><<<SF::gz(nb), SF::NTz, SF::SMz, st>>>(T, D, tw32, Gz, K, sc, bf, gzs);
+      });
+      const size_t ysm = ((size_t)N * (K + 1) + N) * sizeof(float2);
+      c.launch("defl_y", 8.0 * gzs * nb, st, [&] {
+        k_ycoarse<float, N><<<dim3(N, nb), 256, ysm, st>>>(Gz, tw32, Gy, K, sc, gzs, gys);
+      });
+    }
+    c.launch("defl_x", 8.0 * gys * nb, st, [&] {
+      k_xcoarse<float, N, MODE><<<dim3(gw, nb), 256, 0, st>>>(Gy, rh, ct, mt, tw32, dmodes, nh, K, gco, rco, sc, bf,
+                                                              gys, ncp);
+    });
+    c.launch("defl_mu", 4.0 * ncp * ncp * nb, st, [&] {
+      k_defl_mu<float, N, MODE><<<dim3(gw, nb), 256, ncp * sizeof(float), st>>>(Einv, gco, rco, dmodes, nh, ncp,
+                                                                                 out, rsave, dpart, sc, bf);
+    });
+  }
+  // one deflated inner iteration: p = (r - Z mu) + beta p with mu from the coarse projection
+  void defl_iteration(Ctx& c, cudaStream_t st) {
+    const Bat bf = SF::bat();
+    defl_project<1>(c, rh, st);
+    c.launch("fin", 0, st, [&] { k_fin_defl<<<nb, 256, 0, st>>>(dpart, nh, sc); });
+    SF::iteration(c, nb, rh, P0, P1, xh, T, D, ct, mt, unit_m, tw32, part, sc, inv_vc, st, nullptr,
+                  [&](cudaStream_t s) {
+                    c.launch("defl_restore", 0, s, [&] {
+                      k_defl_restore<float, N><<<dim3((nh + 1 + 255) / 256, nb), 256, 0, s>>>(rh, rsave, dmodes, nh,
+                                                                                               sc, bf);
+                    });
+                  });
   }
   wf_status prepare_end(Ctx& c, cudaStream_t st) override {
     const size_t V = SF::V;
@@ -830,6 +946,7 @@ struct GroupMixed : GroupCommon<N> {
     for (int m = 0; m < nb; ++m) h[m].nbar = sys[m]->nbar;
     WF_TRY(this->push_scalars(st));
     c.launch("make_D", 12.0 * V * nb, st, [&] { k_make_D<float><<<dim3(152 * 4, nb), 256, 0, st>>>(W, D, sc, inv_vc, V); });
+    if (K > 0) WF_TRY(defl_setup(c, st));
     // x = 0 (accumulated in S), res = b
     WF_CUDA(cudaMemsetAsync(S, 0, nb * V * sizeof(double), st));
     WF_CUDA(cudaMemcpyAsync(RES, B, nb * V * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -879,12 +996,23 @@ struct GroupMixed : GroupCommon<N> {
       WF_CUDA(cudaMemsetAsync(P0, 0, nb * SPEC * sizeof(float2), st));
       WF_CUDA(cudaMemsetAsync(P1, 0, nb * SPEC * sizeof(float2), st));
       WF_CUDA(cudaMemsetAsync(xh, 0, nb * SPEC * sizeof(float2), st));
+      if (K > 0) {
+        // the start step of the two-level form: p = Z E^-1 Z^T r (in the FP64 scratch spectrum),
+        // taken with alpha = 1 so that x = Z E^-1 Z^T b and Z^T r = 0 afterwards
+        float2* Rc = reinterpret_cast<float2*>(T64);
+        WF_CUDA(cudaMemsetAsync(Rc, 0, nb * SPEC * sizeof(float2), st));
+        c.launch("fin", 0, st, [&] { k_defl_arm<<<nb, 32, 0, st>>>(sc); });
+        defl_project<0>(c, Rc, st);
+        SF::iteration(c, nb, rh, P0, P1, xh, T, D, ct, mt, unit_m, tw32, part, sc, inv_vc, st, Rc);
+      }
       phase = 1;
     }
     if (phase == 1) {
       WF_TRY(this->run_block(c, st, [&](cudaStream_t s2) {
-        for (int i = 0; i < check_every<N>(); ++i)
-          SF::iteration(c, nb, rh, P0, P1, xh, T, D, ct, mt, unit_m, tw32, part, sc, inv_vc, s2);
+        for (int i = 0; i < check_every<N>(); ++i) {
+          if (K > 0) defl_iteration(c, s2);
+          else SF::iteration(c, nb, rh, P0, P1, xh, T, D, ct, mt, unit_m, tw32, part, sc, inv_vc, s2);
+        }
       }));
     } else if (phase == 2) {
       c.launch("axpy", 3 * SF::BS * nb, st,

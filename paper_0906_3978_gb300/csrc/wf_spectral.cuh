@@ -41,12 +41,14 @@ struct __align__(16) CgScal {
   double rr_stop;     // inner solves: stop when rc2 <= rr_stop (absolute)
   double nbar;        // mean density of this system
   double aux[4];
+  double rzo;         // deflated inner solves: <r, z> of the last iteration
   int iter;           // iterations since the solve began
   int max_iter;
   int done;           // 0 running; 1 converged (estimate); 2 iteration cap; 3 breakdown; 4 idle
   int status;
   int lit;            // iterations since the last reset of p: p_old = P[lit & 1]
-  int pad[3];
+  int defl;           // deflated inner solves: 2 start step (alpha = 1) pending, 1 first iteration
+  int pad[2];
 };
 
 // Distances between consecutive systems of a batch (elements of each array type).
@@ -1650,7 +1652,9 @@ static __global__ void k_fin_alpha(const double* __restrict__ partials, int n1, 
   const double pq = pm + pd;
   if (threadIdx.x == 0) {
     sc->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    if (sc->defl == 2) {  // the start step of a deflated solve moves by exactly Z mu
+      sc->alpha = 1.0;
+    } else if (!(pq > 0.0) || !isfinite(pq)) {
       sc->done = 3;
       sc->alpha = 0.0;
       sc->alpha_prev = 0.0;
@@ -1676,6 +1680,7 @@ static __global__ void k_fin_beta(const double* __restrict__ partials, int n, do
     sc->alpha_prev = sc->alpha;
     sc->iter += 1;
     sc->lit += 1;
+    if (sc->defl == 2) sc->defl = 1;
     const double lim = fmax(sc->tol2 * sc->bb, sc->rr_stop);
     if (!isfinite(rr) || !isfinite(rc2)) sc->done = 3;
     else if (rc2 <= lim) sc->done = 1;

@@ -6,7 +6,10 @@ bounded, for use under a kernel profiler:
     python -m paper_0906_3978_gb300.profile_solve --n 256 --what mask
 
 --tune times the launch variants first (wf_autotune) and prints the report; --variant
-xinv/f32/256=1 forces a variant of a pass (the context's tuning table).
+xinv/f32/256=1 forces a variant of a pass (the context's tuning table).  A whole solve of the
+512^3 workload with the coarse-space inner solves:
+
+    python -m paper_0906_3978_gb300.profile_solve --problem c3 --n 512 --tol 1e-6 --iters 5000 --deflate 10
 """
 import argparse
 import os
@@ -29,9 +32,13 @@ def main():
     ap.add_argument("--what", choices=["solve", "mask"], default="solve")
     ap.add_argument("--tune", action="store_true")
     ap.add_argument("--variant", action="append", default=[])
+    ap.add_argument("--problem", choices=["c2", "c3"], default="c2")
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--deflate", type=int, default=0)
     a = ap.parse_args()
     wf.build()
-    pr = synth.problem("c2", n_override=None if a.n == 256 else a.n, cache=False)
+    full = 256 if a.problem == "c2" else 512
+    pr = synth.problem(a.problem, n_override=None if a.n == full else a.n, cache=False)
     if a.what == "mask":
         return mask(wf, pr)
     with wf.Context(0) as ctx:
@@ -46,8 +53,9 @@ def main():
         ctx.profile(True)
         nobs = ctx.grid_assign(torch.from_numpy(pr.pos).cuda(), pr.n, pr.box, pr.scheme, 2)
         w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box)
-        s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-12, max_iter=a.iters,
-                            prec=wf.MIXED if a.prec == "mixed" else wf.FP64, precond=a.precond, check=False)
+        s, info = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=a.tol, max_iter=a.iters,
+                            prec=wf.MIXED if a.prec == "mixed" else wf.FP64, precond=a.precond, check=False,
+                            deflate=a.deflate)
         torch.cuda.synchronize()
         p = ctx.profile_read()
     print("n=%d prec=%s iters=%d status=%d launches=%d" % (pr.n, a.prec, info.iters, info.status, p["launches"]))

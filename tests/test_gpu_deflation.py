@@ -1,0 +1,119 @@
+"""Deflated inner solves (wf_solve_opts.deflate = K): the mixed-precision solve with each inner CG
+preconditioned on the coarse space of the Fourier modes |k| <= K.  Same system, same residual
+contract, same solution as the oracle's converged CG (Sec. 3.3.1, Eq. eq:WF) within the mixed
+path's 1e-6; fewer iterations; batching and serving keep the result of the solve alone.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_0906_3978_gb300 as wf  # noqa: E402
+
+DEV = "cuda:0"
+
+
+def rl2(a, r):
+    a, r = np.asarray(a), np.asarray(r)
+    return float(np.linalg.norm(a - r) / np.linalg.norm(r))
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    wf.build()
+    c = wf.Context(0)
+    yield c
+    c.close()
+
+
+def _inputs(name, n):
+    pr = synth.problem(name, n_override=n, cache=False)
+    fine = oracle.assign(pr.pos, pr.n, pr.box, pr.scheme, 2)
+    nobs = oracle.lowpass(fine, pr.n, 2)
+    w = oracle.window(pr.sel, pr.n, pr.box)
+    d, b, nbar = oracle.build_noise(nobs, w, pr.n_gal)
+    tab = oracle.sinv_table(n, pr.box, pr.pk_k, pr.pk_p)
+    return pr, w, b, nbar, tab
+
+
+@pytest.mark.parametrize("name,n,K", [("c2", 64, 4), ("c2", 64, 12), ("c1", 64, 6), ("c2", 108, 6)])
+def test_deflated_mixed_matches_oracle(ctx, name, n, K):
+    pr, w, b, nbar, tab = _inputs(name, n)
+    ref = oracle.cg(tab, nbar, w, b, tol=1e-12)[0]
+    s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-9, prec=wf.MIXED, deflate=K)
+    assert info.status == wf.OK and info.rel_residual <= 1e-9
+    assert rl2(host(s), ref) <= 1e-6
+    s6, info6 = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-6, prec=wf.MIXED, deflate=K)
+    assert info6.status == wf.OK
+    res = b - oracle.matvec(tab, nbar, w, host(s6))
+    assert np.linalg.norm(res) <= 1.0001e-6 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n,K", [(128, 8), (192, 10)])
+def test_deflation_cuts_iterations(ctx, n, K):
+    """At the 512^3 workload's cell size the coarse space removes the slow long-wavelength modes:
+    fewer than 0.6 x the iterations of the undeflated mixed solve, and the same solution."""
+    pr = synth.problem("c3", n_override=n, cache=False)
+    nobs = ctx.grid_assign(gpu(pr.pos), n, pr.box, pr.scheme, 2)
+    w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box, want_d=False)
+    s0, i0 = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-6, prec=wf.MIXED)
+    s1, i1 = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-6, prec=wf.MIXED, deflate=K)
+    assert i0.status == wf.OK and i1.status == wf.OK and i1.rel_residual <= 1e-6
+    assert i1.iters < 0.6 * i0.iters, (i1.iters, i0.iters)
+    # both within ~1e-6 of the exact solution, so within a few 1e-6 of each other
+    assert rl2(host(s1), host(s0)) <= 5e-6
+
+
+def test_deflated_batch_equals_individual_solves(ctx):
+    """A batch mixing deflated systems (two sizes) with undeflated ones gives every system the
+    result it gets alone."""
+    probs, singles = [], []
+    for i, (name, n, K) in enumerate([("c2", 64, 4), ("c2", 48, 4), ("c2", 64, 4), ("c2", 64, 0), ("c1", 48, 6)]):
+        pr, w, b, nbar, tab = _inputs(name, n)
+        probs.append(dict(w=gpu(w), nbar=nbar, b=gpu(b), box=pr.box, pk_k=pr.pk_k, pk_p=pr.pk_p, tol=1e-8,
+                          prec=wf.MIXED, deflate=K))
+        s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED, deflate=K)
+        singles.append(host(s).copy())
+    st, outs, infos = ctx.solve_batch(probs)
+    assert st == wf.OK
+    for ref, s, info in zip(singles, outs, infos):
+        assert info.status == wf.OK and info.rel_residual <= 1e-8
+        assert rl2(host(s), ref) <= 1e-6
+
+
+def test_deflated_serving_same_as_alone():
+    wf.build()
+    pr, w, b, nbar, tab = _inputs("c2", 64)
+    with wf.Context(0) as c:
+        s_alone, info = c.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED, deflate=5)
+        ref = host(s_alone).copy()
+        ids = [c.submit(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED, deflate=d) for d in (5, 0, 5)]
+        for rid in ids:
+            s = np.empty(pr.n ** 3)
+            st, inf = c.poll(rid, timeout_ms=-1, s_out=s)
+            assert st == wf.OK and inf.rel_residual <= 1e-8
+            assert rl2(s.reshape(ref.shape), ref) <= 1e-6
+
+
+def test_deflate_argument_errors(ctx):
+    pr, w, b, nbar, tab = _inputs("c1", 32)
+    args = (gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p)
+    for prec, K in [(wf.FP64, 4), (wf.MIXED, 8), (wf.MIXED, 13), (wf.MIXED, -1)]:   # 4 K < n; K <= 12
+        s, info = ctx.solve(*args, tol=1e-6, prec=prec, deflate=K, check=False)
+        assert info.status == wf.ERR_ARG
+    assert "deflate" in wf.lib().wf_last_error().decode()
+    s, info = ctx.solve(*args, tol=1e-6, prec=wf.MIXED, deflate=7)
+    assert info.status == wf.OK
