@@ -253,6 +253,18 @@ wf_status autotune(Ctx& c, int n, int prec, std::string& report) {
   }
 }
 
+// The coarse radius deflate = -1 picks: the fastest of a sweep of the radii at each size on the
+// 512^3 workload's recipe and cell size (n 64: 3, <= 128: 4, <= 192: 6, <= 256: 8, above: 10);
+// none below 64, where the iteration counts are small and the extra launches cost more.
+int auto_deflate(int n) {
+  if (n < 64) return 0;
+  if (n == 64) return 3;
+  if (n <= 128) return 4;
+  if (n <= 192) return 6;
+  if (n <= 256) return 8;
+  return 10;
+}
+
 // Coarse modes of radius K: one of each +-k pair, k != 0 (kz > 0, or kz = 0 with ky > 0, or
 // kz = ky = 0 with kx > 0), as (kx, ky, kz, |k|^2), in the order kz, ky, kx.
 std::vector<int4> deflation_modes(int K) {
@@ -395,7 +407,7 @@ wf_status prepare_solve(const wf_grid* grid, const wf_power* power, const double
   if (!(nbar > 0.0) || !std::isfinite(nbar)) return WF_ERR_ARG;
   if (!(opts->tol > 0.0) || opts->max_iter <= 0 || (opts->prec != WF_FP64 && opts->prec != WF_MIXED))
     return WF_ERR_ARG;
-  if (opts->deflate != 0 &&
+  if (opts->deflate != 0 && opts->deflate != -1 &&
       (opts->prec != WF_MIXED || opts->deflate < 1 || opts->deflate > kDeflMaxRadius || 4 * opts->deflate >= grid->n)) {
     set_last_error("deflate: a coarse radius in [1, 12] with 4 K < n, for WF_MIXED solves only", cudaSuccess);
     return WF_ERR_ARG;
@@ -405,6 +417,7 @@ wf_status prepare_solve(const wf_grid* grid, const wf_power* power, const double
   a.b = b;
   a.nbar = nbar;
   a.opts = *opts;
+  if (a.opts.deflate == -1) a.opts.deflate = opts->prec == WF_MIXED ? auto_deflate(grid->n) : 0;
   a.s_out = s_out;
   return build_sinv_table(*grid, *power, a.sinv);
 }
@@ -568,7 +581,7 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
     return WF_ERR_ARG;
   if (!(opts->tol > 0.0) || opts->max_iter <= 0 || (opts->prec != WF_FP64 && opts->prec != WF_MIXED))
     return WF_ERR_ARG;
-  if (opts->deflate != 0 &&
+  if (opts->deflate != 0 && opts->deflate != -1 &&
       (opts->prec != WF_MIXED || opts->deflate < 1 || opts->deflate > kDeflMaxRadius || 4 * opts->deflate >= grid->n)) {
     set_last_error("deflate: a coarse radius in [1, 12] with 4 K < n, for WF_MIXED solves only", cudaSuccess);
     return WF_ERR_ARG;
@@ -610,6 +623,7 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
       a.b = b;
       a.nbar = 1.0;
       a.opts = *opts;
+      if (a.opts.deflate == -1) a.opts.deflate = opts->prec == WF_MIXED ? auto_deflate(grid->n) : 0;
       a.s_out = sj + (size_t)q * V;
       a.sinv = sinv;
       sys.push_back(&a);

@@ -18,7 +18,7 @@
 // basis is orthonormal for the CG inner product (the full-spectrum sum of Re(conj u v)).
 //
 // Per iteration (FP32 vectors, the packed half spectrum of wf_spectral.cuh):
-//   T  = IFFT_x(c r), IFFT_y          (the solver's own passes)
+//   k_xcr       T = IFFT_x(c r); then the solver's y pass, IFFT_y
 //   k_zcoarse   IFFT_z, times D, FFT_z; keep kz <= K (the kz = 0 plane only)   -> Gz [N][N][K+1]
 //   k_ycoarse   DFT along y at |ky| <= K                                      -> Gy [2K+1][K+1][N]
 //   k_xcoarse   DFT along x at the coarse modes; g = coords of (m - 1) r + c Gc, and coords of r
@@ -36,6 +36,80 @@ constexpr int kDeflTile = 64;   // block of the coarse Gauss-Jordan exchange
 // packed-spectrum index of the signed mode (kx, ky, kz), 0 <= kz < N/2
 template <int N> WF_D size_t dslot(int kx, int ky, int kz) {
   return ((size_t)((kx + N) % N) * N + (size_t)((ky + N) % N)) * (N / 2) + kz;
+}
+
+// ------------------------------------------------------------------------------------------
+// x stage of the coarse projection: T = IFFT_x(c (.) r), the first pass of the inverse transform
+// of c r (the CG x pass 1 without its vector updates: r and the table gathers in flight together,
+// the packed column combined with its partner line at -ky).  grid (N/2 / NL, N, systems).
+// ------------------------------------------------------------------------------------------
+template <class R, int N, int RMAX = 8>
+__global__ void __launch_bounds__(XYG<R, N>::NT)
+k_xcr(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* __restrict__ T,
+      const typename Store<R>::S* __restrict__ ctab, const typename Store<R>::T* __restrict__ twtab,
+      const CgScal* __restrict__ sc, Bat bt) {
+  using G = XYG<R, N>;
+  using SS = typename Store<R>::S;
+  using VT = typename G::VT;
+  constexpr int NH = G::NH;
+  static_assert(std::is_same<R, SS>::value, "the CG passes compute in their storage type");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cx<R>* tile = reinterpret_cast<cx<R>*>(smem_raw);
+  cx<R>* tw = tile + G::M * G::LD;
+  const int z = blockIdx.z;
+  if (sc[z].done) return;
+  r += z * bt.spec;
+  T += z * bt.spec;
+  ctab += z * bt.tab;
+  const int tid = threadIdx.x;
+  const int kz0 = blockIdx.x * G::NL, ky = blockIdx.y;
+  const int ky_s = sfreq(ky, N);
+  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
+  const size_t rowstride = (size_t)N * NH;
+  const size_t base = (size_t)ky * NH + kz0;
+  constexpr int CH = 4;
+#pragma unroll
+  for (int k0 = 0; k0 < G::PER; k0 += CH) {
+    VT rv[CH];
+    SS cv[CH][G::VW];
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (G::EVEN || idx < G::NVEC) {
+        const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+        rv[k] = *reinterpret_cast<const VT*>(r + base + (size_t)i * rowstride + c0);
+        const int kxs = sfreq(i, N);
+#pragma unroll
+        for (int u = 0; u < G::VW; ++u) {
+          const int kz = kz0 + c0 + u;
+          cv[k][u] = ctab[kxs * kxs + ky_s * ky_s + kz * kz];
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < CH && k0 + k < G::PER; ++k) {
+      const int idx = tid + (k0 + k) * G::NT;
+      if (G::EVEN || idx < G::NVEC) {
+        const int i = idx / G::NV, c0 = (idx % G::NV) * G::VW;
+        SS* rs = reinterpret_cast<SS*>(&rv[k]);
+#pragma unroll
+        for (int u = 0; u < G::VW; ++u)
+          if (kz0 + c0 + u != 0) {  // column kz = 0 stays raw for the packed-column combine
+            rs[2 * u] *= cv[k][u];
+            rs[2 * u + 1] *= cv[k][u];
+          }
+        vec_to_tile<G>(tile, i, c0, rv[k]);
+      }
+    }
+  }
+  if (kz0 == 0) {  // partner line of column 0: r at (kx, -ky, 0)
+    const size_t pb = (size_t)((N - ky) % N) * NH;
+    for (int i = tid; i < G::M; i += G::NT) tile[i * G::LD + G::NL] = ld_c<R>(r + pb + (size_t)i * rowstride);
+  }
+  __syncthreads();
+  if (kz0 == 0) combine_col0<R, N, G::LD, G::NL>(tile, ky_s, ctab, tid, G::NT);
+  fft_line<R, G::M, G::TPL, G::LD, +1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + tid % G::NL, tid / G::NL, tw);
+  tile_store<G>(tile, T + base, rowstride, tid);
 }
 
 // ------------------------------------------------------------------------------------------

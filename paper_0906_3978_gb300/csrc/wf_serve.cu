@@ -303,7 +303,7 @@ wf_status wf_submit(wf_ctx* ctx, const wf_grid* grid, const wf_power* power, con
   wf_power pw{r->k.data(), r->p.data(), power->n};
   wf_status st = prepare_solve(grid, &pw, r->w, nbar, r->b, opts, r->s, r->args);
   if (st != WF_OK) return st;
-  r->footprint = Group::footprint(grid->n, (int)opts->prec, 1, opts->deflate);
+  r->footprint = Group::footprint(grid->n, (int)opts->prec, 1, r->args.opts.deflate);
   r->t_submit = Clock::now();
   Server* s = server_of(c);
   {

@@ -100,6 +100,7 @@ struct Spec {
     WF_A((k_zturn<R, N>), SMz);
     if constexpr (std::is_same<R, float>::value) {
       WF_A((k_zcoarse<R, N>), SMz);
+      WF_A((k_xcr<R, N>), SMxy);
       WF_A((k_ycoarse<R, N>), (size_t)N * (kDeflMaxRadius + 2) * sizeof(cx<R>));
     }
     if constexpr (PCS > 0) WF_A((k_plane_turn<R, N, PCS, PE>), (PlaneG<R, N, PCS, PE>::SMEM));
@@ -802,7 +803,9 @@ struct GroupMixed : GroupCommon<N> {
 
   wf_status prepare_begin(Ctx& c, cudaStream_t st) override {
     nb = (int)sys.size();
-    key = this->tag + "mix_" + std::to_string(N) + "_";
+    K = sys[0]->opts.deflate;
+    // groups of one size with different coarse radii run side by side: their workspaces differ by K
+    key = this->tag + "mix_" + std::to_string(N) + "_" + (K > 0 ? "k" + std::to_string(K) + "_" : std::string());
     int* err;
     WF_TRY(c.err_word(&err));
     WF_CUDA(SF::attrs());
@@ -827,7 +830,6 @@ struct GroupMixed : GroupCommon<N> {
       WF_CUDA(cudaMemcpyAsync(W + m * V, sys[m]->w, V * sizeof(double), cudaMemcpyDefault, st));
       WF_CUDA(cudaMemcpyAsync(B + m * V, sys[m]->b, V * sizeof(double), cudaMemcpyDefault, st));
     }
-    K = sys[0]->opts.deflate;
     if (K > 0) WF_TRY(defl_alloc(c, st));
     return group_sums_begin<N>(c, *this, NPART, st);
   }
@@ -894,7 +896,9 @@ struct GroupMixed : GroupCommon<N> {
     const Bat bf = SF::bat();
     const int gw = (nh + 1 + 7) / 8;
     if constexpr (MODE == 1) {
-      SF::template xmul<false, true, false>(c, nb, rh, T, ct, tw32, part, sc, st);
+      c.launch("defl_xr", 2 * SF::BS * nb, st, [&] {
+        k_xcr<float, N><<<SF::gxy(nb), SF::NTx, SF::SMxy, st>>>(rh, T, ct, tw32, sc, bf);
+      });
       SF::ypass(c, nb, T, tw32, sc, +1, st);
       c.launch("defl_z", (SF::BS + 4 * SF::BV) * nb, st, [&] {
         k_zcoarse<float, N><<<SF::gz(nb), SF::NTz, SF::SMz, st>>>(T, D, tw32, Gz, K, sc, bf, gzs);

@@ -65,7 +65,10 @@ def test_deflated_mixed_matches_oracle(ctx, name, n, K):
 @pytest.mark.parametrize("n,K", [(128, 8), (192, 10)])
 def test_deflation_cuts_iterations(ctx, n, K):
     """At the 512^3 workload's cell size the coarse space removes the slow long-wavelength modes:
-    fewer than 0.6 x the iterations of the undeflated mixed solve, and the same solution."""
+    fewer than 0.6 x the iterations of the undeflated mixed solve at the same residual, and a
+    solution at least as close to the converged one.  (A relative residual of 1e-6 leaves errors
+    of up to ~1e-4 in the weakly constrained directions, so the two 1e-6 solutions are compared
+    with the solve converged to 1e-10, not with each other.)"""
     pr = synth.problem("c3", n_override=n, cache=False)
     nobs = ctx.grid_assign(gpu(pr.pos), n, pr.box, pr.scheme, 2)
     w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, pr.box, want_d=False)
@@ -73,8 +76,12 @@ def test_deflation_cuts_iterations(ctx, n, K):
     s1, i1 = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-6, prec=wf.MIXED, deflate=K)
     assert i0.status == wf.OK and i1.status == wf.OK and i1.rel_residual <= 1e-6
     assert i1.iters < 0.6 * i0.iters, (i1.iters, i0.iters)
-    # both within ~1e-6 of the exact solution, so within a few 1e-6 of each other
-    assert rl2(host(s1), host(s0)) <= 5e-6
+    s0, s1 = host(s0).copy(), host(s1).copy()
+    ex, ie = ctx.solve(w, nbar, b, pr.box, pr.pk_k, pr.pk_p, tol=1e-10, prec=wf.MIXED)
+    assert ie.status == wf.OK
+    ex = host(ex)
+    e0, e1 = rl2(s0, ex), rl2(s1, ex)
+    assert e1 <= max(2.0 * e0, 1e-6), (e1, e0)
 
 
 def test_deflated_batch_equals_individual_solves(ctx):
@@ -111,9 +118,26 @@ def test_deflated_serving_same_as_alone():
 def test_deflate_argument_errors(ctx):
     pr, w, b, nbar, tab = _inputs("c1", 32)
     args = (gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p)
-    for prec, K in [(wf.FP64, 4), (wf.MIXED, 8), (wf.MIXED, 13), (wf.MIXED, -1)]:   # 4 K < n; K <= 12
+    for prec, K in [(wf.FP64, 4), (wf.MIXED, 8), (wf.MIXED, 13), (wf.MIXED, -2)]:   # 4 K < n; K <= 12
         s, info = ctx.solve(*args, tol=1e-6, prec=prec, deflate=K, check=False)
         assert info.status == wf.ERR_ARG
     assert "deflate" in wf.lib().wf_last_error().decode()
     s, info = ctx.solve(*args, tol=1e-6, prec=wf.MIXED, deflate=7)
     assert info.status == wf.OK
+    # -1 picks the radius by size: none at 32^3 (the plain mixed solve, same iterations), and for
+    # FP64 it is no coarse space at all
+    s0, i0 = ctx.solve(*args, tol=1e-8, prec=wf.MIXED)
+    s1, i1 = ctx.solve(*args, tol=1e-8, prec=wf.MIXED, deflate=-1)
+    assert i1.status == wf.OK and i1.iters == i0.iters
+    s2, i2 = ctx.solve(*args, tol=1e-8, prec=wf.FP64, deflate=-1)
+    assert i2.status == wf.OK
+
+
+def test_automatic_radius_at_64(ctx):
+    """deflate = -1 at 64^3 is the radius-3 coarse space: the same iterations and solution."""
+    pr, w, b, nbar, tab = _inputs("c2", 64)
+    args = (gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p)
+    s3, i3 = ctx.solve(*args, tol=1e-8, prec=wf.MIXED, deflate=3)
+    sa, ia = ctx.solve(*args, tol=1e-8, prec=wf.MIXED, deflate=-1)
+    assert ia.status == wf.OK and ia.iters == i3.iters
+    assert rl2(host(sa), host(s3)) <= 1e-12
