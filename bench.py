@@ -3,10 +3,12 @@
 
 One step = the whole hot path over one synthetic 512^3 catalogue held in HBM:
 supersampled TSC gridding (1024^3 fine grid, ideal low-pass) -> window/noise -> Wiener solve
-to relative residual 1e-6 (mixed precision: FP32-FFT inner CG, FP64 refinement).  The FP64
-form of the same step is timed beside it.  Prints one JSON line (rank 0).
+to relative residual 1e-6 (mixed precision: FP32-FFT inner CG preconditioned on the coarse
+Fourier modes |k| <= K, FP64 refinement).  The same step without the coarse space and the FP64
+form are timed beside it.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wf|reference] [--workload c3|c2|c1]
+                  [--deflate K]   (coarse radius of the mixed solves; -1: by grid size, 0: none)
 """
 from __future__ import annotations
 
@@ -314,17 +316,19 @@ def gpu_arm(args):
     # launch variants of the spectral passes timed once for this size (outside any timed region)
     tuning = {"mixed": ctx.autotune(n, wf.MIXED), "fp64": ctx.autotune(n, wf.FP64)}
 
-    def step(prec, s_out=None, pos_d=pos):
+    defl = args.deflate
+
+    def step(prec, s_out=None, pos_d=pos, deflate=defl):
         with torch.cuda.stream(st):
             nobs = ctx.grid_assign(pos_d, n, box, pr.scheme, 2, stream=st)
             w, d, b, nbar = ctx.build_noise(pr.sel, nobs, pr.n_gal, box, stream=st, want_d=False)
             s, info = ctx.solve(w, nbar, b, box, pr.pk_k, pr.pk_p, tol=tol, max_iter=20000, prec=prec,
-                                s_out=s_out, stream=st)
+                                s_out=s_out, stream=st, deflate=deflate if prec == wf.MIXED else 0)
         return s, info
 
-    def timed(prec, k, w_, profile=False):
+    def timed(prec, k, w_, profile=False, deflate=defl):
         for _ in range(w_):
-            step(prec)
+            step(prec, deflate=deflate)
         torch.cuda.synchronize()
         barrier(ws)
         ctx.profile(profile)
@@ -333,7 +337,7 @@ def gpu_arm(args):
         e0.record(st)
         infos = []
         for _ in range(k):
-            s, info = step(prec)
+            s, info = step(prec, deflate=deflate)
             infos.append(info.as_dict())
         e1.record(st)
         torch.cuda.synchronize()
@@ -350,7 +354,12 @@ def gpu_arm(args):
     # launches instead of graphs): the per-kernel durations behind the roofline
     timed(wf.MIXED, args.steps, 0, profile=True)
     prof = read_profile(ctx)
-    # ---- FP64 form of the same step
+    # ---- the mixed step without the coarse space, and the FP64 form of the same step
+    ctx.profile(False)
+    if defl != 0:
+        ms_plain, infos_plain, s_plain = timed(wf.MIXED, max(1, args.steps // 3), 1, deflate=0)
+        ms_plain = barrier_max(ws, ms_plain)
+        del s_plain
     ms_fp64, infos_fp64, s_fp64 = timed(wf.FP64, max(1, args.steps // 3), 1)
     ms_fp64 = barrier_max(ws, ms_fp64)
     ctx.profile(False)
@@ -397,12 +406,12 @@ def gpu_arm(args):
 
     extra = {}
     if not args.no_forms:
-        extra["postproc"] = bench_postproc(ctx, pr, s_mixed, s_fp64, w_r, b_r, nbar_r)
+        extra["postproc"] = bench_postproc(ctx, pr, s_mixed, s_fp64, w_r, b_r, nbar_r, defl)
     del b_r
     if not args.no_forms:
-        extra["batch"] = bench_batch(ctx, dev)
-        extra["serving"] = bench_serving(ctx, dev)
-        extra["jackknife"] = bench_jackknife(ctx, dev)
+        extra["batch"] = bench_batch(ctx, dev, defl)
+        extra["serving"] = bench_serving(ctx, dev, defl)
+        extra["jackknife"] = bench_jackknife(ctx, dev, defl)
     if rank != 0:
         return 0
     k = args.steps
@@ -429,7 +438,12 @@ def gpu_arm(args):
         "config": config_of(args, pr, ws),
         "mixed": {"iters": infos_mixed[-1]["iters"], "outer": infos_mixed[-1]["outer_iters"],
                   "rel_residual": infos_mixed[-1]["rel_residual"], "rel_l2_vs_fp64_solve": diff,
-                  "rel_l2_vs_converged": err_mixed},
+                  "rel_l2_vs_converged": err_mixed, "deflate": deflate_of(defl, n),
+                  "coarse_space": "inner CG preconditioned on the Fourier modes |k| <= deflate (grid units), "
+                                  "two-level A-DEF2 form; 0 = none"},
+        "mixed_no_coarse_space": None if defl == 0 else {
+            "value": ws * max(1, k // 3) / (ms_plain / 1000.0), "ms_per_step": ms_plain / max(1, k // 3),
+            "iters": infos_plain[-1]["iters"], "rel_residual": infos_plain[-1]["rel_residual"]},
         "fp64": {"value": ws * max(1, k // 3) / (ms_fp64 / 1000.0), "ms_per_step": ms_fp64 / max(1, k // 3),
                  "iters": it_fp64, "rel_residual": infos_fp64[-1]["rel_residual"], "rel_l2_vs_converged": err_fp64},
         "converged_reference": "the same step's system solved to relative residual 1e-10 (mixed with FP64 "
@@ -483,7 +497,7 @@ def batch_mocks(count=96, seed=2000):
     return out
 
 
-def bench_postproc(ctx, pr, s_rec, s_ref, w, b, nbar):
+def bench_postproc(ctx, pr, s_rec, s_ref, w, b, nbar, defl=0):
     """Sec. 4.1 / 5.5 evaluation of the 512^3 reconstruction: Gaussian smoothing at r_S = 10, 20,
     30 Mpc/h (FP64 transforms, FP64-ALU-bound), the quality measures of the mixed solution
     against the FP64 one, and the density statistics of the r_S = 10 field in the paper's radial
@@ -526,11 +540,11 @@ def bench_postproc(ctx, pr, s_rec, s_ref, w, b, nbar):
     torch.cuda.synchronize()
     e0.record()
     s_m, info = ctx.solve_response(w, nbar, b, box, pr.pk_k, pr.pk_p, 1.0, beta, 5.0, tol=1e-6, max_iter=20000,
-                                   prec=wf.MIXED)
+                                   prec=wf.MIXED, deflate=defl)
     e1.record()
     torch.cuda.synchronize()
     out["response_solve"] = {"ms": e0.elapsed_time(e1), "iters": info.iters, "rel_residual": info.rel_residual,
-                             "beta": beta, "sigma_v": 5.0, "bias": 1.0}
+                             "beta": beta, "sigma_v": 5.0, "bias": 1.0, "deflate": deflate_of(defl, n)}
     del s_m
     # the 3D mask from a sky map: 1024 x 512 pixels (a 30-degree cap of completeness 0.9 around
     # the survey axis) and the radial law tabulated every 0.25 Mpc/h to 500 Mpc/h: 1e9 ray samples
@@ -563,7 +577,7 @@ def bench_postproc(ctx, pr, s_rec, s_ref, w, b, nbar):
     return out
 
 
-def bench_batch(ctx, dev):
+def bench_batch(ctx, dev, defl=0):
     import torch
     import paper_0906_3978_gb300 as wf
     mocks = batch_mocks()
@@ -575,7 +589,7 @@ def bench_batch(ctx, dev):
             nobs = ctx.grid_assign(pd, n, box, wf.TSC, 2)
             w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
             probs.append(dict(w=w, nbar=nbar, b=b, box=box, pk_k=k, pk_p=p, tol=1e-6, max_iter=20000,
-                              prec=wf.MIXED))
+                              prec=wf.MIXED, deflate=defl))
         return probs
 
     probs = prepare()
@@ -596,13 +610,15 @@ def bench_batch(ctx, dev):
         for (n, box, sel, pos, k, p), pd in zip(mocks[:2], pos_d[:2]):   # warm each path once
             nobs = ctx.grid_assign(pd, n, box, wf.TSC, 2)
             w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
-            ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec)
+            ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec,
+                      deflate=defl if prec == wf.MIXED else 0)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for (n, box, sel, pos, k, p), pd in zip(mocks, pos_d):
             nobs = ctx.grid_assign(pd, n, box, wf.TSC, 2)
             w, d, b, nbar = ctx.build_noise(sel, nobs, pos.shape[0], box, want_d=False)
-            ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec)
+            ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec,
+                      deflate=defl if prec == wf.MIXED else 0)
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
@@ -613,7 +629,7 @@ def bench_batch(ctx, dev):
         sizes[m[0]] = sizes.get(m[0], 0) + 1
     return {"workload": "96 mocks, N in {64,96,128,192} (counts %s), L = 1.953 N Mpc/h, 1e4-1e5 galaxies; "
                         "gridding + window/noise + one wf_solve_batch (mixed, FP32 inner / FP64 refinement) "
-                        "to 1e-6" % sizes,
+                        "to 1e-6; coarse radius by size (%s)" % (sizes, defl_note(defl)),
             "value": len(mocks) / t_batch, "unit": "solves/s", "status": st,
             "solve_only": {"value": len(mocks) / t_batch_solve, "unit": "solves/s"},
             "max_rel_residual": max(i.rel_residual for i in infos),
@@ -628,7 +644,7 @@ def bench_batch(ctx, dev):
 # Signal-dependent-noise Wiener filter with the Jackknife-like subsamples, at the mock setting of
 # the paper's tests: 128^3 over 500 Mpc/h, ~2.2e5 galaxies, alpha = 1e-3, 200 reconstructions
 # ------------------------------------------------------------------------------------------
-def bench_jackknife(ctx, dev, n=128, box=500.0, n_gal=218020, n_sub=200, alpha=1e-3, seed=4001):
+def bench_jackknife(ctx, dev, defl=0, n=128, box=500.0, n_gal=218020, n_sub=200, alpha=1e-3, seed=4001):
     import numpy as np
     import torch
     import paper_0906_3978_gb300 as wf
@@ -643,28 +659,29 @@ def bench_jackknife(ctx, dev, n=128, box=500.0, n_gal=218020, n_sub=200, alpha=1
     wg = ctx.selection_eval(sel, pd)
     plain = {}
     for name, prec in (("fp64", wf.FP64), ("mixed", wf.MIXED)):
-        ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec)
+        dk = defl if prec == wf.MIXED else 0
+        ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec, deflate=dk)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s, info = ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec)
+        s, info = ctx.solve(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=prec, deflate=dk)
         torch.cuda.synchronize()
         plain[name] = {"solves_per_s": 1.0 / (time.perf_counter() - t0), "iters": info.iters}
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     u = torch.rand((n_sub, pos.shape[0]), dtype=torch.float64, device=dev, generator=gen)
     ctx.jackknife_solve(pd, wg, u[:8].contiguous(), alpha, nobs, w, nbar, n, box, k, p, tol=1e-6, max_iter=20000,
-                        prec=wf.MIXED, check=False)  # warm-up: workspaces of a batch of 8
+                        prec=wf.MIXED, check=False, deflate=defl)  # warm-up: workspaces of a batch of 8
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sm, infos = ctx.jackknife_solve(pd, wg, u, alpha, nobs, w, nbar, n, box, k, p, tol=1e-6, max_iter=20000,
-                                    prec=wf.MIXED, check=False)
+                                    prec=wf.MIXED, check=False, deflate=defl)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     its = np.array([i.iters for i in infos])
     return {"workload": "%d^3 over %.0f Mpc/h, %d galaxies (SDSS-like cone and holes), alpha = %g, %d Jackknife-like "
                         "subsamples (one uniform per galaxy and subsample), signal-dependent-noise Wiener filter each "
-                        "(lambda = N''), mixed precision to 1e-6, mean of the reconstructions" % (n, box, pos.shape[0],
-                                                                                                 alpha, n_sub),
+                        "(lambda = N''), mixed precision to 1e-6 (coarse radius %s), mean of the reconstructions"
+                        % (n, box, pos.shape[0], alpha, n_sub, deflate_of(defl, n)),
             "value": n_sub / t, "unit": "solves/s", "s": t, "ok": int(sum(1 for i in infos if i.status == 0)),
             "iters": {"min": int(its.min()), "median": int(np.median(its)), "max": int(its.max())},
             "plain_filter": plain,
@@ -678,7 +695,7 @@ def bench_jackknife(ctx, dev, n=128, box=500.0, n_gal=218020, n_sub=200, alpha=1
 SERVE_SIZES = [64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384]
 
 
-def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
+def bench_serving(ctx, dev, defl=0, n_req=600, rate=20.0, seed=7):
     import numpy as np
     import torch
     import paper_0906_3978_gb300 as wf
@@ -712,7 +729,7 @@ def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
     # warm the serving path once per size
     for n in SERVE_SIZES:
         w, b, nbar, box = pool[n]
-        ctx.poll(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED), timeout_ms=-1)
+        ctx.poll(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED, deflate=defl), timeout_ms=-1)
     lat, stats = [], []
     t_start = time.perf_counter()
     submitted = []
@@ -722,7 +739,7 @@ def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
         if target > now:
             time.sleep(target - now)
         w, b, nbar, box = pool[int(sizes[i])]
-        submitted.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED))
+        submitted.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED, deflate=defl))
     for rid in submitted:
         st, info = ctx.poll(rid, timeout_ms=-1)
         stats.append(st)
@@ -736,7 +753,7 @@ def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
     ids = []
     for i in range(n_sat):
         w, b, nbar, box = pool[int(sizes[i])]
-        ids.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED))
+        ids.append(ctx.submit(w, nbar, b, box, k, p, tol=1e-6, max_iter=20000, prec=wf.MIXED, deflate=defl))
     sat_lat, sat_ok = [], 0
     for rid in ids:
         st, info = ctx.poll(rid, timeout_ms=-1)
@@ -745,7 +762,8 @@ def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
     t_sat = time.perf_counter() - t0
     return {"workload": "%d requests, Poisson arrivals at %.0f/s, N uniform over %s, L = 1.953 N Mpc/h, "
                         "0.009 N^3 x U(0.5,1.5) galaxies, random cone 20-45 deg and radial peak; mixed "
-                        "precision to 1e-6 through wf_submit/wf_poll" % (n_req, rate, SERVE_SIZES),
+                        "precision to 1e-6 through wf_submit/wf_poll; coarse radius %s"
+                        % (n_req, rate, SERVE_SIZES, defl_note(defl)),
             "value": n_req / t_total, "unit": "solves/s", "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "ok": int(sum(1 for s in stats if s == 0)),
             "capacity": {"value": n_sat / t_sat, "unit": "solves/s", "requests": n_sat, "ok": int(sat_ok),
@@ -753,6 +771,18 @@ def bench_serving(ctx, dev, n_req=600, rate=20.0, seed=7):
                          "note": "all requests submitted at once: the served throughput at saturation"},
             "fp64_sequential": {"value": 1.0 / mean64, "unit": "solves/s",
                                 "note": "1 / mean service time of one plain FP64 wf_solve over the same size mix"}}
+
+
+def deflate_of(defl, n):
+    """The coarse radius a mixed solve of size n runs with for the option value defl (the rule of
+    wf_solve_opts.deflate = -1)."""
+    if defl != -1:
+        return defl
+    return 0 if n < 64 else 3 if n == 64 else 4 if n <= 128 else 6 if n <= 192 else 8 if n <= 256 else 10
+
+
+def defl_note(defl):
+    return "by grid size (0 below 64, 3 at 64, 4 to 128, 6 to 192, 8 to 256, 10 above)" if defl == -1 else str(defl)
 
 
 def read_profile(ctx):
@@ -809,6 +839,8 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-forms", dest="no_forms", action="store_true",
                     help="leave out the batched and served forms (reported after the timed 512^3 steps)")
+    ap.add_argument("--deflate", type=int, default=-1,
+                    help="coarse radius of the mixed solves (-1: by grid size, 10 at 512^3; 0: none)")
     ap.add_argument("--cpu-full", dest="cpu_full", action="store_true",
                     help="only time whole oracle reconstructions of the 64^3 and 256^3 workloads on the host "
                          "(all threads and one thread) and print them as one JSON line")

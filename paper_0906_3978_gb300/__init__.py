@@ -384,7 +384,7 @@ class Context:
 
     def solve_response(self, w, nbar: float, b, box: float, pk_k, pk_p, bias: float, beta: float, sigma_v: float,
                        tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1, s_out=None, stream=None,
-                       check=True):
+                       check=True, deflate=0):
         """(s_m, info): the real-space matter field solving (S^-1 + G nbar diag(w) G) s_m = G b with
         G the Fourier factor bias sqrt(<K D>_mu) (wf_solve_response)."""
         import torch
@@ -394,7 +394,7 @@ class Context:
         g = Grid(n, float(box), 1)
         pw, keep = make_power(pk_k, pk_p)
         rs = Response(float(bias), float(beta), float(sigma_v))
-        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond, deflate)
         info = SolveInfo()
         st = lib().wf_solve_response(self._h, ctypes.byref(g), ctypes.byref(pw), ctypes.byref(rs), _ptr(w),
                                      float(nbar), _ptr(b), ctypes.byref(o), _ptr(s_out), ctypes.byref(info),
@@ -405,7 +405,7 @@ class Context:
 
     def jackknife_solve(self, pos, w_gal, u, alpha: float, n_obs, w, nbar: float, n: int, box: float, pk_k, pk_p,
                         scheme=TSC, supersample=2, tol=1e-6, max_iter=5000, prec=FP64, inner_tol=0.0, precond=1,
-                        stream=None, check=True):
+                        stream=None, check=True, deflate=0):
         """(s_mean, [info]): the mean of the signal-dependent-noise reconstructions of the n_sub
         Jackknife-like subsamples drawn with u [n_sub, n_gal] (wf_jackknife_solve)."""
         import torch
@@ -415,7 +415,7 @@ class Context:
         s_mean = torch.empty((n, n, n), dtype=torch.float64, device=n_obs.device)
         g = Grid(int(n), float(box), int(supersample))
         pw, keep = make_power(pk_k, pk_p)
-        o = make_opts(tol, max_iter, prec, inner_tol, precond)
+        o = make_opts(tol, max_iter, prec, inner_tol, precond, deflate)
         infos = (SolveInfo * n_sub)()
         st = lib().wf_jackknife_solve(self._h, ctypes.byref(g), int(scheme), ctypes.byref(pw), _ptr(pos), n_gal,
                                       _ptr(w_gal), _ptr(u), n_sub, float(alpha), _ptr(n_obs), _ptr(w), float(nbar),
