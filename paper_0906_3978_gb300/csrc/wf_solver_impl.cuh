@@ -100,7 +100,7 @@ struct Spec {
     WF_A((k_zturn<R, N>), SMz);
     if constexpr (std::is_same<R, float>::value) {
       WF_A((k_zcoarse<R, N>), SMz);
-      WF_A((k_xcr<R, N>), SMxy);
+      WF_A((k_xcr<R, N, 32>), SMxy);
       WF_A((k_ycoarse<R, N>), (size_t)N * (kDeflMaxRadius + 2) * sizeof(cx<R>));
     }
     if constexpr (PCS > 0) WF_A((k_plane_turn<R, N, PCS, PE>), (PlaneG<R, N, PCS, PE>::SMEM));
@@ -897,7 +897,7 @@ struct GroupMixed : GroupCommon<N> {
     const int gw = (nh + 1 + 7) / 8;
     if constexpr (MODE == 1) {
       c.launch("defl_xr", 2 * SF::BS * nb, st, [&] {
-        k_xcr<float, N><<<SF::gxy(nb), SF::NTx, SF::SMxy, st>>>(rh, T, ct, tw32, sc, bf);
+        k_xcr<float, N, 32><<<SF::gxy(nb), SF::NTx, SF::SMxy, st>>>(rh, T, ct, tw32, sc, bf);
       });
       SF::ypass(c, nb, T, tw32, sc, +1, st);
       c.launch("defl_z", (SF::BS + 4 * SF::BV) * nb, st, [&] {
