@@ -36,8 +36,10 @@ WORKLOADS = {
 # DRAM traffic of the dominant kernel per launch from one ncu capture, valid while the kernel
 # sources hash to `src`; scaled from the captured size by the units processed (bytes ~ N^3).
 NCU_TRAFFIC = {
-    # profiles/cg_kernels_f32_512_dram.md: one-pass capture of one 512^3 launch, 1684.7 + 1558.1 MB
-    ("cg_xinv", 512): {"bytes": 3242.8e6, "src": "64d981d2e98fd0ea"},
+    # profiles/cg_kernels_f32_512_dram.md: one-pass capture of the launches of a deflated 512^3
+    # iteration: x pass 1 1684.4 + 1555.2 MB; y pass (mean of the +1 and -1 launches) 536.9 + 472.1 MB
+    ("cg_xinv", 512): {"bytes": 3239.6e6, "src": "f795d92c5a0ea8e0"},
+    ("ypass", 512): {"bytes": 1009.0e6, "src": "f795d92c5a0ea8e0"},
 }
 
 
