@@ -781,11 +781,13 @@ def deflate_of(defl, n):
     wf_solve_opts.deflate = -1)."""
     if defl != -1:
         return defl
-    return 0 if n < 64 else 3 if n == 64 else 4 if n <= 128 else 6 if n <= 192 else 8 if n <= 256 else 10
+    return (0 if n < 64 else 3 if n == 64 else 4 if n <= 128 else 6 if n <= 192 else 8 if n <= 256
+            else 10 if n <= 384 else 12)
 
 
 def defl_note(defl):
-    return "by grid size (0 below 64, 3 at 64, 4 to 128, 6 to 192, 8 to 256, 10 above)" if defl == -1 else str(defl)
+    return ("by grid size (0 below 64, 3 at 64, 4 to 128, 6 to 192, 8 to 256, 10 to 384, 12 above)" if defl == -1
+            else str(defl))
 
 
 def read_profile(ctx):
@@ -843,7 +845,7 @@ def main():
     ap.add_argument("--no-forms", dest="no_forms", action="store_true",
                     help="leave out the batched and served forms (reported after the timed 512^3 steps)")
     ap.add_argument("--deflate", type=int, default=-1,
-                    help="coarse radius of the mixed solves (-1: by grid size, 10 at 512^3; 0: none)")
+                    help="coarse radius of the mixed solves (-1: by grid size, 12 at 512^3; 0: none)")
     ap.add_argument("--cpu-full", dest="cpu_full", action="store_true",
                     help="only time whole oracle reconstructions of the 64^3 and 256^3 workloads on the host "
                          "(all threads and one thread) and print them as one JSON line")

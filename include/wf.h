@@ -103,7 +103,8 @@ typedef struct {
                          on the device once per solve (two-level "A-DEF2" form, Tang et al. 2009).
                          Same system, residual and stop rule; fewer iterations where the mask
                          couples the long-wavelength modes.  -1: K by grid size (0 below 64, 3 at
-                         64, 4 up to 128, 6 up to 192, 8 up to 256, 10 above; 0 for WF_FP64 and
+                         64, 4 up to 128, 6 up to 192, 8 up to 256, 10 up to 384, 12 above; 0 for
+                         WF_FP64 and
                          for wf_jackknife_solve, whose signal-dependent weights make the coarse
                          block too ill-conditioned for its FP32 inverse).
                          Errors: WF_ERR_ARG for any other value. */

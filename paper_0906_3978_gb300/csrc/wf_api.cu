@@ -254,15 +254,16 @@ wf_status autotune(Ctx& c, int n, int prec, std::string& report) {
 }
 
 // The coarse radius deflate = -1 picks: the fastest of a sweep of the radii at each size on the
-// 512^3 workload's recipe and cell size (n 64: 3, <= 128: 4, <= 192: 6, <= 256: 8, above: 10);
-// none below 64, where the iteration counts are small and the extra launches cost more.
+// 512^3 workload's recipe and cell size (n 64: 3, <= 128: 4, <= 192: 6, <= 256: 8, <= 384: 10,
+// above: 12); none below 64, where the iteration counts are small and the extra launches cost more.
 int auto_deflate(int n) {
   if (n < 64) return 0;
   if (n == 64) return 3;
   if (n <= 128) return 4;
   if (n <= 192) return 6;
   if (n <= 256) return 8;
-  return 10;
+  if (n <= 384) return 10;
+  return 12;
 }
 
 // Coarse modes of radius K: one of each +-k pair, k != 0 (kz > 0, or kz = 0 with ky > 0, or
@@ -291,7 +292,7 @@ size_t Group::footprint(int n, int prec, int count, int K) {
   if (K > 0) {
     const double ncp = deflation_ncp(K), C = 4.0 * K + 1;
     per += 4 * ncp * ncp + 2 * 4 * 64 * ncp + 8 * ncp + 8 * (double)n * n * (K + 1) +
-           8 * (2.0 * K + 1) * (K + 1) * n + 8 * C * C * C + 24 * ncp + 4 * 64 * 64 + 4.0 * (3 * (n / 2) * (n / 2) + 1);
+           8 * (2.0 * K + 1) * (K + 1) * n + 8 * C * C * C + 24 * ncp + 8 * 64 * 64 + 4.0 * (3 * (n / 2) * (n / 2) + 1);
   }
   return (size_t)(per * count) + (size_t)count * (3 * (n / 2) * (n / 2) + 1) * 24 + (64u << 10);
 }

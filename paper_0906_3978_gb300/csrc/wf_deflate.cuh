@@ -497,122 +497,233 @@ __global__ void k_ebuild(const float2* __restrict__ dh, const S* __restrict__ ct
 // after every block of the diagonal is exchanged, M holds M^-1):
 //   P = M_kk^-1;  M_kj <- -P M_kj;  M_ik <- M_ik P;  M_ij <- M_ij - M_ik P M_kj  (i, j != k).
 // No pivoting: every diagonal block of an SPD matrix's successive Schur complements is SPD.
-// (1) the pivot block, exchanged element by element in shared memory (one CTA, 256 threads)
-static __global__ void __launch_bounds__(256) k_gj_pivot(float* __restrict__ M, float* __restrict__ P, int ncp, int kb) {
+// Step kb: k_gj_panel forms the block row and saves the old block column; k_gj_update updates every
+// other block, and its first CTA, which takes the next diagonal block (kb + 1, kb + 1), also exchanges
+// that block once updated (the next step's P), so that serial work overlaps the update.  P alternates
+// between two buffers: step kb reads P[kb & 1] while the next one is written.
+
+// exchange of the 64 x 64 block a (row stride 68) in shared memory by the threads of the CTA; a
+// becomes its inverse.  The same block Gauss-Jordan exchange one level down: for each of the four
+// 16 x 16 diagonal sub-blocks, exchange it element by element (16 short serial steps), form its
+// sub-row, save its old sub-column, and update the rest by rank-16 products, so the serial steps
+// touch 256 elements instead of 4096.  cbuf holds 2 x 64 x 16 floats.  Runs on exactly 64 threads.
+WF_D void gj_exchange64(float (*a)[68], float* cbuf) {
+  constexpr int B = kDeflTile, S = 16, nt = 64;
+  const int tid = threadIdx.x;
+  for (int s0 = 0; s0 < B; s0 += S) {
+    // (i) the diagonal sub-block, element by element
+    for (int k = s0; k < s0 + S; ++k) {
+      const float inv = 1.f / a[k][k];
+      float nv[S * S / nt];
+#pragma unroll
+      for (int q = 0; q < S * S / nt; ++q) {
+        const int e = tid + q * nt, i = s0 + e / S, j = s0 + e % S;
+        float v;
+        if (i == k && j == k) v = inv;
+        else if (i == k) v = -a[k][j] * inv;
+        else if (j == k) v = a[i][k] * inv;
+        else v = a[i][j] - a[i][k] * (a[k][j] * inv);
+        nv[q] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < S * S / nt; ++q) {
+        const int e = tid + q * nt;
+        a[s0 + e / S][s0 + e % S] = nv[q];
+      }
+      __syncthreads();
+    }
+    // (ii) old sub-column C(i, :) = a[i][s0..s0+S) for i outside the sub-block, kept in cbuf
+    for (int e = tid; e < B * S; e += nt) {
+      const int i = e / S, c = e % S;
+      cbuf[e] = (i >= s0 && i < s0 + S) ? 0.f : a[i][s0 + c];
+    }
+    __syncthreads();
+    // (iii) sub-row R = P a[sub][j] (P = the exchanged sub-block), written as -R; j outside
+    for (int e = tid; e < S * B; e += nt) {
+      const int r = e / B, j = e % B;
+      if (j >= s0 && j < s0 + S) continue;
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < S; ++c) acc = fmaf(a[s0 + r][s0 + c], a[s0 + c][j], acc);
+      cbuf[B * S + e] = acc;  // R(r, j)
+    }
+    __syncthreads();
+    for (int e = tid; e < S * B; e += nt) {
+      const int r = e / B, j = e % B;
+      if (j >= s0 && j < s0 + S) continue;
+      a[s0 + r][j] = -cbuf[B * S + e];
+    }
+    // (iv) every element outside the sub-block's rows: a[i][j] -= C(i, :) R(:, j) for j outside its
+    // columns, a[i][j] = C(i, :) P(:, j) inside them
+    for (int e = tid; e < B * B; e += nt) {
+      const int i = e / B, j = e % B;
+      if (i >= s0 && i < s0 + S) continue;
+      float acc = 0.f;
+      if (j >= s0 && j < s0 + S) {
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc = fmaf(cbuf[i * S + c], a[s0 + c][j], acc);
+        a[i][j] = acc;
+      } else {
+#pragma unroll
+        for (int c = 0; c < S; ++c) acc = fmaf(cbuf[i * S + c], cbuf[B * S + c * B + j], acc);
+        a[i][j] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// (0) the first diagonal block; grid (1, 1, systems), 64 threads
+static __global__ void __launch_bounds__(64) k_gj_pivot(float* __restrict__ M, float* __restrict__ P, int ncp) {
   constexpr int B = kDeflTile;
-  __shared__ float a[B][B + 1];
+  __shared__ __align__(16) float a[B][68];
+  __shared__ float cbuf[2 * B * 16];
   const int z = blockIdx.z;
-  M += (size_t)z * ncp * ncp + (size_t)kb * B * ncp + (size_t)kb * B;
-  P += (size_t)z * B * B;
+  M += (size_t)z * ncp * ncp;
+  P += (size_t)z * 2 * B * B;  // buffer 0 of the system's pair
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) a[e / B][e % B] = M[(size_t)(e / B) * ncp + e % B];
   __syncthreads();
-  float nv[B * B / 256];
-  for (int k = 0; k < B; ++k) {
-    const float inv = 1.f / a[k][k];
-#pragma unroll
-    for (int q = 0; q < B * B / 256; ++q) {
-      const int e = threadIdx.x + q * 256, i = e / B, j = e % B;
-      if (i == k && j == k) nv[q] = inv;
-      else if (i == k) nv[q] = -a[k][j] * inv;
-      else if (j == k) nv[q] = a[i][k] * inv;
-      else nv[q] = a[i][j] - a[i][k] * (a[k][j] * inv);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < B * B / 256; ++q) {
-      const int e = threadIdx.x + q * 256;
-      a[e / B][e % B] = nv[q];
-    }
-    __syncthreads();
-  }
+  gj_exchange64(a, cbuf);
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-    const float v = a[e / B][e % B];
-    M[(size_t)(e / B) * ncp + e % B] = v;
-    P[e] = v;
+    M[(size_t)(e / B) * ncp + e % B] = a[e / B][e % B];
+    P[e] = a[e / B][e % B];
   }
 }
 
-// 64 x 64 x 64 product on 256 threads (4 x 4 outputs each): acc = As^T-stored A times Bs.
-// As[k][i] = A(i, k) and Bs[k][j] = B(k, j), rows padded to 68 floats.
-WF_D void gj_tile_mma(const float (*As)[68], const float (*Bs)[68], float acc[4][4], int ty, int tx) {
-#pragma unroll 8
+// 64 x 64 x 64 product on 64 threads (8 x 8 outputs each): acc += As^T Bs with As[k][i] = A(i, k)
+// and Bs[k][j] = B(k, j), rows of 68 floats.
+WF_D void gj_tile_mma(const float (*As)[68], const float (*Bs)[68], float acc[8][8], int ty, int tx) {
+#pragma unroll 4
   for (int k = 0; k < kDeflTile; ++k) {
-    const float4 a = *reinterpret_cast<const float4*>(&As[k][ty * 4]);
-    const float4 b = *reinterpret_cast<const float4*>(&Bs[k][tx * 4]);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+    const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8 + 4]);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
   }
 }
 
-// (2) the block row: Rp_j = P M_kj (kept for (3)), M_kj <- -Rp_j; and the old block column
-// Cp_j = M_jk copied aside.  grid (ncp / 64, 1, systems), 256 threads.
-static __global__ void __launch_bounds__(256) k_gj_panel(float* __restrict__ M, const float* __restrict__ P,
-                                                  float* __restrict__ Rp, float* __restrict__ Cp, int ncp, int kb) {
+// load a 64 x 64 block (row stride ld) into shared memory, transposed (T = true: S[c][r] = G(r, c))
+// or not, as float4 rows
+template <bool T>
+WF_D void gj_load(float (*S)[68], const float* __restrict__ G, size_t ld) {
+  for (int e = threadIdx.x; e < kDeflTile * kDeflTile / 4; e += blockDim.x) {
+    const int r = e / (kDeflTile / 4), c = (e % (kDeflTile / 4)) * 4;
+    const float4 v = *reinterpret_cast<const float4*>(G + (size_t)r * ld + c);
+    if (T) {
+      S[c][r] = v.x;
+      S[c + 1][r] = v.y;
+      S[c + 2][r] = v.z;
+      S[c + 3][r] = v.w;
+    } else {
+      *reinterpret_cast<float4*>(&S[r][c]) = v;
+    }
+  }
+}
+
+// (1) the block row: Rp_j = P M_kj (kept for (2)), M_kj <- -Rp_j; and the old block column
+// Cp_j = M_jk copied aside.  grid (ncp / 64, 1, systems), 64 threads.
+static __global__ void __launch_bounds__(64) k_gj_panel(float* __restrict__ M, const float* __restrict__ P,
+                                                        float* __restrict__ Rp, float* __restrict__ Cp, int ncp,
+                                                        int kb) {
   constexpr int B = kDeflTile;
   __shared__ __align__(16) float As[B][68];
   __shared__ __align__(16) float Bs[B][68];
   const int z = blockIdx.z, jb = blockIdx.x;
   if (jb == kb) return;
   M += (size_t)z * ncp * ncp;
-  P += (size_t)z * B * B;
+  P += (size_t)z * 2 * B * B + (size_t)(kb & 1) * B * B;
   Rp += (size_t)z * B * ncp;
   Cp += (size_t)z * ncp * B;
   float* Mkj = M + (size_t)kb * B * ncp + (size_t)jb * B;
   const float* Mjk = M + (size_t)jb * B * ncp + (size_t)kb * B;
-  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-    const int i = e / B, j = e % B;
-    As[j][i] = P[e];                      // As[k][i] = P(i, k)
-    Bs[i][j] = Mkj[(size_t)i * ncp + j];  // Bs[k][j] = M_kj(k, j)
-    Cp[((size_t)jb * B + i) * B + j] = Mjk[(size_t)i * ncp + j];
+  gj_load<true>(As, P, B);      // As[k][i] = P(i, k)
+  gj_load<false>(Bs, Mkj, ncp);  // Bs[k][j] = M_kj(k, j)
+  for (int e = threadIdx.x; e < B * B / 4; e += blockDim.x) {
+    const int r = e / (B / 4), c = (e % (B / 4)) * 4;
+    *reinterpret_cast<float4*>(Cp + ((size_t)jb * B + r) * B + c) =
+        *reinterpret_cast<const float4*>(Mjk + (size_t)r * ncp + c);
   }
   __syncthreads();
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  float acc[4][4] = {};
+  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
+  float acc[8][8] = {};
   gj_tile_mma(As, Bs, acc, ty, tx);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int r = ty * 4 + i, c = tx * 4 + j;
-      Rp[(size_t)r * ncp + (size_t)jb * B + c] = acc[i][j];
-      Mkj[(size_t)r * ncp + c] = -acc[i][j];
-    }
+  for (int i = 0; i < 8; ++i) {
+    const int r = ty * 8 + i;
+    float* rp = Rp + (size_t)r * ncp + (size_t)jb * B + tx * 8;
+    float* mk = Mkj + (size_t)r * ncp + tx * 8;
+    *reinterpret_cast<float4*>(rp) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(rp + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    *reinterpret_cast<float4*>(mk) = make_float4(-acc[i][0], -acc[i][1], -acc[i][2], -acc[i][3]);
+    *reinterpret_cast<float4*>(mk + 4) = make_float4(-acc[i][4], -acc[i][5], -acc[i][6], -acc[i][7]);
+  }
 }
 
-// (3) every block (ib, jb), ib != kb: M_ib,jb -= Cp_ib Rp_jb, or M_ib,kb = Cp_ib P.
-// grid (ncp / 64, ncp / 64, systems), 256 threads.
-static __global__ void __launch_bounds__(256) k_gj_update(float* __restrict__ M, const float* __restrict__ P,
-                                                   const float* __restrict__ Rp, const float* __restrict__ Cp,
-                                                   int ncp, int kb) {
+// (2) every block (ib, jb), ib != kb: M_ib,jb -= Cp_ib Rp_jb, or M_ib,kb = Cp_ib P.  The first CTA takes
+// block (kb + 1, kb + 1) (the one it would have had goes to that block's CTA) and exchanges it after
+// its update, writing the next P.  grid (ncp / 64, ncp / 64, systems), 64 threads.
+static __global__ void __launch_bounds__(64) k_gj_update(float* __restrict__ M, float* __restrict__ P,
+                                                         const float* __restrict__ Rp, const float* __restrict__ Cp,
+                                                         int ncp, int kb) {
   constexpr int B = kDeflTile;
   __shared__ __align__(16) float As[B][68];
   __shared__ __align__(16) float Bs[B][68];
-  const int z = blockIdx.z, jb = blockIdx.x, ib = blockIdx.y;
+  const int z = blockIdx.z, nbk = ncp / B, d = kb + 1;
+  int jb = blockIdx.x, ib = blockIdx.y;
+  if (d < nbk) {  // swap the first CTA with the one of the next diagonal block
+    if (ib == 0 && jb == 0) ib = jb = d;
+    else if (ib == d && jb == d) ib = jb = 0;
+  }
   if (ib == kb) return;
   M += (size_t)z * ncp * ncp;
-  P += (size_t)z * B * B;
+  float* Pn = P + (size_t)z * 2 * B * B + (size_t)(d & 1) * B * B;
+  P += (size_t)z * 2 * B * B + (size_t)(kb & 1) * B * B;
   Rp += (size_t)z * B * ncp;
   Cp += (size_t)z * ncp * B;
-  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-    const int i = e / B, j = e % B;
-    As[j][i] = Cp[((size_t)ib * B + i) * B + j];  // As[k][i] = Cp_ib(i, k)
-    Bs[i][j] = jb == kb ? P[e] : Rp[(size_t)i * ncp + (size_t)jb * B + j];
-  }
+  gj_load<true>(As, Cp + (size_t)ib * B * B, B);  // As[k][i] = Cp_ib(i, k)
+  if (jb == kb) gj_load<false>(Bs, P, B);
+  else gj_load<false>(Bs, Rp + (size_t)jb * B, ncp);
   __syncthreads();
-  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-  float acc[4][4] = {};
+  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
+  float acc[8][8] = {};
   gj_tile_mma(As, Bs, acc, ty, tx);
   float* T = M + (size_t)ib * B * ncp + (size_t)jb * B;
+  const bool diag = ib == d && jb == d;
+  if (diag) __syncthreads();  // As / Bs are reused for the block below
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const size_t o = (size_t)(ty * 4 + i) * ncp + tx * 4 + j;
-      T[o] = jb == kb ? acc[i][j] : T[o] - acc[i][j];
+  for (int i = 0; i < 8; ++i) {
+    const int r = ty * 8 + i;
+    float* t = T + (size_t)r * ncp + tx * 8;
+    float4 v0 = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    float4 v1 = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    if (jb != kb) {
+      const float4 o0 = *reinterpret_cast<const float4*>(t), o1 = *reinterpret_cast<const float4*>(t + 4);
+      v0 = make_float4(o0.x - v0.x, o0.y - v0.y, o0.z - v0.z, o0.w - v0.w);
+      v1 = make_float4(o1.x - v1.x, o1.y - v1.y, o1.z - v1.z, o1.w - v1.w);
     }
+    if (diag) {
+      *reinterpret_cast<float4*>(&As[r][tx * 8]) = v0;
+      *reinterpret_cast<float4*>(&As[r][tx * 8 + 4]) = v1;
+    } else {
+      *reinterpret_cast<float4*>(t) = v0;
+      *reinterpret_cast<float4*>(t + 4) = v1;
+    }
+  }
+  if (!diag) return;
+  __syncthreads();
+  gj_exchange64(As, &Bs[0][0]);
+  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
+    const float v = As[e / B][e % B];
+    T[(size_t)(e / B) * ncp + e % B] = v;
+    Pn[e] = v;
+  }
 }
 
 }  // namespace wf

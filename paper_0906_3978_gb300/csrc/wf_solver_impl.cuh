@@ -845,7 +845,7 @@ struct GroupMixed : GroupCommon<N> {
     WF_TRY(c.get(dk + "E", (size_t)nb * ncp * ncp * sizeof(float), (void**)&Einv));
     WF_TRY(c.get(dk + "gco", (size_t)nb * ncp * sizeof(float), (void**)&gco));
     WF_TRY(c.get(dk + "rco", (size_t)nb * ncp * sizeof(float), (void**)&rco));
-    WF_TRY(c.get(dk + "P", (size_t)nb * kDeflTile * kDeflTile * sizeof(float), (void**)&Pb));
+    WF_TRY(c.get(dk + "P", (size_t)nb * 2 * kDeflTile * kDeflTile * sizeof(float), (void**)&Pb));
     WF_TRY(c.get(dk + "Rp", (size_t)nb * kDeflTile * ncp * sizeof(float), (void**)&Rp));
     WF_TRY(c.get(dk + "Cp", (size_t)nb * ncp * kDeflTile * sizeof(float), (void**)&Cp));
     WF_TRY(c.get(dk + "Gz", (size_t)nb * gzs * sizeof(float2), (void**)&Gz));
@@ -881,10 +881,11 @@ struct GroupMixed : GroupCommon<N> {
                                                                             SF::TAB);
     });
     const int nbk = ncp / kDeflTile;
+    c.launch("gj_pivot", 0, st, [&] { k_gj_pivot<<<dim3(1, 1, nb), 64, 0, st>>>(Einv, Pb, ncp); });
     for (int kb = 0; kb < nbk; ++kb) {
-      c.launch("gj", 0, st, [&] { k_gj_pivot<<<dim3(1, 1, nb), 256, 0, st>>>(Einv, Pb, ncp, kb); });
-      c.launch("gj", 0, st, [&] { k_gj_panel<<<dim3(nbk, 1, nb), 256, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
-      c.launch("gj", 0, st, [&] { k_gj_update<<<dim3(nbk, nbk, nb), 256, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
+      c.launch("gj_panel", 0, st, [&] { k_gj_panel<<<dim3(nbk, 1, nb), 64, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
+      c.launch("gj_update", 0, st,
+               [&] { k_gj_update<<<dim3(nbk, nbk, nb), 64, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
     }
     WF_CUDA(cudaGetLastError());
     return WF_OK;

@@ -85,20 +85,23 @@ def test_deflation_cuts_iterations(ctx, n, K):
 
 
 def test_deflated_batch_equals_individual_solves(ctx):
-    """A batch mixing deflated systems (two sizes) with undeflated ones gives every system the
-    result it gets alone."""
+    """A batch mixing deflated systems (two sizes, several systems per coarse block set-up) with
+    undeflated ones gives every system the result and the iteration count it gets alone: a system's
+    arithmetic does not depend on its batch-mates."""
     probs, singles = [], []
-    for i, (name, n, K) in enumerate([("c2", 64, 4), ("c2", 48, 4), ("c2", 64, 4), ("c2", 64, 0), ("c1", 48, 6)]):
+    for i, (name, n, K) in enumerate([("c2", 64, 4), ("c2", 48, 4), ("c1", 64, 4), ("c2", 64, 0), ("c1", 48, 6),
+                                      ("c2", 72, 4)]):
         pr, w, b, nbar, tab = _inputs(name, n)
         probs.append(dict(w=gpu(w), nbar=nbar, b=gpu(b), box=pr.box, pk_k=pr.pk_k, pk_p=pr.pk_p, tol=1e-8,
                           prec=wf.MIXED, deflate=K))
         s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-8, prec=wf.MIXED, deflate=K)
-        singles.append(host(s).copy())
+        singles.append((host(s).copy(), info.iters))
     st, outs, infos = ctx.solve_batch(probs)
-    assert st == wf.OK
-    for ref, s, info in zip(singles, outs, infos):
+    assert st == wf.OK, [i.status for i in infos]
+    for (ref, it), s, info in zip(singles, outs, infos):
         assert info.status == wf.OK and info.rel_residual <= 1e-8
-        assert rl2(host(s), ref) <= 1e-6
+        assert info.iters == it
+        assert rl2(host(s), ref) <= 1e-12
 
 
 def test_deflated_serving_same_as_alone():
