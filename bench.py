@@ -195,8 +195,9 @@ def oracle_sample(pr, iters, deadline_s=40.0, single_thread=True):
 
 
 def fp64_kernels(ctx, prof, n):
-    """The FP64-ALU-bound passes of the step (the three passes of the ideal low-pass) against the
-    device's FP64 rate measured here (wf_fp64_rate) and the nominal 1.25 TFLOP/s.  Algorithmic flops:
+    """The FP64-ALU-bound passes of the step (the three passes of the ideal low-pass and the passes of
+    the FP64 residual) against the device's FP64 rate measured here (wf_fp64_rate) and the nominal
+    1.25 TFLOP/s.  Algorithmic flops:
     2.5 L log2 L per real transform of length L; each pass line takes a real transform of length 2n
     and an inverse of length n; the z pass has (2n)^2 lines, the y pass 2n n, the x pass n n.  The z
     pass skips the rows no galaxy reaches (their output is zero), so its figure counts flops it did
@@ -204,10 +205,16 @@ def fp64_kernels(ctx, prof, n):
     peak = ctx.fp64_rate()
     f_line = 2.5 * 2 * n * math.log2(2 * n) + 2.5 * n * math.log2(n)
     lines = {"lowpass_z": (2 * n) ** 2, "lowpass_y": 2 * n * n, "lowpass_x": n * n}
+    # the FP64 residual's passes (FP64 storage and arithmetic): per launch, the y pass takes n n/2
+    # complex transforms of length n (5 n log2 n each), the x pass with the Fourier table two of them
+    # (forward and inverse), the z passes n^2 real transforms of length n (2.5 n log2 n each)
+    cplx = 5.0 * n * math.log2(n)
+    flops = {"ypass_f64": n * n / 2 * cplx, "xmul_f64": 2 * n * n / 2 * cplx,
+             "zfwd_f64": n * n * cplx / 2, "zinv_f64": n * n * cplx / 2}
     out = []
     for c in prof["classes"]:
-        if c["name"] in lines and c["launches"] > 0:
-            fl = lines[c["name"]] * f_line
+        if (c["name"] in lines or c["name"] in flops) and c["launches"] > 0:
+            fl = lines[c["name"]] * f_line if c["name"] in lines else flops[c["name"]]
             rate = fl / (c["ms"] / c["launches"] / 1000.0)
             out.append({"kernel": c["name"], "bound": "alu", "gflop_per_launch": fl / 1e9,
                         "ms_per_launch": c["ms"] / c["launches"], "achieved_tflops": rate / 1e12,

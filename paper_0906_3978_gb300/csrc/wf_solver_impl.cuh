@@ -77,6 +77,9 @@ struct Spec {
   static dim3 gz(int nb) { return dim3(GZ, 1, nb); }
   static Bat bat() { return Bat{SPEC, V, TAB, NPART}; }
 
+  // launch-profile class of a pass: FP64-storage launches (the solves' FP64 residuals, the FP64
+  // solve) are kept apart from the FP32 inner passes of the same name
+  static const char* cls(const char* f32, const char* f64) { return sizeof(SS) == 8 ? f64 : f32; }
   // algorithmic bytes of one launch per system (DRAM traffic the pass cannot avoid)
   static constexpr double BS = (double)SPEC * sizeof(ST);
   static constexpr double BV = (double)V;
@@ -153,7 +156,7 @@ struct Spec {
         return;
       }
       const unsigned grid = persistent_grid(c, occ, (long long)nb * G::TPS);
-      c.launch("ypass", 2 * BS * nb, st, [&] {
+      c.launch(cls("ypass", "ypass_f64"), 2 * BS * nb, st, [&] {
         if (dir < 0) k_ypass_tma<R, N, -1, NL, STG, RMAX><<<grid, G::NT, G::SMEM, st>>>(m, tw, sc, nb, c.dev_err);
         else k_ypass_tma<R, N, +1, NL, STG, RMAX><<<grid, G::NT, G::SMEM, st>>>(m, tw, sc, nb, c.dev_err);
       });
@@ -219,7 +222,7 @@ struct Spec {
           !map(c, &mt, T, nb))
         return G::TPS;
       const unsigned grid = persistent_grid(c, occ, (long long)nb * G::TPS);
-      c.launch("cg_xinv", 6 * BS * nb, st, [&] {
+      c.launch(cls("cg_xinv", "cg_xinv_f64"), 6 * BS * nb, st, [&] {
         if (unit_m)
           k_cg_xinv_tma<R, N, true, NL, STG, RMAX, EX, COPY><<<grid, G::NT, SM, st>>>(
               mr, m0, m1, mx, mt, r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat(), nb, c.dev_err);
@@ -234,7 +237,7 @@ struct Spec {
       CUtensorMap mt, mr, m0, m1;
       if (!map(c, &mt, T, nb) || !map(c, &mr, r, nb) || !map(c, &m0, P0, nb) || !map(c, &m1, P1, nb)) return G::TPS;
       const unsigned grid = persistent_grid(c, occ, (long long)nb * G::TPS);
-      c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+      c.launch(cls("cg_xupd", "cg_xupd_f64"), 4 * BS * nb, st, [&] {
         if (unit_m)
           k_cg_xupd_tma<R, N, true, NL, STG, RMAX, EX, COPY><<<grid, G::NT, SM, st>>>(
               mt, mr, m0, m1, T, P0, P1, r, ctab, mtab, tw, part, sc, bat(), nb, c.dev_err);
@@ -258,7 +261,7 @@ struct Spec {
     }
     static int xinv(Ctx& c, int nb, ST* r, ST* P0, ST* P1, ST* x, ST* T, const SS* ctab, const SS* mtab, bool unit_m,
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
-      c.launch("cg_xinv", 6 * BS * nb, st, [&] {
+      c.launch(cls("cg_xinv", "cg_xinv_f64"), 6 * BS * nb, st, [&] {
         if (unit_m)
           k_cg_xinv<R, N, true, RMAX, MINB><<<gxy(nb), NTx, SMxy, st>>>(r, P0, P1, x, T, ctab, mtab, tw, part, sc, bat());
         else
@@ -268,7 +271,7 @@ struct Spec {
     }
     static int xupd(Ctx& c, int nb, const ST* T, ST* r, ST* P0, ST* P1, const SS* ctab, const SS* mtab, bool unit_m,
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
-      c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+      c.launch(cls("cg_xupd", "cg_xupd_f64"), 4 * BS * nb, st, [&] {
         if (unit_m)
           k_cg_xupd<R, N, true, RMAX, MINB><<<gxy(nb), NTx, SMxy, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc, bat());
         else
@@ -289,7 +292,7 @@ struct Spec {
     static int xupd(Ctx& c, int nb, const ST* T, ST* r, ST* P0, ST* P1, const SS* ctab, const SS* mtab, bool unit_m,
                     const ST* tw, double* part, CgScal* sc, cudaStream_t st) {
       const dim3 grid(N / 2 / NL, N, nb);
-      c.launch("cg_xupd", 4 * BS * nb, st, [&] {
+      c.launch(cls("cg_xupd", "cg_xupd_f64"), 4 * BS * nb, st, [&] {
         if (unit_m)
           k_cg_xupd_pf<R, N, true, RMAX, NL, EX><<<grid, G::NT, G::SMEM, st>>>(T, r, P0, P1, ctab, mtab, tw, part, sc,
                                                                               bat());
@@ -341,7 +344,7 @@ struct Spec {
     static cudaError_t setup() { return set_smem(k_zturn<R, N, EZ>, ZG<R, N, EZ>::SMEM); }
     static void run(Ctx& c, int nb, ST* T, const SS* D, const ST* tw, double* part, const CgScal* sc,
                     cudaStream_t st) {
-      c.launch("zturn", (2 * BS + sizeof(SS) * BV) * nb, st, [&] {
+      c.launch(cls("zturn", "zturn_f64"), (2 * BS + sizeof(SS) * BV) * nb, st, [&] {
         k_zturn<R, N, EZ><<<gz(nb), ZG<R, N, EZ>::NT, ZG<R, N, EZ>::SMEM, st>>>(T, D, tw, part, sc, bat());
       });
     }
@@ -375,12 +378,12 @@ struct Spec {
   template <bool FWD, bool INV, bool DOT>
   static void xmul(Ctx& c, int nb, const ST* in, ST* out, const SS* tab, const ST* tw, double* part,
                    const CgScal* sc, cudaStream_t st) {
-    c.launch("xmul", 2 * BS * nb, st,
+    c.launch(cls("xmul", "xmul_f64"), 2 * BS * nb, st,
              [&] { k_xmul<R, N, FWD, INV, DOT><<<gxy(nb), NTx, SMxy, st>>>(in, out, tab, tw, part, sc, bat()); });
   }
   static void zfwd(Ctx& c, int nb, const double* in, ST* out, const ST* tw, double* part, bool sq,
                    const CgScal* sc, cudaStream_t st) {
-    c.launch("zfwd", (BS + 8 * BV) * nb, st, [&] {
+    c.launch(cls("zfwd", "zfwd_f64"), (BS + 8 * BV) * nb, st, [&] {
       if (sq) k_zfwd<R, N, true><<<gz(nb), NTz, SMz, st>>>(in, out, tw, part, sc, bat());
       else k_zfwd<R, N, false><<<gz(nb), NTz, SMz, st>>>(in, out, tw, part, sc, bat());
     });
@@ -389,7 +392,7 @@ struct Spec {
   static void zinv(Ctx& c, int nb, const ST* in, double* out, const double* s, const double* w, const double* b,
                    double scl, const ST* tw, double* part, const CgScal* sc, cudaStream_t st) {
     const double vb = MODE == ZI_RESID ? 4 : (MODE == ZI_ACCUM ? 2 : 1);
-    c.launch("zinv", (BS + 8 * vb * BV) * nb, st,
+    c.launch(cls("zinv", "zinv_f64"), (BS + 8 * vb * BV) * nb, st,
              [&] { k_zinv<R, N, MODE><<<gz(nb), NTz, SMz, st>>>(in, out, s, w, b, scl, tw, part, sc, bat()); });
   }
 
