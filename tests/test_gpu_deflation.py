@@ -62,6 +62,24 @@ def test_deflated_mixed_matches_oracle(ctx, name, n, K):
     assert np.linalg.norm(res) <= 1.0001e-6 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("n,K", [(48, 4), (64, 6)])
+def test_fixed_iterations_match_oracle_adef2(ctx, n, K):
+    """After k iterations (the start step x_0 = Q b' is the first), the FP32 inner solve of the mixed
+    path (one refinement step, s = C y_k) holds the iterate of the oracle's FP64 A-DEF2 CG
+    (oracle/coarse.py, numpy FFTs and a dense LU solve of E).  Bound 2e-5: the FP32 operator's
+    4 log2(V) u (4e-6 at these sizes) plus the FP32 inverse of E, whose condition is 1.5e3-3.6e3 here;
+    an emulation of the FP32 arithmetic (FP32 spectra and operator, E inverted in FP32) stays at
+    0.9e-6 to 3.3e-6 for k <= 4.  A wrong sign or a transposed coarse block moves them by 1e-2 or more."""
+    from oracle.coarse import adef2
+    pr, w, b, nbar, tab = _inputs("c2", n)
+    for k in (1, 2, 3):
+        ref = adef2(tab, nbar, w, b, K, tol=1e-15, max_iter=k)[0]
+        s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, prec=wf.MIXED,
+                            deflate=K, check=False)
+        assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k and info.outer_iters == 1
+        assert rl2(host(s), ref) <= 2e-5, (k, rl2(host(s), ref))
+
+
 @pytest.mark.parametrize("n,K", [(128, 8), (192, 10)])
 def test_deflation_cuts_iterations(ctx, n, K):
     """At the 512^3 workload's cell size the coarse space removes the slow long-wavelength modes:

@@ -454,3 +454,98 @@ def test_cg_zero_rhs_and_residual_contract():
     x, it, rel = oracle.cg(t, nbar, w, b, tol=1e-6)
     true = np.linalg.norm(b - oracle.matvec(t, nbar, w, x)) / np.linalg.norm(b)
     assert true <= 1e-6 and abs(true - rel) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- coarse-space CG
+# oracle.coarse.adef2: the mixed solves' inner CG with the two-level A-DEF2 preconditioner on the
+# Fourier modes |k|^2 <= K^2 (test infrastructure for the GPU's coarse-space solves).
+def _dense_solve(t, nbar, w, b):
+    A = _dense_operator(w.shape[0], t, nbar, w)
+    L = np.linalg.cholesky(A)
+    return np.linalg.solve(L.T, np.linalg.solve(L, b.ravel())).reshape(b.shape)
+
+
+def test_adef2_full_coarse_space_solves_in_the_start_step():
+    """With every mode of the 8^3 grid coarse (|k|^2 <= 48 < 7^2), E is the whole operator and the
+    start step x_0 = Z E^-1 Z^H b' is the solution: the dense solve in real space, to 1e-10."""
+    from oracle.coarse import adef2
+    t, nbar, w, b, _ = _small_problem()
+    s, it, rel = adef2(t, nbar, w, b, 7, tol=1e-12, max_iter=20)
+    assert it == 1 and rel <= 1e-12
+    ref = _dense_solve(t, nbar, w, b)
+    assert np.linalg.norm(s - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_adef2_without_coarse_space_is_the_prior_preconditioned_cg():
+    """No coarse modes: Q = 0, the start step is empty, z = r, and k more iterations are the
+    oracle's preconditioned CG with M^-1 = C^2 (oracle.pcg, C code) after k iterations."""
+    from oracle.coarse import adef2
+    t, nbar, w, b, _ = _small_problem(n=12, seed=21)
+    pt = _prior_preconditioner(t, nbar, w)
+    for k in (1, 4, 11):
+        ref = oracle.pcg(t, pt, nbar, w, b, tol=1e-15, max_iter=k, allow_unconverged=True)[0]
+        s = adef2(t, nbar, w, b, None, tol=1e-15, max_iter=k + 1)[0]
+        assert np.linalg.norm(s - ref) <= 1e-11 * np.linalg.norm(ref), k
+
+
+@pytest.mark.parametrize("K", [1, 2, 3])
+def test_adef2_converges_to_the_dense_solution(K):
+    from oracle.coarse import adef2
+    t, nbar, w, b, _ = _small_problem(seed=22)
+    s, it, rel = adef2(t, nbar, w, b, K, tol=1e-13, max_iter=400)
+    assert rel <= 1e-13
+    ref = _dense_solve(t, nbar, w, b)
+    assert np.linalg.norm(s - ref) <= 1e-10 * np.linalg.norm(ref)
+    # the canonical residual of the returned s, by the oracle's own operator
+    assert np.linalg.norm(b - oracle.matvec(t, nbar, w, s)) <= 1e-11 * np.linalg.norm(b)
+
+
+def test_adef2_start_step_leaves_no_coarse_residual():
+    """After the start step the residual has no component on the coarse modes (Z^H r_0 = 0), and
+    CG keeps it so (Z^H A' p = 0 for every search direction)."""
+    from oracle.coarse import adef2
+    t, nbar, w, b, _ = _small_problem(n=12, seed=23)
+    for k in (1, 2, 6):
+        _, _, _, (pb, y, r) = adef2(t, nbar, w, b, 2, tol=1e-15, max_iter=k, return_state=True)
+        assert np.linalg.norm(r[pb.idx]) <= 1e-11 * np.linalg.norm(pb.rhs[pb.idx]), k
+
+
+def test_adef2_iterates_equal_deflated_cg_on_dense_matrices():
+    """Brute force at 4^3: with the start x_0 = Q b', A-DEF2's iterates are those of deflated CG
+    (Saad, Yeung, Erhel and Guyomarc'h 2000: p = r + beta p - Z E^-1 Z^H A' r, alpha and beta from
+    <r, r>), here run on the dense operator A' = diag(m) + diag(c) F diag(nbar w) F^-1 diag(c) built
+    from explicit exponential sums, not an FFT.  A wrong sign of the coarse term, a dropped r in
+    z = r - Q (A' r - r), or a transposed E changes them."""
+    from oracle.coarse import adef2
+    n, K = 4, 1
+    t, nbar, w, b, _ = _small_problem(n=n, seed=24)
+    f = np.fft.fftfreq(n, 1.0 / n).astype(int)
+    modes = np.stack(np.meshgrid(f, f, f, indexing="ij"), -1).reshape(-1, 3)
+    g = np.arange(n)
+    X = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    F = np.exp(-2j * np.pi * (modes @ X.T) / n)                 # forward DFT [modes, cells]
+    n2 = np.sum(modes * modes, axis=1)
+    c = np.where(n2 > 0, 1.0 / np.sqrt(np.where(n2 > 0, t[n2], 1.0)), 1.0 / np.sqrt(nbar * w.sum() / w.size))
+    m = np.where(n2 > 0, 1.0, 0.0)
+    Ap = np.diag(m) + (c[:, None] * F) @ np.diag(nbar * w.ravel()) @ (F.conj().T * c[None, :]) / n ** 3
+    rhs = c * (F @ b.ravel())
+    Z = np.eye(n ** 3)[:, n2 <= K * K]
+    E = Z.T @ Ap @ Z
+    Q = lambda v: Z @ np.linalg.solve(E, Z.T @ v)
+    dot = lambda u, v: float(np.real(np.vdot(u, v)))
+    x = Q(rhs)
+    r = rhs - Ap @ x
+    p = r - Q(Ap @ r)
+    xs = [x.copy()]
+    for _ in range(5):
+        q = Ap @ p
+        rr = dot(r, r)
+        a = rr / dot(p, q)
+        x = x + a * p
+        r = r - a * q
+        xs.append(x.copy())
+        p = r + (dot(r, r) / rr) * p - Q(Ap @ r)
+    for k, xk in enumerate(xs):
+        sk = np.real((F.conj().T @ (c * xk)) / n ** 3).reshape(b.shape)
+        s = adef2(t, nbar, w, b, K, tol=1e-15, max_iter=k + 1)[0]
+        assert np.linalg.norm(s - sk) <= 1e-10 * np.linalg.norm(sk), k
