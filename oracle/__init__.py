@@ -16,6 +16,9 @@ Each function follows the paper (Kitaura et al. 2009, arXiv:0906.3978):
   sinv_table  Sec. 3.3.1, Fourier-diagonal prior S
   matvec/cg   Sec. 3.3.1, Eq. eq:WF, by a Krylov (CG) inversion
   pcg         the same Krylov inversion with a Fourier-diagonal preconditioner
+  coarse.adef2
+              the same Krylov inversion with the two-level (coarse Fourier modes) preconditioner of
+              the library's mixed solves, in numpy (oracle/coarse.py)
 
 Parity is pinned by the ``-m "not gpu"`` tests (closed forms, dense direct solve, brute
 force, invariants); see tests/test_oracle_pins.py.
