@@ -281,7 +281,7 @@ std::vector<int4> deflation_modes(int K) {
 }
 int deflation_ncp(int K) {
   const int nc = 2 * (int)deflation_modes(K).size() + 1;
-  return (nc + 63) / 64 * 64;
+  return (nc + 127) / 128 * 128;  // whole 128 x 128 tiles of the Gauss-Jordan update
 }
 
 // Device bytes of a group (the buffers GroupFP64 / GroupMixed allocate, tables excluded), with the

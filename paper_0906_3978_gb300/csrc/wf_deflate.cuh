@@ -502,72 +502,77 @@ __global__ void k_ebuild(const float2* __restrict__ dh, const S* __restrict__ ct
 // that block once updated (the next step's P), so that serial work overlaps the update.  P alternates
 // between two buffers: step kb reads P[kb & 1] while the next one is written.
 
-// exchange of the 64 x 64 block a (row stride 68) in shared memory by the threads of the CTA; a
+// exchange of the 64 x 64 block a (row stride LDA) in shared memory by the NT threads of the CTA; a
 // becomes its inverse.  The same block Gauss-Jordan exchange one level down: for each of the four
 // 16 x 16 diagonal sub-blocks, exchange it element by element (16 short serial steps), form its
 // sub-row, save its old sub-column, and update the rest by rank-16 products, so the serial steps
-// touch 256 elements instead of 4096.  cbuf holds 2 x 64 x 16 floats.  Runs on exactly 64 threads.
-WF_D void gj_exchange64(float (*a)[68], float* cbuf) {
-  constexpr int B = kDeflTile, S = 16, nt = 64;
+// touch 256 elements instead of 4096.  cbuf holds 2 x 64 x 16 floats.  Every thread of the CTA calls it.
+template <int NT, int LDA>
+WF_D void gj_exchange64(float* a, float* cbuf) {
+  constexpr int B = kDeflTile, S = 16;
+  static_assert((S * S) % NT == 0 || NT > S * S, "threads");
+  constexpr int PER = NT >= S * S ? 1 : S * S / NT;
   const int tid = threadIdx.x;
   for (int s0 = 0; s0 < B; s0 += S) {
     // (i) the diagonal sub-block, element by element
     for (int k = s0; k < s0 + S; ++k) {
-      const float inv = 1.f / a[k][k];
-      float nv[S * S / nt];
+      const float inv = 1.f / a[k * LDA + k];
+      float nv[PER];
 #pragma unroll
-      for (int q = 0; q < S * S / nt; ++q) {
-        const int e = tid + q * nt, i = s0 + e / S, j = s0 + e % S;
-        float v;
-        if (i == k && j == k) v = inv;
-        else if (i == k) v = -a[k][j] * inv;
-        else if (j == k) v = a[i][k] * inv;
-        else v = a[i][j] - a[i][k] * (a[k][j] * inv);
+      for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * NT, i = s0 + e / S, j = s0 + e % S;
+        float v = 0.f;
+        if (e < S * S) {
+          if (i == k && j == k) v = inv;
+          else if (i == k) v = -a[k * LDA + j] * inv;
+          else if (j == k) v = a[i * LDA + k] * inv;
+          else v = a[i * LDA + j] - a[i * LDA + k] * (a[k * LDA + j] * inv);
+        }
         nv[q] = v;
       }
       __syncthreads();
 #pragma unroll
-      for (int q = 0; q < S * S / nt; ++q) {
-        const int e = tid + q * nt;
-        a[s0 + e / S][s0 + e % S] = nv[q];
+      for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * NT;
+        if (e < S * S) a[(s0 + e / S) * LDA + s0 + e % S] = nv[q];
       }
       __syncthreads();
     }
     // (ii) old sub-column C(i, :) = a[i][s0..s0+S) for i outside the sub-block, kept in cbuf
-    for (int e = tid; e < B * S; e += nt) {
+    for (int e = tid; e < B * S; e += NT) {
       const int i = e / S, c = e % S;
-      cbuf[e] = (i >= s0 && i < s0 + S) ? 0.f : a[i][s0 + c];
+      cbuf[e] = (i >= s0 && i < s0 + S) ? 0.f : a[i * LDA + s0 + c];
     }
     __syncthreads();
     // (iii) sub-row R = P a[sub][j] (P = the exchanged sub-block), written as -R; j outside
-    for (int e = tid; e < S * B; e += nt) {
+    for (int e = tid; e < S * B; e += NT) {
       const int r = e / B, j = e % B;
       if (j >= s0 && j < s0 + S) continue;
       float acc = 0.f;
 #pragma unroll
-      for (int c = 0; c < S; ++c) acc = fmaf(a[s0 + r][s0 + c], a[s0 + c][j], acc);
+      for (int c = 0; c < S; ++c) acc = fmaf(a[(s0 + r) * LDA + s0 + c], a[(s0 + c) * LDA + j], acc);
       cbuf[B * S + e] = acc;  // R(r, j)
     }
     __syncthreads();
-    for (int e = tid; e < S * B; e += nt) {
+    for (int e = tid; e < S * B; e += NT) {
       const int r = e / B, j = e % B;
       if (j >= s0 && j < s0 + S) continue;
-      a[s0 + r][j] = -cbuf[B * S + e];
+      a[(s0 + r) * LDA + j] = -cbuf[B * S + e];
     }
     // (iv) every element outside the sub-block's rows: a[i][j] -= C(i, :) R(:, j) for j outside its
     // columns, a[i][j] = C(i, :) P(:, j) inside them
-    for (int e = tid; e < B * B; e += nt) {
+    for (int e = tid; e < B * B; e += NT) {
       const int i = e / B, j = e % B;
       if (i >= s0 && i < s0 + S) continue;
       float acc = 0.f;
       if (j >= s0 && j < s0 + S) {
 #pragma unroll
-        for (int c = 0; c < S; ++c) acc = fmaf(cbuf[i * S + c], a[s0 + c][j], acc);
-        a[i][j] = acc;
+        for (int c = 0; c < S; ++c) acc = fmaf(cbuf[i * S + c], a[(s0 + c) * LDA + j], acc);
+        a[i * LDA + j] = acc;
       } else {
 #pragma unroll
         for (int c = 0; c < S; ++c) acc = fmaf(cbuf[i * S + c], cbuf[B * S + c * B + j], acc);
-        a[i][j] -= acc;
+        a[i * LDA + j] -= acc;
       }
     }
     __syncthreads();
@@ -584,7 +589,7 @@ static __global__ void __launch_bounds__(64) k_gj_pivot(float* __restrict__ M, f
   P += (size_t)z * 2 * B * B;  // buffer 0 of the system's pair
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) a[e / B][e % B] = M[(size_t)(e / B) * ncp + e % B];
   __syncthreads();
-  gj_exchange64(a, cbuf);
+  gj_exchange64<64, 68>(&a[0][0], cbuf);
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
     M[(size_t)(e / B) * ncp + e % B] = a[e / B][e % B];
     P[e] = a[e / B][e % B];
@@ -666,62 +671,101 @@ static __global__ void __launch_bounds__(64) k_gj_panel(float* __restrict__ M, c
   }
 }
 
-// (2) every block (ib, jb), ib != kb: M_ib,jb -= Cp_ib Rp_jb, or M_ib,kb = Cp_ib P.  The first CTA takes
-// block (kb + 1, kb + 1) (the one it would have had goes to that block's CTA) and exchanges it after
-// its update, writing the next P.  grid (ncp / 64, ncp / 64, systems), 64 threads.
-static __global__ void __launch_bounds__(64) k_gj_update(float* __restrict__ M, float* __restrict__ P,
-                                                         const float* __restrict__ Rp, const float* __restrict__ Cp,
-                                                         int ncp, int kb) {
-  constexpr int B = kDeflTile;
-  __shared__ __align__(16) float As[B][68];
-  __shared__ __align__(16) float Bs[B][68];
-  const int z = blockIdx.z, nbk = ncp / B, d = kb + 1;
-  int jb = blockIdx.x, ib = blockIdx.y;
-  if (d < nbk) {  // swap the first CTA with the one of the next diagonal block
-    if (ib == 0 && jb == 0) ib = jb = d;
-    else if (ib == d && jb == d) ib = jb = 0;
+// (2) every block (ib, jb), ib != kb: M_ib,jb -= Cp_ib Rp_jb, or M_ib,kb = Cp_ib P, as 128 x 128
+// tiles of 2 x 2 blocks (256 threads, 8 x 8 outputs each).  The first CTA takes the tile that holds
+// the next diagonal block (kb + 1, kb + 1) (the tile it would have had goes to that tile's CTA) and,
+// once its update is done, exchanges that block in shared memory, writing the next P.
+// grid (ncp / 128, ncp / 128, systems), 256 threads, UPD_SMEM bytes of dynamic shared memory.
+constexpr int kUpdLd = 2 * kDeflTile + 4;  // 132: float4 rows, banks spread
+constexpr size_t kUpdSmem = (size_t)2 * kDeflTile * kUpdLd * sizeof(float);
+static __global__ void __launch_bounds__(256) k_gj_update(float* __restrict__ M, float* __restrict__ P,
+                                                          const float* __restrict__ Rp, const float* __restrict__ Cp,
+                                                          int ncp, int kb) {
+  constexpr int B = kDeflTile, T2 = 2 * B, LD = kUpdLd;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* As = reinterpret_cast<float*>(smem_raw);  // [64 k][132]: As[k][i] = A(i, k), i < 128
+  float* Bs = As + B * LD;                          // [64 k][132]: Bs[k][j] = B(k, j), j < 128
+  const int z = blockIdx.z, ntl = ncp / T2, d = kb + 1;
+  int tj = blockIdx.x, ti = blockIdx.y;
+  const bool has_next = d < ncp / B;
+  if (has_next) {  // swap the first CTA with the one of the tile holding block (d, d)
+    if (ti == 0 && tj == 0) ti = tj = d / 2;
+    else if (ti == d / 2 && tj == d / 2) ti = tj = 0;
   }
-  if (ib == kb) return;
+  (void)ntl;
   M += (size_t)z * ncp * ncp;
   float* Pn = P + (size_t)z * 2 * B * B + (size_t)(d & 1) * B * B;
   P += (size_t)z * 2 * B * B + (size_t)(kb & 1) * B * B;
   Rp += (size_t)z * B * ncp;
   Cp += (size_t)z * ncp * B;
-  gj_load<true>(As, Cp + (size_t)ib * B * B, B);  // As[k][i] = Cp_ib(i, k)
-  if (jb == kb) gj_load<false>(Bs, P, B);
-  else gj_load<false>(Bs, Rp + (size_t)jb * B, ncp);
+  const int tid = threadIdx.x;
+  // A: the old block columns of the tile's two block rows (Cp rows), transposed into As
+  for (int e = tid; e < T2 * B / 4; e += 256) {
+    const int r = e / (B / 4), c = (e % (B / 4)) * 4;  // r < 128: row of the tile, c: k
+    const float4 v = *reinterpret_cast<const float4*>(Cp + ((size_t)ti * T2 + r) * B + c);
+    As[(c + 0) * LD + r] = v.x;
+    As[(c + 1) * LD + r] = v.y;
+    As[(c + 2) * LD + r] = v.z;
+    As[(c + 3) * LD + r] = v.w;
+  }
+  // B: for each of the tile's two block columns, the block row Rp_jb, or P where jb = kb
+  for (int e = tid; e < B * T2 / 4; e += 256) {
+    const int k = e / (T2 / 4), c = (e % (T2 / 4)) * 4;  // c < 128: column of the tile
+    const int jb = tj * 2 + c / B, cc = c % B;
+    const float4 v = jb == kb ? *reinterpret_cast<const float4*>(P + (size_t)k * B + cc)
+                              : *reinterpret_cast<const float4*>(Rp + (size_t)k * ncp + (size_t)jb * B + cc);
+    *reinterpret_cast<float4*>(&Bs[k * LD + c]) = v;
+  }
   __syncthreads();
-  const int ty = threadIdx.x / 8, tx = threadIdx.x % 8;
+  const int ty = tid / 16, tx = tid % 16;
   float acc[8][8] = {};
-  gj_tile_mma(As, Bs, acc, ty, tx);
-  float* T = M + (size_t)ib * B * ncp + (size_t)jb * B;
-  const bool diag = ib == d && jb == d;
-  if (diag) __syncthreads();  // As / Bs are reused for the block below
+#pragma unroll 4
+  for (int k = 0; k < B; ++k) {
+    const float4 a0 = *reinterpret_cast<const float4*>(&As[k * LD + ty * 8]);
+    const float4 a1 = *reinterpret_cast<const float4*>(&As[k * LD + ty * 8 + 4]);
+    const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k * LD + tx * 8]);
+    const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k * LD + tx * 8 + 4]);
+    const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int r = ty * 8 + i;
-    float* t = T + (size_t)r * ncp + tx * 8;
-    float4 v0 = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    float4 v1 = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-    if (jb != kb) {
-      const float4 o0 = *reinterpret_cast<const float4*>(t), o1 = *reinterpret_cast<const float4*>(t + 4);
-      v0 = make_float4(o0.x - v0.x, o0.y - v0.y, o0.z - v0.z, o0.w - v0.w);
-      v1 = make_float4(o1.x - v1.x, o1.y - v1.y, o1.z - v1.z, o1.w - v1.w);
-    }
-    if (diag) {
-      *reinterpret_cast<float4*>(&As[r][tx * 8]) = v0;
-      *reinterpret_cast<float4*>(&As[r][tx * 8 + 4]) = v1;
-    } else {
-      *reinterpret_cast<float4*>(t) = v0;
-      *reinterpret_cast<float4*>(t + 4) = v1;
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+  // the thread's 8 x 8 outputs lie in one block (ib, jb)
+  const int ib = ti * 2 + (ty * 8) / B, jb = tj * 2 + (tx * 8) / B;
+  const bool diag_tile = has_next && ti == d / 2 && tj == d / 2;
+  const bool diag = diag_tile && ib == d && jb == d;
+  if (diag_tile) __syncthreads();  // As / Bs are reused for the block below
+  if (ib != kb) {
+    float* Tb = M + (size_t)(ti * T2 + ty * 8) * ncp + (size_t)tj * T2 + tx * 8;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float* t = Tb + (size_t)i * ncp;
+      float4 v0 = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      float4 v1 = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+      if (jb != kb) {
+        const float4 o0 = *reinterpret_cast<const float4*>(t), o1 = *reinterpret_cast<const float4*>(t + 4);
+        v0 = make_float4(o0.x - v0.x, o0.y - v0.y, o0.z - v0.z, o0.w - v0.w);
+        v1 = make_float4(o1.x - v1.x, o1.y - v1.y, o1.z - v1.z, o1.w - v1.w);
+      }
+      if (diag) {  // the block (d, d) goes to shared memory, rows of 68
+        const int r = (ty * 8) % B + i, c = (tx * 8) % B;
+        *reinterpret_cast<float4*>(&As[r * 68 + c]) = v0;
+        *reinterpret_cast<float4*>(&As[r * 68 + c + 4]) = v1;
+      } else {
+        *reinterpret_cast<float4*>(t) = v0;
+        *reinterpret_cast<float4*>(t + 4) = v1;
+      }
     }
   }
-  if (!diag) return;
+  if (!diag_tile) return;
   __syncthreads();
-  gj_exchange64(As, &Bs[0][0]);
-  for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
-    const float v = As[e / B][e % B];
-    T[(size_t)(e / B) * ncp + e % B] = v;
+  gj_exchange64<256, 68>(As, Bs);
+  float* Td = M + (size_t)d * B * ncp + (size_t)d * B;
+  for (int e = tid; e < B * B; e += 256) {
+    const float v = As[(e / B) * 68 + e % B];
+    Td[(size_t)(e / B) * ncp + e % B] = v;
     Pn[e] = v;
   }
 }

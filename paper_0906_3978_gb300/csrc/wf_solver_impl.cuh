@@ -104,6 +104,7 @@ struct Spec {
     if constexpr (std::is_same<R, float>::value) {
       WF_A((k_zcoarse<R, N>), SMz);
       WF_A((k_xcr<R, N, 32>), SMxy);
+      WF_A(k_gj_update, kUpdSmem);
       WF_A((k_ycoarse<R, N>), (size_t)N * (kDeflMaxRadius + 2) * sizeof(cx<R>));
     }
     if constexpr (PCS > 0) WF_A((k_plane_turn<R, N, PCS, PE>), (PlaneG<R, N, PCS, PE>::SMEM));
@@ -887,8 +888,9 @@ struct GroupMixed : GroupCommon<N> {
     c.launch("gj_pivot", 0, st, [&] { k_gj_pivot<<<dim3(1, 1, nb), 64, 0, st>>>(Einv, Pb, ncp); });
     for (int kb = 0; kb < nbk; ++kb) {
       c.launch("gj_panel", 0, st, [&] { k_gj_panel<<<dim3(nbk, 1, nb), 64, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
-      c.launch("gj_update", 0, st,
-               [&] { k_gj_update<<<dim3(nbk, nbk, nb), 64, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
+      c.launch("gj_update", 0, st, [&] {
+        k_gj_update<<<dim3(nbk / 2, nbk / 2, nb), 256, kUpdSmem, st>>>(Einv, Pb, Rp, Cp, ncp, kb);
+      });
     }
     WF_CUDA(cudaGetLastError());
     return WF_OK;
