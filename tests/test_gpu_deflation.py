@@ -62,22 +62,27 @@ def test_deflated_mixed_matches_oracle(ctx, name, n, K):
     assert np.linalg.norm(res) <= 1.0001e-6 * np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("n,K", [(48, 4), (64, 6)])
+@pytest.mark.parametrize("n,K", [(48, 4), (64, 6), (128, 6)])
 def test_fixed_iterations_match_oracle_adef2(ctx, n, K):
     """After k iterations (the start step x_0 = Q b' is the first), the FP32 inner solve of the mixed
     path (one refinement step, s = C y_k) holds the iterate of the oracle's FP64 A-DEF2 CG
-    (oracle/coarse.py, numpy FFTs and a dense LU solve of E).  Bound 2e-5: the FP32 operator's
-    4 log2(V) u (4e-6 at these sizes) plus the FP32 inverse of E, whose condition is 1.5e3-3.6e3 here;
-    an emulation of the FP32 arithmetic (FP32 spectra and operator, E inverted in FP32) stays at
-    0.9e-6 to 3.3e-6 for k <= 4.  A wrong sign or a transposed coarse block moves them by 1e-2 or more."""
-    from oracle.coarse import adef2
+    (oracle/coarse.py, numpy FFTs and a dense LU solve of E).  Bound: the FP32 operator's
+    4 log2(V) u plus 0.1 kappa(E) u for the FP32 inverse of E (an inverse's forward error grows with
+    the condition); kappa(E) is 1.5e3, 3.6e3 and 1.3e4 for these cases, and the measured deviations
+    are 0.015-0.034 kappa u (an FP32 emulation on the CPU at 48^3 and 64^3: 0.9e-6 to 3.3e-6).  A
+    wrong sign or a transposed coarse block moves the iterates by 1e-2 or more.  From 128^3 up the
+    coarse projection's x pass runs on tensor copies (k_xcr_tma)."""
+    from oracle.coarse import Problem, adef2
     pr, w, b, nbar, tab = _inputs("c2", n)
+    ev = np.linalg.eigvalsh(Problem(tab, nbar, w, b, K).E)
+    u = 2.0 ** -24
+    bound = 4.0 * 3 * np.log2(n) * u + 0.1 * (ev[-1] / ev[0]) * u
     for k in (1, 2, 3):
         ref = adef2(tab, nbar, w, b, K, tol=1e-15, max_iter=k)[0]
         s, info = ctx.solve(gpu(w), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p, tol=1e-14, max_iter=k, prec=wf.MIXED,
                             deflate=K, check=False)
         assert info.status == wf.ERR_NOT_CONVERGED and info.iters == k and info.outer_iters == 1
-        assert rl2(host(s), ref) <= 2e-5, (k, rl2(host(s), ref))
+        assert rl2(host(s), ref) <= bound, (k, rl2(host(s), ref), bound)
 
 
 @pytest.mark.parametrize("n,K", [(128, 8), (192, 10)])
