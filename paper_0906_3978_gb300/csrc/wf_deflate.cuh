@@ -112,107 +112,6 @@ k_xcr(const typename Store<R>::T* __restrict__ r, typename Store<R>::T* __restri
   tile_store<G>(tile, T + base, rowstride, tid);
 }
 
-// The same pass on tensor copies, persistent (the y pass's tile walk, along x): each tile (one ky
-// plane, NL kz columns, all kx rows) arrives by a tensor copy over r (map mr, box {2NL, 1, BR, 1}),
-// is multiplied by c, column 0 of the kz0 = 0 tiles is combined with its partner line (read by plain
-// loads: its 8-byte rows are below the 16-byte tensor-copy minimum), transformed, and leaves by a
-// tensor store into T (map mt).  Bounded barrier waits as in the y pass.  grid: persistent.
-template <class R, int N, int NL, int STG, int RMAX>
-struct XcrG {
-  using G = TG<R, N, NL, STG>;
-  static constexpr size_t SMEM = G::SMEM + (size_t)N * sizeof(cx<R>);
-};
-template <class R, int N, int NL, int STG, int RMAX>
-__global__ void __launch_bounds__(TG<R, N, NL, STG>::NT)
-k_xcr_tma(const __grid_constant__ CUtensorMap mr, const __grid_constant__ CUtensorMap mt,
-          const typename Store<R>::T* __restrict__ r, const typename Store<R>::S* __restrict__ ctab,
-          const typename Store<R>::T* __restrict__ twtab, const CgScal* __restrict__ sc, Bat bt, int nb,
-          int* __restrict__ err) {
-  using G = TG<R, N, NL, STG>;
-  using SS = typename Store<R>::S;
-  constexpr int NH = N / 2;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  cx<R>* buf = reinterpret_cast<cx<R>*>(smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127));
-  cx<R>* tw = buf + STG * G::SSTR;
-  cx<R>* part = tw + G::M;  // the partner line of column 0
-  uint64_t* bar = reinterpret_cast<uint64_t*>(part + G::M);
-  const int tid = threadIdx.x;
-  const TileSeq<G> seq{sc, nb * G::TPS};
-  if (tid == 0) {
-    prefetch_tensormap(&mr);
-    prefetch_tensormap(&mt);
-    for (int s = 0; s < STG; ++s) mbar_init(&bar[s], 1);
-    mbar_init_fence();
-  }
-  __syncthreads();
-  load_tw<R, G::M, 2 * N>(tw, twtab, tid, G::NT);
-  auto issue = [&](int id, int s) {
-    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kz0 = (rem % G::KB) * NL;
-    mbar_expect_tx(&bar[s], G::TILE_BYTES);
-    for (int q = 0; q < G::NBOX; ++q)
-      tma_load_4d(buf + s * G::SSTR + q * G::BR * NL, &mr, 2 * kz0, ky, q * G::BR, z, &bar[s]);
-  };
-  int ids[STG];
-  ids[0] = seq.next(blockIdx.x, gridDim.x);
-  for (int j = 1; j < STG; ++j) ids[j] = seq.next(ids[j - 1] < seq.total ? ids[j - 1] + gridDim.x : seq.total, gridDim.x);
-  unsigned pending = 0;
-  if (tid == 0)
-    for (int j = 0; j < STG - 1; ++j)
-      if (ids[j] < seq.total) {
-        issue(ids[j], j);
-        pending |= 1u << j;
-      }
-  unsigned phase = 0;
-  bool ok = true;
-  for (int k = 0; ids[0] < seq.total; ++k) {
-    const int s = k % STG;
-    if (tid == 0 && ids[STG - 1] < seq.total) {
-      bulk_wait_read<0>();
-      issue(ids[STG - 1], (k + STG - 1) % STG);
-      pending |= 1u << ((k + STG - 1) % STG);
-    }
-    const int id = ids[0];
-    const int z = id / G::TPS, rem = id % G::TPS, ky = rem / G::KB, kz0 = (rem % G::KB) * NL;
-    const int ky_s = sfreq(ky, N);
-    const SS* ct = ctab + (size_t)z * bt.tab;
-    if (kz0 == 0) {  // r at (kx, -ky, 0), read while the tile arrives
-      const typename Store<R>::T* rp = r + (size_t)z * bt.spec + (size_t)((N - ky) % N) * NH;
-      for (int i = tid; i < G::M; i += G::NT) part[i] = ld_c<R>(rp + (size_t)i * N * NH);
-    }
-    ok = tile_arrived<STG>(bar, s, phase, pending, err);
-    if (!ok) break;
-    cx<R>* tile = buf + s * G::SSTR;
-    for (int idx = tid; idx < G::M * NL; idx += G::NT) {
-      const int i = idx / NL, kz = kz0 + idx % NL;
-      if (kz == 0) continue;  // column 0 is combined below, from its raw values
-      const int kxs = sfreq(i, N);
-      tile[idx] = scale(tile[idx], tab_to<R>(ct[kxs * kxs + ky_s * ky_s + kz * kz]));
-    }
-    if (kz0 == 0) {
-      for (int kx = tid; kx < N; kx += G::NT) {
-        const int kxs = sfreq(kx, N);
-        const int n2 = kxs * kxs + ky_s * ky_s;
-        const R m0 = tab_to<R>(ct[n2]), mN = tab_to<R>(ct[n2 + NH * NH]);
-        const R h = RT<R>::c(0.5);
-        const cx<R> zc = tile[kx * NL];
-        const cx<R> zp = conj(part[(N - kx) % N]);
-        tile[kx * NL] = scale(zc, (m0 + mN) * h) + scale(zp, (m0 - mN) * h);
-      }
-    }
-    __syncthreads();
-    fft_line<R, G::M, G::TPL, NL, +1, 1, cmin(RMAX, rmax_for(G::M, G::TPL))>(tile + tid % NL, tid / NL, tw);
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      for (int q = 0; q < G::NBOX; ++q) tma_store_4d(&mt, 2 * kz0, ky, q * G::BR, z, tile + q * G::BR * NL);
-      bulk_commit();
-    }
-    for (int j = 0; j < STG - 1; ++j) ids[j] = ids[j + 1];
-    ids[STG - 1] = seq.next(ids[STG - 2] < seq.total ? ids[STG - 2] + gridDim.x : seq.total, gridDim.x);
-  }
-  if (tid == 0) tiles_drain<STG>(bar, phase, pending, ok);
-}
-
 // ------------------------------------------------------------------------------------------
 // z stage of the coarse projection (the z turn without its full store): each (x, y) line of the
 // y-transformed field is taken to real space, multiplied by D, transformed forward, and its

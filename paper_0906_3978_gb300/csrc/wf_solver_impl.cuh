@@ -864,7 +864,6 @@ struct GroupMixed : GroupCommon<N> {
     WF_CUDA(cudaMemcpyAsync(dmodes, hm, modes.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     WF_CUDA(cudaMemsetAsync(gco, 0, (size_t)nb * ncp * sizeof(float), st));
     WF_CUDA(cudaMemsetAsync(rco, 0, (size_t)nb * ncp * sizeof(float), st));
-    (void)xcr_occ();
     return WF_OK;
   }
   // E^-1 of every system: the transform of w (FP32 passes, P0 as scratch), Dh at the differences
@@ -922,45 +921,14 @@ struct GroupMixed : GroupCommon<N> {
                                                                                  out, rsave, dpart, sc, bf);
     });
   }
-  // T = IFFT_x(c r): on tensor copies from 128^3 up (the persistent tile walk of the y pass), else
-  // the register-staged pass
-  static constexpr int XNL = SF::NLT, XSTG = 3, XRM = 32;
-  // shared memory and resident CTAs of the tensor-copy coarse x pass (set up outside any capture)
-  static int xcr_occ() {
-    static int occ = 0;
-    if constexpr (N >= 128) {
-      if (occ == 0) {
-        constexpr size_t SM = XcrG<float, N, XNL, XSTG, XRM>::SMEM;
-        const auto k = k_xcr_tma<float, N, XNL, XSTG, XRM>;
-        if (set_smem(k, SM) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, TG<float, N, XNL, XSTG>::NT, SM) != cudaSuccess ||
-            occ < 1)
-          occ = 1;
-      }
-    }
-    return occ;
-  }
+  // T = IFFT_x(c r), register-staged (a persistent form on tensor copies along x, the y pass's tile
+  // walk with the table multiply and partner column added, took 0.52 ms at 512^3 against 0.42: one
+  // CTA per SM cannot hide the table gathers and the strided partner loads)
   void defl_xr(Ctx& c, cudaStream_t st) {
     const Bat bf = SF::bat();
-    if constexpr (N >= 128) {
-      constexpr int NL = XNL, STG = XSTG, RM = XRM;
-      using G = TG<float, N, NL, STG>;
-      constexpr size_t SM = XcrG<float, N, NL, STG, RM>::SMEM;
-      const int occ = xcr_occ();
-      CUtensorMap mr, mt;
-      if (!make_spectrum_map(&mr, rh, N, nb, false, NL, 1, G::BR) || !make_spectrum_map(&mt, T, N, nb, false, NL, 1, G::BR)) {
-        c.map_failed = true;
-        return;
-      }
-      const unsigned grid = SF::persistent_grid(c, occ, (long long)nb * G::TPS);
-      c.launch("defl_xr", 2 * SF::BS * nb, st, [&] {
-        k_xcr_tma<float, N, NL, STG, RM><<<grid, G::NT, SM, st>>>(mr, mt, rh, ct, tw32, sc, bf, nb, c.dev_err);
-      });
-    } else {
-      c.launch("defl_xr", 2 * SF::BS * nb, st, [&] {
-        k_xcr<float, N, 32><<<SF::gxy(nb), SF::NTx, SF::SMxy, st>>>(rh, T, ct, tw32, sc, bf);
-      });
-    }
+    c.launch("defl_xr", 2 * SF::BS * nb, st, [&] {
+      k_xcr<float, N, 32><<<SF::gxy(nb), SF::NTx, SF::SMxy, st>>>(rh, T, ct, tw32, sc, bf);
+    });
   }
   // one deflated inner iteration: p = (r - Z mu) + beta p with mu from the coarse projection
   void defl_iteration(Ctx& c, cudaStream_t st) {

@@ -70,8 +70,7 @@ def test_fixed_iterations_match_oracle_adef2(ctx, n, K):
     4 log2(V) u plus 0.1 kappa(E) u for the FP32 inverse of E (an inverse's forward error grows with
     the condition); kappa(E) is 1.5e3, 3.6e3 and 1.3e4 for these cases, and the measured deviations
     are 0.015-0.034 kappa u (an FP32 emulation on the CPU at 48^3 and 64^3: 0.9e-6 to 3.3e-6).  A
-    wrong sign or a transposed coarse block moves the iterates by 1e-2 or more.  From 128^3 up the
-    coarse projection's x pass runs on tensor copies (k_xcr_tma)."""
+    wrong sign or a transposed coarse block moves the iterates by 1e-2 or more."""
     from oracle.coarse import Problem, adef2
     pr, w, b, nbar, tab = _inputs("c2", n)
     ev = np.linalg.eigvalsh(Problem(tab, nbar, w, b, K).E)
