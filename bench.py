@@ -679,19 +679,19 @@ def bench_jackknife(ctx, dev, defl=0, n=128, box=500.0, n_gal=218020, n_sub=200,
     gen.manual_seed(seed)
     u = torch.rand((n_sub, pos.shape[0]), dtype=torch.float64, device=dev, generator=gen)
     ctx.jackknife_solve(pd, wg, u[:8].contiguous(), alpha, nobs, w, nbar, n, box, k, p, tol=1e-6, max_iter=20000,
-                        prec=wf.MIXED, check=False, deflate=min(defl, 0))  # warm-up: workspaces of a batch of 8
+                        prec=wf.MIXED, check=False, deflate=defl)  # warm-up: workspaces of a batch of 8
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     sm, infos = ctx.jackknife_solve(pd, wg, u, alpha, nobs, w, nbar, n, box, k, p, tol=1e-6, max_iter=20000,
-                                    prec=wf.MIXED, check=False, deflate=min(defl, 0))
+                                    prec=wf.MIXED, check=False, deflate=defl)
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
     its = np.array([i.iters for i in infos])
     return {"workload": "%d^3 over %.0f Mpc/h, %d galaxies (SDSS-like cone and holes), alpha = %g, %d Jackknife-like "
                         "subsamples (one uniform per galaxy and subsample), signal-dependent-noise Wiener filter each "
-                        "(lambda = N''), mixed precision to 1e-6 (no coarse space: -1 resolves to none for the "
-                        "signal-dependent noise), mean of the reconstructions; the plain filter's mixed solve with "
-                        "coarse radius %s" % (n, box, pos.shape[0], alpha, n_sub, deflate_of(defl, n)),
+                        "(lambda = N''), mixed precision to 1e-6 with coarse radius %s, mean of the reconstructions; "
+                        "the plain filter's mixed solve with coarse radius %s" % (
+                            n, box, pos.shape[0], alpha, n_sub, jk_deflate_of(defl, n), deflate_of(defl, n)),
             "value": n_sub / t, "unit": "solves/s", "s": t, "ok": int(sum(1 for i in infos if i.status == 0)),
             "iters": {"min": int(its.min()), "median": int(np.median(its)), "max": int(its.max())},
             "plain_filter": plain,
@@ -790,6 +790,17 @@ def deflate_of(defl, n):
         return defl
     return (0 if n < 64 else 3 if n == 64 else 4 if n <= 128 else 6 if n <= 192 else 8 if n <= 256
             else 10 if n <= 384 else 12)
+
+
+def jk_deflate_of(defl, n):
+    """The radius wf_jackknife_solve runs with for the option value defl (-1: the plain rule + 2)."""
+    if defl != -1:
+        return defl
+    k = deflate_of(-1, n)
+    k = k + 2 if k > 0 else 0
+    while k > 0 and (k > 12 or 4 * k >= n):
+        k -= 1
+    return k
 
 
 def defl_note(defl):

@@ -321,20 +321,31 @@ k_defl_mu(const float* __restrict__ Einv, const float* __restrict__ gco, const f
   const float4* rowa = reinterpret_cast<const float4*>(Einv + (size_t)ra * ncp);
   const float4* rowb = reinterpret_cast<const float4*>(Einv + (size_t)(ra + 1) * ncp);
   const float4* g4 = reinterpret_cast<const float4*>(gs);
-  float sa = 0.f, sb = 0.f;
+  // The products are summed exactly in double-float: the rows of E^-1 cancel heavily against g
+  // (its weak directions carry entries up to 1/lambda_min), and an FP32 sum of nc terms loses
+  // ~sqrt(nc) u of the terms' magnitude, which an ill-conditioned E turns into a stalled CG.
+  AccF aa, ab;
   for (int q = lane; q < ncp / 4; q += 32) {
     const float4 g = g4[q];
     const float4 a = __ldg(rowa + q);
-    sa += a.x * g.x + a.y * g.y + a.z * g.z + a.w * g.w;
+    aa.add_prod(a.x, g.x);
+    aa.add_prod(a.y, g.y);
+    aa.add_prod(a.z, g.z);
+    aa.add_prod(a.w, g.w);
     if (warp < nh) {
       const float4 b = __ldg(rowb + q);
-      sb += b.x * g.x + b.y * g.y + b.z * g.z + b.w * g.w;
+      ab.add_prod(b.x, g.x);
+      ab.add_prod(b.y, g.y);
+      ab.add_prod(b.z, g.z);
+      ab.add_prod(b.w, g.w);
     }
   }
+  double da = aa.get(), db = ab.get();
   for (int o = 16; o > 0; o >>= 1) {
-    sa += __shfl_xor_sync(0xffffffffu, sa, o);
-    sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    da += __shfl_xor_sync(0xffffffffu, da, o);
+    db += __shfl_xor_sync(0xffffffffu, db, o);
   }
+  const float sa = (float)da, sb = (float)db;
   if (lane != 0) return;
   if (warp < nh) {
     const int4 md = modes[warp];
