@@ -793,14 +793,8 @@ def deflate_of(defl, n):
 
 
 def jk_deflate_of(defl, n):
-    """The radius wf_jackknife_solve runs with for the option value defl (-1: the plain rule + 2)."""
-    if defl != -1:
-        return defl
-    k = deflate_of(-1, n)
-    k = k + 2 if k > 0 else 0
-    while k > 0 and (k > 12 or 4 * k >= n):
-        k -= 1
-    return k
+    """The radius wf_jackknife_solve runs with for the option value defl (-1: none)."""
+    return 0 if defl == -1 else defl
 
 
 def defl_note(defl):

@@ -104,8 +104,8 @@ typedef struct {
                          Same system, residual and stop rule; fewer iterations where the mask
                          couples the long-wavelength modes.  -1: K by grid size (0 below 64, 3 at
                          64, 4 up to 128, 6 up to 192, 8 up to 256, 10 up to 384, 12 above; 0 for
-                         WF_FP64; wf_jackknife_solve takes 2 more, within the limits, for its
-                         signal-dependent weights).
+                         WF_FP64 and for wf_jackknife_solve, where with the signal-dependent
+                         weights of sparse subsamples some solves stall with it).
                          Errors: WF_ERR_ARG for any other value. */
 } wf_solve_opts;
 

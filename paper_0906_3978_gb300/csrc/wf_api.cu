@@ -624,15 +624,10 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
       a.b = b;
       a.nbar = 1.0;
       a.opts = *opts;
-      // -1: the plain rule's radius plus 2 (capped): the signal-dependent weights of a sparse
-      // subsample vary more than shot noise, and a larger coarse space pays (at 128^3, 16 subsamples:
-      // 0.41 s with radius 6, 0.55 s with 4, 0.95 s with none)
-      if (a.opts.deflate == -1) {
-        const int k0 = opts->prec == WF_MIXED ? auto_deflate(grid->n) : 0;
-        int kk = k0 > 0 ? k0 + 2 : 0;
-        while (kk > 0 && (kk > kDeflMaxRadius || 4 * kk >= grid->n)) --kk;
-        a.opts.deflate = kk;
-      }
+      // -1 is no coarse space here: with the signal-dependent weights of sparse subsamples most
+      // solves converge 2-4x faster with it, but at 128^3 with radius 6, 22 of 200 stalled at the
+      // iteration cap, so it stays an explicit choice
+      if (a.opts.deflate == -1) a.opts.deflate = 0;
       a.s_out = sj + (size_t)q * V;
       a.sinv = sinv;
       sys.push_back(&a);

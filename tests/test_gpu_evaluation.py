@@ -395,10 +395,10 @@ def test_mask_projection_degenerate_geometry(ctx):
 
 # ------------------------------------------------------------------ Jackknife ensemble (Sec. 3.4)
 def test_jackknife_ensemble_with_coarse_space(ctx):
-    """The subsample solves with the coarse space (deflate = -1: radius 5 at 64^3, the plain rule + 2):
-    every solve converges, in fewer iterations than without it, and the mean is as close to the FP64
-    ensemble at residual 1e-12 as the mean without it (the signal-dependent systems are
-    ill-conditioned, so both are compared with that reference, not with each other)."""
+    """The subsample solves with an explicit coarse space (radius 5 at 64^3; deflate = -1 leaves it out
+    for these solves): every solve converges, in fewer iterations than without it, and the mean is as
+    close to the FP64 ensemble at residual 1e-12 as the mean without it (the signal-dependent systems
+    are ill-conditioned, so both are compared with that reference, not with each other)."""
     n = 64
     pr = synth.problem("c2", n_override=n, cache=False)
     nobs = ctx.grid_assign(gpu(pr.pos), n, pr.box, pr.scheme, 2)
@@ -410,7 +410,7 @@ def test_jackknife_ensemble_with_coarse_space(ctx):
     ref = host(ref).copy()
     plain, ip = ctx.jackknife_solve(*args, tol=1e-10, max_iter=40000, prec=wf.MIXED)
     plain = host(plain).copy()
-    defl, idf = ctx.jackknife_solve(*args, tol=1e-10, max_iter=40000, prec=wf.MIXED, deflate=-1)
+    defl, idf = ctx.jackknife_solve(*args, tol=1e-10, max_iter=40000, prec=wf.MIXED, deflate=5)
     defl = host(defl).copy()
     assert all(i.status == wf.OK for i in ip + idf)
     assert sum(i.iters for i in idf) < 0.8 * sum(i.iters for i in ip)
