@@ -32,7 +32,6 @@
 namespace wf {
 
 constexpr int kDeflTile = 64;   // block of the coarse Gauss-Jordan exchange
-constexpr int kDeflFp64Max = 1024;  // coarse blocks up to this order are exchanged in FP64
 
 // packed-spectrum index of the signed mode (kx, ky, kz), 0 <= kz < N/2
 template <int N> WF_D size_t dslot(int kx, int ky, int kz) {
@@ -589,46 +588,6 @@ WF_D void gj_exchange64(float* a, float* cbuf) {
     }
     __syncthreads();
   }
-}
-
-// FP64 exchange of small coarse blocks (ncp <= 1024), element by element: the matrix is promoted to
-// FP64, each step k saves its row and column and then updates every element, and the result goes
-// back to FP32.  For strongly ill-conditioned blocks (condition ~1e7, the Jackknife subsamples'
-// signal-dependent noise) the FP32 block exchange, which does not pivot, loses the weak directions.
-static __global__ void k_gj64_promote(const float* __restrict__ E, double* __restrict__ A, size_t n) {
-  const size_t z = blockIdx.y;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    A[z * n + i] = (double)E[z * n + i];
-}
-static __global__ void k_gj64_demote(const double* __restrict__ A, float* __restrict__ E, size_t n) {
-  const size_t z = blockIdx.y;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    E[z * n + i] = (float)A[z * n + i];
-}
-// row k and column k of every system's matrix, kept for the step; grid (ceil(ncp / 256), systems)
-static __global__ void k_gj64_save(const double* __restrict__ A, double* __restrict__ rc, int ncp, int k) {
-  const int z = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ncp) return;
-  A += (size_t)z * ncp * ncp;
-  rc += (size_t)z * 2 * ncp;
-  rc[i] = A[(size_t)k * ncp + i];         // row k
-  rc[ncp + i] = A[(size_t)i * ncp + k];   // column k
-}
-// the exchange on index k; grid (ceil(ncp^2 / 256), systems)
-static __global__ void k_gj64_step(double* __restrict__ A, const double* __restrict__ rc, int ncp, int k) {
-  const int z = blockIdx.y;
-  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (e >= (size_t)ncp * ncp) return;
-  A += (size_t)z * ncp * ncp;
-  rc += (size_t)z * 2 * ncp;
-  const int i = (int)(e / ncp), j = (int)(e % ncp);
-  const double inv = 1.0 / rc[k];
-  double v;
-  if (i == k && j == k) v = inv;
-  else if (i == k) v = -rc[j] * inv;
-  else if (j == k) v = rc[ncp + i] * inv;
-  else v = A[e] - rc[ncp + i] * (rc[j] * inv);
-  A[e] = v;
 }
 
 // (0) the first diagonal block; grid (1, 1, systems), 64 threads

@@ -885,21 +885,6 @@ struct GroupMixed : GroupCommon<N> {
                                                                             SF::TAB);
     });
     const int nbk = ncp / kDeflTile;
-    if (ncp <= kDeflFp64Max) {  // small blocks: the exchange in FP64 (see k_gj64_step)
-      const size_t nn = (size_t)ncp * ncp;
-      double *A, *rc;
-      WF_TRY(c.get(key + "gj64", (size_t)nb * nn * sizeof(double), (void**)&A));
-      WF_TRY(c.get(key + "gj64rc", (size_t)nb * 2 * ncp * sizeof(double), (void**)&rc));
-      c.launch("gj64", 0, st, [&] { k_gj64_promote<<<dim3(256, nb), 256, 0, st>>>(Einv, A, nn); });
-      const unsigned gs = (unsigned)((ncp + 255) / 256), gu = (unsigned)((nn + 255) / 256);
-      for (int k = 0; k < ncp; ++k) {
-        c.launch("gj64", 0, st, [&] { k_gj64_save<<<dim3(gs, nb), 256, 0, st>>>(A, rc, ncp, k); });
-        c.launch("gj64", 0, st, [&] { k_gj64_step<<<dim3(gu, nb), 256, 0, st>>>(A, rc, ncp, k); });
-      }
-      c.launch("gj64", 0, st, [&] { k_gj64_demote<<<dim3(256, nb), 256, 0, st>>>(A, Einv, nn); });
-      WF_CUDA(cudaGetLastError());
-      return WF_OK;
-    }
     c.launch("gj_pivot", 0, st, [&] { k_gj_pivot<<<dim3(1, 1, nb), 64, 0, st>>>(Einv, Pb, ncp); });
     for (int kb = 0; kb < nbk; ++kb) {
       c.launch("gj_panel", 0, st, [&] { k_gj_panel<<<dim3(nbk, 1, nb), 64, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
