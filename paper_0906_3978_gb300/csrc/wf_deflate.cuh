@@ -324,23 +324,39 @@ k_defl_mu(const float* __restrict__ Einv, const float* __restrict__ gco, const f
   // The products are summed exactly in double-float: the rows of E^-1 cancel heavily against g
   // (its weak directions carry entries up to 1/lambda_min), and an FP32 sum of nc terms loses
   // ~sqrt(nc) u of the terms' magnitude, which an ill-conditioned E turns into a stalled CG.
-  AccF aa, ab;
-  for (int q = lane; q < ncp / 4; q += 32) {
-    const float4 g = g4[q];
-    const float4 a = __ldg(rowa + q);
-    aa.add_prod(a.x, g.x);
-    aa.add_prod(a.y, g.y);
-    aa.add_prod(a.z, g.z);
-    aa.add_prod(a.w, g.w);
-    if (warp < nh) {
-      const float4 b = __ldg(rowb + q);
-      ab.add_prod(b.x, g.x);
-      ab.add_prod(b.y, g.y);
-      ab.add_prod(b.z, g.z);
-      ab.add_prod(b.w, g.w);
+  // one accumulator per vector component (four independent chains per row); the loads of four
+  // vectors of each row are issued before their products, to keep enough of them in flight
+  AccF aa[4], ab[4];
+  const bool two = warp < nh;
+  constexpr int U = 4;
+  const int nq = ncp / 4;  // a multiple of 32: ncp is a multiple of 128
+  for (int q0 = lane; q0 < nq; q0 += 32 * U) {
+    float4 av[U], bv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + 32 * u;
+      av[u] = q < nq ? __ldg(rowa + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      bv[u] = (two && q < nq) ? __ldg(rowb + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int q = q0 + 32 * u;
+      if (q >= nq) break;
+      const float4 g = g4[q];
+      aa[0].add_prod(av[u].x, g.x);
+      aa[1].add_prod(av[u].y, g.y);
+      aa[2].add_prod(av[u].z, g.z);
+      aa[3].add_prod(av[u].w, g.w);
+      if (two) {
+        ab[0].add_prod(bv[u].x, g.x);
+        ab[1].add_prod(bv[u].y, g.y);
+        ab[2].add_prod(bv[u].z, g.z);
+        ab[3].add_prod(bv[u].w, g.w);
+      }
     }
   }
-  double da = aa.get(), db = ab.get();
+  double da = (aa[0].get() + aa[1].get()) + (aa[2].get() + aa[3].get());
+  double db = (ab[0].get() + ab[1].get()) + (ab[2].get() + ab[3].get());
   for (int o = 16; o > 0; o >>= 1) {
     da += __shfl_xor_sync(0xffffffffu, da, o);
     db += __shfl_xor_sync(0xffffffffu, db, o);
