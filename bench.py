@@ -784,12 +784,12 @@ def bench_serving(ctx, dev, defl=0, n_req=600, rate=20.0, seed=7):
 
 
 def deflate_of(defl, n):
-    """The coarse radius a mixed solve of size n runs with for the option value defl (the rule of
-    wf_solve_opts.deflate = -1)."""
+    """The coarse radius a mixed solve of size n runs with for the option value defl (-1: the
+    library's rule, wf_deflate_radius)."""
     if defl != -1:
         return defl
-    return (0 if n < 64 else 3 if n == 64 else 4 if n <= 128 else 6 if n <= 192 else 8 if n <= 256
-            else 10 if n <= 384 else 12)
+    import paper_0906_3978_gb300 as wf
+    return wf.deflate_radius(n)
 
 
 def jk_deflate_of(defl, n):

@@ -134,6 +134,10 @@ wf_status wf_destroy(wf_ctx* ctx);
 /* 1 if grid size n is compiled into this library, else 0.  Host only, never fails. */
 int wf_supported_size(int n);
 
+/* The coarse radius wf_solve_opts.deflate = -1 resolves to for a wf_solve / wf_solve_batch /
+ * wf_submit solve of grid size n and precision prec (0: no coarse space).  Host only, never fails. */
+int wf_deflate_radius(int n, wf_precision prec);
+
 /* A static description of status s ("unknown status" for values outside wf_status). */
 const char* wf_status_string(wf_status s);
 

@@ -97,6 +97,8 @@ def lib():
         L.wf_create.argtypes = [P(c_void_p), c_int, ctypes.c_size_t]
         L.wf_destroy.argtypes = [c_void_p]
         L.wf_supported_size.argtypes = [c_int]
+        L.wf_deflate_radius.argtypes = [c_int, c_int]
+        L.wf_deflate_radius.restype = c_int
         L.wf_status_string.argtypes = [c_int]
         L.wf_status_string.restype = ctypes.c_char_p
         L.wf_last_error.restype = ctypes.c_char_p
@@ -178,6 +180,11 @@ def status_string(s: int) -> str:
 
 def supported_size(n: int) -> bool:
     return bool(lib().wf_supported_size(n))
+
+
+def deflate_radius(n: int, prec=None) -> int:
+    """The coarse radius deflate = -1 takes for a solve of grid size n (wf_deflate_radius)."""
+    return int(lib().wf_deflate_radius(int(n), int(MIXED if prec is None else prec)))
 
 
 def _ptr(t):

@@ -431,6 +431,8 @@ extern "C" {
 
 int wf_supported_size(int n) { return supported_size(n); }
 
+int wf_deflate_radius(int n, wf_precision prec) { return prec == WF_MIXED ? auto_deflate(n) : 0; }
+
 const char* wf_last_error(void) { return g_last_error.c_str(); }
 
 const char* wf_status_string(wf_status s) {

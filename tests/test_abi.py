@@ -111,3 +111,15 @@ def test_header_is_plain_c_and_links(lib):
     assert r.returncode == 0, r.stderr
     out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert out.returncode == 0 and out.stdout.split() == ["invalid", "argument", "1"]
+
+
+def test_automatic_coarse_radius(lib):
+    """deflate = -1's radius by grid size for mixed solves (none for FP64), within its limits
+    (1 <= K <= 12, 4 K < n) wherever it is not 0."""
+    want = {16: 0, 32: 0, 48: 0, 64: 3, 96: 4, 128: 4, 192: 6, 256: 8, 384: 10, 512: 12}
+    for n, k in want.items():
+        assert wf.deflate_radius(n) == k, n
+        assert wf.deflate_radius(n, wf.FP64) == 0
+    for n in range(16, 513, 8):
+        k = wf.deflate_radius(n)
+        assert k == 0 or (1 <= k <= 12 and 4 * k < n), n
