@@ -99,10 +99,13 @@ typedef struct {
                          (same canonical system and residual); 0: plain CG on A */
   int deflate;        /* WF_MIXED only: 0 off; K in [1, 12] with 4 K < n: each inner CG is
                          preconditioned on the coarse space of the Fourier modes |k|^2 <= K^2
-                         (grid units), whose Galerkin block Z^T (C A C) Z is formed and inverted
+                         (grid units), whose Galerkin block E = Z^T (C A C) Z is formed and inverted
                          on the device once per solve (two-level "A-DEF2" form, Tang et al. 2009).
                          Same system, residual and stop rule; fewer iterations where the mask
-                         couples the long-wavelength modes.  -1: K by grid size (0 below 64, 3 at
+                         couples the long-wavelength modes.  A system whose block has
+                         ||E||_inf ||E^-1||_inf above 1e8 (beyond what the FP32 block holds) runs
+                         its inner CG without it; its batch-mates keep theirs.
+                         -1: K by grid size (0 below 64, 3 at
                          64, 4 up to 128, 6 up to 192, 8 up to 256, 10 up to 384, 12 above; 0 for
                          WF_FP64 and for wf_jackknife_solve, where with the signal-dependent
                          weights of sparse subsamples some solves stall with it).

@@ -289,7 +289,8 @@ k_xcoarse(const typename Store<R>::T* __restrict__ gy, const typename Store<R>::
 }
 
 // ------------------------------------------------------------------------------------------
-// mu = E^-1 g, one warp per half-space mode (rows 1 + 2j, 2 + 2j; warp nh: row 0), and its use:
+// mu = E^-1 g, one warp per half-space mode (rows 1 + 2j, 2 + 2j; warp nh: row 0), and its use
+// (mu = 0 for a system with off[z] set):
 // MODE 0: vec (zeroed) receives Z mu (the start vector).
 // MODE 1: the coarse entries of vec (= r) are saved to rsave and replaced by r - Z mu; the
 //         partial <r, Z mu> = rco . mu of the warp goes to dpart[warp].
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(256)
 k_defl_mu(const float* __restrict__ Einv, const float* __restrict__ gco, const float* __restrict__ rco,
           const int4* __restrict__ modes, int nh, int ncp, typename Store<R>::T* __restrict__ vec,
           typename Store<R>::T* __restrict__ rsave, double* __restrict__ dpart, const CgScal* __restrict__ sc,
-          Bat bt) {
+          Bat bt, const int* __restrict__ off) {
   using ST = typename Store<R>::T;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float* gs = reinterpret_cast<float*>(smem_raw);
@@ -361,7 +362,8 @@ k_defl_mu(const float* __restrict__ Einv, const float* __restrict__ gco, const f
     da += __shfl_xor_sync(0xffffffffu, da, o);
     db += __shfl_xor_sync(0xffffffffu, db, o);
   }
-  const float sa = (float)da, sb = (float)db;
+  // a system whose coarse block failed the condition guard (k_defl_guard) gets mu = 0: plain CG
+  const float sa = off[z] ? 0.f : (float)da, sb = off[z] ? 0.f : (float)db;
   if (lane != 0) return;
   if (warp < nh) {
     const int4 md = modes[warp];
@@ -518,6 +520,58 @@ __global__ void k_ebuild(const float2* __restrict__ dh, const S* __restrict__ ct
     else v = dg + cc * ((double)A.x - (double)B.x);
   }
   E[(size_t)i * ncp + j] = (float)v;
+}
+
+// Condition guard.  A coarse block built and inverted in FP32 cannot hold a condition number far
+// beyond 1/u.  With the signal-dependent noise of sparse Jackknife subsamples (128^3, |k| <= 4 or 6),
+// blocks with kappa_inf(E) of 8e8 and more stalled or broke down the deflated CG, while blocks up to
+// 6e7 mostly converge 2-4x faster (below 1e8 kappa alone does not decide: a few failed from 1.4e7).
+// Systems above kDeflCondMax run as plain CG (mu = 0); the plain filter's blocks sit near 1e3-1e4.
+constexpr double kDeflCondMax = 1e8;
+// max over the rows of one warp-group of the row sums of |M|; grid (ncp / 8, systems), 256 threads:
+// one warp per row, the CTA's maximum to part[z * (ncp / 8) + blockIdx.x]
+static __global__ void __launch_bounds__(256) k_defl_rownorm(const float* __restrict__ M, int ncp,
+                                                             double* __restrict__ part) {
+  __shared__ double red[8];
+  const int z = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 8 + warp;
+  const float* m = M + (size_t)z * ncp * ncp + (size_t)row * ncp;
+  double acc = 0.0;
+  for (int j = lane; j < ncp; j += 32) acc += fabs((double)m[j]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = red[0];
+    for (int w = 1; w < 8; ++w) mx = fmax(mx, red[w]);
+    part[(size_t)z * (ncp / 8) + blockIdx.x] = mx;
+  }
+}
+// off[z] = 1 when kappa_inf = ||E||_inf ||E^-1||_inf exceeds kDeflCondMax or is not finite; grid =
+// systems, 256 threads
+static __global__ void k_defl_guard(const double* __restrict__ pe, const double* __restrict__ pi, int ncp,
+                                    int* __restrict__ off) {
+  __shared__ double r1[256], r2[256];
+  const int z = blockIdx.x, nblk = ncp / 8;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+    a = fmax(a, pe[(size_t)z * nblk + i]);
+    b = fmax(b, pi[(size_t)z * nblk + i]);
+  }
+  r1[threadIdx.x] = a;
+  r2[threadIdx.x] = b;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      r1[threadIdx.x] = fmax(r1[threadIdx.x], r1[threadIdx.x + h]);
+      r2[threadIdx.x] = fmax(r2[threadIdx.x], r2[threadIdx.x + h]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double k = r1[0] * r2[0];
+    off[z] = (isfinite(k) && k <= kDeflCondMax) ? 0 : 1;
+  }
 }
 
 // Block Gauss-Jordan exchange on block row / column kb of the SPD matrix M (ncp x ncp, row-major;

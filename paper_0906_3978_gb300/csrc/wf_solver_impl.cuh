@@ -802,7 +802,8 @@ struct GroupMixed : GroupCommon<N> {
   int4* dmodes = nullptr;
   float *Einv = nullptr, *gco = nullptr, *rco = nullptr, *Pb = nullptr, *Rp = nullptr, *Cp = nullptr;
   float2 *Gz = nullptr, *Gy = nullptr, *rsave = nullptr, *DH = nullptr;
-  double* dpart = nullptr;
+  double *dpart = nullptr, *normp = nullptr;  // normp: per-CTA row-sum maxima of E and E^-1
+  int* doff = nullptr;  // per system: 1 = the coarse block failed the condition guard (plain CG)
   size_t gzs = 0, gys = 0;
 
   wf_status prepare_begin(Ctx& c, cudaStream_t st) override {
@@ -857,6 +858,8 @@ struct GroupMixed : GroupCommon<N> {
     WF_TRY(c.get(dk + "rsave", (size_t)nb * (2 * nh + 1) * sizeof(float2), (void**)&rsave));
     WF_TRY(c.get(dk + "DH", (size_t)nb * C * C * C * sizeof(float2), (void**)&DH));
     WF_TRY(c.get(dk + "dpart", (size_t)nb * (nh + 1) * sizeof(double), (void**)&dpart));
+    WF_TRY(c.get(dk + "normp", (size_t)nb * 2 * (ncp / 8) * sizeof(double), (void**)&normp));
+    WF_TRY(c.get(dk + "doff", (size_t)nb * sizeof(int), (void**)&doff));
     WF_TRY(c.get(dk + "modes", modes.size() * sizeof(int4), (void**)&dmodes));
     int4* hm;
     WF_TRY(c.get_pinned(dk + "hmodes", modes.size() * sizeof(int4), (void**)&hm));
@@ -885,6 +888,9 @@ struct GroupMixed : GroupCommon<N> {
                                                                             SF::TAB);
     });
     const int nbk = ncp / kDeflTile;
+    double* pe = normp;
+    double* pi = normp + (size_t)nb * (ncp / 8);
+    c.launch("defl_norm", 0, st, [&] { k_defl_rownorm<<<dim3(ncp / 8, nb), 256, 0, st>>>(Einv, ncp, pe); });
     c.launch("gj_pivot", 0, st, [&] { k_gj_pivot<<<dim3(1, 1, nb), 64, 0, st>>>(Einv, Pb, ncp); });
     for (int kb = 0; kb < nbk; ++kb) {
       c.launch("gj_panel", 0, st, [&] { k_gj_panel<<<dim3(nbk, 1, nb), 64, 0, st>>>(Einv, Pb, Rp, Cp, ncp, kb); });
@@ -892,6 +898,8 @@ struct GroupMixed : GroupCommon<N> {
         k_gj_update<<<dim3(nbk / 2, nbk / 2, nb), 256, kUpdSmem, st>>>(Einv, Pb, Rp, Cp, ncp, kb);
       });
     }
+    c.launch("defl_norm", 0, st, [&] { k_defl_rownorm<<<dim3(ncp / 8, nb), 256, 0, st>>>(Einv, ncp, pi); });
+    c.launch("defl_norm", 0, st, [&] { k_defl_guard<<<nb, 256, 0, st>>>(pe, pi, ncp, doff); });
     WF_CUDA(cudaGetLastError());
     return WF_OK;
   }
@@ -918,7 +926,7 @@ struct GroupMixed : GroupCommon<N> {
     });
     c.launch("defl_mu", 4.0 * ncp * ncp * nb, st, [&] {
       k_defl_mu<float, N, MODE><<<dim3(gw, nb), 256, ncp * sizeof(float), st>>>(Einv, gco, rco, dmodes, nh, ncp,
-                                                                                 out, rsave, dpart, sc, bf);
+                                                                                 out, rsave, dpart, sc, bf, doff);
     });
   }
   // T = IFFT_x(c r), register-staged (a persistent form on tensor copies along x, the y pass's tile

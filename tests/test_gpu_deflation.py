@@ -166,3 +166,45 @@ def test_automatic_radius_at_64(ctx):
     sa, ia = ctx.solve(*args, tol=1e-8, prec=wf.MIXED, deflate=-1)
     assert ia.status == wf.OK and ia.iters == i3.iters
     assert rl2(host(sa), host(s3)) <= 1e-12
+
+
+def _ball_window(n, radius, amp):
+    """A window concentrated in a ball: amp inside radius cells of the centre, 1e-9 amp outside."""
+    x = np.indices((n, n, n)) - n // 2
+    return np.where(np.sqrt((x ** 2).sum(0)) <= radius, amp, 1e-9 * amp)
+
+
+def test_condition_guard_turns_an_ill_conditioned_coarse_space_off(ctx):
+    """Noise weights concentrated in a ball of radius 6 cells at 48^3, coarse radius 4.  At amplitude 1
+    the coarse block E has kappa_inf ~ 1e4 and the coarse space halves the iterations (26 for 52).  At
+    amplitude 1e3 (kappa_inf 1.5e9 in FP64, far past what a block built and inverted in FP32 holds)
+    the guard on ||E||_inf ||E^-1||_inf turns it off for that system: the solve runs as plain CG
+    (the undeflated iteration count, plus the start step) and converges to the oracle's solution.
+    In a batch each system keeps the decision and the result it gets alone."""
+    from oracle.coarse import Problem
+    n, K = 48, 4
+    pr, w, b, nbar, tab = _inputs("c2", n)
+    batch, alone = [], []
+    for amp, well in ((1.0, True), (1e3, False)):
+        wb = _ball_window(n, 6, amp)
+        E = Problem(tab, nbar, wb, b, K).E
+        kinf = np.abs(E).sum(1).max() * np.abs(np.linalg.inv(E)).sum(1).max()
+        assert (kinf < 1e5) if well else (kinf > 1e9), kinf
+        ref = oracle.cg(tab, nbar, wb, b, tol=1e-11)[0]
+        args = (gpu(wb), nbar, gpu(b), pr.box, pr.pk_k, pr.pk_p)
+        s0, i0 = ctx.solve(*args, tol=1e-9, prec=wf.MIXED)
+        s1, i1 = ctx.solve(*args, tol=1e-9, prec=wf.MIXED, deflate=K)
+        assert i0.status == wf.OK and i1.status == wf.OK and i1.rel_residual <= 1e-9
+        assert rl2(host(s1), ref) <= 1e-6
+        if well:
+            assert i1.iters < 0.6 * i0.iters, (i1.iters, i0.iters)
+        else:
+            assert abs(i1.iters - (i0.iters + 1)) <= 0.02 * i0.iters + 2, (i1.iters, i0.iters)
+        alone.append((host(s1).copy(), i1.iters))
+        batch.append(dict(w=args[0], nbar=nbar, b=args[2], box=pr.box, pk_k=pr.pk_k, pk_p=pr.pk_p, tol=1e-9,
+                          prec=wf.MIXED, deflate=K))
+    st, outs, infos = ctx.solve_batch(batch[::-1])
+    assert st == wf.OK
+    for (ref, it), s, info in zip(alone[::-1], outs, infos):
+        assert info.status == wf.OK and info.iters == it
+        assert rl2(host(s), ref) <= 1e-12
