@@ -691,7 +691,7 @@ def bench_jackknife(ctx, dev, defl=0, n=128, box=500.0, n_gal=218020, n_sub=200,
                         "subsamples (one uniform per galaxy and subsample), signal-dependent-noise Wiener filter each "
                         "(lambda = N''), mixed precision to 1e-6 with coarse radius %s, mean of the reconstructions; "
                         "the plain filter's mixed solve with coarse radius %s" % (
-                            n, box, pos.shape[0], alpha, n_sub, jk_deflate_of(defl, n), deflate_of(defl, n)),
+                            n, box, pos.shape[0], alpha, n_sub, deflate_of(defl, n), deflate_of(defl, n)),
             "value": n_sub / t, "unit": "solves/s", "s": t, "ok": int(sum(1 for i in infos if i.status == 0)),
             "iters": {"min": int(its.min()), "median": int(np.median(its)), "max": int(its.max())},
             "plain_filter": plain,
@@ -790,11 +790,6 @@ def deflate_of(defl, n):
         return defl
     import paper_0906_3978_gb300 as wf
     return wf.deflate_radius(n)
-
-
-def jk_deflate_of(defl, n):
-    """The radius wf_jackknife_solve runs with for the option value defl (-1: none)."""
-    return 0 if defl == -1 else defl
 
 
 def defl_note(defl):

@@ -104,11 +104,10 @@ typedef struct {
                          Same system, residual and stop rule; fewer iterations where the mask
                          couples the long-wavelength modes.  A system whose block has
                          ||E||_inf ||E^-1||_inf above 1e8 (beyond what the FP32 block holds) runs
-                         its inner CG without it; its batch-mates keep theirs.
-                         -1: K by grid size (0 below 64, 3 at
-                         64, 4 up to 128, 6 up to 192, 8 up to 256, 10 up to 384, 12 above; 0 for
-                         WF_FP64 and for wf_jackknife_solve, where with the signal-dependent
-                         weights of sparse subsamples some solves stall with it).
+                         its inner CG without it, and so do the later inner solves of a system
+                         whose deflated inner solve broke down or reached 1200 iterations; its
+                         batch-mates keep theirs.  -1: K by grid size (0 below 64, 3 at 64, 4 up to
+                         128, 6 up to 192, 8 up to 256, 10 up to 384, 12 above; 0 for WF_FP64).
                          Errors: WF_ERR_ARG for any other value. */
 } wf_solve_opts;
 

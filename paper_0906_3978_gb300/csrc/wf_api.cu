@@ -626,10 +626,9 @@ wf_status wf_jackknife_solve(wf_ctx* ctx, const wf_grid* grid, wf_scheme scheme,
       a.b = b;
       a.nbar = 1.0;
       a.opts = *opts;
-      // -1 is no coarse space here: with the signal-dependent weights of sparse subsamples most
-      // solves converge 2-4x faster with it, but at 128^3 with radius 6, 22 of 200 stalled at the
-      // iteration cap, so it stays an explicit choice
-      if (a.opts.deflate == -1) a.opts.deflate = 0;
+      // -1: the radius by grid size, as for wf_solve.  Subsamples whose deflated inner solves break
+      // down or stall (a few percent of sparse ones) continue as plain CG (wf_solver_impl.cuh)
+      if (a.opts.deflate == -1) a.opts.deflate = opts->prec == WF_MIXED ? auto_deflate(grid->n) : 0;
       a.s_out = sj + (size_t)q * V;
       a.sinv = sinv;
       sys.push_back(&a);

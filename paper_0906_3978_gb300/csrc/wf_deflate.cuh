@@ -290,7 +290,7 @@ k_xcoarse(const typename Store<R>::T* __restrict__ gy, const typename Store<R>::
 
 // ------------------------------------------------------------------------------------------
 // mu = E^-1 g, one warp per half-space mode (rows 1 + 2j, 2 + 2j; warp nh: row 0), and its use
-// (mu = 0 for a system with off[z] set):
+// (mu = 0 for a system with off[z] or its noco set):
 // MODE 0: vec (zeroed) receives Z mu (the start vector).
 // MODE 1: the coarse entries of vec (= r) are saved to rsave and replaced by r - Z mu; the
 //         partial <r, Z mu> = rco . mu of the warp goes to dpart[warp].
@@ -362,8 +362,10 @@ k_defl_mu(const float* __restrict__ Einv, const float* __restrict__ gco, const f
     da += __shfl_xor_sync(0xffffffffu, da, o);
     db += __shfl_xor_sync(0xffffffffu, db, o);
   }
-  // a system whose coarse block failed the condition guard (k_defl_guard) gets mu = 0: plain CG
-  const float sa = off[z] ? 0.f : (float)da, sb = off[z] ? 0.f : (float)db;
+  // a system whose coarse block failed the condition guard (k_defl_guard), or whose deflated inner
+  // solve failed (noco, set by the host), gets mu = 0: plain CG
+  const bool plain = off[z] || sc[z].noco;
+  const float sa = plain ? 0.f : (float)da, sb = plain ? 0.f : (float)db;
   if (lane != 0) return;
   if (warp < nh) {
     const int4 md = modes[warp];
@@ -528,6 +530,10 @@ __global__ void k_ebuild(const float2* __restrict__ dh, const S* __restrict__ ct
 // 6e7 mostly converge 2-4x faster (below 1e8 kappa alone does not decide: a few failed from 1.4e7).
 // Systems above kDeflCondMax run as plain CG (mu = 0); the plain filter's blocks sit near 1e3-1e4.
 constexpr double kDeflCondMax = 1e8;
+// Iteration cap of one deflated inner solve.  Deflated inner solves take ~40-50 iterations at 512^3
+// and up to a few hundred on the Jackknife subsamples; one that reaches the cap (or breaks down)
+// has lost the coarse space's benefit, and the system's later inner solves run as plain CG.
+constexpr int kDeflInnerCap = 1200;
 // max over the rows of one warp-group of the row sums of |M|; grid (ncp / 8, systems), 256 threads:
 // one warp per row, the CTA's maximum to part[z * (ncp / 8) + blockIdx.x]
 static __global__ void __launch_bounds__(256) k_defl_rownorm(const float* __restrict__ M, int ncp,

@@ -795,6 +795,7 @@ struct GroupMixed : GroupCommon<N> {
   float *ct, *mt;
   double* stab;
   std::vector<int> outer, iters;
+  std::vector<int> noco;  // per system: inner solves without the coarse space after a failed one
   bool unit_m = true;
   static constexpr int NPART = SF::NPART > SD::NPART ? SF::NPART : SD::NPART;
   // coarse space of a deflated group (K > 0; every system of the group has the same K)
@@ -979,6 +980,7 @@ struct GroupMixed : GroupCommon<N> {
     state.assign(this->bad.begin(), this->bad.end());
     outer.assign(nb, 0);
     iters.assign(nb, 0);
+    noco.assign(nb, 0);
     for (int m = 0; m < nb; ++m)
       if (bb0[m] == 0.0 && !state[m]) {
         state[m] = 1;
@@ -1008,6 +1010,8 @@ struct GroupMixed : GroupCommon<N> {
           z.tol2 = target * target;
           z.bb = rel[m] * rel[m] * bb0[m];
           z.max_iter = std::max(1, sys[m]->opts.max_iter - iters[m]);
+          if (K > 0 && !noco[m]) z.max_iter = std::min(z.max_iter, kDeflInnerCap);
+          z.noco = noco[m];
           outer[m] += 1;
         }
         h[m] = z;
@@ -1071,11 +1075,18 @@ struct GroupMixed : GroupCommon<N> {
         iters[m] += h[m].iter;
         const double rn = std::sqrt(h[m].aux[0] / bb0[m]);
         const bool broke = h[m].done == 3 && !(rn < rel[m]);
+        // a deflated inner solve that broke down or reached kDeflInnerCap hands the system to plain
+        // CG from the next refinement step on (its FP64 residual restarts the inner solve)
+        const bool defl_failed = K > 0 && !noco[m] && std::isfinite(rn) &&
+                                 (h[m].done == 3 || (h[m].done == 2 && h[m].iter >= kDeflInnerCap));
         rel[m] = rn;
         wf_status st = WF_OK;
         bool fin = true;
         if (rel[m] <= sys[m]->opts.tol) st = WF_OK;
-        else if (broke) st = WF_ERR_BREAKDOWN;
+        else if (defl_failed && outer[m] < 12 && iters[m] < sys[m]->opts.max_iter) {
+          noco[m] = 1;
+          fin = false;
+        } else if (broke) st = WF_ERR_BREAKDOWN;
         else if (outer[m] >= 12 || iters[m] >= sys[m]->opts.max_iter) st = WF_ERR_NOT_CONVERGED;
         else fin = false;
         if (fin) {

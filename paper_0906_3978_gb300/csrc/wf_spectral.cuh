@@ -48,7 +48,8 @@ struct __align__(16) CgScal {
   int status;
   int lit;            // iterations since the last reset of p: p_old = P[lit & 1]
   int defl;           // deflated inner solves: 2 start step (alpha = 1) pending, 1 first iteration
-  int pad[2];
+  int noco;           // deflated groups: 1 = this system runs its inner solves without the coarse space
+  int pad;
 };
 
 // Distances between consecutive systems of a batch (elements of each array type).
